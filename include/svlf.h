@@ -1,0 +1,178 @@
+/*
+ * svlf.h - C ABI of the SVLF hot path (sparse voxel light field rendering and
+ * training) for NVIDIA B300 (sm_103a).
+ *
+ * The operations follow the method of "RTMV: A Ray-Traced Multi-View
+ * Synthetic Dataset for Novel View Synthesis" (Sec. 4, Sparse Voxel Light
+ * Field): a ray is mapped, voxel by voxel, to an optical thickness tau and a
+ * colour c (Sec. 4, opening paragraph), and a pixel is the alpha composite of
+ * the voxels the ray meets, in order (Sec. 4.3, Eq. 3).
+ *
+ * Conventions shared by every call:
+ *  - Return value: SVLF_OK (0) or a negative SVLF_ERR_* code. Nothing aborts
+ *    or throws across this boundary. Argument errors are reported before any
+ *    work is queued. Device-side errors (a traversal step limit, an index out
+ *    of range) are latched in a device status word read by
+ *    svlf_get_device_status().
+ *  - Pointers named "device" are CUDA device memory owned by the caller; the
+ *    library never frees them. Pointers named "host" are host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Gradients ACCUMULATE (+=) into caller-zeroed buffers.
+ *  - A leaf (occupied finest-level voxel) is identified by its rank in
+ *    ascending Morton order of its integer coordinates (i, j, k), with bit
+ *    3b = bit b of i, 3b+1 = bit b of j, 3b+2 = bit b of k. The rank is the
+ *    leaf's row in the feature table and the value reported in hit lists
+ *    (-1 = empty slot).
+ *  - Voxel (i, j, k) at depth L is the box [i, i+1] x [j, j+1] x [k, k+1] *
+ *    2^-L inside the unit cube (Sec. 3.1 normalises every scene to a unit
+ *    cube). Supported depths: 2 <= L <= 10.
+ */
+#ifndef SVLF_H
+#define SVLF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SVLF_OK 0
+#define SVLF_ERR_ARG (-1)          /* invalid argument (null pointer, size, range) */
+#define SVLF_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define SVLF_ERR_DEVICE (-3)       /* a kernel latched an error (see device status) */
+#define SVLF_ERR_UNSUPPORTED (-4)  /* shape or mode this build does not handle */
+#define SVLF_ERR_WORKSPACE (-5)    /* workspace missing, misaligned or too small */
+
+/* device status bits (svlf_get_device_status) */
+#define SVLF_DEV_STEP_LIMIT 1      /* a traversal exceeded its step bound */
+#define SVLF_DEV_BAD_INDEX 2       /* a node, brick or leaf index was out of range */
+#define SVLF_DEV_SAMPLE_OVERFLOW 4 /* more samples than the workspace holds */
+#define SVLF_DEV_WAIT_TIMEOUT 8    /* a bounded wait on an mbarrier gave up */
+
+/* network arithmetic */
+#define SVLF_FP32 0  /* SIMT float32 throughout */
+#define SVLF_BF16 1  /* tcgen05 tensor cores, bfloat16 operands, float32 accumulate */
+#define SVLF_FP16 2  /* tcgen05 tensor cores, float16 operands, float32 accumulate */
+
+/* feature table storage */
+#define SVLF_FEAT_F32 0
+#define SVLF_FEAT_BF16 1
+
+/* ------------------------------------------------------------------ types */
+typedef struct svlf_octree_s *svlf_octree; /* opaque, library-owned */
+
+/* The per-sample network. Input h0 = [z (feat_dim) | ray direction (3) |
+ * p~1 (3) | p~2 (3)], in_dim = feat_dim + 9; n_hidden ReLU layers of width
+ * `hidden`; a linear output layer of out_dim = 4 values [r, g, b, tau_pre].
+ * Colour = sigmoid(r, g, b), optical thickness tau = max(tau_pre, 0)
+ * (Sec. 4.5 "Architecture": ReLU decoders, sigmoid colour, ReLU thickness).
+ * Parameters are one flat float32 array: for each layer, W (out x in,
+ * row-major) followed by b (out). */
+typedef struct {
+    int feat_dim;   /* F: 8..64, multiple of 8 */
+    int hidden;     /* H: 32..256, multiple of 16 (tensor-core paths: 64 or 128) */
+    int n_hidden;   /* 1..6 */
+    int out_dim;    /* must be 4 */
+    int precision;  /* SVLF_FP32 | SVLF_BF16 | SVLF_FP16 */
+    int feat_dtype; /* SVLF_FEAT_F32 | SVLF_FEAT_BF16 */
+} svlf_mlp_desc;
+
+typedef struct {
+    int K;        /* hits evaluated per ray (the first K leaves): 1, 2, 4, 8, 16 or 32 */
+    float bg[3];  /* colour multiplied by the transmittance left after the K-th hit */
+} svlf_render_opts;
+
+/* ------------------------------------------------------------ octree */
+/* Build the sparse octree over the given leaves (Sec. 4.1 "Scene volume":
+ * only voxels that contain a surface are stored).
+ *   leaf_ijk: device, n x 3 int32 (i, j, k); duplicates are merged.
+ *   depth: L, 2..10. Coordinates must lie in [0, 2^L), else SVLF_ERR_ARG.
+ *   out: receives the handle. n_leaves_out (host, may be NULL): unique leaves.
+ * Synchronises `stream` (the leaf list is read back to the host, sorted there
+ * and the node arrays uploaded). Not on the per-frame path. */
+int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
+                      svlf_octree *out, int64_t *n_leaves_out);
+
+/* Leaf coordinates in rank order. out_ijk: device, n_leaves x 3 int32. */
+int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *stream);
+
+/* Sizes: depth, leaves, internal node words, leaf bricks (host outputs, any
+ * may be NULL). */
+int svlf_octree_info(svlf_octree tree, int *depth, int64_t *n_leaves, int64_t *n_nodes,
+                     int64_t *n_bricks);
+
+int svlf_free_octree(svlf_octree tree);
+
+/* ------------------------------------------------------------ rendering */
+/* Bytes of workspace a render (and the matching backward) needs. */
+int svlf_workspace_size(const svlf_mlp_desc *mlp, int64_t n_rays, int K, size_t *bytes);
+
+/* Render rays (Sec. 4.3): for each ray, the first K leaves it meets in
+ * ascending t (slab test, Sec. 4.2), each evaluated once by the network on
+ * [z | d | r] with r = [p~1 | p~2] the ray's entry and exit points on the
+ * leaf's minimum bounding sphere, relative to the leaf centre and scaled to
+ * unit norm (Sec. 4.1 "Ray parameterization"), then composited by Eq. 3:
+ *   C = sum_i T_i (1 - exp(-tau_i)) c_i + T_{n+1} bg,  T_i = prod_{j<i} exp(-tau_j)
+ *   D = sum_i T_i (1 - exp(-tau_i)) (t_in,i + t_out,i) / 2      (0 if no hit)
+ * Arguments (all device unless noted):
+ *   features: n_leaves x feat_dim, float32 or bfloat16 (mlp->feat_dtype),
+ *             row-major, 16-byte aligned rows.
+ *   mlp_params: flat float32 parameters (layout in svlf_mlp_desc).
+ *   rays: n_rays x 6 float32 (ox, oy, oz, dx, dy, dz), |d| = 1.
+ *   rgb: n_rays x 3 float32 out; depth: n_rays float32 out.
+ *   hits: n_rays x K int32 out (leaf ranks, -1 = none) or NULL.
+ *   t_io: n_rays x K x 2 float32 out (t_in, t_out) or NULL.
+ *   workspace: >= svlf_workspace_size() bytes, 256-byte aligned. The samples
+ *             and network outputs it holds afterwards are what
+ *             svlf_render_rays_backward() reads: pass it unchanged.
+ * Errors: SVLF_ERR_ARG / _UNSUPPORTED / _WORKSPACE before launch. */
+int svlf_render_rays(svlf_octree tree, const void *features, const float *mlp_params,
+                     const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
+                     const svlf_render_opts *opts, float *rgb, float *depth, int32_t *hits,
+                     float *t_io, void *workspace, size_t ws_bytes, void *stream);
+
+/* Backward of svlf_render_rays with respect to the features and the network
+ * parameters, given d_rgb (n_rays x 3) and d_depth (n_rays) (device). Reads
+ * the samples and outputs the forward call left in `workspace` (same tree,
+ * features, parameters, rays and options), recomputes the network
+ * activations, and accumulates into d_features (n_leaves x feat_dim float32)
+ * and d_mlp_params (flat float32, same layout as mlp_params). Either output
+ * may be NULL to skip it. */
+int svlf_render_rays_backward(svlf_octree tree, const void *features, const float *mlp_params,
+                              const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
+                              const svlf_render_opts *opts, const float *d_rgb,
+                              const float *d_depth, float *d_features, float *d_mlp_params,
+                              void *workspace, size_t ws_bytes, void *stream);
+
+/* Training loss over n rays (device buffers):
+ *   L = (1/n) sum_r [ |C_r - C*_r|^2 + depth_weight * m_r |D_r - D*_r| ]
+ * Writes dL/dC (n x 3) into d_rgb and dL/dD (n) into d_depth (overwritten,
+ * sign(0) = 0) and adds L to *loss_accum (device double). */
+int svlf_loss(const float *rgb, const float *depth, const float *rgb_target,
+              const float *depth_target, const float *mask, int64_t n, float depth_weight,
+              float *d_rgb, float *d_depth, double *loss_accum, void *stream);
+
+/* ------------------------------------------------------------ optimiser */
+/* One bias-corrected Adam step (Sec. 4.5 trains with Adam; Kingma & Ba) over
+ * n float32 parameters (device): m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;
+ * p <- p - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * step >= 1. If bf16_shadow (device, n bfloat16) is not NULL, the updated
+ * parameters are also written there rounded to bfloat16. */
+int svlf_adam_step(float *params, const float *grads, float *m, float *v, int64_t n, float lr,
+                   float beta1, float beta2, float eps, int64_t step, void *bf16_shadow,
+                   void *stream);
+
+/* ------------------------------------------------------------ status */
+/* Reads and clears the device status word (bitwise OR of SVLF_DEV_*).
+ * Synchronises the device. */
+int svlf_get_device_status(int *status);
+
+const char *svlf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVLF_H */

@@ -1,0 +1,357 @@
+// The per-sample network in plain float32 on the SIMT cores (SVLF_FP32), and
+// the shared pieces every network path uses: the input row
+// h0 = [z | d | p~1 | p~2] (Sec. 4.1 ray parameterisation) and the output
+// activations (sigmoid colour, ReLU optical thickness; Sec. 4.5).
+//
+// Forward: tiles of 128 samples, activations feature-major in shared memory
+// ([k][s]), each of 256 threads computing an (H/16) x 8 block of the next
+// layer; weights are read transposed (packed as W^T) through the read-only
+// cache.
+// Backward: tiles of 64 samples; the forward is recomputed and every layer's
+// input kept in shared memory; dW = delta^T a is formed per tile in 4 x 4
+// register blocks and added to the global gradient with one atomic per
+// element per tile; dz (the feature gradient) is scattered with atomics.
+#include "svlf_internal.cuh"
+#include "mlp_common.cuh"
+
+namespace svlf {
+
+constexpr int kTsF = 128;  // forward tile (samples)
+constexpr int kTsB = 64;   // backward tile (samples)
+constexpr int kPadB = 68;  // row stride (floats) of backward tiles
+
+// Y[j][s] = relu(b_j + sum_k WT[k][j] X[k][s]) for j < H, s < TS (row stride ts)
+template <int H, int TS, int SPT>
+__device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int in, int ts,
+                                              const float *__restrict__ WT,
+                                              const float *__restrict__ bias, float *__restrict__ Y,
+                                              bool relu) {
+    constexpr int JT = H / 16;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const int j0 = ty * JT, s0 = tx * SPT;
+    float acc[JT][SPT];
+#pragma unroll
+    for (int j = 0; j < JT; ++j) {
+        const float b = __ldg(bias + j0 + j);
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) acc[j][s] = b;
+    }
+    for (int k = 0; k < in; ++k) {
+        float x[SPT];
+#pragma unroll
+        for (int s4 = 0; s4 < SPT / 4; ++s4) {
+            const float4 v = *reinterpret_cast<const float4 *>(X + k * ts + s0 + 4 * s4);
+            x[4 * s4] = v.x; x[4 * s4 + 1] = v.y; x[4 * s4 + 2] = v.z; x[4 * s4 + 3] = v.w;
+        }
+        float w[JT];
+#pragma unroll
+        for (int j4 = 0; j4 < JT / 4; ++j4) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(WT + k * H + j0 + 4 * j4));
+            w[4 * j4] = v.x; w[4 * j4 + 1] = v.y; w[4 * j4 + 2] = v.z; w[4 * j4 + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < JT; ++j)
+#pragma unroll
+            for (int s = 0; s < SPT; ++s) acc[j][s] = fmaf(w[j], x[s], acc[j][s]);
+    }
+#pragma unroll
+    for (int j = 0; j < JT; ++j)
+#pragma unroll
+        for (int s4 = 0; s4 < SPT / 4; ++s4) {
+            float4 v;
+            v.x = relu ? fmaxf(acc[j][4 * s4], 0.f) : acc[j][4 * s4];
+            v.y = relu ? fmaxf(acc[j][4 * s4 + 1], 0.f) : acc[j][4 * s4 + 1];
+            v.z = relu ? fmaxf(acc[j][4 * s4 + 2], 0.f) : acc[j][4 * s4 + 2];
+            v.w = relu ? fmaxf(acc[j][4 * s4 + 3], 0.f) : acc[j][4 * s4 + 3];
+            *reinterpret_cast<float4 *>(Y + (j0 + j) * ts + s0 + 4 * s4) = v;
+        }
+}
+
+// Write h0 of sample s (or zeros) into column `col` of X (row stride ts).
+__device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
+                                                   const void *feats, int feat_bf16,
+                                                   const float *rays, const Sample *samples,
+                                                   int64_t s, int64_t S, float *X, int ts,
+                                                   int col, int rows_padded) {
+    float h0[kMaxIn];
+    if (s < S) {
+        make_input_row(md, depth, feats, feat_bf16, rays, samples[s], h0);
+        for (int k = 0; k < md.in0; ++k) X[k * ts + col] = h0[k];
+    } else {
+        for (int k = 0; k < md.in0; ++k) X[k * ts + col] = 0.f;
+    }
+    for (int k = md.in0; k < rows_padded; ++k) X[k * ts + col] = 0.f;
+}
+
+template <int H>
+__global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
+    MlpDims md, int depth, const void *__restrict__ feats, int feat_bf16,
+    const float *__restrict__ packed, const float *__restrict__ rays,
+    const Sample *__restrict__ samples, const unsigned int *__restrict__ counter,
+    int64_t max_samples, float4 *__restrict__ outputs) {
+    extern __shared__ float4 smem_f4[];
+    float *X = reinterpret_cast<float *>(smem_f4);
+    const int dmax = md.in0 > H ? md.in0 : H;
+    float *Y = X + dmax * kTsF;
+    const int64_t S = min((int64_t)counter[0], max_samples);
+    const int64_t n_tiles = (S + kTsF - 1) / kTsF;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t s0 = tile * kTsF;
+        if (threadIdx.x < kTsF)
+            build_input_column(md, depth, feats, feat_bf16, rays, samples, s0 + threadIdx.x, S, X,
+                               kTsF, threadIdx.x, md.in0);
+        __syncthreads();
+        int in = md.in0;
+        float *A = X, *B = Y;
+        for (int l = 0; l < md.nh; ++l) {
+            gemm_relu_f32<H, kTsF, 8>(A, in, kTsF, packed + md.wt_off[l], packed + md.b_off[l], B,
+                                      true);
+            __syncthreads();
+            float *t = A; A = B; B = t;
+            in = H;
+        }
+        if (threadIdx.x < kTsF && s0 + threadIdx.x < S) {
+            const float *WT = packed + md.wt_off[md.nh];
+            const float *b = packed + md.b_off[md.nh];
+            float o0 = __ldg(b), o1 = __ldg(b + 1), o2 = __ldg(b + 2), o3 = __ldg(b + 3);
+            for (int k = 0; k < H; ++k) {
+                const float a = A[k * kTsF + threadIdx.x];
+                const float4 w = __ldg(reinterpret_cast<const float4 *>(WT + 4 * k));
+                o0 = fmaf(w.x, a, o0); o1 = fmaf(w.y, a, o1);
+                o2 = fmaf(w.z, a, o2); o3 = fmaf(w.w, a, o3);
+            }
+            outputs[s0 + threadIdx.x] = output_activation(o0, o1, o2, o3);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- backward
+// dW[j][k] += sum_s D[j][s] A[k][s] over a tile (rows j < nj, k < nk).
+__device__ __forceinline__ void accumulate_dw(const float *D, const float *A, int nj, int nk,
+                                              float *__restrict__ dW, int ld) {
+    const int bj = (nj + 3) / 4, bk = (nk + 3) / 4;
+    for (int blk = threadIdx.x; blk < bj * bk; blk += blockDim.x) {
+        const int j0 = (blk / bk) * 4, k0 = (blk % bk) * 4;
+        float acc[4][4] = {};
+        for (int s = 0; s < kTsB; s += 4) {
+            float4 d[4], a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                d[q] = *reinterpret_cast<const float4 *>(D + (j0 + q) * kPadB + s);
+                a[q] = *reinterpret_cast<const float4 *>(A + (k0 + q) * kPadB + s);
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc[p][q] += d[p].x * a[q].x + d[p].y * a[q].y + d[p].z * a[q].z +
+                                 d[p].w * a[q].w;
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + p < nj && k0 + q < nk) atomicAdd(dW + (j0 + p) * ld + k0 + q, acc[p][q]);
+    }
+}
+
+// Dst[k][s] = (sum_j W[j][k] D[j][s]) * mask(A[k][s] > 0), k < nk (W row-major, ld = nk_full)
+template <bool MASK>
+__device__ __forceinline__ void backprop_delta(const float *__restrict__ W, int nj, int nk,
+                                               int ldw, const float *D, const float *A,
+                                               float *Dst) {
+    const int bk = (nk + 3) / 4;
+    for (int blk = threadIdx.x; blk < bk * (kTsB / 4); blk += blockDim.x) {
+        const int k0 = (blk % bk) * 4, s0 = (blk / bk) * 4;
+        float acc[4][4] = {};
+        for (int j = 0; j < nj; ++j) {
+            const float4 d = *reinterpret_cast<const float4 *>(D + j * kPadB + s0);
+            float w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = (k0 + q < nk) ? __ldg(W + j * ldw + k0 + q) : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q][0] = fmaf(w[q], d.x, acc[q][0]);
+                acc[q][1] = fmaf(w[q], d.y, acc[q][1]);
+                acc[q][2] = fmaf(w[q], d.z, acc[q][2]);
+                acc[q][3] = fmaf(w[q], d.w, acc[q][3]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (k0 + q >= nk) continue;
+            float4 v = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+            if (MASK) {
+                const float4 a = *reinterpret_cast<const float4 *>(A + (k0 + q) * kPadB + s0);
+                v.x = a.x > 0.f ? v.x : 0.f;
+                v.y = a.y > 0.f ? v.y : 0.f;
+                v.z = a.z > 0.f ? v.z : 0.f;
+                v.w = a.w > 0.f ? v.w : 0.f;
+            }
+            *reinterpret_cast<float4 *>(Dst + (k0 + q) * kPadB + s0) = v;
+        }
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
+    MlpDims md, int depth, const void *__restrict__ feats, int feat_bf16,
+    const float *__restrict__ params, const float *__restrict__ packed,
+    const float *__restrict__ rays, const Sample *__restrict__ samples,
+    const unsigned int *__restrict__ counter, int64_t max_samples,
+    const float4 *__restrict__ dout, float *__restrict__ d_feat, float *__restrict__ d_params) {
+    extern __shared__ float4 smem_f4[];
+    float *base = reinterpret_cast<float *>(smem_f4);
+    const int in0p = (md.in0 + 3) & ~3;
+    // activations: A[0] = h0 (in0p rows), A[l] = input of layer l (H rows)
+    float *A[kMaxLayers];
+    A[0] = base;
+    for (int l = 1; l <= md.nh; ++l) A[l] = A[0] + in0p * kPadB + (l - 1) * H * kPadB;
+    const int dmax = in0p > H ? in0p : H;
+    float *Dc = A[md.nh] + H * kPadB;  // delta of the current layer's output
+    float *Dn = Dc + dmax * kPadB;     // delta one layer down (or dL/dz)
+    __shared__ int s_leaf[kTsB];
+    const int64_t S = min((int64_t)counter[0], max_samples);
+    const int64_t n_tiles = (S + kTsB - 1) / kTsB;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t s0 = tile * kTsB;
+        if (threadIdx.x < kTsB) {
+            const int64_t s = s0 + threadIdx.x;
+            build_input_column(md, depth, feats, feat_bf16, rays, samples, s, S, A[0], kPadB,
+                               threadIdx.x, in0p);
+            s_leaf[threadIdx.x] = s < S ? samples[s].leaf : -1;
+            const float4 g = s < S ? dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            Dc[0 * kPadB + threadIdx.x] = g.x;
+            Dc[1 * kPadB + threadIdx.x] = g.y;
+            Dc[2 * kPadB + threadIdx.x] = g.z;
+            Dc[3 * kPadB + threadIdx.x] = g.w;
+        }
+        __syncthreads();
+        // recompute the forward (inputs of every layer)
+        for (int l = 0; l < md.nh; ++l) {
+            gemm_relu_f32<H, kTsB, 4>(A[l], l == 0 ? md.in0 : H, kPadB, packed + md.wt_off[l],
+                                      packed + md.b_off[l], A[l + 1], true);
+            __syncthreads();
+        }
+        // layers from the output down
+        for (int l = md.nh; l >= 0; --l) {
+            const int nj = (l == md.nh) ? 4 : H;
+            const int nk = (l == 0) ? md.in0 : H;
+            float *dW = d_params + md.w_off[l];
+            float *db = dW + nj * nk;
+            if (d_params) {
+                accumulate_dw(Dc, A[l], nj, nk, dW, nk);
+                for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+                    float acc = 0.f;
+                    for (int s = 0; s < kTsB; ++s) acc += Dc[j * kPadB + s];
+                    atomicAdd(db + j, acc);
+                }
+            }
+            const float *W = params + md.w_off[l];
+            if (l > 0) {
+                backprop_delta<true>(W, nj, nk, nk, Dc, A[l], Dn);
+            } else if (d_feat) {
+                backprop_delta<false>(W, nj, md.F, nk, Dc, nullptr, Dn);
+            }
+            __syncthreads();
+            float *t = Dc; Dc = Dn; Dn = t;
+        }
+        // feature gradient: Dc now holds dL/dz (F rows)
+        if (d_feat) {
+            for (int e = threadIdx.x; e < kTsB * md.F; e += blockDim.x) {
+                const int s = e / md.F, f = e % md.F;
+                const int leaf = s_leaf[s];
+                if (leaf >= 0) atomicAdd(d_feat + (int64_t)leaf * md.F + f, Dc[f * kPadB + s]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- packing
+__global__ void pack_f32_kernel(MlpDims md, const float *__restrict__ params,
+                                float *__restrict__ packed) {
+    for (int l = 0; l <= md.nh; ++l) {
+        const int out = md.out_l[l], in = md.in_l[l];
+        const float *W = params + md.w_off[l];
+        const float *b = W + out * in;
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < out * in; e += gridDim.x * blockDim.x) {
+            const int j = e / in, k = e % in;
+            packed[md.wt_off[l] + k * out + j] = W[e];
+        }
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < out; j += gridDim.x * blockDim.x)
+            packed[md.b_off[l] + j] = b[j];
+    }
+}
+
+size_t packed_f32_floats(const MlpDims &md) {
+    return (size_t)md.b_off[md.nh] + 4;
+}
+
+int launch_pack_f32(const MlpDims &md, const float *params, float *packed, cudaStream_t s) {
+    pack_f32_kernel<<<64, 256, 0, s>>>(md, params, packed);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+template <int H>
+static int fwd_f32(const MlpDims &md, int depth, const void *feats, int fb, const float *packed,
+                   const float *rays, const Workspace &ws, int64_t max_samples, cudaStream_t s) {
+    const int dmax = md.in0 > H ? md.in0 : H;
+    const size_t smem = sizeof(float) * (size_t)(dmax + H) * kTsF;
+    if (cudaFuncSetAttribute(mlp_forward_f32_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    int blocks = num_sms() * (smem <= 100 * 1024 ? 2 : 1);
+    mlp_forward_f32_kernel<H><<<blocks, 256, smem, s>>>(md, depth, feats, fb, packed, rays,
+                                                        ws.samples, ws.counter, max_samples,
+                                                        ws.outputs);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+int launch_mlp_forward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+                           const float *packed, const float *rays, const Workspace &ws,
+                           int64_t max_samples, cudaStream_t s) {
+    switch (md.H) {
+        case 32: return fwd_f32<32>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
+        case 64: return fwd_f32<64>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
+        case 128: return fwd_f32<128>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
+        case 256: return fwd_f32<256>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
+        default: return SVLF_ERR_UNSUPPORTED;
+    }
+}
+
+size_t backward_f32_smem(const MlpDims &md) {
+    const int in0p = (md.in0 + 3) & ~3;
+    const int dmax = in0p > md.H ? in0p : md.H;
+    return sizeof(float) * (size_t)kPadB * (size_t)(in0p + md.nh * md.H + 2 * dmax);
+}
+
+template <int H>
+static int bwd_f32(const MlpDims &md, int depth, const void *feats, int fb, const float *params,
+                   const float *packed, const float *rays, const Workspace &ws,
+                   int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
+    const size_t smem = backward_f32_smem(md);
+    if (smem > 220 * 1024) return SVLF_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(mlp_backward_f32_kernel<H>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    mlp_backward_f32_kernel<H><<<num_sms(), 256, smem, s>>>(md, depth, feats, fb, params, packed,
+                                                            rays, ws.samples, ws.counter,
+                                                            max_samples, ws.dout, d_feat, d_params);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+int launch_mlp_backward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+                            const float *params, const float *packed, const float *rays,
+                            const Workspace &ws, int64_t max_samples, float *d_feat,
+                            float *d_params, cudaStream_t s) {
+    switch (md.H) {
+        case 32: return bwd_f32<32>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        case 64: return bwd_f32<64>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        case 128: return bwd_f32<128>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        default: return SVLF_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace svlf

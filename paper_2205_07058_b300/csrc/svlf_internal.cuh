@@ -1,0 +1,183 @@
+// Internal declarations shared by the CUDA translation units of libsvlf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/svlf.h"
+
+namespace svlf {
+
+constexpr int kMaxDepth = 10;
+constexpr int kMaxK = 32;
+constexpr int kSmemNodeWords = 8192;  // octree node words staged in shared memory per CTA
+
+// ---------------------------------------------------------------- octree
+// Device layout of the sparse octree (built in octree.cu):
+//  * node words for levels 0 .. L-3, level-major, Morton order inside a level:
+//      bits 31..24 child mask (bit o set = child octant o occupied,
+//      octant bit 0 = x, 1 = y, 2 = z), bits 23..0 index of the first child
+//      (into the node words for levels < L-3, into the bricks for level L-3).
+//  * bricks = the occupied nodes of level L-2, each covering 4^3 leaves:
+//      x, y = 64-bit leaf mask (bit = Morton code of the leaf inside the brick),
+//      z = rank of the brick's first leaf, w = 0.
+//  Leaf rank = brick.z + popcount(mask & ((1 << bit) - 1)).
+struct OctreeView {
+    int depth;
+    int n_node_levels;  // L - 2
+    int64_t n_leaves;
+    int n_nodes, n_bricks;
+    const uint32_t *nodes;
+    const uint4 *bricks;
+    int root_is_brick;  // depth 2: the root itself is the only brick
+    int empty;          // no leaves
+};
+
+struct OctreeHost {
+    OctreeView view;
+    int32_t *leaf_ijk_dev;  // n_leaves x 3, rank order
+    uint32_t *nodes_dev;
+    uint4 *bricks_dev;
+};
+
+// ---------------------------------------------------------------- samples
+// One record per (ray, hit): leaf rank, ray index, packed voxel coordinates
+// (i | j << 10 | k << 20), segment midpoint (t_in + t_out)/2 as float bits.
+struct __align__(16) Sample {
+    int32_t leaf;
+    int32_t ray;
+    uint32_t cell;
+    float tmid;
+};
+
+// Workspace layout (byte offsets from a 256-aligned base).
+struct Workspace {
+    Sample *samples;       // n_rays*K
+    float4 *outputs;       // n_rays*K: sigmoid colour (xyz), tau (w)
+    float4 *dout;          // n_rays*K: dL/d(network output)
+    int2 *ray_span;        // n_rays: first sample, count
+    unsigned int *counter; // [0] samples written, [1] tiles claimed (forward), [2] (backward)
+    void *packed_w;        // network weights packed for the kernels
+    size_t bytes;
+};
+
+Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K);
+size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K);
+size_t packed_weight_bytes(const svlf_mlp_desc &mlp);
+
+// ---------------------------------------------------------------- device status
+extern __device__ unsigned int g_device_status;
+
+__device__ __forceinline__ void raise_status(unsigned int bit) {
+    atomicOr(&g_device_status, bit);
+}
+
+// ---------------------------------------------------------------- launches
+int launch_trace(const OctreeView &tree, const float *rays, int64_t n_rays, int K,
+                 const Workspace &ws, int32_t *hits, float *t_io, cudaStream_t s);
+int launch_composite(const Workspace &ws, int64_t n_rays, const float bg[3], float *rgb,
+                     float *depth, cudaStream_t s);
+int launch_composite_backward(const Workspace &ws, int64_t n_rays, const float bg[3],
+                              const float *d_rgb, const float *d_depth, cudaStream_t s);
+int launch_pack_weights(const svlf_mlp_desc &mlp, const float *params, void *packed,
+                        cudaStream_t s);
+int launch_mlp_forward(const svlf_mlp_desc &mlp, int depth, const void *features,
+                       const float *params, const float *rays, const Workspace &ws,
+                       int64_t max_samples, cudaStream_t s);
+int launch_mlp_backward(const svlf_mlp_desc &mlp, int depth, const void *features,
+                        const float *params, const float *rays, const Workspace &ws,
+                        int64_t max_samples, float *d_features, float *d_params,
+                        cudaStream_t s);
+
+int num_sms();
+
+// ---------------------------------------------------------------- geometry
+// Ray parameterisation r = [p~1 | p~2] (Sec. 4.1): the ray's entry and exit
+// points on the minimum bounding sphere of voxel `cell`, relative to the voxel
+// centre c = (ijk + 1/2) 2^-L, scaled to unit norm.
+//
+// The perpendicular offset q of the ray from c is tiny (at most the sphere
+// radius, ~1e-3) next to |o - c| (~2.5), so it is formed in double-float
+// arithmetic (Dekker 1971: exact TwoSum / TwoProduct with FMA): o - c exactly,
+// t_f = -(d.(o-c)) / |d|^2 and q = (o - c) + t_f d to about 1e-12 absolute.
+// The half chord and the normalisation are then plain float32.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void sphere_param(const float o[3], const float d[3], uint32_t cell,
+                                             int depth, float p1[3], float p2[3]) {
+    const float h = ldexpf(1.0f, -depth);
+    const float R = 0.8660254037844386f * h;
+    float oc_hi[3], oc_lo[3];
+    {
+        int ijk[3] = {(int)(cell & 1023u), (int)((cell >> 10) & 1023u), (int)((cell >> 20) & 1023u)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float c = ((float)ijk[a] + 0.5f) * h;  // exact
+            two_sum(o[a], -c, oc_hi[a], oc_lo[a]);
+        }
+    }
+    // b = d . (o - c) and dd = d . d in double-float
+    float b_hi = 0.f, b_lo = 0.f, dd_hi = 0.f, dd_lo = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p, pe, s, se;
+        two_prod(d[a], oc_hi[a], p, pe);
+        two_sum(b_hi, p, s, se);
+        b_hi = s;
+        b_lo += se + pe + d[a] * oc_lo[a];
+        two_prod(d[a], d[a], p, pe);
+        two_sum(dd_hi, p, s, se);
+        dd_hi = s;
+        dd_lo += se + pe;
+    }
+    {
+        float s, se;
+        two_sum(b_hi, b_lo, s, se);
+        b_hi = s;
+        b_lo = se;
+    }
+    // 1/dd = 1 + e + O(e^2) with e = 1 - dd (|e| ~ 1e-7 for a float32 unit vector)
+    const float e = (1.0f - dd_hi) - dd_lo;
+    // t_f = -b (1 + e) as (tf_hi, tf_lo)
+    const float tf_hi = -b_hi;
+    const float tf_lo = -b_lo - b_hi * e;
+    float q[3];
+    float qq = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p, pe;
+        two_prod(tf_hi, d[a], p, pe);
+        q[a] = (oc_hi[a] + p) + (oc_lo[a] + pe + tf_lo * d[a]);
+        qq = fmaf(q[a], q[a], qq);
+    }
+    const float half = sqrtf(fmaxf(R * R - qq, 0.0f) * (1.0f + e));
+    float n1 = 0.f, n2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p1[a] = q[a] - half * d[a];
+        p2[a] = q[a] + half * d[a];
+        n1 = fmaf(p1[a], p1[a], n1);
+        n2 = fmaf(p2[a], p2[a], n2);
+    }
+    const float i1 = rsqrtf(n1), i2 = rsqrtf(n2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p1[a] *= i1;
+        p2[a] *= i2;
+    }
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+}  // namespace svlf

@@ -1,0 +1,293 @@
+// Per-ray sparse-octree traversal: the first K occupied leaves along each ray,
+// in ascending t, with their segments [t_in, t_out] (Sec. 4.3 "Evaluating
+// intersected voxels"; slab test of Sec. 4.2).
+//
+// Design (one ray per thread, stackless):
+//  * The ray is walked voxel-block by voxel-block. At every position the
+//    octree is descended from the root to find either the largest empty
+//    block containing the current finest cell, or the cell's brick (the 4^3
+//    leaves under a level L-2 node, held as a 64-bit mask). The brick of the
+//    current cell stays cached in registers, so consecutive cells inside it
+//    cost no memory access.
+//  * The node words of the top levels (up to kSmemNodeWords) are staged in
+//    shared memory; deeper levels and bricks come through the read-only path.
+//  * Plane crossings are t = (k 2^-L - o) / d with an IEEE division, and the
+//    cell after a crossing is found by counting the planes whose crossing is
+//    <= the current t. A voxel is therefore entered at exactly the t the slab
+//    test would give as its t_in and left at its t_out, every visited voxel
+//    has t_out > t_in, and no voxel with a positive segment is skipped.
+//  * Hits stay in registers (K is a template parameter); at the end each warp
+//    reserves space for its rays' samples with one atomic and writes them
+//    contiguously per ray.
+#include "svlf_internal.cuh"
+
+namespace svlf {
+
+__device__ unsigned int g_device_status = 0;
+
+template <int K>
+struct HitBuf {
+    int rank[K];
+    uint32_t cell[K];
+    float tin[K], tout[K];
+};
+
+struct RayState {
+    float o[3], d[3];
+    float h;
+    int n;  // 2^L
+};
+
+__device__ __forceinline__ float cross_t(const RayState &R, int a, int k) {
+    return ((float)k * R.h - R.o[a]) / R.d[a];
+}
+
+// Cell index along axis a occupied just after time t, searched in [lo, hi].
+__device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int lo, int hi) {
+    float pos = (R.o[a] + t * R.d[a]) * (float)R.n;
+    int k = (int)floorf(fminf(fmaxf(pos, -1.0f), (float)R.n));
+    k = min(max(k, lo), hi);
+    if (R.d[a] > 0.f) {
+        for (int it = 0; it < 64 && k > lo && cross_t(R, a, k) > t; ++it) --k;
+        for (int it = 0; it < 64 && k < hi && cross_t(R, a, k + 1) <= t; ++it) ++k;
+    } else {
+        for (int it = 0; it < 64 && k < hi && cross_t(R, a, k + 1) > t; ++it) ++k;
+        for (int it = 0; it < 64 && k > lo && cross_t(R, a, k) <= t; ++it) --k;
+    }
+    return k;
+}
+
+template <int K>
+__device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem, RayState &R,
+                        HitBuf<K> &hb) {
+    if (T.empty) return 0;
+    const int L = T.depth;
+    const int n = R.n;
+    float t0 = 0.f, t1 = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] == 0.f) {
+            if (R.o[a] < 0.f || R.o[a] > 1.f) return 0;
+            continue;
+        }
+        float ta = cross_t(R, a, 0), tb = cross_t(R, a, n);
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    if (!(t1 - t0 > 0.f)) return 0;
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] == 0.f) {
+            c[a] = min(max((int)floorf(R.o[a] * (float)n), 0), n - 1);
+        } else {
+            c[a] = cell_after(R, a, t0, 0, n - 1);
+        }
+    }
+    float t = t0;
+    int nh = 0;
+    uint32_t cached = 0xFFFFFFFFu;
+    uint64_t bmask = 0;
+    int bbase = 0;
+    const int max_steps = 3 * n + 64;
+    for (int step = 0;; ++step) {
+        if (step >= max_steps) {
+            raise_status(SVLF_DEV_STEP_LIMIT);
+            break;
+        }
+        const uint32_t key = (uint32_t)(c[0] >> 2) | ((uint32_t)(c[1] >> 2) << 10) |
+                             ((uint32_t)(c[2] >> 2) << 20);
+        int sz_log = 0;
+        bool leaf = false;
+        int rank = -1;
+        if (key != cached) {
+            int node = 0;
+            bool found = true;
+            for (int l = 0; l < T.n_node_levels; ++l) {
+                const int s = L - 1 - l;
+                const int oct = ((c[0] >> s) & 1) | (((c[1] >> s) & 1) << 1) | (((c[2] >> s) & 1) << 2);
+                uint32_t w;
+                if (node < n_smem) {
+                    w = s_nodes[node];
+                } else if (node < T.n_nodes) {
+                    w = __ldg(T.nodes + node);
+                } else {
+                    raise_status(SVLF_DEV_BAD_INDEX);
+                    return nh;
+                }
+                const uint32_t m = w >> 24;
+                if (!((m >> oct) & 1u)) {
+                    sz_log = s;
+                    found = false;
+                    break;
+                }
+                node = (int)(w & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
+            }
+            if (found) {
+                if (node >= T.n_bricks) {
+                    raise_status(SVLF_DEV_BAD_INDEX);
+                    return nh;
+                }
+                const uint4 b = __ldg(T.bricks + node);
+                bmask = (uint64_t)b.x | ((uint64_t)b.y << 32);
+                bbase = (int)b.z;
+                cached = key;
+            } else {
+                cached = 0xFFFFFFFFu;
+            }
+        }
+        if (cached == key) {
+            const int bit = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2) |
+                            (((c[0] >> 1) & 1) << 3) | (((c[1] >> 1) & 1) << 4) |
+                            (((c[2] >> 1) & 1) << 5);
+            if (((bmask >> (bit & 56)) & 0xFFull) == 0) {
+                sz_log = 1;
+            } else if (!((bmask >> bit) & 1ull)) {
+                sz_log = 0;
+            } else {
+                leaf = true;
+                rank = bbase + __popcll(bmask & ((1ull << bit) - 1ull));
+            }
+        }
+        const int sz = 1 << sz_log;
+        int B[3];
+        float ta[3];
+        float tx = INFINITY;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            B[a] = c[a] & ~(sz - 1);
+            ta[a] = R.d[a] > 0.f ? cross_t(R, a, B[a] + sz)
+                  : R.d[a] < 0.f ? cross_t(R, a, B[a]) : INFINITY;
+            tx = fminf(tx, ta[a]);
+        }
+        if (leaf) {
+            const uint32_t packed = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (j == nh) {
+                    hb.rank[j] = rank;
+                    hb.cell[j] = packed;
+                    hb.tin[j] = t;
+                    hb.tout[j] = tx;
+                }
+            }
+            if (++nh == K) break;
+        }
+        bool out = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (R.d[a] == 0.f) continue;
+            if (ta[a] <= tx) {
+                c[a] = R.d[a] > 0.f ? B[a] + sz : B[a] - 1;
+            } else if (sz > 1) {
+                const int lo = R.d[a] > 0.f ? c[a] : B[a];
+                const int hi = R.d[a] > 0.f ? B[a] + sz - 1 : c[a];
+                c[a] = cell_after(R, a, tx, lo, hi);
+            }
+            out |= (c[a] < 0) | (c[a] >= n);
+        }
+        if (out) break;
+        t = tx;
+    }
+    return nh;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *__restrict__ rays,
+                                                    int64_t n_rays, Sample *__restrict__ samples,
+                                                    int2 *__restrict__ ray_span,
+                                                    unsigned int *__restrict__ counter,
+                                                    int64_t max_samples, int32_t *__restrict__ hits,
+                                                    float *__restrict__ t_io) {
+    extern __shared__ uint32_t s_nodes[];
+    const int n_smem = min(T.n_nodes, kSmemNodeWords);
+    for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_nodes[i] = T.nodes[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_rays;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = base + threadIdx.x;
+        const bool valid = r < n_rays;
+        HitBuf<K> hb;
+        int nh = 0;
+        if (valid) {
+            RayState R;
+            const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * r);
+            const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
+            R.o[0] = a.x; R.o[1] = a.y; R.o[2] = b.x;
+            R.d[0] = b.y; R.d[1] = cc.x; R.d[2] = cc.y;
+            R.n = 1 << T.depth;
+            R.h = ldexpf(1.0f, -T.depth);
+            nh = traverse<K>(T, s_nodes, n_smem, R, hb);
+        }
+        // warp-aggregated reservation of nh samples per lane
+        int incl = nh;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long wbase = 0;
+        if (lane == 31 && total > 0) wbase = atomicAdd(counter, (unsigned int)total);
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+        const int64_t first = (int64_t)wbase + (incl - nh);
+        if (valid) {
+            int keep = nh;
+            if (first + nh > max_samples) {
+                raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
+                keep = (int)max((int64_t)0, max_samples - first);
+            }
+            ray_span[r] = make_int2((int)first, keep);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (j < keep) {
+                    Sample sm;
+                    sm.leaf = hb.rank[j];
+                    sm.ray = (int32_t)r;
+                    sm.cell = hb.cell[j];
+                    sm.tmid = 0.5f * (hb.tin[j] + hb.tout[j]);
+                    reinterpret_cast<int4 *>(samples)[first + j] =
+                        make_int4(sm.leaf, sm.ray, (int)sm.cell, __float_as_int(sm.tmid));
+                }
+                if (hits) hits[r * K + j] = j < nh ? hb.rank[j] : -1;
+                if (t_io) {
+                    reinterpret_cast<float2 *>(t_io)[r * K + j] =
+                        j < nh ? make_float2(hb.tin[j], hb.tout[j]) : make_float2(0.f, 0.f);
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+static int launch_trace_k(const OctreeView &T, const float *rays, int64_t n_rays,
+                          const Workspace &ws, int32_t *hits, float *t_io, int64_t max_samples,
+                          cudaStream_t s) {
+    const int threads = 256;
+    const size_t smem = sizeof(uint32_t) * (size_t)min(T.n_nodes, kSmemNodeWords);
+    int64_t blocks = (n_rays + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * 6;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    trace_kernel<K><<<(unsigned)blocks, threads, smem, s>>>(T, rays, n_rays, ws.samples,
+                                                            ws.ray_span, ws.counter, max_samples,
+                                                            hits, t_io);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+int launch_trace(const OctreeView &T, const float *rays, int64_t n_rays, int K,
+                 const Workspace &ws, int32_t *hits, float *t_io, cudaStream_t s) {
+    const int64_t max_samples = n_rays * (int64_t)K;
+    switch (K) {  // the hit buffer lives in registers: one instantiation per K
+        case 1: return launch_trace_k<1>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        case 2: return launch_trace_k<2>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        case 4: return launch_trace_k<4>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        case 8: return launch_trace_k<8>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        case 16: return launch_trace_k<16>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        case 32: return launch_trace_k<32>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
+        default: return SVLF_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace svlf

@@ -1,0 +1,277 @@
+"""Python binding of libsvlf (the C ABI in include/svlf.h).
+
+Argument marshalling only: every step of the render/train path runs in the
+library's CUDA kernels. PyTorch supplies device memory and the current CUDA
+stream. Importing this module on a machine without the built library raises;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsvlf.so")
+
+SVLF_OK = 0
+SVLF_ERR_ARG = -1
+SVLF_ERR_CUDA = -2
+SVLF_ERR_DEVICE = -3
+SVLF_ERR_UNSUPPORTED = -4
+SVLF_ERR_WORKSPACE = -5
+
+SVLF_DEV_STEP_LIMIT = 1
+SVLF_DEV_BAD_INDEX = 2
+SVLF_DEV_SAMPLE_OVERFLOW = 4
+SVLF_DEV_WAIT_TIMEOUT = 8
+
+FP32, BF16, FP16 = 0, 1, 2
+FEAT_F32, FEAT_BF16 = 0, 1
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
+
+
+class SvlfError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {code} ({status_string(code)})")
+        self.code = code
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("feat_dim", ctypes.c_int), ("hidden", ctypes.c_int), ("n_hidden", ctypes.c_int),
+                ("out_dim", ctypes.c_int), ("precision", ctypes.c_int), ("feat_dtype", ctypes.c_int)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3)]
+
+
+EXPORTS = [
+    "svlf_build_octree", "svlf_octree_leaf_ijk", "svlf_octree_info", "svlf_free_octree",
+    "svlf_workspace_size", "svlf_render_rays", "svlf_render_rays_backward", "svlf_loss",
+    "svlf_adam_step", "svlf_get_device_status", "svlf_status_string",
+]
+
+_lib = None
+
+
+def lib():
+    """Load libsvlf.so (built in-tree by build_lib.py). Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsvlf.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.svlf_build_octree.argtypes = [vp, i64, i32, vp, P(vp), P(i64)]
+    L.svlf_octree_leaf_ijk.argtypes = [vp, vp, vp]
+    L.svlf_octree_info.argtypes = [vp, P(i32), P(i64), P(i64), P(i64)]
+    L.svlf_free_octree.argtypes = [vp]
+    L.svlf_workspace_size.argtypes = [P(MlpDesc), i64, i32, P(sz)]
+    L.svlf_render_rays.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp, vp, vp, vp,
+                                   vp, sz, vp]
+    L.svlf_render_rays_backward.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp,
+                                            vp, vp, vp, vp, sz, vp]
+    L.svlf_loss.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp, vp, vp]
+    L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
+    L.svlf_get_device_status.argtypes = [P(i32)]
+    L.svlf_status_string.argtypes = [i32]
+    L.svlf_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "svlf_status_string":
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().svlf_status_string(int(code)).decode()
+
+
+def _check(fn: str, rc: int):
+    if rc != SVLF_OK:
+        raise SvlfError(fn, rc)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# octree
+# ---------------------------------------------------------------------------
+class Octree:
+    """Library-owned sparse octree (svlf_build_octree)."""
+
+    def __init__(self, leaf_ijk: torch.Tensor, depth: int, stream=None):
+        ijk = leaf_ijk.to(device="cuda", dtype=torch.int32).contiguous()
+        h = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check("svlf_build_octree", lib().svlf_build_octree(
+            _ptr(ijk), ijk.shape[0], int(depth), _stream(stream), ctypes.byref(h), ctypes.byref(n)))
+        self.handle = h
+        self.depth = int(depth)
+        self.n_leaves = int(n.value)
+
+    def info(self):
+        d, nl, nn, nb = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check("svlf_octree_info", lib().svlf_octree_info(self.handle, ctypes.byref(d), ctypes.byref(nl),
+                                                           ctypes.byref(nn), ctypes.byref(nb)))
+        return {"depth": d.value, "n_leaves": nl.value, "n_nodes": nn.value, "n_bricks": nb.value}
+
+    def leaf_ijk(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n_leaves, 3), dtype=torch.int32, device="cuda")
+        _check("svlf_octree_leaf_ijk", lib().svlf_octree_leaf_ijk(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().svlf_free_octree(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# rendering
+# ---------------------------------------------------------------------------
+@dataclass
+class Network:
+    feat_dim: int
+    hidden: int
+    n_hidden: int
+    precision: int = FP32
+    feat_dtype: int = FEAT_F32
+
+    def desc(self) -> MlpDesc:
+        return MlpDesc(self.feat_dim, self.hidden, self.n_hidden, 4, self.precision, self.feat_dtype)
+
+
+def workspace_size(net: Network, n_rays: int, K: int) -> int:
+    b = ctypes.c_size_t()
+    d = net.desc()
+    _check("svlf_workspace_size", lib().svlf_workspace_size(ctypes.byref(d), int(n_rays), int(K), ctypes.byref(b)))
+    return int(b.value)
+
+
+def alloc_workspace(net: Network, n_rays: int, K: int) -> torch.Tensor:
+    """A 256-byte aligned device buffer of svlf_workspace_size bytes."""
+    return torch.empty(workspace_size(net, n_rays, K) + 256, dtype=torch.uint8, device="cuda")
+
+
+def _ws_ptr(ws: torch.Tensor):
+    p = ws.data_ptr()
+    aligned = (p + 255) & ~255
+    return ctypes.c_void_p(aligned), ws.numel() - (aligned - p)
+
+
+def _opts(K: int, bg: Sequence[float]) -> RenderOpts:
+    o = RenderOpts()
+    o.K = int(K)
+    for i in range(3):
+        o.bg[i] = float(bg[i])
+    return o
+
+
+def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
+                     rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
+                     want_hits: bool = False, out: Optional[tuple] = None, stream=None):
+    """Returns (rgb (N,3), depth (N,), hits (N,K) or None, t_io (N,K,2) or None, workspace)."""
+    N = rays.shape[0]
+    if workspace is None:
+        workspace = alloc_workspace(net, N, K)
+    if out is None:
+        rgb = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+        depth = torch.empty((N,), dtype=torch.float32, device="cuda")
+    else:
+        rgb, depth = out
+    hits = torch.empty((N, K), dtype=torch.int32, device="cuda") if want_hits else None
+    t_io = torch.empty((N, K, 2), dtype=torch.float32, device="cuda") if want_hits else None
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays", lib().svlf_render_rays(
+        tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
+        _ptr(rgb), _ptr(depth), _ptr(hits), _ptr(t_io), wp, wb, _stream(stream)))
+    return rgb, depth, hits, t_io, workspace
+
+
+def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
+                              rays: torch.Tensor, K: int, bg, d_rgb: torch.Tensor, d_depth: torch.Tensor,
+                              d_features: Optional[torch.Tensor], d_params: Optional[torch.Tensor],
+                              workspace: torch.Tensor, stream=None):
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays_backward", lib().svlf_render_rays_backward(
+        tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), rays.shape[0],
+        ctypes.byref(o), _ptr(d_rgb), _ptr(d_depth), _ptr(d_features), _ptr(d_params), wp, wb,
+        _stream(stream)))
+
+
+def svlf_loss(rgb, depth, rgb_t, depth_t, mask, depth_weight: float, d_rgb, d_depth, loss_accum, stream=None):
+    _check("svlf_loss", lib().svlf_loss(_ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), _ptr(mask),
+                                        rgb.shape[0], float(depth_weight), _ptr(d_rgb), _ptr(d_depth),
+                                        _ptr(loss_accum), _stream(stream)))
+
+
+def svlf_adam_step(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   bf16_shadow: Optional[torch.Tensor] = None, stream=None):
+    _check("svlf_adam_step", lib().svlf_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(),
+                                                  float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                                  _ptr(bf16_shadow), _stream(stream)))
+
+
+def svlf_get_device_status() -> int:
+    s = ctypes.c_int()
+    _check("svlf_get_device_status", lib().svlf_get_device_status(ctypes.byref(s)))
+    return int(s.value)
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+class SvlfRender(torch.autograd.Function):
+    """rgb, depth = render(features, params); backward through the library's
+    hand-written kernels (activations recomputed, not stored)."""
+
+    @staticmethod
+    def forward(ctx, features, params, tree, net, rays, K, bg):
+        rgb, depth, _, _, ws = svlf_render_rays(tree, features, params, net, rays, K, bg)
+        ctx.save_for_backward(features, params, rays)
+        ctx.tree, ctx.net, ctx.K, ctx.bg, ctx.ws = tree, net, K, bg, ws
+        return rgb, depth
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth):
+        features, params, rays = ctx.saved_tensors
+        df = torch.zeros(features.shape, dtype=torch.float32, device="cuda") if ctx.needs_input_grad[0] else None
+        dp = torch.zeros_like(params) if ctx.needs_input_grad[1] else None
+        svlf_render_rays_backward(ctx.tree, features, params, ctx.net, rays, ctx.K, ctx.bg,
+                                  g_rgb.contiguous(), g_depth.contiguous(), df, dp, ctx.ws)
+        ctx.ws = None
+        return df, dp, None, None, None, None, None
+
+
+def render(features, params, tree: Octree, net: Network, rays, K: int, bg=(0.0, 0.0, 0.0)):
+    return SvlfRender.apply(features, params, tree, net, rays, K, tuple(bg))
