@@ -172,6 +172,16 @@ int svlf_get_device_status(int *status);
 
 const char *svlf_status_string(int status);
 
+/* ------------------------------------------------------------ self-test */
+/* Test aid, not part of the rendering method: D = A B^T for one tile through
+ * the tensor cores, with the operands staged in the shared-memory layouts the
+ * network kernels use (K-major, or MN-major when the flag is set).
+ * A: device, 128 x K 16-bit values (bf16 if bf16 != 0, else f16), row-major.
+ * B: device, N x K, row-major. D: device, 128 x N float32.
+ * N in {32, 64, ..., 256}, K in {16, 32, ..., 256}. */
+int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
+                      int a_mn_major, int b_mn_major, int bf16, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

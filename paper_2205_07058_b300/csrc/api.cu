@@ -104,12 +104,14 @@ static int check_mlp(const svlf_mlp_desc *m) {
 static int check_common(svlf_octree tree, const void *features, const float *params,
                         const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
                         const svlf_render_opts *opts, void *workspace, size_t ws_bytes) {
-    if (!tree || !params || !rays || !opts || n_rays < 0) return SVLF_ERR_ARG;
-    if (!features && octree_view(tree).n_leaves > 0) return SVLF_ERR_ARG;
+    if (!tree || !opts || n_rays < 0) return SVLF_ERR_ARG;
     int rc = check_mlp(mlp);
     if (rc) return rc;
     const int K = opts->K;
     if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SVLF_ERR_UNSUPPORTED;
+    if (n_rays == 0) return SVLF_OK;  // nothing to read or write
+    if (!params || !rays) return SVLF_ERR_ARG;
+    if (!features && octree_view(tree).n_leaves > 0) return SVLF_ERR_ARG;
     if ((int64_t)n_rays * K >= ((int64_t)1 << 31)) return SVLF_ERR_UNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(features) % 16 || reinterpret_cast<uintptr_t>(rays) % 8)
         return SVLF_ERR_ARG;
@@ -143,8 +145,8 @@ extern "C" int svlf_render_rays(svlf_octree tree, const void *features, const fl
                                 void *stream) {
     int rc = check_common(tree, features, mlp_params, mlp, rays, n_rays, opts, workspace, ws_bytes);
     if (rc) return rc;
-    if (!rgb || !depth) return SVLF_ERR_ARG;
     if (n_rays == 0) return SVLF_OK;
+    if (!rgb || !depth) return SVLF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int K = opts->K;
     Workspace ws = carve_workspace(workspace, *mlp, n_rays, K);
@@ -174,8 +176,8 @@ extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
                                          void *stream) {
     int rc = check_common(tree, features, mlp_params, mlp, rays, n_rays, opts, workspace, ws_bytes);
     if (rc) return rc;
-    if (!d_rgb || !d_depth) return SVLF_ERR_ARG;
     if (n_rays == 0 || (!d_features && !d_mlp_params)) return SVLF_OK;
+    if (!d_rgb || !d_depth) return SVLF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int K = opts->K;
     Workspace ws = carve_workspace(workspace, *mlp, n_rays, K);

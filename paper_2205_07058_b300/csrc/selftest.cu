@@ -1,0 +1,93 @@
+// Self-test of the tensor-core operand layouts: one 128 x N x K product
+// D = A B^T through tcgen05.mma, with either operand in K-major or MN-major
+// shared-memory layout. Test aid for the descriptor conventions the network
+// kernels rely on; not part of the rendering method.
+#include "svlf_internal.cuh"
+#include "tc_common.cuh"
+
+namespace svlf {
+
+__global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__restrict__ A,
+                                                              const uint16_t *__restrict__ B,
+                                                              float *__restrict__ D, int N, int K,
+                                                              int a_mn, int b_mn, int bf16) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    uint8_t *sa = smem;
+    uint8_t *sb = smem + 128 * K * 2;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int e = tid; e < 128 * K; e += 128) {
+        const int m = e / K, k = e % K;
+        const uint32_t off = a_mn ? tc::cm_offset(k, m, K) : tc::cm_offset(m, k, 128);
+        *reinterpret_cast<uint16_t *>(sa + off) = A[e];
+    }
+    for (int e = tid; e < N * K; e += 128) {
+        const int n = e / K, k = e % K;
+        const uint32_t off = b_mn ? tc::cm_offset(k, n, K) : tc::cm_offset(n, k, N);
+        *reinterpret_cast<uint16_t *>(sb + off) = B[e];
+    }
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(&s_mbar), 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&s_tmem), 256);
+        tc::tmem_relinquish();
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_f16(128, N, bf16, a_mn, b_mn);
+        for (int k = 0; k < K; k += 16) {
+            const uint64_t da = a_mn ? tc::sdesc(tc::smem_u32(sa) + (k >> 3) * 128, 128, K * 16)
+                                     : tc::sdesc(tc::smem_u32(sa) + (k >> 3) * 2048, 2048, 128);
+            const uint64_t db = b_mn ? tc::sdesc(tc::smem_u32(sb) + (k >> 3) * 128, 128, K * 16)
+                                     : tc::sdesc(tc::smem_u32(sb) + (k >> 3) * (N * 16), N * 16, 128);
+            tc::mma_f16(tmem, da, db, idesc, k > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(tc::smem_u32(&s_mbar));
+    }
+    const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar), 0, 200000000ll);
+    if (!ok && tid == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+    tc::fence_after_sync();
+    if (ok) {
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < N; c += 32) {
+            uint32_t v[32];
+            tc::tmem_ld32(trow + c, v);
+            tc::tmem_wait_ld();
+            for (int e = 0; e < 32 && c + e < N; ++e) D[tid * N + c + e] = __uint_as_float(v[e]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 256);
+    }
+}
+
+}  // namespace svlf
+
+using namespace svlf;
+
+extern "C" int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
+                                 int a_mn_major, int b_mn_major, int bf16, void *stream) {
+    if (!A || !B || !D || N < 32 || N > 256 || N % 32 || K < 16 || K > 256 || K % 16)
+        return SVLF_ERR_ARG;
+    // Generous on purpose: every read the descriptors can address stays inside
+    // the allocation even if a layout were misread.
+    const size_t need = (size_t)(128 + N) * K * 2 + 128;
+    const size_t smem = need > 200 * 1024 ? need : 200 * 1024;
+    if (cudaFuncSetAttribute(mma_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    mma_selftest_kernel<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, N, K, a_mn_major,
+                                                                 b_mn_major, bf16);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
