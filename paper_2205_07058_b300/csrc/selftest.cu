@@ -10,14 +10,21 @@ namespace svlf {
 __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__restrict__ A,
                                                               const uint16_t *__restrict__ B,
                                                               float *__restrict__ D, int N, int K,
-                                                              int a_mn, int b_mn, int bf16) {
+                                                              int a_mn, int b_mn, int bf16,
+                                                              int flags) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
-    uint8_t *sa = smem;
-    uint8_t *sb = smem + 128 * K * 2;
+    // flags: bit 0 swap the two descriptor byte offsets, bit 1 place B before A,
+    // bit 2 / bit 3 start the B / A descriptor 16 bytes later
+    const int swap = flags & 1;
+    const int gap = (flags >> 8) & 0xFFFF;  // bytes between the two staged operands
+    uint8_t *sa = (flags & 2) ? smem + N * K * 2 + gap : smem;
+    uint8_t *sb = (flags & 2) ? smem : smem + 128 * K * 2 + gap;
+    const uint32_t adj_b = (flags & 4) ? 16u : 0u, adj_a = (flags & 8) ? 16u : 0u;
     const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0 && (flags & 16)) D[0] = (float)tc::smem_u32(smem);
     for (int e = tid; e < 128 * K; e += 128) {
         const int m = e / K, k = e % K;
         const uint32_t off = a_mn ? tc::cm_offset(k, m, K) : tc::cm_offset(m, k, 128);
@@ -44,10 +51,15 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
     if (tid == 0) {
         const uint32_t idesc = tc::idesc_f16(128, N, bf16, a_mn, b_mn);
         for (int k = 0; k < K; k += 16) {
-            const uint64_t da = a_mn ? tc::sdesc(tc::smem_u32(sa) + (k >> 3) * 128, 128, K * 16)
-                                     : tc::sdesc(tc::smem_u32(sa) + (k >> 3) * 2048, 2048, 128);
-            const uint64_t db = b_mn ? tc::sdesc(tc::smem_u32(sb) + (k >> 3) * 128, 128, K * 16)
-                                     : tc::sdesc(tc::smem_u32(sb) + (k >> 3) * (N * 16), N * 16, 128);
+            // (leading, stride) byte offsets: K-direction and M/N-direction core-matrix steps
+            uint32_t la = a_mn ? 128u : 2048u, sa_ = a_mn ? (uint32_t)K * 16 : 128u;
+            uint32_t lb = b_mn ? 128u : (uint32_t)N * 16, sb_ = b_mn ? (uint32_t)K * 16 : 128u;
+            if (swap) {
+                uint32_t t = la; la = sa_; sa_ = t;
+                t = lb; lb = sb_; sb_ = t;
+            }
+            const uint64_t da = tc::sdesc(tc::smem_u32(sa) + adj_a + (k >> 3) * (a_mn ? 128 : 2048), la, sa_);
+            const uint64_t db = tc::sdesc(tc::smem_u32(sb) + adj_b + (k >> 3) * (b_mn ? 128 : N * 16), lb, sb_);
             tc::mma_f16(tmem, da, db, idesc, k > 0 ? 1u : 0u);
         }
         tc::mma_commit(tc::smem_u32(&s_mbar));
@@ -55,7 +67,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
     const bool ok = tc::mbar_wait(tc::smem_u32(&s_mbar), 0, 200000000ll);
     if (!ok && tid == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
     tc::fence_after_sync();
-    if (ok) {
+    if (ok && !(flags & 16)) {
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c = 0; c < N; c += 32) {
             uint32_t v[32];
@@ -77,17 +89,18 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
 using namespace svlf;
 
 extern "C" int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
-                                 int a_mn_major, int b_mn_major, int bf16, void *stream) {
+                                 int a_mn_major, int b_mn_major, int bf16, int flags,
+                                 void *stream) {
     if (!A || !B || !D || N < 32 || N > 256 || N % 32 || K < 16 || K > 256 || K % 16)
         return SVLF_ERR_ARG;
     // Generous on purpose: every read the descriptors can address stays inside
     // the allocation even if a layout were misread.
-    const size_t need = (size_t)(128 + N) * K * 2 + 128;
+    const size_t need = (size_t)(128 + N) * K * 2 + ((flags >> 8) & 0xFFFF) + 128;
     const size_t smem = need > 200 * 1024 ? need : 200 * 1024;
     if (cudaFuncSetAttribute(mma_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     mma_selftest_kernel<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, N, K, a_mn_major,
-                                                                 b_mn_major, bf16);
+                                                                 b_mn_major, bf16, flags);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

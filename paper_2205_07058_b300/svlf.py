@@ -80,7 +80,7 @@ def lib():
     L.svlf_loss.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp, vp, vp]
     L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
     L.svlf_get_device_status.argtypes = [P(i32)]
-    L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp]
+    L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]
     L.svlf_status_string.argtypes = [i32]
     L.svlf_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -243,12 +243,13 @@ def svlf_adam_step(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.9
                                                   _ptr(bf16_shadow), _stream(stream)))
 
 
-def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_major=False, stream=None):
+def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_major=False, flags=0,
+                      stream=None):
     """D = A @ B.T (A: 128 x K, B: N x K, bf16 or fp16) through one tcgen05 tile."""
     D = torch.empty((128, B.shape[0]), dtype=torch.float32, device="cuda")
     _check("svlf_selftest_mma", lib().svlf_selftest_mma(
         _ptr(A), _ptr(B), _ptr(D), B.shape[0], A.shape[1], int(a_mn_major), int(b_mn_major),
-        int(A.dtype == torch.bfloat16), _stream(stream)))
+        int(A.dtype == torch.bfloat16), int(flags), _stream(stream)))
     return D
 
 
