@@ -1,0 +1,532 @@
+#!/usr/bin/env python
+"""Benchmark of the SVLF hot path on one B300 (or N replicas under torchrun).
+
+One step = one render pass over 4 views of 1600 x 1600 rays (10.24 M rays) of
+the depth-9 union-of-primitives scene (1.69 M leaves, features 32 x fp32,
+network 41 -> 3 x 128 -> 4, K = 8), plus one training step on a batch of
+2^18 rays drawn from 100 views of 800 x 800 of the same scene (render with
+the hits saved, L2 colour + 0.1 L1 depth loss, backward with recomputation,
+Adam over every feature and network parameter). Every rays/s figure counts
+render rays plus training rays.
+
+Prints one JSON line (see README of the driver contract in the design doc).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+RENDER_VIEWS = 4
+RENDER_RES = 1600
+TRAIN_VIEWS = 100
+TRAIN_RES = 800
+TRAIN_BATCH = 1 << 18
+K_HITS = 8
+FEAT, HIDDEN, N_HIDDEN = 32, 128, 3
+SCENE_SEED = 1002
+TEACHER_SEED = 2000
+LR = 1e-3
+DEPTH_WEIGHT = 0.1
+WORKLOAD = ("render 4x1600^2 + train 2^18 rays (100 views of 800^2); depth-9 octree over 64 "
+            "spheres + 32 box shells (1.69 M leaves), F=32 fp32, MLP 41->3x128->4, K=8")
+
+
+def flops_per_sample(feat=FEAT, hidden=HIDDEN, n_hidden=N_HIDDEN):
+    d_in = feat + 9
+    return 2 * (d_in * hidden + (n_hidden - 1) * hidden * hidden + 4 * hidden)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--views", type=int, default=RENDER_VIEWS)
+    p.add_argument("--res", type=int, default=RENDER_RES)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def make_workload(rank: int, views: int, res: int):
+    from paper_2205_07058_b300 import inputs as I
+    rng = np.random.default_rng(SCENE_SEED)
+    scene = I.make_scene(rng, 9, 64, 32)
+    shape = I.MLPShape(FEAT, HIDDEN, N_HIDDEN)
+    feats = I.make_features(rng, scene.n_leaves, FEAT)
+    params = I.make_mlp(rng, shape)
+    az, el = I.random_view_angles(rng, views)
+    if rank > 0:  # replicas render their own views of the same scene
+        az, el = I.random_view_angles(np.random.default_rng(SCENE_SEED + 7919 * rank), views)
+    render_rays = np.concatenate([I.pinhole_rays(az[v], el[v], res, res) for v in range(views)])
+    trng = np.random.default_rng(SCENE_SEED + 1 + 7919 * rank)
+    taz, tel = I.random_view_angles(trng, TRAIN_VIEWS)
+    train_rays = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel)
+    depth_t, mask = I.analytic_depth(train_rays, scene)
+    teacher = I.make_mlp(np.random.default_rng(TEACHER_SEED), shape)
+    return dict(scene=scene, shape=shape, feats=feats, params=params, render_rays=render_rays,
+                train_rays=train_rays, depth_t=depth_t, mask=mask, teacher=teacher)
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+def kernel_source_hash(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2205_07058_b300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "mlp_forward_tc": ["mlp_tc.cu", "tc_common.cuh", "mlp_common.cuh", "svlf_internal.cuh"],
+    "mlp_backward_tc": ["mlp_tc.cu", "tc_common.cuh", "mlp_common.cuh", "svlf_internal.cuh"],
+    "trace": ["trace.cu", "svlf_internal.cuh"],
+    "adam": ["adam.cu"],
+    "composite": ["composite.cu"],
+    "mlp_forward_f32": ["mlp_simt.cu", "mlp_common.cuh", "svlf_internal.cuh"],
+    "mlp_backward_f32": ["mlp_simt.cu", "mlp_common.cuh", "svlf_internal.cuh"],
+}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per unit for `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    ent = tab.get(kernel)
+    if not ent or kernel not in KERNEL_SOURCES:
+        return None
+    if ent.get("source_hash") != kernel_source_hash(KERNEL_SOURCES[kernel]):
+        return None
+    return ent
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2205_07058_b300 import svlf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=dev)
+        dist = dist_mod
+
+    W = make_workload(rank, args.views, args.res)
+    prec = svlf.PRECISIONS[args.precision]
+    tprec = svlf.PRECISIONS[args.train_precision or args.precision]
+    net = svlf.Network(FEAT, HIDDEN, N_HIDDEN, prec)
+    tnet = svlf.Network(FEAT, HIDDEN, N_HIDDEN, tprec)
+    scene = W["scene"]
+    tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), scene.depth)
+    feats = torch.from_numpy(W["feats"]).to(dev)
+    params = torch.from_numpy(W["params"]).to(dev)
+    rays = torch.from_numpy(W["render_rays"]).to(dev)
+    trays = torch.from_numpy(W["train_rays"]).to(dev)
+    N, NT = rays.shape[0], trays.shape[0]
+    # targets: the teacher network rendered through the FP32 path, analytic depth
+    teacher = torch.from_numpy(W["teacher"]).to(dev)
+    rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats, teacher, svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32),
+                                              trays, K_HITS)
+    depth_t = torch.from_numpy(W["depth_t"]).to(dev)
+    mask = torch.from_numpy(W["mask"]).to(dev)
+    del teacher
+
+    ws_r = svlf.alloc_workspace(net, N, K_HITS)
+    ws_t = svlf.alloc_workspace(tnet, NT, K_HITS)
+    rgb = torch.empty((N, 3), device=dev)
+    depth = torch.empty((N,), device=dev)
+    trgb = torch.empty((NT, 3), device=dev)
+    tdepth = torch.empty((NT,), device=dev)
+    d_rgb = torch.empty_like(trgb)
+    d_depth = torch.empty_like(tdepth)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g_feat = torch.zeros_like(feats)
+    g_par = torch.zeros_like(params)
+    m_feat, v_feat = torch.zeros_like(feats), torch.zeros_like(feats)
+    m_par, v_par = torch.zeros_like(params), torch.zeros_like(params)
+    stream = torch.cuda.current_stream()
+    step_no = [0]
+    ev = {}
+
+    def render_phase():
+        svlf.svlf_render_rays(tree, feats, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
+
+    def train_phase():
+        step_no[0] += 1
+        g_feat.zero_()
+        g_par.zero_()
+        loss.zero_()
+        svlf.svlf_render_rays(tree, feats, params, tnet, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
+        svlf.svlf_loss(trgb, tdepth, rgb_t, depth_t, mask, DEPTH_WEIGHT, d_rgb, d_depth, loss)
+        svlf.svlf_render_rays_backward(tree, feats, params, tnet, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb,
+                                       d_depth, g_feat, g_par, ws_t)
+        svlf.svlf_adam_step(feats, g_feat, m_feat, v_feat, step_no[0], lr=LR)
+        svlf.svlf_adam_step(params, g_par, m_par, v_par, step_no[0], lr=LR)
+
+    def step(record=None):
+        if record is not None:
+            record.append(torch.cuda.Event(enable_timing=True))
+            record[-1].record(stream)
+        render_phase()
+        if record is not None:
+            record.append(torch.cuda.Event(enable_timing=True))
+            record[-1].record(stream)
+        train_phase()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
+    n_samples_train = svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
+    loss_first = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-timed region
+    svlf.svlf_profile_enable(True)
+    svlf.svlf_profile_report()  # clear
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    marks = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(marks)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    kstats = svlf.svlf_profile_report()
+    svlf.svlf_profile_enable(False)
+    total_ms = e0.elapsed_time(e1)
+    render_ms = sum(marks[2 * i].elapsed_time(marks[2 * i + 1]) for i in range(args.steps))
+    train_ms = total_ms - render_ms
+    status = svlf.svlf_get_device_status()
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    rays_per_step = N + NT
+    value = rays_per_step * world * args.steps / (t_max / 1e3)
+
+    # ---- end-to-end through host buffers (H2D of the step's inputs, D2H of its results)
+    e2e = None
+    if not args.no_e2e:
+        h_rays = torch.from_numpy(W["render_rays"]).pin_memory()
+        h_trays = torch.from_numpy(W["train_rays"]).pin_memory()
+        h_tgt = torch.cat([rgb_t.cpu(), depth_t.cpu()[:, None], mask.cpu()[:, None]], dim=1).contiguous().pin_memory()
+        d_tgt = torch.empty(h_tgt.shape, device=dev)
+        h_rgb = torch.empty((N, 3)).pin_memory()
+        h_depth = torch.empty((N,)).pin_memory()
+        h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = h_rays.numel() * 4 + h_trays.numel() * 4 + h_tgt.numel() * 4
+        d2h = h_rgb.numel() * 4 + h_depth.numel() * 4 + 8
+
+        def e2e_step():
+            rays.copy_(h_rays, non_blocking=True)
+            trays.copy_(h_trays, non_blocking=True)
+            d_tgt.copy_(h_tgt, non_blocking=True)
+            rgb_t.copy_(d_tgt[:, :3])
+            depth_t.copy_(d_tgt[:, 3])
+            mask.copy_(d_tgt[:, 4])
+            step()
+            h_rgb.copy_(rgb, non_blocking=True)
+            h_depth.copy_(depth, non_blocking=True)
+            h_loss.copy_(loss, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = a.elapsed_time(b)
+        if dist is not None:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": rays_per_step * world * args.steps / (te / 1e3), "unit": "rays/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    fps = flops_per_sample()
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / max(1e-9, sum(x[1] for x in kstats.values())), 4)}
+                  for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+    roof = None
+    if dom:
+        launches, ms = kstats[dom]
+        avg_s = ms / launches / 1e3
+        S_r, S_t = n_samples_render, n_samples_train
+        if dom == "mlp_forward_tc":
+            # one launch per render and one per training forward, alternating
+            work = (S_r + S_t) * fps / 2.0
+            bound, unit = "tensor", "TFLOP/s"
+            peak = peaks.get("bf16_tflops_sustained", 1400.0)
+            achieved = work / avg_s / 1e12
+        elif dom == "mlp_backward_tc":
+            work = S_t * 3.0 * fps
+            bound, unit = "tensor", "TFLOP/s"
+            peak = peaks.get("bf16_tflops_sustained", 1400.0)
+            achieved = work / avg_s / 1e12
+        elif dom in ("mlp_forward_f32", "mlp_backward_f32"):
+            mult = 1.0 if dom == "mlp_forward_f32" else 3.0
+            work = ((S_r + S_t) / 2.0 if dom == "mlp_forward_f32" else S_t) * mult * fps
+            bound, unit = "alu", "TFLOP/s"
+            peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+            achieved = work / avg_s / 1e12
+        elif dom == "adam":
+            n_par = feats.numel() + params.numel()
+            work = n_par * 28.0 / 2.0  # two launches per step (features, network)
+            bound, unit = "hbm", "GB/s"
+            peak = peaks["hbm_gbs"]
+            achieved = work / avg_s / 1e9
+        else:  # trace / composite: bytes of their own inputs and outputs
+            work = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0
+            bound, unit = "hbm", "GB/s"
+            peak = peaks["hbm_gbs"]
+            achieved = work / avg_s / 1e9
+        tr = ncu_traffic(dom)
+        roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+                "peak_source": f"{peak_src} ({'sustained' if bound == 'tensor' else 'copy'})",
+                "unit": unit, "frac": round(achieved / peak, 4),
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "avg_launch_ms": round(ms / launches, 4)}
+
+    gpu_launches = int(sum(v[0] for v in kstats.values()))
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each",
+            "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic (seeded sphere/box-shell scene, pinhole views; stands in for RTMV)",
+            "config": {"workload": WORKLOAD, "render_rays": N, "train_rays": NT, "K": K_HITS,
+                       "network_precision": args.precision, "train_precision": args.train_precision or args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (features 216 MB + rays 246 MB per step)"},
+            "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
+            "train_rays_per_s": round(NT * args.steps / (train_ms / 1e3), 1),
+            "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
+            "samples_per_step": {"render": n_samples_render, "train": n_samples_train},
+            "e2e": e2e, "gpu_launches": gpu_launches, "kernels": per_kernel,
+            "roofline": roof, "clocks": clk, "device_status": status,
+        }
+    if dist is not None:
+        dist.destroy_process_group()
+    return out, W
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ----------------------------------------------------------------------------
+ORACLE_RENDER_SAMPLE = 4096
+ORACLE_TRAIN_SAMPLE = 128
+
+
+def oracle_step(W, tree_o, rng, adam_state):
+    """One bounded-sample step of the workload through the FP64 oracle:
+    render ORACLE_RENDER_SAMPLE rays, then a training step on
+    ORACLE_TRAIN_SAMPLE rays with Adam over every parameter."""
+    from oracle import oracle as O
+    dims = O.layer_dims(FEAT, HIDDEN, N_HIDDEN)
+    rr = W["render_rays"][rng.choice(W["render_rays"].shape[0], ORACLE_RENDER_SAMPLE, replace=False)]
+    O.render(tree_o, W["feats"], W["params"], dims, rr, K_HITS)
+    sel = rng.choice(W["train_rays"].shape[0], ORACLE_TRAIN_SAMPLE, replace=False)
+    tr = W["train_rays"][sel]
+    teach = O.render(tree_o, W["feats"], W["teacher"], dims, tr, K_HITS)
+    r = O.render(tree_o, W["feats"], W["params"], dims, tr, K_HITS, hits=teach.hits)
+    O.loss(r.rgb, r.depth, teach.rgb, W["depth_t"][sel], W["mask"][sel])
+    dfeat, dpar, _, _ = O.backward(tree_o, r, W["params"], dims, teach.rgb, W["depth_t"][sel].astype(np.float64),
+                                   W["mask"][sel].astype(np.float64), (0, 0, 0), tree_o.n_leaves, FEAT)
+    adam_state["t"] += 1
+    t = adam_state["t"]
+    adam_state["pf"], adam_state["mf"], adam_state["vf"] = O.adam(adam_state["pf"], dfeat.reshape(-1), adam_state["mf"], adam_state["vf"], t)
+    adam_state["pp"], adam_state["mp"], adam_state["vp"] = O.adam(adam_state["pp"], dpar, adam_state["mp"], adam_state["vp"], t)
+    return ORACLE_RENDER_SAMPLE + ORACLE_TRAIN_SAMPLE
+
+
+def oracle_setup(W):
+    from oracle import oracle as O
+    tree_o = O.build_octree(W["scene"].leaf_ijk, W["scene"].depth)
+    n_f = W["feats"].size
+    st = {"t": 0, "pf": W["feats"].reshape(-1).astype(np.float64), "mf": np.zeros(n_f), "vf": np.zeros(n_f),
+          "pp": W["params"].astype(np.float64), "mp": np.zeros(W["params"].size), "vp": np.zeros(W["params"].size)}
+    return tree_o, st
+
+
+def cpu_sample_desc():
+    return (f"{ORACLE_RENDER_SAMPLE} random render rays + a training step on {ORACLE_TRAIN_SAMPLE} random "
+            f"training rays (teacher targets from the oracle) with Adam over all 54 M parameters, per step")
+
+
+def cpu_baseline(W, steps=2):
+    from oracle import oracle as O
+    tree_o, st = oracle_setup(W)
+    rng = np.random.default_rng(12345)
+    oracle_step(W, tree_o, rng, st)
+    t0 = time.perf_counter()
+    rays = 0
+    for _ in range(steps):
+        rays += oracle_step(W, tree_o, rng, st)
+    dt = time.perf_counter() - t0
+    return {"value": round(rays / dt, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": cpu_sample_desc() + f"; {steps} steps timed after 1 untimed"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    W = make_workload(0, args.views, args.res)
+    tree_o, st = oracle_setup(W)
+    rng = np.random.default_rng(12345)
+    for _ in range(args.warmup):
+        oracle_step(W, tree_o, rng, st)
+    t0 = time.perf_counter()
+    rays = 0
+    for _ in range(args.steps):
+        rays += oracle_step(W, tree_o, rng, st)
+    dt = time.perf_counter() - t0
+    v = rays / dt
+    return {"impl": "reference",
+            "metric": "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each",
+            "value": round(v, 2), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample per step, see cpu_baseline.sample)"},
+            "cpu_baseline": {"value": round(v, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
+                             "sample": cpu_sample_desc()},
+            "e2e": {"value": round(v, 2), "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, W = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(W)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

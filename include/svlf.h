@@ -172,6 +172,26 @@ int svlf_get_device_status(int *status);
 
 const char *svlf_status_string(int status);
 
+/* ------------------------------------------------------------ measurement */
+/* Per-kernel timing (measurement aid, not part of the method). When enabled,
+ * every kernel the library launches is bracketed by CUDA events on its own
+ * launch stream. svlf_profile_report() synchronises the device, writes up to
+ * max_entries per-kernel sums into `out` (host), the number of distinct
+ * kernels into *n_entries, and clears the record. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} svlf_kernel_stat;
+
+int svlf_profile_enable(int on);
+int svlf_profile_report(svlf_kernel_stat *out, int max_entries, int *n_entries);
+
+/* Number of (ray, hit) samples the last render left in `workspace` (device
+ * counter copied to *n_samples on the host; synchronises `stream`). */
+int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc *mlp, int64_t n_rays, int K,
+                           int64_t *n_samples, void *stream);
+
 /* ------------------------------------------------------------ self-test */
 /* Test aid, not part of the rendering method: D = A B^T for one tile through
  * the tensor cores, with the operands staged in the shared-memory layouts the

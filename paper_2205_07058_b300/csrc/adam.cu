@@ -38,8 +38,10 @@ extern "C" int svlf_adam_step(float *params, const float *grads, float *m, float
     int64_t blocks = (n + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
+    prof_begin("adam", (cudaStream_t)stream);
     adam_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
         params, grads, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2,
         (__nv_bfloat16 *)bf16_shadow);
+    prof_end((cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -194,6 +194,24 @@ extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
                                   max_samples, d_features, d_mlp_params, s);
 }
 
+extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc *mlp,
+                                      int64_t n_rays, int K, int64_t *n_samples, void *stream) {
+    if (!workspace || !mlp || !n_samples || n_rays < 0 || K < 1) return SVLF_ERR_ARG;
+    if (n_rays == 0) {
+        *n_samples = 0;
+        return SVLF_OK;
+    }
+    Workspace ws = carve_workspace(const_cast<void *>(workspace), *mlp, n_rays, K);
+    unsigned int c = 0;
+    if (cudaMemcpyAsync(&c, ws.counter, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    const int64_t cap = n_rays * (int64_t)K;
+    *n_samples = (int64_t)c < cap ? (int64_t)c : cap;
+    return SVLF_OK;
+}
+
 extern "C" int svlf_get_device_status(int *status) {
     if (!status) return SVLF_ERR_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return SVLF_ERR_CUDA;

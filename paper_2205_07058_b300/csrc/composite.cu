@@ -125,15 +125,19 @@ static unsigned grid_for(int64_t n, int threads) {
 
 int launch_composite(const Workspace &ws, int64_t n_rays, const float bg[3], float *rgb,
                      float *depth, cudaStream_t s) {
+    prof_begin("composite", s);
     composite_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(ws.ray_span, ws.samples, ws.outputs,
                                                            n_rays, bg[0], bg[1], bg[2], rgb, depth);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
 int launch_composite_backward(const Workspace &ws, int64_t n_rays, const float bg[3],
                               const float *d_rgb, const float *d_depth, cudaStream_t s) {
+    prof_begin("composite_backward", s);
     composite_backward_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(
         ws.ray_span, ws.samples, ws.outputs, n_rays, bg[0], bg[1], bg[2], d_rgb, d_depth, ws.dout);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
@@ -148,7 +152,9 @@ extern "C" int svlf_loss(const float *rgb, const float *depth, const float *rgb_
     if (n <= 0 || !rgb || !depth || !rgb_target || !depth_target || !d_rgb || !d_depth ||
         !loss_accum)
         return SVLF_ERR_ARG;
+    prof_begin("loss", (cudaStream_t)stream);
     loss_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
         rgb, depth, rgb_target, depth_target, mask, n, depth_weight, d_rgb, d_depth, loss_accum);
+    prof_end((cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

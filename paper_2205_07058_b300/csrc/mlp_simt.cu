@@ -290,7 +290,9 @@ size_t packed_f32_floats(const MlpDims &md) {
 }
 
 int launch_pack_f32(const MlpDims &md, const float *params, float *packed, cudaStream_t s) {
+    prof_begin("pack_weights_f32", s);
     pack_f32_kernel<<<64, 256, 0, s>>>(md, params, packed);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
@@ -303,9 +305,11 @@ static int fwd_f32(const MlpDims &md, int depth, const void *feats, int fb, cons
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     int blocks = num_sms() * (smem <= 100 * 1024 ? 2 : 1);
+    prof_begin("mlp_forward_f32", s);
     mlp_forward_f32_kernel<H><<<blocks, 256, smem, s>>>(md, depth, feats, fb, packed, rays,
                                                         ws.samples, ws.counter, max_samples,
                                                         ws.outputs);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
@@ -336,9 +340,11 @@ static int bwd_f32(const MlpDims &md, int depth, const void *feats, int fb, cons
     if (cudaFuncSetAttribute(mlp_backward_f32_kernel<H>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
+    prof_begin("mlp_backward_f32", s);
     mlp_backward_f32_kernel<H><<<num_sms(), 256, smem, s>>>(md, depth, feats, fb, params, packed,
                                                             rays, ws.samples, ws.counter,
                                                             max_samples, ws.dout, d_feat, d_params);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 

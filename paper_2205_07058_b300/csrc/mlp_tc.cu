@@ -102,7 +102,9 @@ int launch_pack_tc(const MlpDims &md, int precision, const float *params, void *
                    cudaStream_t s) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     const TcLayout lay = tc_layout(md);
+    prof_begin("pack_weights_tc", s);
     pack_tc_kernel<<<64, 256, 0, s>>>(md, lay, precision == SVLF_FP16, params, (uint8_t *)packed);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
@@ -293,7 +295,9 @@ static int fwd_tc(const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay,
     if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
+    prof_begin("mlp_forward_tc", s);
     mlp_forward_tc_kernel<H><<<num_sms(), 128 * P.n_wg, smem, s>>>(P);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 

@@ -93,6 +93,10 @@ int launch_mlp_backward(const svlf_mlp_desc &mlp, int depth, const void *feature
 
 int num_sms();
 
+// per-kernel timing (profile.cu); no-ops unless svlf_profile_enable(1)
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+
 // ---------------------------------------------------------------- geometry
 // Ray parameterisation r = [p~1 | p~2] (Sec. 4.1): the ray's entry and exit
 // points on the minimum bounding sphere of voxel `cell`, relative to the voxel

@@ -270,9 +270,11 @@ static int launch_trace_k(const OctreeView &T, const float *rays, int64_t n_rays
     const int64_t cap = (int64_t)num_sms() * 6;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    prof_begin("trace", s);
     trace_kernel<K><<<(unsigned)blocks, threads, smem, s>>>(T, rays, n_rays, ws.samples,
                                                             ws.ray_span, ws.counter, max_samples,
                                                             hits, t_io);
+    prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 

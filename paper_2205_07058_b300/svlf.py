@@ -49,10 +49,15 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 EXPORTS = [
     "svlf_build_octree", "svlf_octree_leaf_ijk", "svlf_octree_info", "svlf_free_octree",
     "svlf_workspace_size", "svlf_render_rays", "svlf_render_rays_backward", "svlf_loss",
     "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma",
+    "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
 ]
 
 _lib = None
@@ -81,6 +86,9 @@ def lib():
     L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
     L.svlf_get_device_status.argtypes = [P(i32)]
     L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]
+    L.svlf_profile_enable.argtypes = [i32]
+    L.svlf_profile_report.argtypes = [P(KernelStat), i32, P(i32)]
+    L.svlf_workspace_samples.argtypes = [vp, P(MlpDesc), i64, i32, P(i64), vp]
     L.svlf_status_string.argtypes = [i32]
     L.svlf_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -251,6 +259,27 @@ def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_m
         _ptr(A), _ptr(B), _ptr(D), B.shape[0], A.shape[1], int(a_mn_major), int(b_mn_major),
         int(A.dtype == torch.bfloat16), int(flags), _stream(stream)))
     return D
+
+
+def svlf_profile_enable(on: bool = True):
+    _check("svlf_profile_enable", lib().svlf_profile_enable(int(on)))
+
+
+def svlf_profile_report() -> dict:
+    """{kernel name: (launches, total ms)} since the last report (synchronises)."""
+    arr = (KernelStat * 64)()
+    n = ctypes.c_int()
+    _check("svlf_profile_report", lib().svlf_profile_report(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def svlf_workspace_samples(workspace: torch.Tensor, net: Network, n_rays: int, K: int, stream=None) -> int:
+    d = net.desc()
+    wp, _ = _ws_ptr(workspace)
+    n = ctypes.c_int64()
+    _check("svlf_workspace_samples", lib().svlf_workspace_samples(wp, ctypes.byref(d), int(n_rays), int(K),
+                                                                   ctypes.byref(n), _stream(stream)))
+    return int(n.value)
 
 
 def svlf_get_device_status() -> int:
