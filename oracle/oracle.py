@@ -197,6 +197,21 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def fp16_round(x: np.ndarray) -> np.ndarray:
+    """Round float64 values to the nearest IEEE half (ties to even)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def _rounder(lowp):
+    if lowp in (None, False):
+        return None
+    if lowp in (True, "bf16"):
+        return bf16_round
+    if lowp == "fp16":
+        return fp16_round
+    raise ValueError(lowp)
+
+
 def split_params(flat: np.ndarray, dims: Sequence[Tuple[int, int]]):
     out, off = [], 0
     flat = np.asarray(flat, dtype=np.float64)
@@ -214,16 +229,18 @@ def layer_dims(feat_dim: int, hidden: int, n_hidden: int, out_dim: int = 4):
     return [(dims[i + 1], dims[i]) for i in range(len(dims) - 1)]
 
 
-def mlp_forward(h0: np.ndarray, layers, bf16: bool = False):
+def mlp_forward(h0: np.ndarray, layers, bf16=False):
     """Returns (inputs of every layer, pre-activations of every layer).
-    Hidden layers are ReLU; the last layer is linear. With bf16=True each
-    layer's input activations and weights are rounded to bfloat16 first and
-    the products and sums stay in float64 (the biases are not rounded)."""
+    Hidden layers are ReLU; the last layer is linear. With bf16 = True/"bf16"
+    (or "fp16") each layer's input activations and weights are rounded to that
+    16-bit format first and the products and sums stay in float64 (the biases
+    are not rounded)."""
+    rnd = _rounder(bf16)
     xs, pres = [], []
     x = h0
     for li, (W, b) in enumerate(layers):
-        xin = bf16_round(x) if bf16 else x
-        Wl = bf16_round(W) if bf16 else W
+        xin = rnd(x) if rnd else x
+        Wl = rnd(W) if rnd else W
         pre = xin @ Wl.T + b
         xs.append(x)
         pres.append(pre)
@@ -291,7 +308,7 @@ def composite(N: int, K: int, ray_of, slot, colour, tau, tmid, bg):
 
 
 def render(tree: Octree, features: np.ndarray, params: np.ndarray, dims, rays: np.ndarray,
-           K: int, bg=(0.0, 0.0, 0.0), bf16: bool = False, hits: Optional[Hits] = None,
+           K: int, bg=(0.0, 0.0, 0.0), bf16=False, hits: Optional[Hits] = None,
            feat_bf16_storage: bool = False) -> Render:
     rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
     N = rays.shape[0]
@@ -322,7 +339,7 @@ def loss(rgb, depth, rgb_t, depth_t, mask) -> float:
 
 
 def backward(tree: Octree, r: Render, params: np.ndarray, dims, rgb_t, depth_t, mask, bg,
-             n_leaves: int, feat_dim: int, bf16: bool = False):
+             n_leaves: int, feat_dim: int, bf16=False):
     """Hand-derived adjoint of loss(render(...)). Returns (dL/dfeatures (dense,
     n_leaves x F), dL/dparams (flat, same layout as params), dC, dD)."""
     N, K = r.hits.rank.shape
@@ -354,13 +371,14 @@ def backward(tree: Octree, r: Render, params: np.ndarray, dims, rgb_t, depth_t, 
     dout[:, :3] = dcol[r.ray_of, r.slot] * r.colour * (1.0 - r.colour)
     dout[:, 3] = dtau[r.ray_of, r.slot] * (r.out[:, 3] > 0)
     # through the network
+    rnd = _rounder(bf16)
     layers = split_params(params, dims)
     grads = []
     delta = dout
     for li in range(len(layers) - 1, -1, -1):
         W, b = layers[li]
-        xin = bf16_round(r.xs[li]) if bf16 else r.xs[li]
-        Wl = bf16_round(W) if bf16 else W
+        xin = rnd(r.xs[li]) if rnd else r.xs[li]
+        Wl = rnd(W) if rnd else W
         dW = delta.T @ xin
         db = delta.sum(axis=0)
         grads.append((dW, db))

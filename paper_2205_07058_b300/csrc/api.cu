@@ -183,6 +183,7 @@ extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
     Workspace ws = carve_workspace(workspace, *mlp, n_rays, K);
     const MlpDims md = make_dims(*mlp);
     const OctreeView &T = octree_view(tree);
+    if (cudaMemsetAsync(ws.counter + 3, 0, sizeof(unsigned int), s) != cudaSuccess) return SVLF_ERR_CUDA;
     if ((rc = launch_composite_backward(ws, n_rays, opts->bg, d_rgb, d_depth, s))) return rc;
     const int64_t max_samples = n_rays * (int64_t)K;
     const int fb = mlp->feat_dtype == SVLF_FEAT_BF16;

@@ -47,7 +47,9 @@ __global__ void composite_backward_kernel(const int2 *__restrict__ ray_span,
                                           float bg0, float bg1, float bg2,
                                           const float *__restrict__ d_rgb,
                                           const float *__restrict__ d_depth,
-                                          float4 *__restrict__ dout) {
+                                          float4 *__restrict__ dout,
+                                          unsigned int *__restrict__ max_abs_bits) {
+    float gmax = 0.f;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rays;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int2 sp = ray_span[r];
@@ -73,6 +75,7 @@ __global__ void composite_backward_kernel(const int2 *__restrict__ ray_span,
             g.z = w * g2 * o.z * (1.f - o.z);
             g.w = o.w > 0.f ? dtau : 0.f;
             dout[sp.x + j] = g;
+            gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(g.x), fabsf(g.y)), fmaxf(fabsf(g.z), fabsf(g.w))));
             S0 = fmaf(w, o.x, S0);
             S1 = fmaf(w, o.y, S1);
             S2 = fmaf(w, o.z, S2);
@@ -80,6 +83,10 @@ __global__ void composite_backward_kernel(const int2 *__restrict__ ray_span,
             Q += o.w;
         }
     }
+    // largest |dL/d(network output)| of the launch (non-negative float bits
+    // order like unsigned integers); the FP16 backward scales by it
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xFFFFFFFFu, gmax, o));
+    if ((threadIdx.x & 31) == 0 && gmax > 0.f) atomicMax(max_abs_bits, __float_as_uint(gmax));
 }
 
 // L = (1/n) sum_r [ |C - C*|^2 + lambda m |D - D*| ]
@@ -136,7 +143,8 @@ int launch_composite_backward(const Workspace &ws, int64_t n_rays, const float b
                               const float *d_rgb, const float *d_depth, cudaStream_t s) {
     prof_begin("composite_backward", s);
     composite_backward_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(
-        ws.ray_span, ws.samples, ws.outputs, n_rays, bg[0], bg[1], bg[2], d_rgb, d_depth, ws.dout);
+        ws.ray_span, ws.samples, ws.outputs, n_rays, bg[0], bg[1], bg[2], d_rgb, d_depth, ws.dout,
+        ws.counter + 3);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -28,6 +28,7 @@ namespace svlf {
 
 constexpr int kTcTile = 128;     // samples per tile (MMA M)
 constexpr int kTcOutN = 16;      // output layer width padded to the smallest legal N
+constexpr int kHp = 128;         // hidden width inside the tensor-core path (zero-padded)
 
 struct TcLayout {
     int K0;                      // first-layer K, in0 rounded up to 16
@@ -47,8 +48,8 @@ static TcLayout tc_layout(const MlpDims &md) {
     t.n_layers = md.nh + 1;
     uint32_t off = 0;
     for (int l = 0; l <= md.nh; ++l) {
-        t.w_rows[l] = l == md.nh ? kTcOutN : md.H;
-        t.w_cols[l] = l == 0 ? t.K0 : md.H;
+        t.w_rows[l] = l == md.nh ? kTcOutN : kHp;
+        t.w_cols[l] = l == 0 ? t.K0 : kHp;
         t.w_off[l] = off;
         off += t.w_rows[l] * t.w_cols[l] * 2;
     }
@@ -64,7 +65,7 @@ static TcLayout tc_layout(const MlpDims &md) {
 }
 
 bool tc_supported(const MlpDims &md) {
-    return (md.H == 64 || md.H == 128) && md.in0 <= 80 && md.nh >= 1 && md.nh <= 6;
+    return md.H <= kHp && md.H % 16 == 0 && md.in0 <= 80 && md.nh >= 1 && md.nh <= 6;
 }
 
 size_t packed_tc_bytes(const MlpDims &md) {
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParam
 
 static int tc_forward_config(const MlpDims &md, const TcLayout &lay, int &n_wg, uint32_t &abuf,
                              size_t &smem) {
-    const int kmax = lay.K0 > md.H ? lay.K0 : md.H;
+    const int kmax = lay.K0 > kHp ? lay.K0 : kHp;
     abuf = (uint32_t)(kTcTile * kmax * 2);
     const size_t limit = 227 * 1024 - 256;
     for (n_wg = 4; n_wg >= 1; --n_wg) {
@@ -321,14 +322,434 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int depth, const voi
     P.counter = ws.counter;
     P.max_samples = max_samples;
     P.outputs = ws.outputs;
-    if (md.H == 64) return fwd_tc<64>(P, md, P.lay, s, g_tc_wg_override);
-    return fwd_tc<128>(P, md, P.lay, s, g_tc_wg_override);
+    return fwd_tc<kHp>(P, md, P.lay, s, g_tc_wg_override);
 }
 
-int launch_mlp_backward_tc(const MlpDims &, int, int, const void *, int, const void *,
-                           const float *, const Workspace &, int64_t, float *, float *,
-                           cudaStream_t) {
-    return SVLF_ERR_UNSUPPORTED;
+// ---------------------------------------------------------------- backward
+// Backward kernel (persistent, one warpgroup per CTA, one CTA per SM). Per
+// tile of 128 samples (thread t = sample t = TMEM lane t):
+//  1. network input X_0 and dL/d(output) G_out (from the compositing
+//     backward) are written as 16-bit A operands;
+//  2. the forward is recomputed layer by layer, keeping every layer's input
+//     X_l in shared memory (activations are recomputed, never stored in HBM);
+//  3. from the output down, per layer one commit group of MMAs:
+//       dW_l  += G_{l+1}^T X_l     (M = out features, N = in features, K = 128
+//                                   samples; both operands read MN-major)
+//       db_l  += G_{l+1}^T 1       (the same with a block of ones, N = 16)
+//       G_l    = G_{l+1} W_l       (M = samples, N = in features, K = out;
+//                                   W_l read MN-major from the forward image)
+//     and the epilogue masks G_l with the ReLU pattern X_l > 0 in place of X_l;
+//     for layer 0 only the first F columns of G_0 (dL/dz) are formed and
+//     scattered to the feature gradient, one float4 atomic group per distinct
+//     leaf in a warp (warp-aggregated).
+//  dW and db stay in TMEM across all tiles of the CTA and are added to the
+//  global gradient once at the end.
+//  With float16 operands the deltas are scaled by a power of two chosen from
+//  the largest |dL/d(output)| of the launch (so that they stay clear of the
+//  float16 underflow range), and every gradient is unscaled in float32 before
+//  it leaves the kernel. bfloat16 has float32's exponent range and is not
+//  scaled.
+struct TcBwdParams {
+    MlpDims md;
+    TcLayout lay;
+    int depth, fp16, feat_bf16;
+    const void *feats;
+    const uint8_t *image;
+    const float *rays;
+    const Sample *samples;
+    const unsigned int *counter;
+    int64_t max_samples;
+    const float4 *dout;
+    float *d_feat;
+    float *d_params;
+    uint32_t x_off[kMaxLayers];  // X_l buffers (byte offsets after the weight image)
+    uint32_t gout_off, ones_off;
+    uint32_t col_dwout, col_dw[kMaxLayers], col_db[kMaxLayers], tmem_cols;
+};
+
+static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
+    const TcLayout &lay = P.lay;
+    uint32_t off = lay.bytes;
+    P.x_off[0] = off;
+    off += kTcTile * lay.K0 * 2;
+    for (int l = 1; l <= md.nh; ++l) {
+        P.x_off[l] = off;
+        off += kTcTile * kHp * 2;
+    }
+    P.gout_off = off;
+    off += kTcTile * kTcOutN * 2;
+    P.ones_off = off;
+    off += kTcOutN * kTcTile * 2;
+    smem = off + 128;
+    // TMEM columns: [0, 128) work accumulator, then the 128-wide dW_l (l >= 1)
+    // at multiples of 128, dW_0 (K0 wide), and the 16-wide dW_out^T and db_l.
+    uint32_t col = kHp;
+    for (int l = 1; l < md.nh; ++l) {
+        P.col_dw[l] = col;
+        col += kHp;
+    }
+    P.col_dw[0] = col;
+    col += lay.K0;
+    P.col_dwout = col;
+    col += kTcOutN;
+    for (int l = 0; l < md.nh; ++l) {
+        P.col_db[l] = col;
+        col += 16;
+    }
+    if (col > 512 || smem > 227 * 1024) return false;
+    uint32_t n = 32;
+    while (n < col) n <<= 1;
+    P.tmem_cols = n;
+    return true;
+}
+
+__device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32_t a_kstep,
+                                        uint32_t a_lbo, uint32_t a_sbo, uint32_t b_base,
+                                        uint32_t b_kstep, uint32_t b_lbo, uint32_t b_sbo, int K,
+                                        uint32_t idesc, bool accumulate) {
+    for (int k = 0; k < K; k += 16) {
+        const uint64_t da = tc::sdesc(a_base + (uint32_t)(k >> 4) * a_kstep, a_lbo, a_sbo);
+        const uint64_t db = tc::sdesc(b_base + (uint32_t)(k >> 4) * b_kstep, b_lbo, b_sbo);
+        tc::mma_f16(tmem_d, da, db, idesc, (accumulate || k > 0) ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdParams P) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t s_mbar[2];  // [0] MMA commits, [1] weight load
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_dbout[4];
+
+    const int row = threadIdx.x;  // sample within the tile = TMEM lane
+    const int warp = row >> 5, lane = row & 31;
+    const MlpDims &md = P.md;
+    const TcLayout &lay = P.lay;
+    uint8_t *wimg = smem;
+    const float *bias = reinterpret_cast<const float *>(wimg + lay.bias_off);
+    const uint32_t s_base = tc::smem_u32(smem);
+
+    if (row == 0) {
+        tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
+        tc::mbar_init_fence();
+    }
+    if (row < 4) s_dbout[row] = 0.f;
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&s_tmem), P.tmem_cols);
+        tc::tmem_relinquish();
+    }
+    // block of ones (B operand of the bias sums): every 16-bit value = 1.0
+    {
+        const uint32_t one2 = tc::pack2(1.f, 1.f, P.fp16);
+        uint4 *o = reinterpret_cast<uint4 *>(smem + P.ones_off);
+        for (int i = row; i < kTcOutN * kTcTile * 2 / 16; i += 128) o[i] = make_uint4(one2, one2, one2, one2);
+    }
+    __syncthreads();
+    if (row == 0) {
+        const uint32_t mb = tc::smem_u32(&s_mbar[1]);
+        tc::mbar_expect_tx(mb, lay.bytes);
+        for (uint32_t off = 0; off < lay.bytes; off += 32768u)
+            tc::bulk_g2s(tc::smem_u32(wimg + off), P.image + off, min(32768u, lay.bytes - off), mb);
+    }
+    bool aborted = !tc::mbar_wait(tc::smem_u32(&s_mbar[1]), 0);
+    aborted = tc::wg_sync_or(0, aborted);
+    if (aborted && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t mbar = tc::smem_u32(&s_mbar[0]);
+    const int bf16 = P.fp16 ? 0 : 1;
+    const int nh = md.nh;
+    uint32_t phase = 0;
+    int tiles_done = 0;
+
+    const int64_t S = min((int64_t)P.counter[0], P.max_samples);
+    const int64_t n_tiles = (S + kTcTile - 1) / kTcTile;
+    const int Fn = (md.F + 15) & ~15;
+    float gscale = 1.f;
+    if (P.fp16) {
+        const float gmax = __uint_as_float(P.counter[3]);
+        if (gmax > 0.f && isfinite(gmax)) {
+            int e;
+            frexpf(gmax, &e);                          // gmax in [2^(e-1), 2^e)
+            gscale = ldexpf(1.f, max(-60, min(60, 12 - e)));  // largest |delta_out| -> [2^11, 2^12)
+        }
+    }
+    const float ginv = 1.f / gscale;
+
+    // issue (by row 0) the MMAs queued by `fn`, commit, wait; returns false on timeout
+    auto run = [&](auto &&fn) -> bool {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        tc::wg_sync_or(0, false);
+        if (row == 0) {
+            tc::fence_after_sync();
+            fn();
+            tc::mma_commit(mbar);
+        }
+        const bool to = !tc::mbar_wait(mbar, phase);
+        phase ^= 1u;
+        const bool any = tc::wg_sync_or(0, to);
+        tc::fence_after_sync();
+        return !any;
+    };
+
+    for (int64_t tile = blockIdx.x; !aborted && tile < n_tiles; tile += gridDim.x) {
+        const int64_t s = tile * kTcTile + row;
+        const bool valid = s < S;
+        int leaf = -1;
+        // ---- 1. X_0 and G_out
+        {
+            float h0[kMaxIn];
+            if (valid) {
+                const Sample sm = P.samples[s];
+                leaf = sm.leaf;
+                make_input_row(md, P.depth, P.feats, P.feat_bf16, P.rays, sm, h0);
+            }
+            uint8_t *x0 = smem + P.x_off[0];
+            for (int kb = 0; kb < lay.K0 / 8; ++kb) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = kb * 8 + e;
+                    v[e] = (valid && k < md.in0) ? h0[k] : 0.f;
+                }
+                st_chunk(x0, row, kb, tc::pack2(v[0], v[1], P.fp16), tc::pack2(v[2], v[3], P.fp16),
+                         tc::pack2(v[4], v[5], P.fp16), tc::pack2(v[6], v[7], P.fp16));
+            }
+            const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            uint8_t *go = smem + P.gout_off;
+            st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
+                     tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
+            st_chunk(go, row, 1, 0u, 0u, 0u, 0u);
+            // bias gradient of the output layer: warp sums, then shared atomics
+            float gs[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float v = gs[c];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                if (lane == 0) atomicAdd(&s_dbout[c], v);
+            }
+        }
+        // ---- 2. forward recompute: X_{l+1} = relu(W_l X_l + b_l)
+        for (int l = 0; l < nh && !aborted; ++l) {
+            const int Kl = l == 0 ? lay.K0 : kHp;
+            const uint32_t xa = s_base + P.x_off[l];
+            const uint32_t wb = s_base + lay.w_off[l];
+            if (!run([&] {
+                    mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
+                            128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), false);
+                })) {
+                aborted = true;
+                break;
+            }
+            const float *b = bias + lay.bias_l[l];
+            uint8_t *xn = smem + P.x_off[l + 1];
+#pragma unroll 1
+            for (int c = 0; c < kHp / 32; ++c) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
+                tc::tmem_wait_ld();
+                uint32_t p[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    p[e] = tc::pack2(fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f),
+                                     fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f),
+                                     P.fp16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    st_chunk(xn, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+            }
+            tc::fence_before_sync();
+        }
+        if (aborted) break;
+        const bool acc = tiles_done > 0;
+        // ---- 3. output layer: dW_out^T += X_nh^T G_out ; G_nh = G_out W_out (masked)
+        {
+            const uint32_t xa = s_base + P.x_off[nh];
+            const uint32_t go = s_base + P.gout_off;
+            const uint32_t wo = s_base + lay.w_off[nh];
+            if (!run([&] {
+                    mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
+                            kTcTile, tc::idesc_f16(kHp, kTcOutN, bf16, 1, 1), acc);
+                    mma_seq(tmem, go, 0, kTcTile * 16, 128, wo, 0, 128, kTcOutN * 16, kTcOutN,
+                            tc::idesc_f16(kTcTile, kHp, bf16, 0, 1), false);
+                })) {
+                aborted = true;
+                break;
+            }
+        }
+        // masked delta of the last hidden layer, in place of X_nh
+        auto mask_epilogue = [&](int l) {
+            uint8_t *x = smem + P.x_off[l];
+#pragma unroll 1
+            for (int c = 0; c < kHp / 32; ++c) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 *ptr = reinterpret_cast<uint4 *>(x + (c * 4 + q) * (kTcTile * 16) +
+                                                           (row >> 3) * 128 + (row & 7) * 16);
+                    const uint4 xv = *ptr;
+                    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        // a 16-bit activation is positive iff its sign bit is clear and it is non-zero
+                        const uint32_t lo = xw[e] & 0xFFFFu, hi = xw[e] >> 16;
+                        const float g0 = (lo != 0u && !(lo & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e]) : 0.f;
+                        const float g1 = (hi != 0u && !(hi & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e + 1]) : 0.f;
+                        o[e] = tc::pack2(g0, g1, P.fp16);
+                    }
+                    *ptr = make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+            tc::fence_before_sync();
+        };
+        mask_epilogue(nh);
+        // ---- 4. hidden layers, from the top down
+        for (int l = nh - 1; l >= 0 && !aborted; --l) {
+            const uint32_t g = s_base + P.x_off[l + 1];  // G_{l+1} (delta of layer l's output)
+            const uint32_t xa = s_base + P.x_off[l];
+            const uint32_t wb = s_base + lay.w_off[l];
+            const int Nin = l == 0 ? lay.K0 : kHp;
+            const bool want_dx = l > 0 || P.d_feat != nullptr;
+            const int Ndx = l > 0 ? kHp : Fn;
+            if (!run([&] {
+                    // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
+                    mma_seq(tmem + P.col_dw[l], g, 256, 128, kTcTile * 16, xa, 256, 128, kTcTile * 16,
+                            kTcTile, tc::idesc_f16(kHp, Nin, bf16, 1, 1), acc);
+                    // db_l += G^T 1
+                    mma_seq(tmem + P.col_db[l], g, 256, 128, kTcTile * 16, s_base + P.ones_off,
+                            2 * kTcOutN * 16, kTcOutN * 16, 128, kTcTile,
+                            tc::idesc_f16(kHp, kTcOutN, bf16, 1, 0), acc);
+                    // G_l = G W_l  (A: G K-major, B: W_l MN-major)
+                    if (want_dx)
+                        mma_seq(tmem, g, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 256, 128, kHp * 16,
+                                kHp, tc::idesc_f16(kTcTile, Ndx, bf16, 0, 1), false);
+                })) {
+                aborted = true;
+                break;
+            }
+            if (l > 0) {
+                mask_epilogue(l);
+            } else if (P.d_feat) {
+                // dL/dz: stage rows in shared memory (X_1's buffer is free now)
+                float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
+                const int F = md.F;
+                for (int c = 0; c < Fn; c += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + lane_off + (uint32_t)c, v);
+                    tc::tmem_wait_ld();
+                    for (int e = 0; e < 16 && c + e < F; ++e) stage[row * F + c + e] = __uint_as_float(v[e]) * ginv;
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                // warp-aggregated scatter: the lowest lane of each group of equal leaves sums it
+                const unsigned act = __ballot_sync(0xFFFFFFFFu, leaf >= 0);
+                const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
+                if (leaf >= 0 && (grp & act) && lane == __ffs(grp) - 1) {
+                    float4 *dst = reinterpret_cast<float4 *>(P.d_feat + (int64_t)leaf * F);
+                    for (int f4 = 0; f4 < F / 4; ++f4) {
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                        unsigned m = grp;
+                        while (m) {
+                            const int src = (warp << 5) + __ffs(m) - 1;
+                            m &= m - 1;
+                            const float4 v = *reinterpret_cast<const float4 *>(stage + src * F + 4 * f4);
+                            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                        }
+                        atomicAdd(dst + f4, a);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        ++tiles_done;
+    }
+    // ---- flush the TMEM gradient accumulators (one atomic per element per CTA)
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!aborted && tiles_done > 0 && P.d_params) {
+        const int H = md.H;
+        // dW_out^T: lane = input feature k, columns = output j (< 4)
+        {
+            uint32_t v[16];
+            tc::tmem_ld16(tmem + lane_off + P.col_dwout, v);
+            tc::tmem_wait_ld();
+            if (row < H) {
+                float *dW = P.d_params + md.w_off[nh];
+                for (int j = 0; j < 4; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
+            }
+            if (row < 4) atomicAdd(P.d_params + md.w_off[nh] + 4 * H + row, s_dbout[row]);
+        }
+        for (int l = 0; l < nh; ++l) {
+            const int in = md.in_l[l];
+            const int ncol = l == 0 ? lay.K0 : kHp;
+            float *dW = P.d_params + md.w_off[l];
+            for (int c = 0; c < ncol; c += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
+                tc::tmem_wait_ld();
+                if (row < H)
+                    for (int e = 0; e < 16; ++e)
+                        if (c + e < in) atomicAdd(dW + row * in + c + e, __uint_as_float(v[e]) * ginv);
+            }
+            uint32_t v[4];
+            tc::tmem_ld4(tmem + lane_off + P.col_db[l], v);
+            tc::tmem_wait_ld();
+            if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, P.tmem_cols);
+    }
+}
+
+bool tc_backward_supported(const MlpDims &md) {
+    if (!tc_supported(md)) return false;
+    TcBwdParams P;
+    memset(&P, 0, sizeof(P));
+    P.lay = tc_layout(md);
+    size_t smem;
+    return tc_bwd_plan(md, P, smem);
+}
+
+int launch_mlp_backward_tc(const MlpDims &md, int precision, int depth, const void *feats, int fb,
+                           const void *packed, const float *rays, const Workspace &ws,
+                           int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
+    if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
+    TcBwdParams P;
+    memset(&P, 0, sizeof(P));
+    P.md = md;
+    P.lay = tc_layout(md);
+    size_t smem;
+    if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
+    P.depth = depth;
+    P.fp16 = precision == SVLF_FP16;
+    P.feat_bf16 = fb;
+    P.feats = feats;
+    P.image = (const uint8_t *)packed;
+    P.rays = rays;
+    P.samples = ws.samples;
+    P.counter = ws.counter;
+    P.max_samples = max_samples;
+    P.dout = ws.dout;
+    P.d_feat = d_feat;
+    P.d_params = d_params;
+    if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
+    if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    prof_begin("mlp_backward_tc", s);
+    mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(P);
+    prof_end(s);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
 }  // namespace svlf

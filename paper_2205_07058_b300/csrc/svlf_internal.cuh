@@ -58,7 +58,7 @@ struct Workspace {
     float4 *outputs;       // n_rays*K: sigmoid colour (xyz), tau (w)
     float4 *dout;          // n_rays*K: dL/d(network output)
     int2 *ray_span;        // n_rays: first sample, count
-    unsigned int *counter; // [0] samples written, [1] tiles claimed (forward), [2] (backward)
+    unsigned int *counter; // [0] samples written, [3] float bits of max |dL/d(output)|
     void *packed_w;        // network weights packed for the kernels
     size_t bytes;
 };

@@ -90,3 +90,12 @@ def test_composite_invariants(tiny):
     assert np.array_equal(r.rgb[empty], np.broadcast_to(bg, (empty.sum(), 3)))
     assert np.all(r.depth[empty] == 0)
     assert np.all((r.rgb >= 0) & (r.rgb <= 1))
+
+
+def test_fp16_rounding_matches_torch():
+    assert O.fp16_round(np.array([1.0 + 2.0 ** -11]))[0] == 1.0          # tie -> even (down)
+    assert O.fp16_round(np.array([1.0 + 3 * 2.0 ** -11]))[0] == 1.0 + 2.0 ** -9
+    # float32 values (what the GPU rounds), so torch converts with one rounding too
+    x = (np.random.default_rng(1).standard_normal(100000) * 10.0).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.fp16_round(x.astype(np.float64)), ref)
