@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--render-only", action="store_true",
+                   help="time only the render pass (profiling aid; not the benchmark step)")
     p.add_argument("--views", type=int, default=RENDER_VIEWS)
     p.add_argument("--res", type=int, default=RENDER_RES)
     return p.parse_args()
@@ -222,8 +224,11 @@ def run_ours(args, rank, world, local_rank):
     N, NT = rays.shape[0], trays.shape[0]
     # targets: the teacher network rendered through the FP32 path, analytic depth
     teacher = torch.from_numpy(W["teacher"]).to(dev)
-    rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats, teacher, svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32),
-                                              trays, K_HITS)
+    if args.render_only:
+        rgb_t = torch.zeros((NT, 3), device=dev)
+    else:
+        rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats, teacher,
+                                                  svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32), trays, K_HITS)
     depth_t = torch.from_numpy(W["depth_t"]).to(dev)
     mask = torch.from_numpy(W["mask"]).to(dev)
     del teacher
@@ -268,13 +273,14 @@ def run_ours(args, rank, world, local_rank):
         if record is not None:
             record.append(torch.cuda.Event(enable_timing=True))
             record[-1].record(stream)
-        train_phase()
+        if not args.render_only:
+            train_phase()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
-    n_samples_train = svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
+    n_samples_train = 0 if args.render_only else svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
     loss_first = None
 
     def barrier():
@@ -310,12 +316,12 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    rays_per_step = N + NT
+    rays_per_step = N + (0 if args.render_only else NT)
     value = rays_per_step * world * args.steps / (t_max / 1e3)
 
     # ---- end-to-end through host buffers (H2D of the step's inputs, D2H of its results)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.render_only:
         h_rays = torch.from_numpy(W["render_rays"]).pin_memory()
         h_trays = torch.from_numpy(W["train_rays"]).pin_memory()
         h_tgt = torch.cat([rgb_t.cpu(), depth_t.cpu()[:, None], mask.cpu()[:, None]], dim=1).contiguous().pin_memory()
@@ -417,7 +423,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (features 216 MB + rays 246 MB per step)"},
             "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
-            "train_rays_per_s": round(NT * args.steps / (train_ms / 1e3), 1),
+            "train_rays_per_s": None if args.render_only else round(NT * args.steps / (train_ms / 1e3), 1),
             "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
             "samples_per_step": {"render": n_samples_render, "train": n_samples_train},
             "e2e": e2e, "gpu_launches": gpu_launches, "kernels": per_kernel,
@@ -523,7 +529,7 @@ def main():
         return
     out, W = run_ours(args, rank, world, local_rank)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and not args.render_only:
             out["cpu_baseline"] = cpu_baseline(W)
         print(json.dumps(out), flush=True)
 

@@ -81,7 +81,7 @@ typedef struct {
 } svlf_mlp_desc;
 
 typedef struct {
-    int K;        /* hits evaluated per ray (the first K leaves): 1, 2, 4, 8, 16 or 32 */
+    int K;        /* hits evaluated per ray (the first K leaves): 1..32 */
     float bg[3];  /* colour multiplied by the transmittance left after the K-th hit */
 } svlf_render_opts;
 

@@ -108,7 +108,7 @@ static int check_common(svlf_octree tree, const void *features, const float *par
     int rc = check_mlp(mlp);
     if (rc) return rc;
     const int K = opts->K;
-    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SVLF_ERR_UNSUPPORTED;
+    if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     if (n_rays == 0) return SVLF_OK;  // nothing to read or write
     if (!params || !rays) return SVLF_ERR_ARG;
     if (!features && octree_view(tree).n_leaves > 0) return SVLF_ERR_ARG;

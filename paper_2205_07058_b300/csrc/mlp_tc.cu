@@ -134,6 +134,56 @@ __device__ __forceinline__ void st_chunk(uint8_t *abuf, int row, int kb, uint32_
         make_uint4(a, b, c, d);
 }
 
+// Network input h0 = [z | d | p~1 | p~2] of sample `s` written straight into
+// row `row` of a 16-bit A operand (K0 columns): F/8 chunks of features, two
+// chunks of ray direction and entry/exit parameters, zero chunks up to K0.
+__device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, int depth,
+                                                   const void *feats, int feat_bf16,
+                                                   const float *rays, const Sample *samples,
+                                                   int64_t s, bool valid, int fp16, uint8_t *abuf,
+                                                   int row, int *leaf_out) {
+    const int F = md.F;
+    int kb = 0;
+    if (valid) {
+        const Sample sm = samples[s];
+        if (leaf_out) *leaf_out = sm.leaf;
+        const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * (int64_t)sm.ray);
+        const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
+        if (feat_bf16) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(
+                reinterpret_cast<const __nv_bfloat16 *>(feats) + (int64_t)sm.leaf * F);
+            for (int q = 0; q < F / 8; ++q, ++kb) {
+                uint4 v = __ldg(src + q);
+                if (fp16) {
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        o[e] = tc::pack2(__uint_as_float(w[e] << 16), __uint_as_float(w[e] & 0xFFFF0000u), true);
+                    v = make_uint4(o[0], o[1], o[2], o[3]);
+                }
+                st_chunk(abuf, row, kb, v.x, v.y, v.z, v.w);
+            }
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(
+                reinterpret_cast<const float *>(feats) + (int64_t)sm.leaf * F);
+            for (int q = 0; q < F / 8; ++q, ++kb) {
+                const float4 a = __ldg(src + 2 * q), b = __ldg(src + 2 * q + 1);
+                st_chunk(abuf, row, kb, tc::pack2(a.x, a.y, fp16), tc::pack2(a.z, a.w, fp16),
+                         tc::pack2(b.x, b.y, fp16), tc::pack2(b.z, b.w, fp16));
+            }
+        }
+        const float o[3] = {ra.x, ra.y, rb.x};
+        const float d[3] = {rb.y, rc.x, rc.y};
+        float p1[3], p2[3];
+        sphere_param(o, d, sm.cell, depth, p1, p2);
+        st_chunk(abuf, row, kb++, tc::pack2(d[0], d[1], fp16), tc::pack2(d[2], p1[0], fp16),
+                 tc::pack2(p1[1], p1[2], fp16), tc::pack2(p2[0], p2[1], fp16));
+        st_chunk(abuf, row, kb++, tc::pack2(p2[2], 0.f, fp16), 0u, 0u, 0u);
+    }
+    for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+}
+
 template <int H>
 __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -192,21 +242,8 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParam
          tile += (int64_t)gridDim.x * P.n_wg) {
         const int64_t s = tile * kTcTile + row;
         // ---- network input row -> A operand (K0 columns)
-        {
-            float h0[kMaxIn];
-            const bool valid = s < S;
-            if (valid) make_input_row(P.md, P.depth, P.feats, P.feat_bf16, P.rays, P.samples[s], h0);
-            for (int kb = 0; kb < P.lay.K0 / 8; ++kb) {
-                float v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = kb * 8 + e;
-                    v[e] = (valid && k < P.md.in0) ? h0[k] : 0.f;
-                }
-                st_chunk(abuf, row, kb, tc::pack2(v[0], v[1], P.fp16), tc::pack2(v[2], v[3], P.fp16),
-                         tc::pack2(v[4], v[5], P.fp16), tc::pack2(v[6], v[7], P.fp16));
-            }
-        }
+        build_input_chunks(P.md, P.lay.K0, P.depth, P.feats, P.feat_bf16, P.rays, P.samples, s,
+                           s < S, P.fp16, abuf, row, nullptr);
         for (int l = 0; l < P.lay.n_layers; ++l) {
             const int N = P.lay.w_rows[l];
             const int Kl = P.lay.w_cols[l];
@@ -501,23 +538,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdPara
         int leaf = -1;
         // ---- 1. X_0 and G_out
         {
-            float h0[kMaxIn];
-            if (valid) {
-                const Sample sm = P.samples[s];
-                leaf = sm.leaf;
-                make_input_row(md, P.depth, P.feats, P.feat_bf16, P.rays, sm, h0);
-            }
-            uint8_t *x0 = smem + P.x_off[0];
-            for (int kb = 0; kb < lay.K0 / 8; ++kb) {
-                float v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = kb * 8 + e;
-                    v[e] = (valid && k < md.in0) ? h0[k] : 0.f;
-                }
-                st_chunk(x0, row, kb, tc::pack2(v[0], v[1], P.fp16), tc::pack2(v[2], v[3], P.fp16),
-                         tc::pack2(v[4], v[5], P.fp16), tc::pack2(v[6], v[7], P.fp16));
-            }
+            build_input_chunks(md, lay.K0, P.depth, P.feats, P.feat_bf16, P.rays, P.samples, s, valid,
+                               P.fp16, smem + P.x_off[0], row, &leaf);
             const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
             uint8_t *go = smem + P.gout_off;
             st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),

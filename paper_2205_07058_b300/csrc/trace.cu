@@ -11,35 +11,35 @@
 //    cost no memory access.
 //  * The node words of the top levels (up to kSmemNodeWords) are staged in
 //    shared memory; deeper levels and bricks come through the read-only path.
-//  * Plane crossings are t = (k 2^-L - o) / d with an IEEE division, and the
-//    cell after a crossing is found by counting the planes whose crossing is
-//    <= the current t. A voxel is therefore entered at exactly the t the slab
-//    test would give as its t_in and left at its t_out, every visited voxel
-//    has t_out > t_in, and no voxel with a positive segment is skipped.
-//  * Hits stay in registers (K is a template parameter); at the end each warp
-//    reserves space for its rays' samples with one atomic and writes them
-//    contiguously per ray.
+//  * Plane crossings t = (k 2^-L - o) / d are evaluated without a division:
+//    k 2^-L - o is split exactly into hi + lo (TwoSum) and multiplied by 1/d
+//    held as a double-float (r_hi + r_lo, formed once per ray with an FMA
+//    residual), so each crossing carries about half an ulp of error. The cell
+//    after a crossing is found by counting the planes whose crossing is <= the
+//    current t. A voxel is therefore entered at the t its slab test gives as
+//    t_in and left at its t_out, every visited voxel has t_out > t_in, and no
+//    voxel with a positive segment is skipped.
+//  * Hits go straight to the ray's K slots in a scratch area (the network
+//    output buffer, not yet in use), keeping registers free for occupancy; at
+//    the end each warp reserves space for its rays' samples with one atomic
+//    and copies them contiguously per ray from the (cache-hot) slots.
 #include "svlf_internal.cuh"
 
 namespace svlf {
 
 __device__ unsigned int g_device_status = 0;
 
-template <int K>
-struct HitBuf {
-    int rank[K];
-    uint32_t cell[K];
-    float tin[K], tout[K];
-};
-
 struct RayState {
     float o[3], d[3];
+    float rhi[3], rlo[3];  // 1/d as a double-float
     float h;
     int n;  // 2^L
 };
 
 __device__ __forceinline__ float cross_t(const RayState &R, int a, int k) {
-    return ((float)k * R.h - R.o[a]) / R.d[a];
+    float xh, xl;
+    two_sum((float)k * R.h, -R.o[a], xh, xl);  // k 2^-L exact; difference split exactly
+    return fmaf(xh, R.rhi[a], fmaf(xh, R.rlo[a], xl * R.rhi[a]));
 }
 
 // Cell index along axis a occupied just after time t, searched in [lo, hi].
@@ -57,9 +57,10 @@ __device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int
     return k;
 }
 
-template <int K>
+// Hits are written to slot[0 .. K-1] (16 bytes each: rank, packed cell,
+// t_in, t_out); returns their number.
 __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem, RayState &R,
-                        HitBuf<K> &hb) {
+                        int K, int4 *__restrict__ slot) {
     if (T.empty) return 0;
     const int L = T.depth;
     const int n = R.n;
@@ -162,15 +163,7 @@ __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem
         }
         if (leaf) {
             const uint32_t packed = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                if (j == nh) {
-                    hb.rank[j] = rank;
-                    hb.cell[j] = packed;
-                    hb.tin[j] = t;
-                    hb.tout[j] = tx;
-                }
-            }
+            slot[nh] = make_int4(rank, (int)packed, __float_as_int(t), __float_as_int(tx));
             if (++nh == K) break;
         }
         bool out = false;
@@ -192,9 +185,10 @@ __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem
     return nh;
 }
 
-template <int K>
 __global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *__restrict__ rays,
-                                                    int64_t n_rays, Sample *__restrict__ samples,
+                                                    int64_t n_rays, int K,
+                                                    Sample *__restrict__ samples,
+                                                    int4 *__restrict__ slots,
                                                     int2 *__restrict__ ray_span,
                                                     unsigned int *__restrict__ counter,
                                                     int64_t max_samples, int32_t *__restrict__ hits,
@@ -208,17 +202,23 @@ __global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *_
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = base + threadIdx.x;
         const bool valid = r < n_rays;
-        HitBuf<K> hb;
         int nh = 0;
+        int4 *slot = slots + r * K;
         if (valid) {
             RayState R;
             const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * r);
             const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
             R.o[0] = a.x; R.o[1] = a.y; R.o[2] = b.x;
             R.d[0] = b.y; R.d[1] = cc.x; R.d[2] = cc.y;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float rh = 1.0f / R.d[q];  // inf for d = 0 (that axis is never crossed)
+                R.rhi[q] = rh;
+                R.rlo[q] = R.d[q] != 0.f ? fmaf(-R.d[q], rh, 1.0f) * rh : 0.f;
+            }
             R.n = 1 << T.depth;
             R.h = ldexpf(1.0f, -T.depth);
-            nh = traverse<K>(T, s_nodes, n_smem, R, hb);
+            nh = traverse(T, s_nodes, n_smem, R, K, slot);
         }
         // warp-aggregated reservation of nh samples per lane
         int incl = nh;
@@ -239,57 +239,49 @@ __global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *_
                 keep = (int)max((int64_t)0, max_samples - first);
             }
             ray_span[r] = make_int2((int)first, keep);
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                if (j < keep) {
-                    Sample sm;
-                    sm.leaf = hb.rank[j];
-                    sm.ray = (int32_t)r;
-                    sm.cell = hb.cell[j];
-                    sm.tmid = 0.5f * (hb.tin[j] + hb.tout[j]);
-                    reinterpret_cast<int4 *>(samples)[first + j] =
-                        make_int4(sm.leaf, sm.ray, (int)sm.cell, __float_as_int(sm.tmid));
-                }
-                if (hits) hits[r * K + j] = j < nh ? hb.rank[j] : -1;
-                if (t_io) {
-                    reinterpret_cast<float2 *>(t_io)[r * K + j] =
-                        j < nh ? make_float2(hb.tin[j], hb.tout[j]) : make_float2(0.f, 0.f);
+            for (int j = 0; j < keep; ++j) {
+                const int4 h = slot[j];
+                const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
+                reinterpret_cast<int4 *>(samples)[first + j] =
+                    make_int4(h.x, (int)r, h.y, __float_as_int(tm));
+            }
+            if (hits || t_io) {
+                for (int j = 0; j < K; ++j) {
+                    const int4 h = j < nh ? slot[j] : make_int4(-1, 0, 0, 0);
+                    if (hits) hits[r * K + j] = h.x;
+                    if (t_io)
+                        reinterpret_cast<float2 *>(t_io)[r * K + j] =
+                            j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
+                                   : make_float2(0.f, 0.f);
                 }
             }
         }
     }
 }
 
-template <int K>
-static int launch_trace_k(const OctreeView &T, const float *rays, int64_t n_rays,
-                          const Workspace &ws, int32_t *hits, float *t_io, int64_t max_samples,
-                          cudaStream_t s) {
-    const int threads = 256;
-    const size_t smem = sizeof(uint32_t) * (size_t)min(T.n_nodes, kSmemNodeWords);
-    int64_t blocks = (n_rays + threads - 1) / threads;
-    const int64_t cap = (int64_t)num_sms() * 6;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    prof_begin("trace", s);
-    trace_kernel<K><<<(unsigned)blocks, threads, smem, s>>>(T, rays, n_rays, ws.samples,
-                                                            ws.ray_span, ws.counter, max_samples,
-                                                            hits, t_io);
-    prof_end(s);
-    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
-}
-
 int launch_trace(const OctreeView &T, const float *rays, int64_t n_rays, int K,
                  const Workspace &ws, int32_t *hits, float *t_io, cudaStream_t s) {
+    if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     const int64_t max_samples = n_rays * (int64_t)K;
-    switch (K) {  // the hit buffer lives in registers: one instantiation per K
-        case 1: return launch_trace_k<1>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        case 2: return launch_trace_k<2>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        case 4: return launch_trace_k<4>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        case 8: return launch_trace_k<8>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        case 16: return launch_trace_k<16>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        case 32: return launch_trace_k<32>(T, rays, n_rays, ws, hits, t_io, max_samples, s);
-        default: return SVLF_ERR_UNSUPPORTED;
-    }
+    const int threads = 256;
+    const size_t smem = sizeof(uint32_t) * (size_t)min(T.n_nodes, kSmemNodeWords);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t blocks = (n_rays + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * per_sm;  // persistent: one wave of resident blocks
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    // the per-ray hit slots live in the network-output buffer (n_rays*K x 16 B),
+    // which the network kernels only write after this kernel is done
+    prof_begin("trace", s);
+    trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, rays, n_rays, K, ws.samples,
+                                                         reinterpret_cast<int4 *>(ws.outputs),
+                                                         ws.ray_span, ws.counter, max_samples,
+                                                         hits, t_io);
+    prof_end(s);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
 }  // namespace svlf

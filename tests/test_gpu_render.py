@@ -42,7 +42,7 @@ def test_duplicate_and_out_of_range_leaves():
     assert e.value.code == svlf.SVLF_ERR_ARG
 
 
-@pytest.mark.parametrize("K", [1, 4, 32])
+@pytest.mark.parametrize("K", [1, 3, 4, 32])
 def test_hit_lists_bit_exact_tiny(tiny, K):
     from paper_2205_07058_b300 import svlf
     rng = np.random.default_rng(3)
@@ -115,8 +115,9 @@ def test_empty_octree_and_zero_rays(tiny):
 def test_bad_arguments_are_reported(tiny):
     from paper_2205_07058_b300 import svlf
     tree, f, p, r = gpu_inputs(tiny)
+    ws32 = svlf.alloc_workspace(net_for(tiny, svlf.FP32), r.shape[0], 32)
     with pytest.raises(svlf.SvlfError) as e:
-        svlf.svlf_render_rays(tree, f, p, net_for(tiny, svlf.FP32), r, 3)
+        svlf.svlf_render_rays(tree, f, p, net_for(tiny, svlf.FP32), r, 33, workspace=ws32)
     assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
     bad = svlf.Network(16, 64, 2, svlf.FP32)
     ws = torch.empty(64, dtype=torch.uint8, device="cuda")
