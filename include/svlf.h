@@ -172,6 +172,26 @@ int svlf_get_device_status(int *status);
 
 const char *svlf_status_string(int status);
 
+/* ------------------------------------------------------------ no allocation */
+/* svlf_render_rays for callers that cannot allocate device memory: hosts that
+ * give a renderer a fixed device-memory budget at start-up and forbid later
+ * allocations, and frame loops that must not call cudaMalloc because it can
+ * synchronise the device. The paper has no counterpart; this is a deployment
+ * variant of svlf_render_rays with the same arguments minus the workspace and
+ * the optional hit outputs.
+ * Its scratch is a fixed 32 MiB array inside the library (every GPU that
+ * loads the library holds it until exit). A call fits when
+ * svlf_workspace_size(mlp, n_rays, K) <= 32 MiB, e.g. about 85 000 rays at
+ * K = 8 for a 41 -> 3 x 128 -> 4 network; larger calls return
+ * SVLF_ERR_WORKSPACE before any work is queued. The call allocates nothing.
+ * All calls share the array and it keeps the previous call's contents (the
+ * sample counter is cleared by each call): calls that overlap on the GPU
+ * race. The first call on a device looks up the array's device address;
+ * make it before any stream capture. */
+int svlf_render_rays_static(svlf_octree tree, const void *features, const float *mlp_params,
+                            const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
+                            const svlf_render_opts *opts, float *rgb, float *depth, void *stream);
+
 /* ------------------------------------------------------------ measurement */
 /* Per-kernel timing (measurement aid, not part of the method). When enabled,
  * every kernel the library launches is bracketed by CUDA events on its own

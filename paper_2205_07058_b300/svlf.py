@@ -58,6 +58,7 @@ EXPORTS = [
     "svlf_workspace_size", "svlf_render_rays", "svlf_render_rays_backward", "svlf_loss",
     "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma",
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
+    "svlf_render_rays_static",
 ]
 
 _lib = None
@@ -86,6 +87,7 @@ def lib():
     L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
     L.svlf_get_device_status.argtypes = [P(i32)]
     L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]
+    L.svlf_render_rays_static.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp, vp, vp]
     L.svlf_profile_enable.argtypes = [i32]
     L.svlf_profile_report.argtypes = [P(KernelStat), i32, P(i32)]
     L.svlf_workspace_samples.argtypes = [vp, P(MlpDesc), i64, i32, P(i64), vp]
@@ -223,6 +225,24 @@ def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor,
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
         _ptr(rgb), _ptr(depth), _ptr(hits), _ptr(t_io), wp, wb, _stream(stream)))
     return rgb, depth, hits, t_io, workspace
+
+
+def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
+                            rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), out: Optional[tuple] = None,
+                            stream=None):
+    """Render without a workspace (the library's fixed scratch array); for
+    callers that may not allocate device memory. Returns (rgb, depth)."""
+    N = rays.shape[0]
+    if out is None:
+        out = (torch.empty((N, 3), dtype=torch.float32, device="cuda"),
+               torch.empty((N,), dtype=torch.float32, device="cuda"))
+    rgb, depth = out
+    d = net.desc()
+    o = _opts(K, bg)
+    _check("svlf_render_rays_static", lib().svlf_render_rays_static(
+        tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
+        _ptr(rgb), _ptr(depth), _stream(stream)))
+    return rgb, depth
 
 
 def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
