@@ -155,6 +155,42 @@ int svlf_loss(const float *rgb, const float *depth, const float *rgb_target,
               const float *depth_target, const float *mask, int64_t n, float depth_weight,
               float *d_rgb, float *d_depth, double *loss_accum, void *stream);
 
+/* ------------------------------------------------------------ batched form */
+/* Many scenes of uneven octree size in one call (one launch per kernel for
+ * all of them; the calls queue no host-device copy and can be captured in a
+ * CUDA graph). Each scene has its own octree, features, network parameters
+ * (same network shape for all, given by `mlp`), rays and outputs. All device
+ * pointers as in svlf_render_rays; the d_* members are only read or written
+ * by the backward call. Up to 64 scenes per call; the tensor-core precisions
+ * (SVLF_BF16, SVLF_FP16) handle any number, SVLF_FP32 a single scene. */
+typedef struct {
+    svlf_octree tree;
+    const void *features;       /* n_leaves x feat_dim, fp32 or bf16 */
+    const float *mlp_params;    /* flat float32 network parameters */
+    const float *rays;          /* n_rays x 6 */
+    int64_t n_rays;
+    float *rgb, *depth;         /* render outputs: n_rays x 3, n_rays */
+    const float *d_rgb, *d_depth;      /* backward inputs */
+    float *d_features, *d_mlp_params;  /* backward outputs (accumulate), or NULL */
+} svlf_scene;
+
+/* Workspace for a batched call over n_scenes scenes and total_rays rays. */
+int svlf_workspace_size_batched(const svlf_mlp_desc *mlp, int64_t total_rays, int n_scenes, int K,
+                                size_t *bytes);
+
+/* Render every scene (Sec. 4.3; see svlf_render_rays). The workspace keeps
+ * what the matching batched backward reads. */
+int svlf_render_rays_batched(const svlf_scene *scenes, int n_scenes, const svlf_mlp_desc *mlp,
+                             const svlf_render_opts *opts, void *workspace, size_t ws_bytes,
+                             void *stream);
+
+/* Backward of svlf_render_rays_batched for every scene (see
+ * svlf_render_rays_backward). Either gradient may be skipped by passing NULL
+ * for it in every scene. */
+int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
+                                      const svlf_mlp_desc *mlp, const svlf_render_opts *opts,
+                                      void *workspace, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------ optimiser */
 /* One bias-corrected Adam step (Sec. 4.5 trains with Adam; Kingma & Ba) over
  * n float32 parameters (device): m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;

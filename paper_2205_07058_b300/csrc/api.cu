@@ -53,19 +53,20 @@ size_t packed_weight_bytes(const svlf_mlp_desc &mlp) {
     return align256(a > b ? a : b);
 }
 
-size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K) {
+size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K, int n_scenes) {
     const size_t S = (size_t)n_rays * (size_t)K;
     size_t b = 0;
     b += align256(sizeof(Sample) * S);
     b += align256(sizeof(float4) * S);
     b += align256(sizeof(float4) * S);
     b += align256(sizeof(int2) * (size_t)n_rays);
-    b += 256;  // counters
-    b += packed_weight_bytes(mlp);
+    b += kCounterBytes;
+    b += (size_t)n_scenes * packed_weight_bytes(mlp);
     return b;
 }
 
-Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K) {
+Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K,
+                          int n_scenes) {
     Workspace w;
     const size_t S = (size_t)n_rays * (size_t)K;
     char *p = static_cast<char *>(base);
@@ -78,9 +79,10 @@ Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, 
     w.ray_span = reinterpret_cast<int2 *>(p);
     p += align256(sizeof(int2) * (size_t)n_rays);
     w.counter = reinterpret_cast<unsigned int *>(p);
-    p += 256;
+    p += kCounterBytes;
     w.packed_w = p;
-    p += packed_weight_bytes(mlp);
+    w.packed_stride = packed_weight_bytes(mlp);
+    p += (size_t)n_scenes * w.packed_stride;
     w.bytes = (size_t)(p - static_cast<char *>(base));
     return w;
 }
@@ -101,30 +103,112 @@ static int check_mlp(const svlf_mlp_desc *m) {
     return SVLF_OK;
 }
 
-static int check_common(svlf_octree tree, const void *features, const float *params,
-                        const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
-                        const svlf_render_opts *opts, void *workspace, size_t ws_bytes) {
-    if (!tree || !opts || n_rays < 0) return SVLF_ERR_ARG;
+static int check_scene(const svlf_scene &sc, bool need_outputs) {
+    if (!sc.tree || sc.n_rays < 0) return SVLF_ERR_ARG;
+    if (sc.n_rays == 0) return SVLF_OK;  // nothing to read or write
+    if (!sc.mlp_params || !sc.rays) return SVLF_ERR_ARG;
+    if (!sc.features && octree_view(sc.tree).n_leaves > 0) return SVLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(sc.features) % 16 || reinterpret_cast<uintptr_t>(sc.rays) % 8)
+        return SVLF_ERR_ARG;
+    if (need_outputs && (!sc.rgb || !sc.depth)) return SVLF_ERR_ARG;
+    return SVLF_OK;
+}
+
+// Validate a call and build its scene table (device-side view of the scenes).
+static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_desc *mlp,
+                      const svlf_render_opts *opts, void *workspace, size_t ws_bytes,
+                      bool backward, SceneTable &T) {
+    if (!scenes || n_scenes < 1 || !opts) return SVLF_ERR_ARG;
+    if (n_scenes > kMaxScenes) return SVLF_ERR_UNSUPPORTED;
     int rc = check_mlp(mlp);
     if (rc) return rc;
     const int K = opts->K;
     if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
-    if (n_rays == 0) return SVLF_OK;  // nothing to read or write
-    if (!params || !rays) return SVLF_ERR_ARG;
-    if (!features && octree_view(tree).n_leaves > 0) return SVLF_ERR_ARG;
-    if ((int64_t)n_rays * K >= ((int64_t)1 << 31)) return SVLF_ERR_UNSUPPORTED;
-    if (reinterpret_cast<uintptr_t>(features) % 16 || reinterpret_cast<uintptr_t>(rays) % 8)
-        return SVLF_ERR_ARG;
+    std::memset(&T, 0, sizeof(T));
+    T.n = n_scenes;
+    T.K = K;
+    int64_t rays = 0, chunks = 0;
+    for (int i = 0; i < n_scenes; ++i) {
+        const svlf_scene &sc = scenes[i];
+        if ((rc = check_scene(sc, !backward))) return rc;
+        if (backward && sc.n_rays > 0 && (!sc.d_rgb || !sc.d_depth)) return SVLF_ERR_ARG;
+        SceneDev &d = T.s[i];
+        d.tree = octree_view(sc.tree);
+        d.feats = sc.features;
+        d.params = sc.mlp_params;
+        d.rays = sc.rays;
+        d.rgb = sc.rgb;
+        d.depth = sc.depth;
+        d.d_rgb = sc.d_rgb;
+        d.d_depth = sc.d_depth;
+        d.d_feat = sc.d_features;
+        d.d_params = sc.d_mlp_params;
+        d.ray_begin = rays;
+        d.n_rays = sc.n_rays;
+        d.chunk_begin = chunks;
+        rays += sc.n_rays;
+        chunks += (sc.n_rays + kTraceChunk - 1) / kTraceChunk;
+    }
+    T.total_rays = rays;
+    T.total_chunks = chunks;
+    if (rays * K >= ((int64_t)1 << 31)) return SVLF_ERR_UNSUPPORTED;
+    if (rays == 0) return SVLF_OK;
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
-    if (ws_bytes < workspace_bytes(*mlp, n_rays, K)) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes(*mlp, rays, K, n_scenes)) return SVLF_ERR_WORKSPACE;
     return SVLF_OK;
 }
 
-int launch_pack_weights(const svlf_mlp_desc &mlp, const float *params, void *packed,
+int launch_pack_weights(const svlf_mlp_desc &mlp, const SceneTable &T, const Workspace &ws,
                         cudaStream_t s) {
     const MlpDims md = make_dims(mlp);
-    if (mlp.precision == SVLF_FP32) return launch_pack_f32(md, params, (float *)packed, s);
-    return launch_pack_tc(md, mlp.precision, params, packed, s);
+    if (mlp.precision == SVLF_FP32) {
+        int rc = SVLF_OK;
+        for (int i = 0; i < T.n && !rc; ++i)
+            rc = launch_pack_f32(md, T.s[i].params, (float *)((char *)ws.packed_w + i * ws.packed_stride), s);
+        return rc;
+    }
+    return launch_pack_tc(md, mlp.precision, T, ws.packed_w, ws.packed_stride, s);
+}
+
+static int render_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svlf_render_opts &opts,
+                        void *workspace, int32_t *hits, float *t_io, cudaStream_t s) {
+    if (T.total_rays == 0) return SVLF_OK;
+    Workspace ws = carve_workspace(workspace, mlp, T.total_rays, T.K, T.n);
+    int rc;
+    if (cudaMemsetAsync(ws.counter, 0, kCounterBytes, s) != cudaSuccess) return SVLF_ERR_CUDA;
+    if ((rc = launch_pack_weights(mlp, T, ws, s))) return rc;
+    if ((rc = launch_trace(T, ws, hits, t_io, s))) return rc;
+    const MlpDims md = make_dims(mlp);
+    const int fb = mlp.feat_dtype == SVLF_FEAT_BF16;
+    if (mlp.precision == SVLF_FP32) {
+        if (T.n != 1) return SVLF_ERR_UNSUPPORTED;
+        rc = launch_mlp_forward_f32(md, T.s[0].tree.depth, T.s[0].feats, fb, (const float *)ws.packed_w,
+                                    T.s[0].rays, ws, T.total_rays * (int64_t)T.K, s);
+    } else {
+        rc = launch_mlp_forward_tc(md, mlp.precision, fb, T, ws, s);
+    }
+    if (rc) return rc;
+    return launch_composite(T, ws, opts.bg, s);
+}
+
+static int backward_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svlf_render_opts &opts,
+                          void *workspace, bool want_feat, bool want_params, cudaStream_t s) {
+    if (T.total_rays == 0 || (!want_feat && !want_params)) return SVLF_OK;
+    Workspace ws = carve_workspace(workspace, mlp, T.total_rays, T.K, T.n);
+    int rc;
+    if (cudaMemsetAsync(ws.counter + kCtrMaxAbsDout, 0, sizeof(unsigned int), s) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    if ((rc = launch_composite_backward(T, ws, opts.bg, s))) return rc;
+    const MlpDims md = make_dims(mlp);
+    const int fb = mlp.feat_dtype == SVLF_FEAT_BF16;
+    if (mlp.precision == SVLF_FP32) {
+        if (T.n != 1) return SVLF_ERR_UNSUPPORTED;
+        const SceneDev &d = T.s[0];
+        return launch_mlp_backward_f32(md, d.tree.depth, d.feats, fb, d.params, (const float *)ws.packed_w,
+                                       d.rays, ws, T.total_rays * (int64_t)T.K,
+                                       want_feat ? d.d_feat : nullptr, want_params ? d.d_params : nullptr, s);
+    }
+    return launch_mlp_backward_tc(md, mlp.precision, fb, T, ws, want_feat, want_params, s);
 }
 
 }  // namespace svlf
@@ -134,8 +218,29 @@ using namespace svlf;
 extern "C" int svlf_workspace_size(const svlf_mlp_desc *mlp, int64_t n_rays, int K,
                                    size_t *bytes) {
     if (!mlp || !bytes || n_rays < 0 || K < 1 || K > kMaxK) return SVLF_ERR_ARG;
-    *bytes = workspace_bytes(*mlp, n_rays, K);
+    *bytes = workspace_bytes(*mlp, n_rays, K, 1);
     return SVLF_OK;
+}
+
+extern "C" int svlf_workspace_size_batched(const svlf_mlp_desc *mlp, int64_t total_rays,
+                                           int n_scenes, int K, size_t *bytes) {
+    if (!mlp || !bytes || total_rays < 0 || K < 1 || K > kMaxK || n_scenes < 1 ||
+        n_scenes > kMaxScenes)
+        return SVLF_ERR_ARG;
+    *bytes = workspace_bytes(*mlp, total_rays, K, n_scenes);
+    return SVLF_OK;
+}
+
+static svlf_scene one_scene(svlf_octree tree, const void *features, const float *mlp_params,
+                            const float *rays, int64_t n_rays) {
+    svlf_scene sc;
+    std::memset(&sc, 0, sizeof(sc));
+    sc.tree = tree;
+    sc.features = features;
+    sc.mlp_params = mlp_params;
+    sc.rays = rays;
+    sc.n_rays = n_rays;
+    return sc;
 }
 
 extern "C" int svlf_render_rays(svlf_octree tree, const void *features, const float *mlp_params,
@@ -143,28 +248,14 @@ extern "C" int svlf_render_rays(svlf_octree tree, const void *features, const fl
                                 const svlf_render_opts *opts, float *rgb, float *depth,
                                 int32_t *hits, float *t_io, void *workspace, size_t ws_bytes,
                                 void *stream) {
-    int rc = check_common(tree, features, mlp_params, mlp, rays, n_rays, opts, workspace, ws_bytes);
+    if (!tree) return SVLF_ERR_ARG;
+    svlf_scene sc = one_scene(tree, features, mlp_params, rays, n_rays);
+    sc.rgb = rgb;
+    sc.depth = depth;
+    SceneTable T;
+    int rc = make_table(&sc, 1, mlp, opts, workspace, ws_bytes, false, T);
     if (rc) return rc;
-    if (n_rays == 0) return SVLF_OK;
-    if (!rgb || !depth) return SVLF_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int K = opts->K;
-    Workspace ws = carve_workspace(workspace, *mlp, n_rays, K);
-    const MlpDims md = make_dims(*mlp);
-    if (cudaMemsetAsync(ws.counter, 0, 256, s) != cudaSuccess) return SVLF_ERR_CUDA;
-    if ((rc = launch_pack_weights(*mlp, mlp_params, ws.packed_w, s))) return rc;
-    const OctreeView &T = octree_view(tree);
-    if ((rc = launch_trace(T, rays, n_rays, K, ws, hits, t_io, s))) return rc;
-    const int64_t max_samples = n_rays * (int64_t)K;
-    const int fb = mlp->feat_dtype == SVLF_FEAT_BF16;
-    if (mlp->precision == SVLF_FP32)
-        rc = launch_mlp_forward_f32(md, T.depth, features, fb, (const float *)ws.packed_w, rays, ws,
-                                    max_samples, s);
-    else
-        rc = launch_mlp_forward_tc(md, mlp->precision, T.depth, features, fb, ws.packed_w, rays,
-                                   ws, max_samples, s);
-    if (rc) return rc;
-    return launch_composite(ws, n_rays, opts->bg, rgb, depth, s);
+    return render_table(T, *mlp, *opts, workspace, hits, t_io, (cudaStream_t)stream);
 }
 
 extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
@@ -174,25 +265,46 @@ extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
                                          const float *d_depth, float *d_features,
                                          float *d_mlp_params, void *workspace, size_t ws_bytes,
                                          void *stream) {
-    int rc = check_common(tree, features, mlp_params, mlp, rays, n_rays, opts, workspace, ws_bytes);
+    if (!tree) return SVLF_ERR_ARG;
+    svlf_scene sc = one_scene(tree, features, mlp_params, rays, n_rays);
+    sc.d_rgb = d_rgb;
+    sc.d_depth = d_depth;
+    sc.d_features = d_features;
+    sc.d_mlp_params = d_mlp_params;
+    SceneTable T;
+    int rc = make_table(&sc, 1, mlp, opts, workspace, ws_bytes, true, T);
     if (rc) return rc;
-    if (n_rays == 0 || (!d_features && !d_mlp_params)) return SVLF_OK;
-    if (!d_rgb || !d_depth) return SVLF_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int K = opts->K;
-    Workspace ws = carve_workspace(workspace, *mlp, n_rays, K);
-    const MlpDims md = make_dims(*mlp);
-    const OctreeView &T = octree_view(tree);
-    if (cudaMemsetAsync(ws.counter + 3, 0, sizeof(unsigned int), s) != cudaSuccess) return SVLF_ERR_CUDA;
-    if ((rc = launch_composite_backward(ws, n_rays, opts->bg, d_rgb, d_depth, s))) return rc;
-    const int64_t max_samples = n_rays * (int64_t)K;
-    const int fb = mlp->feat_dtype == SVLF_FEAT_BF16;
-    if (mlp->precision == SVLF_FP32)
-        return launch_mlp_backward_f32(md, T.depth, features, fb, mlp_params,
-                                       (const float *)ws.packed_w, rays, ws, max_samples,
-                                       d_features, d_mlp_params, s);
-    return launch_mlp_backward_tc(md, mlp->precision, T.depth, features, fb, ws.packed_w, rays, ws,
-                                  max_samples, d_features, d_mlp_params, s);
+    return backward_table(T, *mlp, *opts, workspace, d_features != nullptr, d_mlp_params != nullptr,
+                          (cudaStream_t)stream);
+}
+
+extern "C" int svlf_render_rays_batched(const svlf_scene *scenes, int n_scenes,
+                                        const svlf_mlp_desc *mlp, const svlf_render_opts *opts,
+                                        void *workspace, size_t ws_bytes, void *stream) {
+    SceneTable T;
+    int rc = make_table(scenes, n_scenes, mlp, opts, workspace, ws_bytes, false, T);
+    if (rc) return rc;
+    if (mlp->precision == SVLF_FP32 && n_scenes > 1) return SVLF_ERR_UNSUPPORTED;
+    return render_table(T, *mlp, *opts, workspace, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
+                                                 const svlf_mlp_desc *mlp,
+                                                 const svlf_render_opts *opts, void *workspace,
+                                                 size_t ws_bytes, void *stream) {
+    SceneTable T;
+    int rc = make_table(scenes, n_scenes, mlp, opts, workspace, ws_bytes, true, T);
+    if (rc) return rc;
+    if (mlp->precision == SVLF_FP32 && n_scenes > 1) return SVLF_ERR_UNSUPPORTED;
+    bool want_feat = false, want_params = false;
+    for (int i = 0; i < n_scenes; ++i) {
+        want_feat |= scenes[i].d_features != nullptr;
+        want_params |= scenes[i].d_mlp_params != nullptr;
+    }
+    for (int i = 0; i < n_scenes; ++i)  // a batched backward forms each gradient for all scenes or none
+        if ((want_feat && !scenes[i].d_features) || (want_params && !scenes[i].d_mlp_params))
+            if (scenes[i].n_rays > 0) return SVLF_ERR_ARG;
+    return backward_table(T, *mlp, *opts, workspace, want_feat, want_params, (cudaStream_t)stream);
 }
 
 extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc *mlp,
@@ -204,7 +316,7 @@ extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc
     }
     Workspace ws = carve_workspace(const_cast<void *>(workspace), *mlp, n_rays, K);
     unsigned int c = 0;
-    if (cudaMemcpyAsync(&c, ws.counter, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+    if (cudaMemcpyAsync(&c, ws.counter + kCtrScene, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
             cudaSuccess ||
         cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
         return SVLF_ERR_CUDA;

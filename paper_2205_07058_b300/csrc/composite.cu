@@ -7,13 +7,15 @@ namespace svlf {
 
 // C = sum_i T_i alpha_i c_i + T_{n+1} bg,  alpha_i = 1 - exp(-tau_i),
 // T_{i+1} = T_i exp(-tau_i);  D = sum_i T_i alpha_i tmid_i.
-__global__ void composite_kernel(const int2 *__restrict__ ray_span,
+__global__ void composite_kernel(const __grid_constant__ SceneTable Tb,
+                                 const int2 *__restrict__ ray_span,
                                  const Sample *__restrict__ samples,
-                                 const float4 *__restrict__ outputs, int64_t n_rays, float bg0,
-                                 float bg1, float bg2, float *__restrict__ rgb,
-                                 float *__restrict__ depth) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rays;
+                                 const float4 *__restrict__ outputs, float bg0, float bg1,
+                                 float bg2) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Tb.total_rays;
          r += (int64_t)gridDim.x * blockDim.x) {
+        const SceneDev &S = Tb.s[scene_of_ray(Tb, r)];
+        const int64_t rl = r - S.ray_begin;  // ray index within its scene
         const int2 sp = ray_span[r];
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
         for (int j = 0; j < sp.y; ++j) {
@@ -26,10 +28,10 @@ __global__ void composite_kernel(const int2 *__restrict__ ray_span,
             D = fmaf(w, tm, D);
             T *= expf(-o.w);
         }
-        rgb[3 * r + 0] = fmaf(T, bg0, C0);
-        rgb[3 * r + 1] = fmaf(T, bg1, C1);
-        rgb[3 * r + 2] = fmaf(T, bg2, C2);
-        depth[r] = D;
+        S.rgb[3 * rl + 0] = fmaf(T, bg0, C0);
+        S.rgb[3 * rl + 1] = fmaf(T, bg1, C1);
+        S.rgb[3 * rl + 2] = fmaf(T, bg2, C2);
+        S.depth[rl] = D;
     }
 }
 
@@ -41,21 +43,21 @@ __global__ void composite_kernel(const int2 *__restrict__ ray_span,
 // suffix sum of tau, so no division by a small transmittance is needed.
 // Then through the output activations: sigmoid'(x) = c (1 - c) for the colour
 // and the ReLU step (tau > 0) for the optical thickness.
-__global__ void composite_backward_kernel(const int2 *__restrict__ ray_span,
+__global__ void composite_backward_kernel(const __grid_constant__ SceneTable Tb,
+                                          const int2 *__restrict__ ray_span,
                                           const Sample *__restrict__ samples,
-                                          const float4 *__restrict__ outputs, int64_t n_rays,
-                                          float bg0, float bg1, float bg2,
-                                          const float *__restrict__ d_rgb,
-                                          const float *__restrict__ d_depth,
-                                          float4 *__restrict__ dout,
+                                          const float4 *__restrict__ outputs, float bg0,
+                                          float bg1, float bg2, float4 *__restrict__ dout,
                                           unsigned int *__restrict__ max_abs_bits) {
     float gmax = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rays;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Tb.total_rays;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int2 sp = ray_span[r];
         if (sp.y == 0) continue;
-        const float g0 = d_rgb[3 * r + 0], g1 = d_rgb[3 * r + 1], g2 = d_rgb[3 * r + 2];
-        const float gD = d_depth[r];
+        const SceneDev &S = Tb.s[scene_of_ray(Tb, r)];
+        const int64_t rl = r - S.ray_begin;
+        const float g0 = S.d_rgb[3 * rl + 0], g1 = S.d_rgb[3 * rl + 1], g2 = S.d_rgb[3 * rl + 2];
+        const float gD = S.d_depth[rl];
         float tau_sum = 0.f;
         for (int j = 0; j < sp.y; ++j) tau_sum += outputs[sp.x + j].w;
         const float Tn = expf(-tau_sum);
@@ -130,21 +132,20 @@ static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-int launch_composite(const Workspace &ws, int64_t n_rays, const float bg[3], float *rgb,
-                     float *depth, cudaStream_t s) {
+int launch_composite(const SceneTable &T, const Workspace &ws, const float bg[3], cudaStream_t s) {
     prof_begin("composite", s);
-    composite_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(ws.ray_span, ws.samples, ws.outputs,
-                                                           n_rays, bg[0], bg[1], bg[2], rgb, depth);
+    composite_kernel<<<grid_for(T.total_rays, 256), 256, 0, s>>>(T, ws.ray_span, ws.samples,
+                                                                 ws.outputs, bg[0], bg[1], bg[2]);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
-int launch_composite_backward(const Workspace &ws, int64_t n_rays, const float bg[3],
-                              const float *d_rgb, const float *d_depth, cudaStream_t s) {
+int launch_composite_backward(const SceneTable &T, const Workspace &ws, const float bg[3],
+                              cudaStream_t s) {
     prof_begin("composite_backward", s);
-    composite_backward_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(
-        ws.ray_span, ws.samples, ws.outputs, n_rays, bg[0], bg[1], bg[2], d_rgb, d_depth, ws.dout,
-        ws.counter + 3);
+    composite_backward_kernel<<<grid_for(T.total_rays, 256), 256, 0, s>>>(
+        T, ws.ray_span, ws.samples, ws.outputs, bg[0], bg[1], bg[2], ws.dout,
+        ws.counter + kCtrMaxAbsDout);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -75,13 +75,13 @@ __device__ __forceinline__ float4 output_activation(float o0, float o1, float o2
 namespace svlf {
 // tensor-core (tcgen05) network path, mlp_tc.cu
 bool tc_supported(const MlpDims &md);
+bool tc_backward_supported(const MlpDims &md);
 size_t packed_tc_bytes(const MlpDims &md);
-int launch_pack_tc(const MlpDims &md, int precision, const float *params, void *packed,
-                   cudaStream_t s);
-int launch_mlp_forward_tc(const MlpDims &md, int precision, int depth, const void *feats, int fb,
-                          const void *packed, const float *rays, const Workspace &ws,
-                          int64_t max_samples, cudaStream_t s);
-int launch_mlp_backward_tc(const MlpDims &md, int precision, int depth, const void *feats, int fb,
-                           const void *packed, const float *rays, const Workspace &ws,
-                           int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s);
+void set_tc_warpgroups(int n);
+int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *packed,
+                   size_t stride, cudaStream_t s);
+int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
+                          const Workspace &ws, cudaStream_t s);
+int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
+                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s);
 }  // namespace svlf

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
     float *X = reinterpret_cast<float *>(smem_f4);
     const int dmax = md.in0 > H ? md.in0 : H;
     float *Y = X + dmax * kTsF;
-    const int64_t S = min((int64_t)counter[0], max_samples);
+    const int64_t S = min((int64_t)counter[kCtrScene], max_samples);
     const int64_t n_tiles = (S + kTsF - 1) / kTsF;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t s0 = tile * kTsF;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     float *Dc = A[md.nh] + H * kPadB;  // delta of the current layer's output
     float *Dn = Dc + dmax * kPadB;     // delta one layer down (or dL/dz)
     __shared__ int s_leaf[kTsB];
-    const int64_t S = min((int64_t)counter[0], max_samples);
+    const int64_t S = min((int64_t)counter[kCtrScene], max_samples);
     const int64_t n_tiles = (S + kTsB - 1) / kTsB;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t s0 = tile * kTsB;

@@ -18,6 +18,11 @@
 //    thickness per sample.
 //  Warpgroups run independently, so the tensor core works on one tile while
 //  the others gather inputs or run their epilogues.
+//
+// Batched form: one launch serves every scene of a SceneTable. Each CTA takes
+// a contiguous range of the global tile list (scenes in order, tiles of 128
+// samples of one scene each) and walks it scene segment by scene segment,
+// reloading the resident weights only when the scene changes.
 #include <cstring>
 
 #include "svlf_internal.cuh"
@@ -99,12 +104,14 @@ __global__ void pack_tc_kernel(MlpDims md, TcLayout lay, int fp16, const float *
     }
 }
 
-int launch_pack_tc(const MlpDims &md, int precision, const float *params, void *packed,
-                   cudaStream_t s) {
+int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *packed,
+                   size_t stride, cudaStream_t s) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     const TcLayout lay = tc_layout(md);
     prof_begin("pack_weights_tc", s);
-    pack_tc_kernel<<<64, 256, 0, s>>>(md, lay, precision == SVLF_FP16, params, (uint8_t *)packed);
+    for (int i = 0; i < T.n; ++i)
+        pack_tc_kernel<<<32, 256, 0, s>>>(md, lay, precision == SVLF_FP16, T.s[i].params,
+                                          (uint8_t *)packed + i * stride);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
@@ -113,19 +120,40 @@ int launch_pack_tc(const MlpDims &md, int precision, const float *params, void *
 struct TcFwdParams {
     MlpDims md;
     TcLayout lay;
-    int depth;
     int fp16;
-    const void *feats;
     int feat_bf16;
-    const uint8_t *image;
-    const float *rays;
+    const uint8_t *images;  // packed weights, scene i at images + i * image_stride
+    size_t image_stride;
     const Sample *samples;
     const unsigned int *counter;
-    int64_t max_samples;
     float4 *outputs;
     int n_wg;            // warpgroups per CTA
     uint32_t abuf_bytes; // activation buffer per warpgroup
 };
+
+// Per-CTA view of the global tile list: scene s owns global tiles
+// [tile0[s], tile0[s+1]); its tile t covers its samples [t*128, t*128+128) of
+// the S[s] it wrote, which start at global sample index K * ray_begin_s.
+struct TileMap {
+    int64_t tile0[kMaxScenes + 1];
+    int64_t S[kMaxScenes];
+};
+
+__device__ __forceinline__ void tile_map_build(const SceneTable &T, const unsigned int *counter,
+                                               TileMap &m) {
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < T.n; ++i) {
+            const int64_t cap = T.s[i].n_rays * (int64_t)T.K;
+            const int64_t Si = min((int64_t)counter[kCtrScene + i], cap);
+            m.S[i] = Si;
+            m.tile0[i] = acc;
+            acc += (Si + kTcTile - 1) / kTcTile;
+        }
+        m.tile0[T.n] = acc;
+    }
+    __syncthreads();
+}
 
 // Store one 16-bit row chunk (8 values packed in 4 words) at column block kb.
 __device__ __forceinline__ void st_chunk(uint8_t *abuf, int row, int kb, uint32_t a, uint32_t b,
@@ -139,15 +167,16 @@ __device__ __forceinline__ void st_chunk(uint8_t *abuf, int row, int kb, uint32_
 // chunks of ray direction and entry/exit parameters, zero chunks up to K0.
 __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, int depth,
                                                    const void *feats, int feat_bf16,
-                                                   const float *rays, const Sample *samples,
-                                                   int64_t s, bool valid, int fp16, uint8_t *abuf,
-                                                   int row, int *leaf_out) {
+                                                   const float *rays, int64_t ray_begin,
+                                                   const Sample *samples, int64_t s, bool valid,
+                                                   int fp16, uint8_t *abuf, int row,
+                                                   int *leaf_out) {
     const int F = md.F;
     int kb = 0;
     if (valid) {
         const Sample sm = samples[s];
         if (leaf_out) *leaf_out = sm.leaf;
-        const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * (int64_t)sm.ray);
+        const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
         const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
         if (feat_bf16) {
             const uint4 *src = reinterpret_cast<const uint4 *>(
@@ -185,12 +214,14 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
 }
 
 template <int H>
-__global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParams P) {
+__global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const __grid_constant__ SceneTable T,
+                                                                const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t s_mbar[5];  // [0..3] per warpgroup, [4] weight load
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
+    __shared__ TileMap s_map;
 
     const int tid = threadIdx.x;
     const int wg = tid >> 7;        // warpgroup
@@ -211,20 +242,7 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParam
         tc::tmem_relinquish();
     }
     __syncthreads();
-    // resident weights: bulk copies into shared memory
-    if (tid == 0) {
-        const uint32_t mb = tc::smem_u32(&s_mbar[4]);
-        tc::mbar_expect_tx(mb, P.lay.bytes);
-        for (uint32_t off = 0; off < P.lay.bytes; off += 32768u) {
-            const uint32_t n = min(32768u, P.lay.bytes - off);
-            tc::bulk_g2s(tc::smem_u32(wimg + off), P.image + off, n, mb);
-        }
-    }
-    if (!tc::mbar_wait(tc::smem_u32(&s_mbar[4]), 0)) {
-        raise_status(SVLF_DEV_WAIT_TIMEOUT);
-        atomicExch(&s_abort, 1);
-    }
-    __syncthreads();
+    tile_map_build(T, P.counter, s_map);
     tc::fence_after_sync();
     const uint32_t tmem_base = s_tmem;
     const uint32_t tmem_wg = tmem_base + (uint32_t)(wg * 128);            // column base
@@ -233,73 +251,107 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const TcFwdParam
     const uint32_t abuf_s = tc::smem_u32(abuf);
     const uint32_t wimg_s = tc::smem_u32(wimg);
     const int bf16 = P.fp16 ? 0 : 1;
-    uint32_t phase = 0;
+    uint32_t phase = 0, wphase = 0;
 
-    const int64_t S = min((int64_t)P.counter[0], P.max_samples);
-    const int64_t n_tiles = (S + kTcTile - 1) / kTcTile;
-    bool aborted = s_abort != 0;
-    for (int64_t tile = (int64_t)blockIdx.x * P.n_wg + wg; !aborted && tile < n_tiles;
-         tile += (int64_t)gridDim.x * P.n_wg) {
-        const int64_t s = tile * kTcTile + row;
-        // ---- network input row -> A operand (K0 columns)
-        build_input_chunks(P.md, P.lay.K0, P.depth, P.feats, P.feat_bf16, P.rays, P.samples, s,
-                           s < S, P.fp16, abuf, row, nullptr);
-        for (int l = 0; l < P.lay.n_layers; ++l) {
-            const int N = P.lay.w_rows[l];
-            const int Kl = P.lay.w_cols[l];
-            // A operand written by all threads -> visible to the tensor core
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            tc::wg_sync_or(wg, false);
-            if (row == 0) {
-                tc::fence_after_sync();
-                const uint32_t idesc = tc::idesc_f16(kTcTile, N, bf16, 0, 0);
-                const uint32_t b_base = wimg_s + P.lay.w_off[l];
-                for (int k = 0; k < Kl; k += 16) {
-                    const uint64_t da = tc::sdesc(abuf_s + (k >> 3) * (kTcTile * 16), kTcTile * 16, 128);
-                    const uint64_t db = tc::sdesc(b_base + (k >> 3) * (N * 16), N * 16, 128);
-                    tc::mma_f16(tmem_wg, da, db, idesc, k > 0 ? 1u : 0u);
-                }
-                tc::mma_commit(mbar);
-            }
-            const bool timeout = !tc::mbar_wait(mbar, phase);
-            phase ^= 1u;
-            if (tc::wg_sync_or(wg, timeout)) {
-                if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
-                aborted = true;
-                break;
-            }
-            tc::fence_after_sync();
-            const float *b = bias + P.lay.bias_l[l];
-            if (l + 1 < P.lay.n_layers) {
-                // hidden layer epilogue: bias + ReLU -> 16-bit A operand of the next layer
-#pragma unroll
-                for (int c = 0; c < H / 32; ++c) {
-                    uint32_t v[32];
-                    tc::tmem_ld32(tmem_row + (uint32_t)(c * 32), v);
-                    tc::tmem_wait_ld();
-                    uint32_t p[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const float x0 = fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f);
-                        const float x1 = fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f);
-                        p[e] = tc::pack2(x0, x1, P.fp16);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        st_chunk(abuf, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
-                }
-            } else {
-                uint32_t v[4];
-                tc::tmem_ld4(tmem_row, v);
-                tc::tmem_wait_ld();
-                if (s < S)
-                    P.outputs[s] = output_activation(__uint_as_float(v[0]) + b[0], __uint_as_float(v[1]) + b[1],
-                                                     __uint_as_float(v[2]) + b[2], __uint_as_float(v[3]) + b[3]);
-            }
+    // this CTA's contiguous range of the global tile list
+    const int64_t n_tiles = s_map.tile0[T.n];
+    const int64_t lo = n_tiles * blockIdx.x / gridDim.x;
+    const int64_t hi = n_tiles * (blockIdx.x + 1) / gridDim.x;
+    int sc = 0;
+    while (sc + 1 < T.n && s_map.tile0[sc + 1] <= lo) ++sc;
+    for (int64_t seg = lo; seg < hi; ++sc) {
+        const int64_t seg_end = min(hi, s_map.tile0[sc + 1]);
+        if (seg_end <= seg) continue;
+        const SceneDev &SD = T.s[sc];
+        // resident weights of this scene: bulk copies into shared memory
+        __syncthreads();
+        if (s_abort) break;  // uniform: read after the barrier
+        if (tid == 0) {
+            const uint32_t mb = tc::smem_u32(&s_mbar[4]);
+            const uint8_t *img = P.images + sc * P.image_stride;
+            tc::mbar_expect_tx(mb, P.lay.bytes);
+            for (uint32_t off = 0; off < P.lay.bytes; off += 32768u)
+                tc::bulk_g2s(tc::smem_u32(wimg + off), img + off, min(32768u, P.lay.bytes - off), mb);
         }
-        // all TMEM reads of this tile are done before the next tile's MMAs
-        tc::fence_before_sync();
+        if (!tc::mbar_wait(tc::smem_u32(&s_mbar[4]), wphase)) {
+            raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            atomicExch(&s_abort, 1);
+        }
+        wphase ^= 1u;
+        __syncthreads();
+        tc::fence_after_sync();
+        if (s_abort) break;
+        const int64_t S_sc = s_map.S[sc];
+        const int64_t sbase = SD.ray_begin * T.K;  // the scene's first sample slot
+        const int depth = SD.tree.depth;
+        bool aborted = false;
+        for (int64_t tile = seg + wg; !aborted && tile < seg_end; tile += P.n_wg) {
+            const int64_t sl = (tile - s_map.tile0[sc]) * kTcTile + row;  // sample within the scene
+            const int64_t s = sbase + sl;
+            // ---- network input row -> A operand (K0 columns)
+            build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                               P.samples, s, sl < S_sc, P.fp16, abuf, row, nullptr);
+            for (int l = 0; l < P.lay.n_layers; ++l) {
+                const int N = P.lay.w_rows[l];
+                const int Kl = P.lay.w_cols[l];
+                // A operand written by all threads -> visible to the tensor core
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                tc::wg_sync_or(wg, false);
+                if (row == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t idesc = tc::idesc_f16(kTcTile, N, bf16, 0, 0);
+                    const uint32_t b_base = wimg_s + P.lay.w_off[l];
+                    for (int k = 0; k < Kl; k += 16) {
+                        const uint64_t da = tc::sdesc(abuf_s + (k >> 3) * (kTcTile * 16), kTcTile * 16, 128);
+                        const uint64_t db = tc::sdesc(b_base + (k >> 3) * (N * 16), N * 16, 128);
+                        tc::mma_f16(tmem_wg, da, db, idesc, k > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(mbar);
+                }
+                const bool timeout = !tc::mbar_wait(mbar, phase);
+                phase ^= 1u;
+                if (tc::wg_sync_or(wg, timeout)) {
+                    if (row == 0) {
+                        raise_status(SVLF_DEV_WAIT_TIMEOUT);
+                        atomicExch(&s_abort, 1);
+                    }
+                    aborted = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const float *b = bias + P.lay.bias_l[l];
+                if (l + 1 < P.lay.n_layers) {
+                    // hidden layer epilogue: bias + ReLU -> 16-bit A operand of the next layer
+#pragma unroll
+                    for (int c = 0; c < H / 32; ++c) {
+                        uint32_t v[32];
+                        tc::tmem_ld32(tmem_row + (uint32_t)(c * 32), v);
+                        tc::tmem_wait_ld();
+                        uint32_t p[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float x0 = fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f);
+                            const float x1 = fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f);
+                            p[e] = tc::pack2(x0, x1, P.fp16);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            st_chunk(abuf, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+                    }
+                } else {
+                    uint32_t v[4];
+                    tc::tmem_ld4(tmem_row, v);
+                    tc::tmem_wait_ld();
+                    if (sl < S_sc)
+                        P.outputs[s] = output_activation(__uint_as_float(v[0]) + b[0], __uint_as_float(v[1]) + b[1],
+                                                         __uint_as_float(v[2]) + b[2], __uint_as_float(v[3]) + b[3]);
+                }
+            }
+            // all TMEM reads of this tile are done before the next tile's MMAs
+            tc::fence_before_sync();
+        }
+        seg = seg_end;
     }
     __syncthreads();
     if (warp == 0) {
@@ -323,8 +375,8 @@ static int tc_forward_config(const MlpDims &md, const TcLayout &lay, int &n_wg, 
 }
 
 template <int H>
-static int fwd_tc(const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay, cudaStream_t s,
-                  int n_wg_override) {
+static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay,
+                  cudaStream_t s, int n_wg_override) {
     TcFwdParams P = P0;
     size_t smem;
     int rc = tc_forward_config(md, lay, P.n_wg, P.abuf_bytes, smem);
@@ -334,32 +386,30 @@ static int fwd_tc(const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     prof_begin("mlp_forward_tc", s);
-    mlp_forward_tc_kernel<H><<<num_sms(), 128 * P.n_wg, smem, s>>>(P);
+    mlp_forward_tc_kernel<H><<<num_sms(), 128 * P.n_wg, smem, s>>>(T, P);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
 static int g_tc_wg_override = 0;
 
-int launch_mlp_forward_tc(const MlpDims &md, int precision, int depth, const void *feats, int fb,
-                          const void *packed, const float *rays, const Workspace &ws,
-                          int64_t max_samples, cudaStream_t s) {
+void set_tc_warpgroups(int n) { g_tc_wg_override = n; }
+
+int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
+                          const Workspace &ws, cudaStream_t s) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcFwdParams P;
     memset(&P, 0, sizeof(P));
     P.md = md;
     P.lay = tc_layout(md);
-    P.depth = depth;
     P.fp16 = precision == SVLF_FP16;
-    P.feats = feats;
     P.feat_bf16 = fb;
-    P.image = (const uint8_t *)packed;
-    P.rays = rays;
+    P.images = (const uint8_t *)ws.packed_w;
+    P.image_stride = ws.packed_stride;
     P.samples = ws.samples;
     P.counter = ws.counter;
-    P.max_samples = max_samples;
     P.outputs = ws.outputs;
-    return fwd_tc<kHp>(P, md, P.lay, s, g_tc_wg_override);
+    return fwd_tc<kHp>(T, P, md, P.lay, s, g_tc_wg_override);
 }
 
 // ---------------------------------------------------------------- backward
@@ -389,16 +439,13 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int depth, const voi
 struct TcBwdParams {
     MlpDims md;
     TcLayout lay;
-    int depth, fp16, feat_bf16;
-    const void *feats;
-    const uint8_t *image;
-    const float *rays;
+    int fp16, feat_bf16;
+    int want_feat, want_params;  // which gradients to form
+    const uint8_t *images;
+    size_t image_stride;
     const Sample *samples;
     const unsigned int *counter;
-    int64_t max_samples;
     const float4 *dout;
-    float *d_feat;
-    float *d_params;
     uint32_t x_off[kMaxLayers];  // X_l buffers (byte offsets after the weight image)
     uint32_t gout_off, ones_off;
     uint32_t col_dwout, col_dw[kMaxLayers], col_db[kMaxLayers], tmem_cols;
@@ -451,12 +498,14 @@ __device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32
     }
 }
 
-__global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdParams P) {
+__global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_constant__ SceneTable T,
+                                                                 const TcBwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t s_mbar[2];  // [0] MMA commits, [1] weight load
     __shared__ uint32_t s_tmem;
     __shared__ float s_dbout[4];
+    __shared__ TileMap s_map;
 
     const int row = threadIdx.x;  // sample within the tile = TMEM lane
     const int warp = row >> 5, lane = row & 31;
@@ -471,7 +520,6 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdPara
         tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
         tc::mbar_init_fence();
     }
-    if (row < 4) s_dbout[row] = 0.f;
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&s_tmem), P.tmem_cols);
         tc::tmem_relinquish();
@@ -483,33 +531,23 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdPara
         for (int i = row; i < kTcOutN * kTcTile * 2 / 16; i += 128) o[i] = make_uint4(one2, one2, one2, one2);
     }
     __syncthreads();
-    if (row == 0) {
-        const uint32_t mb = tc::smem_u32(&s_mbar[1]);
-        tc::mbar_expect_tx(mb, lay.bytes);
-        for (uint32_t off = 0; off < lay.bytes; off += 32768u)
-            tc::bulk_g2s(tc::smem_u32(wimg + off), P.image + off, min(32768u, lay.bytes - off), mb);
-    }
-    bool aborted = !tc::mbar_wait(tc::smem_u32(&s_mbar[1]), 0);
-    aborted = tc::wg_sync_or(0, aborted);
-    if (aborted && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+    tile_map_build(T, P.counter, s_map);
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     const uint32_t mbar = tc::smem_u32(&s_mbar[0]);
     const int bf16 = P.fp16 ? 0 : 1;
     const int nh = md.nh;
-    uint32_t phase = 0;
-    int tiles_done = 0;
-
-    const int64_t S = min((int64_t)P.counter[0], P.max_samples);
-    const int64_t n_tiles = (S + kTcTile - 1) / kTcTile;
     const int Fn = (md.F + 15) & ~15;
+    uint32_t phase = 0, wphase = 0;
+    bool aborted = false;
+
     float gscale = 1.f;
     if (P.fp16) {
-        const float gmax = __uint_as_float(P.counter[3]);
+        const float gmax = __uint_as_float(P.counter[kCtrMaxAbsDout]);
         if (gmax > 0.f && isfinite(gmax)) {
             int e;
-            frexpf(gmax, &e);                          // gmax in [2^(e-1), 2^e)
+            frexpf(gmax, &e);                                 // gmax in [2^(e-1), 2^e)
             gscale = ldexpf(1.f, max(-60, min(60, 12 - e)));  // largest |delta_out| -> [2^11, 2^12)
         }
     }
@@ -529,203 +567,238 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const TcBwdPara
         phase ^= 1u;
         const bool any = tc::wg_sync_or(0, to);
         tc::fence_after_sync();
+        if (any && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
         return !any;
     };
 
-    for (int64_t tile = blockIdx.x; !aborted && tile < n_tiles; tile += gridDim.x) {
-        const int64_t s = tile * kTcTile + row;
-        const bool valid = s < S;
-        int leaf = -1;
-        // ---- 1. X_0 and G_out
-        {
-            build_input_chunks(md, lay.K0, P.depth, P.feats, P.feat_bf16, P.rays, P.samples, s, valid,
-                               P.fp16, smem + P.x_off[0], row, &leaf);
-            const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-            uint8_t *go = smem + P.gout_off;
-            st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
-                     tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
-            st_chunk(go, row, 1, 0u, 0u, 0u, 0u);
-            // bias gradient of the output layer: warp sums, then shared atomics
-            float gs[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float v = gs[c];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                if (lane == 0) atomicAdd(&s_dbout[c], v);
-            }
+    const int64_t n_tiles = s_map.tile0[T.n];
+    const int64_t lo = n_tiles * blockIdx.x / gridDim.x;
+    const int64_t hi = n_tiles * (blockIdx.x + 1) / gridDim.x;
+    int sc = 0;
+    while (sc + 1 < T.n && s_map.tile0[sc + 1] <= lo) ++sc;
+    for (int64_t seg = lo; seg < hi && !aborted; ++sc) {
+        const int64_t seg_end = min(hi, s_map.tile0[sc + 1]);
+        if (seg_end <= seg) continue;
+        const SceneDev &SD = T.s[sc];
+        // this scene's resident weights
+        __syncthreads();
+        if (row < 4) s_dbout[row] = 0.f;
+        if (row == 0) {
+            const uint32_t mb = tc::smem_u32(&s_mbar[1]);
+            const uint8_t *img = P.images + sc * P.image_stride;
+            tc::mbar_expect_tx(mb, lay.bytes);
+            for (uint32_t off = 0; off < lay.bytes; off += 32768u)
+                tc::bulk_g2s(tc::smem_u32(wimg + off), img + off, min(32768u, lay.bytes - off), mb);
         }
-        // ---- 2. forward recompute: X_{l+1} = relu(W_l X_l + b_l)
-        for (int l = 0; l < nh && !aborted; ++l) {
-            const int Kl = l == 0 ? lay.K0 : kHp;
-            const uint32_t xa = s_base + P.x_off[l];
-            const uint32_t wb = s_base + lay.w_off[l];
-            if (!run([&] {
-                    mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
-                            128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), false);
-                })) {
-                aborted = true;
-                break;
-            }
-            const float *b = bias + lay.bias_l[l];
-            uint8_t *xn = smem + P.x_off[l + 1];
-#pragma unroll 1
-            for (int c = 0; c < kHp / 32; ++c) {
-                uint32_t v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
-                tc::tmem_wait_ld();
-                uint32_t p[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    p[e] = tc::pack2(fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f),
-                                     fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f),
-                                     P.fp16);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    st_chunk(xn, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
-            }
-            tc::fence_before_sync();
+        aborted = tc::wg_sync_or(0, !tc::mbar_wait(tc::smem_u32(&s_mbar[1]), wphase));
+        wphase ^= 1u;
+        tc::fence_after_sync();
+        if (aborted) {
+            if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            break;
         }
-        if (aborted) break;
-        const bool acc = tiles_done > 0;
-        // ---- 3. output layer: dW_out^T += X_nh^T G_out ; G_nh = G_out W_out (masked)
-        {
-            const uint32_t xa = s_base + P.x_off[nh];
-            const uint32_t go = s_base + P.gout_off;
-            const uint32_t wo = s_base + lay.w_off[nh];
-            if (!run([&] {
-                    mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
-                            kTcTile, tc::idesc_f16(kHp, kTcOutN, bf16, 1, 1), acc);
-                    mma_seq(tmem, go, 0, kTcTile * 16, 128, wo, 0, 128, kTcOutN * 16, kTcOutN,
-                            tc::idesc_f16(kTcTile, kHp, bf16, 0, 1), false);
-                })) {
-                aborted = true;
-                break;
-            }
-        }
-        // masked delta of the last hidden layer, in place of X_nh
-        auto mask_epilogue = [&](int l) {
-            uint8_t *x = smem + P.x_off[l];
-#pragma unroll 1
-            for (int c = 0; c < kHp / 32; ++c) {
-                uint32_t v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
-                tc::tmem_wait_ld();
+        const int64_t S_sc = s_map.S[sc];
+        const int64_t sbase = SD.ray_begin * T.K;
+        const int depth = SD.tree.depth;
+        float *d_feat = P.want_feat ? SD.d_feat : nullptr;
+        int tiles_done = 0;
+        for (int64_t tile = seg; !aborted && tile < seg_end; ++tile) {
+            const int64_t sl = (tile - s_map.tile0[sc]) * kTcTile + row;
+            const int64_t s = sbase + sl;
+            const bool valid = sl < S_sc;
+            int leaf = -1;
+            // ---- 1. X_0 and G_out
+            {
+                build_input_chunks(md, lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                                   P.samples, s, valid, P.fp16, smem + P.x_off[0], row, &leaf);
+                const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                uint8_t *go = smem + P.gout_off;
+                st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
+                         tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
+                st_chunk(go, row, 1, 0u, 0u, 0u, 0u);
+                // bias gradient of the output layer: warp sums, then shared atomics
+                float gs[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 *ptr = reinterpret_cast<uint4 *>(x + (c * 4 + q) * (kTcTile * 16) +
-                                                           (row >> 3) * 128 + (row & 7) * 16);
-                    const uint4 xv = *ptr;
-                    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-                    uint32_t o[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        // a 16-bit activation is positive iff its sign bit is clear and it is non-zero
-                        const uint32_t lo = xw[e] & 0xFFFFu, hi = xw[e] >> 16;
-                        const float g0 = (lo != 0u && !(lo & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e]) : 0.f;
-                        const float g1 = (hi != 0u && !(hi & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e + 1]) : 0.f;
-                        o[e] = tc::pack2(g0, g1, P.fp16);
-                    }
-                    *ptr = make_uint4(o[0], o[1], o[2], o[3]);
+                for (int c = 0; c < 4; ++c) {
+                    float v = gs[c];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                    if (lane == 0) atomicAdd(&s_dbout[c], v);
                 }
             }
-            tc::fence_before_sync();
-        };
-        mask_epilogue(nh);
-        // ---- 4. hidden layers, from the top down
-        for (int l = nh - 1; l >= 0 && !aborted; --l) {
-            const uint32_t g = s_base + P.x_off[l + 1];  // G_{l+1} (delta of layer l's output)
-            const uint32_t xa = s_base + P.x_off[l];
-            const uint32_t wb = s_base + lay.w_off[l];
-            const int Nin = l == 0 ? lay.K0 : kHp;
-            const bool want_dx = l > 0 || P.d_feat != nullptr;
-            const int Ndx = l > 0 ? kHp : Fn;
-            if (!run([&] {
-                    // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
-                    mma_seq(tmem + P.col_dw[l], g, 256, 128, kTcTile * 16, xa, 256, 128, kTcTile * 16,
-                            kTcTile, tc::idesc_f16(kHp, Nin, bf16, 1, 1), acc);
-                    // db_l += G^T 1
-                    mma_seq(tmem + P.col_db[l], g, 256, 128, kTcTile * 16, s_base + P.ones_off,
-                            2 * kTcOutN * 16, kTcOutN * 16, 128, kTcTile,
-                            tc::idesc_f16(kHp, kTcOutN, bf16, 1, 0), acc);
-                    // G_l = G W_l  (A: G K-major, B: W_l MN-major)
-                    if (want_dx)
-                        mma_seq(tmem, g, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 256, 128, kHp * 16,
-                                kHp, tc::idesc_f16(kTcTile, Ndx, bf16, 0, 1), false);
-                })) {
-                aborted = true;
-                break;
-            }
-            if (l > 0) {
-                mask_epilogue(l);
-            } else if (P.d_feat) {
-                // dL/dz: stage rows in shared memory (X_1's buffer is free now)
-                float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
-                const int F = md.F;
-                for (int c = 0; c < Fn; c += 16) {
-                    uint32_t v[16];
-                    tc::tmem_ld16(tmem + lane_off + (uint32_t)c, v);
+            // ---- 2. forward recompute: X_{l+1} = relu(W_l X_l + b_l)
+            for (int l = 0; l < nh && !aborted; ++l) {
+                const int Kl = l == 0 ? lay.K0 : kHp;
+                const uint32_t xa = s_base + P.x_off[l];
+                const uint32_t wb = s_base + lay.w_off[l];
+                if (!run([&] {
+                        mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
+                                128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), false);
+                    })) {
+                    aborted = true;
+                    break;
+                }
+                const float *b = bias + lay.bias_l[l];
+                uint8_t *xn = smem + P.x_off[l + 1];
+#pragma unroll 1
+                for (int c = 0; c < kHp / 32; ++c) {
+                    uint32_t v[32];
+                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
                     tc::tmem_wait_ld();
-                    for (int e = 0; e < 16 && c + e < F; ++e) stage[row * F + c + e] = __uint_as_float(v[e]) * ginv;
+                    uint32_t p[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        p[e] = tc::pack2(fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f),
+                                         fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f),
+                                         P.fp16);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        st_chunk(xn, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
                 }
                 tc::fence_before_sync();
-                __syncwarp();
-                // warp-aggregated scatter: the lowest lane of each group of equal leaves sums it
-                const unsigned act = __ballot_sync(0xFFFFFFFFu, leaf >= 0);
-                const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
-                if (leaf >= 0 && (grp & act) && lane == __ffs(grp) - 1) {
-                    float4 *dst = reinterpret_cast<float4 *>(P.d_feat + (int64_t)leaf * F);
-                    for (int f4 = 0; f4 < F / 4; ++f4) {
-                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                        unsigned m = grp;
-                        while (m) {
-                            const int src = (warp << 5) + __ffs(m) - 1;
-                            m &= m - 1;
-                            const float4 v = *reinterpret_cast<const float4 *>(stage + src * F + 4 * f4);
-                            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+            }
+            if (aborted) break;
+            const bool acc = tiles_done > 0;
+            // ---- 3. output layer: dW_out^T += X_nh^T G_out ; G_nh = G_out W_out (masked)
+            {
+                const uint32_t xa = s_base + P.x_off[nh];
+                const uint32_t go = s_base + P.gout_off;
+                const uint32_t wo = s_base + lay.w_off[nh];
+                if (!run([&] {
+                        mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
+                                kTcTile, tc::idesc_f16(kHp, kTcOutN, bf16, 1, 1), acc);
+                        mma_seq(tmem, go, 0, kTcTile * 16, 128, wo, 0, 128, kTcOutN * 16, kTcOutN,
+                                tc::idesc_f16(kTcTile, kHp, bf16, 0, 1), false);
+                    })) {
+                    aborted = true;
+                    break;
+                }
+            }
+            // masked delta in place of the layer input X_l
+            auto mask_epilogue = [&](int l) {
+                uint8_t *x = smem + P.x_off[l];
+#pragma unroll 1
+                for (int c = 0; c < kHp / 32; ++c) {
+                    uint32_t v[32];
+                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 *ptr = reinterpret_cast<uint4 *>(x + (c * 4 + q) * (kTcTile * 16) +
+                                                               (row >> 3) * 128 + (row & 7) * 16);
+                        const uint4 xv = *ptr;
+                        const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+                        uint32_t o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            // a 16-bit activation is positive iff its sign bit is clear and it is non-zero
+                            const uint32_t lo16 = xw[e] & 0xFFFFu, hi16 = xw[e] >> 16;
+                            const float g0 = (lo16 != 0u && !(lo16 & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e]) : 0.f;
+                            const float g1 = (hi16 != 0u && !(hi16 & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e + 1]) : 0.f;
+                            o[e] = tc::pack2(g0, g1, P.fp16);
                         }
-                        atomicAdd(dst + f4, a);
+                        *ptr = make_uint4(o[0], o[1], o[2], o[3]);
                     }
                 }
-                __syncwarp();
+                tc::fence_before_sync();
+            };
+            mask_epilogue(nh);
+            // ---- 4. hidden layers, from the top down
+            for (int l = nh - 1; l >= 0 && !aborted; --l) {
+                const uint32_t g = s_base + P.x_off[l + 1];  // G_{l+1} (delta of layer l's output)
+                const uint32_t xa = s_base + P.x_off[l];
+                const uint32_t wb = s_base + lay.w_off[l];
+                const int Nin = l == 0 ? lay.K0 : kHp;
+                const bool want_dx = l > 0 || d_feat != nullptr;
+                const int Ndx = l > 0 ? kHp : Fn;
+                if (!run([&] {
+                        // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
+                        mma_seq(tmem + P.col_dw[l], g, 256, 128, kTcTile * 16, xa, 256, 128, kTcTile * 16,
+                                kTcTile, tc::idesc_f16(kHp, Nin, bf16, 1, 1), acc);
+                        // db_l += G^T 1
+                        mma_seq(tmem + P.col_db[l], g, 256, 128, kTcTile * 16, s_base + P.ones_off,
+                                2 * kTcOutN * 16, kTcOutN * 16, 128, kTcTile,
+                                tc::idesc_f16(kHp, kTcOutN, bf16, 1, 0), acc);
+                        // G_l = G W_l  (A: G K-major, B: W_l MN-major)
+                        if (want_dx)
+                            mma_seq(tmem, g, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 256, 128, kHp * 16,
+                                    kHp, tc::idesc_f16(kTcTile, Ndx, bf16, 0, 1), false);
+                    })) {
+                    aborted = true;
+                    break;
+                }
+                if (l > 0) {
+                    mask_epilogue(l);
+                } else if (d_feat) {
+                    // dL/dz: stage rows in shared memory (X_1's buffer is free now)
+                    float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
+                    const int F = md.F;
+                    for (int c = 0; c < Fn; c += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(tmem + lane_off + (uint32_t)c, v);
+                        tc::tmem_wait_ld();
+                        for (int e = 0; e < 16 && c + e < F; ++e) stage[row * F + c + e] = __uint_as_float(v[e]) * ginv;
+                    }
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    // warp-aggregated scatter: the lowest lane of each group of equal leaves sums it
+                    const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
+                    if (leaf >= 0 && lane == __ffs(grp) - 1) {
+                        float4 *dst = reinterpret_cast<float4 *>(d_feat + (int64_t)leaf * F);
+                        for (int f4 = 0; f4 < F / 4; ++f4) {
+                            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                            unsigned m = grp;
+                            while (m) {
+                                const int src = (warp << 5) + __ffs(m) - 1;
+                                m &= m - 1;
+                                const float4 v = *reinterpret_cast<const float4 *>(stage + src * F + 4 * f4);
+                                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                            }
+                            atomicAdd(dst + f4, a);
+                        }
+                    }
+                    __syncwarp();
+                }
             }
+            if (!aborted) ++tiles_done;
         }
-        ++tiles_done;
-    }
-    // ---- flush the TMEM gradient accumulators (one atomic per element per CTA)
-    __syncthreads();
-    tc::fence_after_sync();
-    if (!aborted && tiles_done > 0 && P.d_params) {
-        const int H = md.H;
-        // dW_out^T: lane = input feature k, columns = output j (< 4)
-        {
-            uint32_t v[16];
-            tc::tmem_ld16(tmem + lane_off + P.col_dwout, v);
-            tc::tmem_wait_ld();
-            if (row < H) {
-                float *dW = P.d_params + md.w_off[nh];
-                for (int j = 0; j < 4; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
-            }
-            if (row < 4) atomicAdd(P.d_params + md.w_off[nh] + 4 * H + row, s_dbout[row]);
-        }
-        for (int l = 0; l < nh; ++l) {
-            const int in = md.in_l[l];
-            const int ncol = l == 0 ? lay.K0 : kHp;
-            float *dW = P.d_params + md.w_off[l];
-            for (int c = 0; c < ncol; c += 16) {
+        // ---- flush this scene's TMEM gradient accumulators (one atomic per element)
+        __syncthreads();
+        tc::fence_after_sync();
+        if (!aborted && tiles_done > 0 && P.want_params) {
+            const int H = md.H;
+            float *dpar = SD.d_params;
+            // dW_out^T: lane = input feature k, columns = output j (< 4)
+            {
                 uint32_t v[16];
-                tc::tmem_ld16(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
+                tc::tmem_ld16(tmem + lane_off + P.col_dwout, v);
                 tc::tmem_wait_ld();
-                if (row < H)
-                    for (int e = 0; e < 16; ++e)
-                        if (c + e < in) atomicAdd(dW + row * in + c + e, __uint_as_float(v[e]) * ginv);
+                if (row < H) {
+                    float *dW = dpar + md.w_off[nh];
+                    for (int j = 0; j < 4; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
+                }
+                if (row < 4) atomicAdd(dpar + md.w_off[nh] + 4 * H + row, s_dbout[row]);
             }
-            uint32_t v[4];
-            tc::tmem_ld4(tmem + lane_off + P.col_db[l], v);
-            tc::tmem_wait_ld();
-            if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
+            for (int l = 0; l < nh; ++l) {
+                const int in = md.in_l[l];
+                const int ncol = l == 0 ? lay.K0 : kHp;
+                float *dW = dpar + md.w_off[l];
+                for (int c = 0; c < ncol; c += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
+                    tc::tmem_wait_ld();
+                    if (row < H)
+                        for (int e = 0; e < 16; ++e)
+                            if (c + e < in) atomicAdd(dW + row * in + c + e, __uint_as_float(v[e]) * ginv);
+                }
+                uint32_t v[4];
+                tc::tmem_ld4(tmem + lane_off + P.col_db[l], v);
+                tc::tmem_wait_ld();
+                if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
+            }
         }
+        tc::fence_before_sync();
+        seg = seg_end;
     }
-    tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
@@ -742,9 +815,8 @@ bool tc_backward_supported(const MlpDims &md) {
     return tc_bwd_plan(md, P, smem);
 }
 
-int launch_mlp_backward_tc(const MlpDims &md, int precision, int depth, const void *feats, int fb,
-                           const void *packed, const float *rays, const Workspace &ws,
-                           int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
+int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
+                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcBwdParams P;
     memset(&P, 0, sizeof(P));
@@ -752,24 +824,21 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int depth, const vo
     P.lay = tc_layout(md);
     size_t smem;
     if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
-    P.depth = depth;
     P.fp16 = precision == SVLF_FP16;
     P.feat_bf16 = fb;
-    P.feats = feats;
-    P.image = (const uint8_t *)packed;
-    P.rays = rays;
+    P.want_feat = want_feat;
+    P.want_params = want_params;
+    P.images = (const uint8_t *)ws.packed_w;
+    P.image_stride = ws.packed_stride;
     P.samples = ws.samples;
     P.counter = ws.counter;
-    P.max_samples = max_samples;
     P.dout = ws.dout;
-    P.d_feat = d_feat;
-    P.d_params = d_params;
     if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
     if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     prof_begin("mlp_backward_tc", s);
-    mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(P);
+    mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(T, P);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -52,19 +52,77 @@ struct __align__(16) Sample {
     float tmid;
 };
 
-// Workspace layout (byte offsets from a 256-aligned base).
+// ---------------------------------------------------------------- scenes
+// One render / backward call covers up to kMaxScenes scenes, each with its
+// own octree, features, network parameters, rays and outputs (the batched
+// form; a single-scene call is a table of one). The table travels by value
+// as a kernel parameter, so a call needs no host-to-device copy and can be
+// captured in a CUDA graph.
+constexpr int kMaxScenes = 64;
+constexpr int kTraceChunk = 256;  // rays per traversal work item (one block)
+
+struct SceneDev {
+    OctreeView tree;
+    const void *feats;
+    const float *params;  // flat float32 network parameters
+    const float *rays;
+    float *rgb, *depth;
+    const float *d_rgb, *d_depth;
+    float *d_feat, *d_params;
+    int64_t ray_begin;    // first global ray index of the scene
+    int64_t n_rays;
+    int64_t chunk_begin;  // first traversal chunk of the scene
+};
+
+struct SceneTable {
+    int n;
+    int K;
+    int64_t total_rays;
+    int64_t total_chunks;
+    SceneDev s[kMaxScenes];
+};
+
+// Index of the scene holding global ray g (the table is sorted by ray_begin).
+__host__ __device__ __forceinline__ int scene_of_ray(const SceneTable &T, int64_t g) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.s[mid].ray_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ __forceinline__ int scene_of_chunk(const SceneTable &T, int64_t c) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.s[mid].chunk_begin <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Counters at the start of the workspace's counter block.
+constexpr int kCtrMaxAbsDout = 3;    // float bits of max |dL/d(network output)|
+constexpr int kCtrTraceChunks = 4;   // traversal work items claimed
+constexpr int kCtrScene = 16;        // + s: samples written for scene s
+constexpr size_t kCounterBytes = 4096;
+
+// Workspace layout (byte offsets from a 256-aligned base). Scene s owns the
+// sample slots [K * ray_begin_s, K * (ray_begin_s + n_rays_s)).
 struct Workspace {
-    Sample *samples;       // n_rays*K
-    float4 *outputs;       // n_rays*K: sigmoid colour (xyz), tau (w)
-    float4 *dout;          // n_rays*K: dL/d(network output)
-    int2 *ray_span;        // n_rays: first sample, count
-    unsigned int *counter; // [0] samples written, [3] float bits of max |dL/d(output)|
-    void *packed_w;        // network weights packed for the kernels
+    Sample *samples;       // total_rays*K
+    float4 *outputs;       // total_rays*K: sigmoid colour (xyz), tau (w)
+    float4 *dout;          // total_rays*K: dL/d(network output)
+    int2 *ray_span;        // total_rays: first sample, count
+    unsigned int *counter; // see kCtr*
+    void *packed_w;        // network weights packed for the kernels, per scene
+    size_t packed_stride;  // bytes between the packed weights of consecutive scenes
     size_t bytes;
 };
 
-Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K);
-size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K);
+Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K,
+                          int n_scenes = 1);
+size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K, int n_scenes = 1);
 size_t packed_weight_bytes(const svlf_mlp_desc &mlp);
 
 // ---------------------------------------------------------------- device status
@@ -75,20 +133,12 @@ __device__ __forceinline__ void raise_status(unsigned int bit) {
 }
 
 // ---------------------------------------------------------------- launches
-int launch_trace(const OctreeView &tree, const float *rays, int64_t n_rays, int K,
-                 const Workspace &ws, int32_t *hits, float *t_io, cudaStream_t s);
-int launch_composite(const Workspace &ws, int64_t n_rays, const float bg[3], float *rgb,
-                     float *depth, cudaStream_t s);
-int launch_composite_backward(const Workspace &ws, int64_t n_rays, const float bg[3],
-                              const float *d_rgb, const float *d_depth, cudaStream_t s);
-int launch_pack_weights(const svlf_mlp_desc &mlp, const float *params, void *packed,
-                        cudaStream_t s);
-int launch_mlp_forward(const svlf_mlp_desc &mlp, int depth, const void *features,
-                       const float *params, const float *rays, const Workspace &ws,
-                       int64_t max_samples, cudaStream_t s);
-int launch_mlp_backward(const svlf_mlp_desc &mlp, int depth, const void *features,
-                        const float *params, const float *rays, const Workspace &ws,
-                        int64_t max_samples, float *d_features, float *d_params,
+int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float *t_io,
+                 cudaStream_t s);
+int launch_composite(const SceneTable &T, const Workspace &ws, const float bg[3], cudaStream_t s);
+int launch_composite_backward(const SceneTable &T, const Workspace &ws, const float bg[3],
+                              cudaStream_t s);
+int launch_pack_weights(const svlf_mlp_desc &mlp, const SceneTable &T, const Workspace &ws,
                         cudaStream_t s);
 
 int num_sms();

@@ -23,6 +23,7 @@
 //    output buffer, not yet in use), keeping registers free for occupancy; at
 //    the end each warp reserves space for its rays' samples with one atomic
 //    and copies them contiguously per ray from the (cache-hot) slots.
+//  * Many scenes can be traced in one launch (see SceneTable).
 #include "svlf_internal.cuh"
 
 namespace svlf {
@@ -185,28 +186,44 @@ __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem
     return nh;
 }
 
-__global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *__restrict__ rays,
-                                                    int64_t n_rays, int K,
-                                                    Sample *__restrict__ samples,
-                                                    int4 *__restrict__ slots,
-                                                    int2 *__restrict__ ray_span,
-                                                    unsigned int *__restrict__ counter,
-                                                    int64_t max_samples, int32_t *__restrict__ hits,
-                                                    float *__restrict__ t_io) {
+// Work items are chunks of kTraceChunk rays of one scene, claimed in order
+// from a global counter (dynamic balancing; a block's consecutive chunks are
+// usually of the same scene, so its staged top levels stay valid).
+__global__ void __launch_bounds__(kTraceChunk) trace_kernel(const __grid_constant__ SceneTable T,
+                                                            Sample *__restrict__ samples,
+                                                            int4 *__restrict__ slots,
+                                                            int2 *__restrict__ ray_span,
+                                                            unsigned int *__restrict__ counter,
+                                                            int32_t *__restrict__ hits,
+                                                            float *__restrict__ t_io) {
     extern __shared__ uint32_t s_nodes[];
-    const int n_smem = min(T.n_nodes, kSmemNodeWords);
-    for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_nodes[i] = T.nodes[i];
-    __syncthreads();
+    __shared__ long long s_chunk;
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_rays;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = base + threadIdx.x;
-        const bool valid = r < n_rays;
+    const int K = T.K;
+    int staged = -1;
+    int n_smem = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
+        __syncthreads();
+        const int64_t chunk = s_chunk;
+        if (chunk >= T.total_chunks) break;
+        const int sc = scene_of_chunk(T, chunk);
+        const SceneDev &S = T.s[sc];
+        const OctreeView &tree = S.tree;
+        if (sc != staged) {  // stage this scene's top octree levels
+            n_smem = min(tree.n_nodes, kSmemNodeWords);
+            for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_nodes[i] = tree.nodes[i];
+            staged = sc;
+        }
+        __syncthreads();
+        const int64_t r_local = (chunk - S.chunk_begin) * kTraceChunk + threadIdx.x;
+        const bool valid = r_local < S.n_rays;
+        const int64_t g = S.ray_begin + r_local;  // global ray index
         int nh = 0;
-        int4 *slot = slots + r * K;
+        int4 *slot = slots + g * K;
         if (valid) {
             RayState R;
-            const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * r);
+            const float2 *rp = reinterpret_cast<const float2 *>(S.rays + 6 * r_local);
             const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
             R.o[0] = a.x; R.o[1] = a.y; R.o[2] = b.x;
             R.d[0] = b.y; R.d[1] = cc.x; R.d[2] = cc.y;
@@ -216,11 +233,11 @@ __global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *_
                 R.rhi[q] = rh;
                 R.rlo[q] = R.d[q] != 0.f ? fmaf(-R.d[q], rh, 1.0f) * rh : 0.f;
             }
-            R.n = 1 << T.depth;
-            R.h = ldexpf(1.0f, -T.depth);
-            nh = traverse(T, s_nodes, n_smem, R, K, slot);
+            R.n = 1 << tree.depth;
+            R.h = ldexpf(1.0f, -tree.depth);
+            nh = traverse(tree, s_nodes, n_smem, R, K, slot);
         }
-        // warp-aggregated reservation of nh samples per lane
+        // warp-aggregated reservation of nh samples per lane in the scene's region
         int incl = nh;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -228,58 +245,59 @@ __global__ void __launch_bounds__(256) trace_kernel(OctreeView T, const float *_
             if (lane >= off) incl += v;
         }
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        unsigned long long wbase = 0;
-        if (lane == 31 && total > 0) wbase = atomicAdd(counter, (unsigned int)total);
+        unsigned int wbase = 0;
+        if (lane == 31 && total > 0) wbase = atomicAdd(counter + kCtrScene + sc, (unsigned int)total);
         wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+        const int64_t cap = S.n_rays * (int64_t)K;  // the scene's slot region
         const int64_t first = (int64_t)wbase + (incl - nh);
         if (valid) {
             int keep = nh;
-            if (first + nh > max_samples) {
+            if (first + nh > cap) {
                 raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
-                keep = (int)max((int64_t)0, max_samples - first);
+                keep = (int)max((int64_t)0, cap - first);
             }
-            ray_span[r] = make_int2((int)first, keep);
+            const int64_t base = S.ray_begin * K + first;  // global sample index
+            ray_span[g] = make_int2((int)base, keep);
             for (int j = 0; j < keep; ++j) {
                 const int4 h = slot[j];
                 const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
-                reinterpret_cast<int4 *>(samples)[first + j] =
-                    make_int4(h.x, (int)r, h.y, __float_as_int(tm));
+                reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
             }
             if (hits || t_io) {
                 for (int j = 0; j < K; ++j) {
                     const int4 h = j < nh ? slot[j] : make_int4(-1, 0, 0, 0);
-                    if (hits) hits[r * K + j] = h.x;
+                    if (hits) hits[g * K + j] = h.x;
                     if (t_io)
-                        reinterpret_cast<float2 *>(t_io)[r * K + j] =
+                        reinterpret_cast<float2 *>(t_io)[g * K + j] =
                             j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
                                    : make_float2(0.f, 0.f);
                 }
             }
         }
+        __syncthreads();  // s_chunk / s_nodes are rewritten next iteration
     }
 }
 
-int launch_trace(const OctreeView &T, const float *rays, int64_t n_rays, int K,
-                 const Workspace &ws, int32_t *hits, float *t_io, cudaStream_t s) {
-    if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
-    const int64_t max_samples = n_rays * (int64_t)K;
-    const int threads = 256;
-    const size_t smem = sizeof(uint32_t) * (size_t)min(T.n_nodes, kSmemNodeWords);
+int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float *t_io,
+                 cudaStream_t s) {
+    if (T.K < 1 || T.K > kMaxK) return SVLF_ERR_UNSUPPORTED;
+    int max_nodes = 0;
+    for (int i = 0; i < T.n; ++i) max_nodes = max(max_nodes, T.s[i].tree.n_nodes);
+    const size_t smem = sizeof(uint32_t) * (size_t)min(max_nodes, kSmemNodeWords);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, kTraceChunk, smem) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
-    int64_t blocks = (n_rays + threads - 1) / threads;
+    int64_t blocks = T.total_chunks;
     const int64_t cap = (int64_t)num_sms() * per_sm;  // persistent: one wave of resident blocks
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    // the per-ray hit slots live in the network-output buffer (n_rays*K x 16 B),
+    // the per-ray hit slots live in the network-output buffer (total_rays*K x 16 B),
     // which the network kernels only write after this kernel is done
     prof_begin("trace", s);
-    trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, rays, n_rays, K, ws.samples,
-                                                         reinterpret_cast<int4 *>(ws.outputs),
-                                                         ws.ray_span, ws.counter, max_samples,
-                                                         hits, t_io);
+    trace_kernel<<<(unsigned)blocks, kTraceChunk, smem, s>>>(T, ws.samples,
+                                                             reinterpret_cast<int4 *>(ws.outputs),
+                                                             ws.ray_span, ws.counter, hits, t_io);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

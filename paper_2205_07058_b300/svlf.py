@@ -49,6 +49,13 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3)]
 
 
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("tree", ctypes.c_void_p), ("features", ctypes.c_void_p), ("mlp_params", ctypes.c_void_p),
+                ("rays", ctypes.c_void_p), ("n_rays", ctypes.c_int64), ("rgb", ctypes.c_void_p),
+                ("depth", ctypes.c_void_p), ("d_rgb", ctypes.c_void_p), ("d_depth", ctypes.c_void_p),
+                ("d_features", ctypes.c_void_p), ("d_mlp_params", ctypes.c_void_p)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -58,7 +65,8 @@ EXPORTS = [
     "svlf_workspace_size", "svlf_render_rays", "svlf_render_rays_backward", "svlf_loss",
     "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma",
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
-    "svlf_render_rays_static",
+    "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
+    "svlf_render_rays_backward_batched",
 ]
 
 _lib = None
@@ -87,6 +95,9 @@ def lib():
     L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
     L.svlf_get_device_status.argtypes = [P(i32)]
     L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]
+    L.svlf_workspace_size_batched.argtypes = [P(MlpDesc), i64, i32, i32, P(sz)]
+    L.svlf_render_rays_batched.argtypes = [P(SceneDesc), i32, P(MlpDesc), P(RenderOpts), vp, sz, vp]
+    L.svlf_render_rays_backward_batched.argtypes = [P(SceneDesc), i32, P(MlpDesc), P(RenderOpts), vp, sz, vp]
     L.svlf_render_rays_static.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp, vp, vp]
     L.svlf_profile_enable.argtypes = [i32]
     L.svlf_profile_report.argtypes = [P(KernelStat), i32, P(i32)]
@@ -243,6 +254,70 @@ def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
         _ptr(rgb), _ptr(depth), _stream(stream)))
     return rgb, depth
+
+
+@dataclass
+class BatchScene:
+    """One scene of a batched call; tensors are CUDA and contiguous."""
+    tree: "Octree"
+    features: torch.Tensor
+    params: torch.Tensor
+    rays: torch.Tensor
+    rgb: Optional[torch.Tensor] = None
+    depth: Optional[torch.Tensor] = None
+    d_rgb: Optional[torch.Tensor] = None
+    d_depth: Optional[torch.Tensor] = None
+    d_features: Optional[torch.Tensor] = None
+    d_params: Optional[torch.Tensor] = None
+
+    def desc(self) -> SceneDesc:
+        v = lambda t: None if t is None else _ptr(t)
+        return SceneDesc(self.tree.handle, v(self.features), v(self.params), v(self.rays), self.rays.shape[0],
+                         v(self.rgb), v(self.depth), v(self.d_rgb), v(self.d_depth), v(self.d_features),
+                         v(self.d_params))
+
+
+def workspace_size_batched(net: Network, total_rays: int, n_scenes: int, K: int) -> int:
+    b = ctypes.c_size_t()
+    d = net.desc()
+    _check("svlf_workspace_size_batched", lib().svlf_workspace_size_batched(
+        ctypes.byref(d), int(total_rays), int(n_scenes), int(K), ctypes.byref(b)))
+    return int(b.value)
+
+
+def alloc_workspace_batched(net: Network, scenes: Sequence[BatchScene], K: int) -> torch.Tensor:
+    total = sum(s.rays.shape[0] for s in scenes)
+    return torch.empty(workspace_size_batched(net, total, len(scenes), K) + 256, dtype=torch.uint8, device="cuda")
+
+
+def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg=(0.0, 0.0, 0.0),
+                             workspace: Optional[torch.Tensor] = None, stream=None):
+    """Render every scene in one call; fills each scene's rgb/depth (allocated
+    here when missing). Returns the workspace (needed by the backward)."""
+    for s in scenes:
+        if s.rgb is None:
+            s.rgb = torch.empty((s.rays.shape[0], 3), dtype=torch.float32, device="cuda")
+        if s.depth is None:
+            s.depth = torch.empty((s.rays.shape[0],), dtype=torch.float32, device="cuda")
+    if workspace is None:
+        workspace = alloc_workspace_batched(net, scenes, K)
+    arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays_batched", lib().svlf_render_rays_batched(
+        arr, len(scenes), ctypes.byref(d), ctypes.byref(o), wp, wb, _stream(stream)))
+    return workspace
+
+
+def svlf_render_rays_backward_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg, workspace,
+                                      stream=None):
+    arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays_backward_batched", lib().svlf_render_rays_backward_batched(
+        arr, len(scenes), ctypes.byref(d), ctypes.byref(o), wp, wb, _stream(stream)))
 
 
 def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,

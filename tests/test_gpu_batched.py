@@ -1,0 +1,116 @@
+"""Batched form: many scenes of uneven octree size in one launch per kernel,
+against one call per scene and against the oracle; CUDA-graph capture."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2205_07058_b300 import inputs as I
+from tests.gpu_common import requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+SHAPE = I.MLPShape(32, 128, 3)
+
+
+def _scenes(n=5, seed=40):
+    """Scenes of depth 6..9 with different primitive counts, features,
+    networks and views (a few thousand rays each, some with none)."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        depth = [6, 7, 8, 9, 7][i % 5]
+        sc = I.make_scene(rng, depth, int(rng.integers(2, 10)), int(rng.integers(0, 4)))
+        feats = I.make_features(rng, sc.n_leaves, 32)
+        params = I.make_mlp(rng, SHAPE, bias_std=0.2)
+        az, el = I.random_view_angles(rng, 1)
+        res = [48, 64, 32, 40, 0][i % 5]
+        rays = I.pinhole_rays(az[0], el[0], res, res) if res else np.zeros((0, 6), np.float32)
+        out.append(dict(scene=sc, feats=feats, params=params, rays=rays,
+                        tree=svlf.Octree(torch.from_numpy(sc.leaf_ijk), depth)))
+    return out
+
+
+def _batch(scenes):
+    from paper_2205_07058_b300 import svlf
+    return [svlf.BatchScene(s["tree"], torch.from_numpy(s["feats"]).cuda(), torch.from_numpy(s["params"]).cuda(),
+                            torch.from_numpy(s["rays"]).cuda()) for s in scenes]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_batched_render_matches_single_calls_and_oracle(prec):
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes()
+    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
+    bg = (0.1, 0.2, 0.3)
+    batch = _batch(scenes)
+    svlf.svlf_render_rays_batched(batch, net, 8, bg=bg)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    for s, b in zip(scenes, batch):
+        if s["rays"].shape[0] == 0:
+            assert b.rgb.shape == (0, 3)
+            continue
+        rgb, depth, _, _, _ = svlf.svlf_render_rays(b.tree, b.features, b.params, net, b.rays, 8, bg=bg)
+        torch.testing.assert_close(b.rgb, rgb, rtol=0, atol=1e-6)
+        torch.testing.assert_close(b.depth, depth, rtol=0, atol=1e-6)
+        tree = O.build_octree(s["scene"].leaf_ijk, s["scene"].depth)
+        emu = O.render(tree, s["feats"], s["params"], O.layer_dims(32, 128, 3), s["rays"], 8, bg=bg, bf16=prec)
+        ok = ~emu.hits.degenerate
+        assert np.abs(b.rgb.cpu().numpy()[ok] - emu.rgb[ok]).max() <= 2e-3
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_batched_backward_matches_single_calls(prec):
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes(seed=41)
+    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
+    batch = _batch(scenes)
+    ws = svlf.svlf_render_rays_batched(batch, net, 8)
+    rng = np.random.default_rng(0)
+    for b in batch:
+        n = b.rays.shape[0]
+        b.d_rgb = torch.from_numpy(rng.standard_normal((n, 3)).astype(np.float32) * 1e-3).cuda()
+        b.d_depth = torch.from_numpy(rng.standard_normal(n).astype(np.float32) * 1e-4).cuda()
+        b.d_features = torch.zeros_like(b.features)
+        b.d_params = torch.zeros_like(b.params)
+    svlf.svlf_render_rays_backward_batched(batch, net, 8, (0, 0, 0), ws)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    for b in batch:
+        if b.rays.shape[0] == 0:
+            assert torch.all(b.d_params == 0)
+            continue
+        _, _, _, _, w1 = svlf.svlf_render_rays(b.tree, b.features, b.params, net, b.rays, 8)
+        df = torch.zeros_like(b.features)
+        dp = torch.zeros_like(b.params)
+        svlf.svlf_render_rays_backward(b.tree, b.features, b.params, net, b.rays, 8, (0, 0, 0), b.d_rgb,
+                                       b.d_depth, df, dp, w1)
+        torch.cuda.synchronize()
+        assert (torch.linalg.norm(b.d_params - dp) / torch.linalg.norm(dp)).item() <= 1e-4
+        assert (torch.linalg.norm(b.d_features - df) / torch.linalg.norm(df)).item() <= 1e-4
+
+
+def test_batched_render_under_cuda_graph():
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes(seed=42)
+    net = svlf.Network(32, 128, 3, svlf.BF16)
+    batch = _batch(scenes)
+    ws = svlf.svlf_render_rays_batched(batch, net, 8)  # allocates outputs, warms up
+    torch.cuda.synchronize()
+    ref = [b.rgb.clone() for b in batch]
+    for b in batch:
+        b.rgb.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            svlf.svlf_render_rays_batched(batch, net, 8, workspace=ws)
+    for _ in range(2):
+        for b in batch:
+            b.rgb.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for b, r in zip(batch, ref):
+            torch.testing.assert_close(b.rgb, r, rtol=0, atol=1e-6)
