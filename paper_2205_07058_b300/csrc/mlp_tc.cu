@@ -168,13 +168,11 @@ __device__ __forceinline__ void st_chunk(uint8_t *abuf, int row, int kb, uint32_
 __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, int depth,
                                                    const void *feats, int feat_bf16,
                                                    const float *rays, int64_t ray_begin,
-                                                   const Sample *samples, int64_t s, bool valid,
-                                                   int fp16, uint8_t *abuf, int row,
-                                                   int *leaf_out) {
+                                                   const Sample &sm, bool valid, int fp16,
+                                                   uint8_t *abuf, int row, int *leaf_out) {
     const int F = md.F;
     int kb = 0;
     if (valid) {
-        const Sample sm = samples[s];
         if (leaf_out) *leaf_out = sm.leaf;
         const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
         const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
@@ -211,6 +209,38 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
         st_chunk(abuf, row, kb++, tc::pack2(p2[2], 0.f, fp16), 0u, 0u, 0u);
     }
     for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+}
+
+// The gather of a tile is latency-bound, so each warpgroup keeps the sample
+// records of its next two tiles in registers and, one tile ahead, prefetches
+// the next tile's feature rows and rays into L2 while the current tile runs
+// through the tensor cores.
+struct TilePrefetch {
+    Sample cur, nxt;
+    bool v_cur, v_nxt;
+};
+
+__device__ __forceinline__ bool load_record(const Sample *samples, int64_t sbase, int64_t tile0,
+                                            int64_t tile, int64_t seg_end, int64_t S_sc, int row,
+                                            Sample &r) {
+    const int64_t sl = (tile - tile0) * kTcTile + row;
+    const bool v = tile < seg_end && sl < S_sc;
+    if (v) r = samples[sbase + sl];
+    return v;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_gather(const Sample &r, const void *feats, int feat_bf16,
+                                                int F, const float *rays, int64_t ray_begin) {
+    const size_t row_bytes = (size_t)F * (feat_bf16 ? 2 : 4);
+    const char *f = reinterpret_cast<const char *>(feats) + (size_t)r.leaf * row_bytes;
+    for (size_t b = 0; b < row_bytes; b += 128) prefetch_l2(f + b);
+    const float *ray = rays + 6 * ((int64_t)r.ray - ray_begin);
+    prefetch_l2(ray);
+    prefetch_l2(ray + 5);
 }
 
 template <int H>
@@ -283,14 +313,24 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const __grid_con
         if (s_abort) break;
         const int64_t S_sc = s_map.S[sc];
         const int64_t sbase = SD.ray_begin * T.K;  // the scene's first sample slot
+        const int64_t tile0 = s_map.tile0[sc];
         const int depth = SD.tree.depth;
         bool aborted = false;
+        TilePrefetch pf;
+        pf.v_cur = load_record(P.samples, sbase, tile0, seg + wg, seg_end, S_sc, row, pf.cur);
+        pf.v_nxt = load_record(P.samples, sbase, tile0, seg + wg + P.n_wg, seg_end, S_sc, row, pf.nxt);
         for (int64_t tile = seg + wg; !aborted && tile < seg_end; tile += P.n_wg) {
-            const int64_t sl = (tile - s_map.tile0[sc]) * kTcTile + row;  // sample within the scene
+            const int64_t sl = (tile - tile0) * kTcTile + row;  // sample within the scene
             const int64_t s = sbase + sl;
+            const Sample rec = pf.cur;
+            const bool valid = pf.v_cur;
+            if (pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, P.md.F, SD.rays, SD.ray_begin);
+            pf.cur = pf.nxt;
+            pf.v_cur = pf.v_nxt;
+            pf.v_nxt = load_record(P.samples, sbase, tile0, tile + 2 * P.n_wg, seg_end, S_sc, row, pf.nxt);
             // ---- network input row -> A operand (K0 columns)
             build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
-                               P.samples, s, sl < S_sc, P.fp16, abuf, row, nullptr);
+                               rec, valid, P.fp16, abuf, row, nullptr);
             for (int l = 0; l < P.lay.n_layers; ++l) {
                 const int N = P.lay.w_rows[l];
                 const int Kl = P.lay.w_cols[l];
@@ -441,6 +481,7 @@ struct TcBwdParams {
     TcLayout lay;
     int fp16, feat_bf16;
     int want_feat, want_params;  // which gradients to form
+    int l_min, l_top, with_out;  // this pass: dW of hidden layers [l_min, l_top] (+ output layer)
     const uint8_t *images;
     size_t image_stride;
     const Sample *samples;
@@ -450,6 +491,18 @@ struct TcBwdParams {
     uint32_t gout_off, ones_off;
     uint32_t col_dwout, col_dw[kMaxLayers], col_db[kMaxLayers], tmem_cols;
 };
+
+// Shared-memory and TMEM plan of one backward pass (P.l_min, P.l_top,
+// P.with_out set by the caller). TMEM holds the work accumulator and the dW /
+// db accumulators of the pass's layers; networks whose accumulators do not
+// fit in 512 columns are split into several passes over the same tiles.
+static uint32_t tc_bwd_cols(const MlpDims &md, const TcLayout &lay, int l_min, int l_top,
+                            int with_out) {
+    uint32_t col = kHp;
+    for (int l = l_min; l <= l_top; ++l) col += (l == 0 ? lay.K0 : kHp) + 16;
+    if (with_out) col += kTcOutN;
+    return col;
+}
 
 static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
     const TcLayout &lay = P.lay;
@@ -468,15 +521,20 @@ static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
     // TMEM columns: [0, 128) work accumulator, then the 128-wide dW_l (l >= 1)
     // at multiples of 128, dW_0 (K0 wide), and the 16-wide dW_out^T and db_l.
     uint32_t col = kHp;
-    for (int l = 1; l < md.nh; ++l) {
+    for (int l = P.l_min; l <= P.l_top; ++l) {
+        if (l == 0) continue;
         P.col_dw[l] = col;
         col += kHp;
     }
-    P.col_dw[0] = col;
-    col += lay.K0;
-    P.col_dwout = col;
-    col += kTcOutN;
-    for (int l = 0; l < md.nh; ++l) {
+    if (P.l_min == 0) {
+        P.col_dw[0] = col;
+        col += lay.K0;
+    }
+    if (P.with_out) {
+        P.col_dwout = col;
+        col += kTcOutN;
+    }
+    for (int l = P.l_min; l <= P.l_top; ++l) {
         P.col_db[l] = col;
         col += 16;
     }
@@ -600,17 +658,26 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         const int64_t S_sc = s_map.S[sc];
         const int64_t sbase = SD.ray_begin * T.K;
         const int depth = SD.tree.depth;
-        float *d_feat = P.want_feat ? SD.d_feat : nullptr;
+        float *d_feat = (P.want_feat && P.l_min == 0) ? SD.d_feat : nullptr;
         int tiles_done = 0;
+        const int64_t tile0 = s_map.tile0[sc];
+        TilePrefetch pf;
+        pf.v_cur = load_record(P.samples, sbase, tile0, seg, seg_end, S_sc, row, pf.cur);
+        pf.v_nxt = load_record(P.samples, sbase, tile0, seg + 1, seg_end, S_sc, row, pf.nxt);
         for (int64_t tile = seg; !aborted && tile < seg_end; ++tile) {
-            const int64_t sl = (tile - s_map.tile0[sc]) * kTcTile + row;
+            const int64_t sl = (tile - tile0) * kTcTile + row;
             const int64_t s = sbase + sl;
-            const bool valid = sl < S_sc;
+            const Sample rec = pf.cur;
+            const bool valid = pf.v_cur;
+            if (pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, md.F, SD.rays, SD.ray_begin);
+            pf.cur = pf.nxt;
+            pf.v_cur = pf.v_nxt;
+            pf.v_nxt = load_record(P.samples, sbase, tile0, tile + 2, seg_end, S_sc, row, pf.nxt);
             int leaf = -1;
             // ---- 1. X_0 and G_out
             {
                 build_input_chunks(md, lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
-                                   P.samples, s, valid, P.fp16, smem + P.x_off[0], row, &leaf);
+                                   rec, valid, P.fp16, smem + P.x_off[0], row, &leaf);
                 const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
                 uint8_t *go = smem + P.gout_off;
                 st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
@@ -664,8 +731,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 const uint32_t go = s_base + P.gout_off;
                 const uint32_t wo = s_base + lay.w_off[nh];
                 if (!run([&] {
-                        mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
-                                kTcTile, tc::idesc_f16(kHp, kTcOutN, bf16, 1, 1), acc);
+                        if (P.with_out)
+                            mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
+                                    kTcTile, tc::idesc_f16(kHp, kTcOutN, bf16, 1, 1), acc);
                         mma_seq(tmem, go, 0, kTcTile * 16, 128, wo, 0, 128, kTcOutN * 16, kTcOutN,
                                 tc::idesc_f16(kTcTile, kHp, bf16, 0, 1), false);
                     })) {
@@ -703,21 +771,25 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             };
             mask_epilogue(nh);
             // ---- 4. hidden layers, from the top down
-            for (int l = nh - 1; l >= 0 && !aborted; --l) {
+            for (int l = nh - 1; l >= P.l_min && !aborted; --l) {
                 const uint32_t g = s_base + P.x_off[l + 1];  // G_{l+1} (delta of layer l's output)
                 const uint32_t xa = s_base + P.x_off[l];
                 const uint32_t wb = s_base + lay.w_off[l];
                 const int Nin = l == 0 ? lay.K0 : kHp;
-                const bool want_dx = l > 0 || d_feat != nullptr;
+                const bool want_dw = l <= P.l_top;
+                const bool want_dx = l > P.l_min || (l == 0 && d_feat != nullptr);
                 const int Ndx = l > 0 ? kHp : Fn;
+                if (!want_dw && !want_dx) continue;
                 if (!run([&] {
-                        // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
-                        mma_seq(tmem + P.col_dw[l], g, 256, 128, kTcTile * 16, xa, 256, 128, kTcTile * 16,
-                                kTcTile, tc::idesc_f16(kHp, Nin, bf16, 1, 1), acc);
-                        // db_l += G^T 1
-                        mma_seq(tmem + P.col_db[l], g, 256, 128, kTcTile * 16, s_base + P.ones_off,
-                                2 * kTcOutN * 16, kTcOutN * 16, 128, kTcTile,
-                                tc::idesc_f16(kHp, kTcOutN, bf16, 1, 0), acc);
+                        if (want_dw) {
+                            // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
+                            mma_seq(tmem + P.col_dw[l], g, 256, 128, kTcTile * 16, xa, 256, 128, kTcTile * 16,
+                                    kTcTile, tc::idesc_f16(kHp, Nin, bf16, 1, 1), acc);
+                            // db_l += G^T 1
+                            mma_seq(tmem + P.col_db[l], g, 256, 128, kTcTile * 16, s_base + P.ones_off,
+                                    2 * kTcOutN * 16, kTcOutN * 16, 128, kTcTile,
+                                    tc::idesc_f16(kHp, kTcOutN, bf16, 1, 0), acc);
+                        }
                         // G_l = G W_l  (A: G K-major, B: W_l MN-major)
                         if (want_dx)
                             mma_seq(tmem, g, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 256, 128, kHp * 16,
@@ -727,7 +799,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     break;
                 }
                 if (l > 0) {
-                    mask_epilogue(l);
+                    if (want_dx) mask_epilogue(l);
                 } else if (d_feat) {
                     // dL/dz: stage rows in shared memory (X_1's buffer is free now)
                     float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
@@ -768,7 +840,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             const int H = md.H;
             float *dpar = SD.d_params;
             // dW_out^T: lane = input feature k, columns = output j (< 4)
-            {
+            if (P.with_out) {
                 uint32_t v[16];
                 tc::tmem_ld16(tmem + lane_off + P.col_dwout, v);
                 tc::tmem_wait_ld();
@@ -778,7 +850,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 }
                 if (row < 4) atomicAdd(dpar + md.w_off[nh] + 4 * H + row, s_dbout[row]);
             }
-            for (int l = 0; l < nh; ++l) {
+            for (int l = P.l_min; l <= P.l_top; ++l) {
                 const int in = md.in_l[l];
                 const int ncol = l == 0 ? lay.K0 : kHp;
                 float *dW = dpar + md.w_off[l];
@@ -806,13 +878,33 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     }
 }
 
+// Split the layers into backward passes from the top down, as few as the
+// 512 TMEM columns allow. Returns the number of passes (0 = cannot).
+static int tc_bwd_passes(const MlpDims &md, const TcLayout &lay, int l_min[], int l_top[],
+                         int with_out[]) {
+    int n = 0, top = md.nh - 1, out = 1;
+    while (top >= 0 && n < kMaxLayers) {
+        int lo = top + 1;
+        while (lo - 1 >= 0 && tc_bwd_cols(md, lay, lo - 1, top, out) <= 512) --lo;
+        if (lo > top) {  // not even one layer fits
+            if (out && tc_bwd_cols(md, lay, top + 1, top, out) <= 512 && n == 0) {
+                l_min[n] = top + 1; l_top[n] = top; with_out[n] = 1; ++n; out = 0;
+                continue;
+            }
+            return 0;
+        }
+        l_min[n] = lo; l_top[n] = top; with_out[n] = out; ++n;
+        out = 0;
+        top = lo - 1;
+    }
+    return n;
+}
+
 bool tc_backward_supported(const MlpDims &md) {
     if (!tc_supported(md)) return false;
-    TcBwdParams P;
-    memset(&P, 0, sizeof(P));
-    P.lay = tc_layout(md);
-    size_t smem;
-    return tc_bwd_plan(md, P, smem);
+    const TcLayout lay = tc_layout(md);
+    int a[kMaxLayers], b[kMaxLayers], c[kMaxLayers];
+    return tc_bwd_passes(md, lay, a, b, c) > 0;
 }
 
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
@@ -822,8 +914,9 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
     memset(&P, 0, sizeof(P));
     P.md = md;
     P.lay = tc_layout(md);
-    size_t smem;
-    if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
+    int pl_min[kMaxLayers], pl_top[kMaxLayers], pout[kMaxLayers];
+    const int n_pass = tc_bwd_passes(md, P.lay, pl_min, pl_top, pout);
+    if (n_pass == 0) return SVLF_ERR_UNSUPPORTED;
     P.fp16 = precision == SVLF_FP16;
     P.feat_bf16 = fb;
     P.want_feat = want_feat;
@@ -833,14 +926,23 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
     P.samples = ws.samples;
     P.counter = ws.counter;
     P.dout = ws.dout;
-    if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
-    if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return SVLF_ERR_CUDA;
-    prof_begin("mlp_backward_tc", s);
-    mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(T, P);
-    prof_end(s);
-    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+    for (int pass = 0; pass < n_pass; ++pass) {
+        if (pl_min[pass] > 0 && !want_params) continue;  // only the last pass forms dL/dz
+        P.l_min = pl_min[pass];
+        P.l_top = pl_top[pass];
+        P.with_out = pout[pass];
+        size_t smem;
+        if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
+        if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
+        if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return SVLF_ERR_CUDA;
+        prof_begin("mlp_backward_tc", s);
+        mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(T, P);
+        prof_end(s);
+        if (cudaGetLastError() != cudaSuccess) return SVLF_ERR_CUDA;
+    }
+    return SVLF_OK;
 }
 
 }  // namespace svlf

@@ -59,7 +59,7 @@ struct __align__(16) Sample {
 // as a kernel parameter, so a call needs no host-to-device copy and can be
 // captured in a CUDA graph.
 constexpr int kMaxScenes = 64;
-constexpr int kTraceChunk = 256;  // rays per traversal work item (one block)
+constexpr int kTraceChunk = 128;  // rays per traversal work item (one warp)
 
 struct SceneDev {
     OctreeView tree;

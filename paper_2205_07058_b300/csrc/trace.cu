@@ -7,8 +7,9 @@
 //    octree is descended from the root to find either the largest empty
 //    block containing the current finest cell, or the cell's brick (the 4^3
 //    leaves under a level L-2 node, held as a 64-bit mask). The brick of the
-//    current cell stays cached in registers, so consecutive cells inside it
-//    cost no memory access.
+//    current cell and its parent node (8^3 cells) stay cached in registers,
+//    so consecutive cells inside a brick cost no memory access and a move to
+//    a neighbouring brick of the same parent costs one brick load.
 //  * The node words of the top levels (up to kSmemNodeWords) are staged in
 //    shared memory; deeper levels and bricks come through the read-only path.
 //  * Plane crossings t = (k 2^-L - o) / d are evaluated without a division:
@@ -24,11 +25,24 @@
 //    the end each warp reserves space for its rays' samples with one atomic
 //    and copies them contiguously per ray from the (cache-hot) slots.
 //  * Many scenes can be traced in one launch (see SceneTable).
+//  * Warps fetch their own chunks of rays and refill lanes as rays finish
+//    (persistent warps), so no lane waits for the longest ray of its warp
+//    and no warp waits for the rest of its block.
 #include "svlf_internal.cuh"
 
 namespace svlf {
 
 __device__ unsigned int g_device_status = 0;
+
+#ifdef SVLF_TRACE_STATS
+// [0] walk steps, [1] full descents, [2] node words read in descents,
+// [3] parent-cache hits, [4] brick loads, [5] rays entering the cube,
+// [6] steps inside a cached brick, [7] rays
+__device__ unsigned long long g_trace_stats[8];
+#define TRACE_STAT(i, v) atomicAdd(&g_trace_stats[i], (unsigned long long)(v))
+#else
+#define TRACE_STAT(i, v) ((void)0)
+#endif
 
 struct RayState {
     float o[3], d[3];
@@ -58,97 +72,172 @@ __device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int
     return k;
 }
 
-// Hits are written to slot[0 .. K-1] (16 bytes each: rank, packed cell,
-// t_in, t_out); returns their number.
-__device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem, RayState &R,
-                        int K, int4 *__restrict__ slot) {
-    if (T.empty) return 0;
-    const int L = T.depth;
+// Traversal state of one ray, kept in registers across the rounds of the
+// warp loop below.
+struct Walk {
+    RayState R;
+    int c[3];        // current finest cell
+    float t;         // entry t of the current cell
+    int nh;          // hits so far
+    int steps;
+    uint32_t cached;  // brick (level L-2) of the current cell
+    uint64_t bmask;
+    int bbase;
+    uint32_t pcached;  // its parent node (level L-3, 8^3 cells)
+    uint32_t pword;
+    uint32_t skey;     // packed cell whose root path the ancestor stack holds
+    int svalid;        // levels 0 .. svalid-1 of the stack are valid
+};
+
+// Root clip (slab test against the unit cube) and the first cell. Returns
+// false when the ray does not enter the cube with a positive segment.
+__device__ __forceinline__ bool walk_init(const OctreeView &T, Walk &w) {
+    if (T.empty) return false;
+    RayState &R = w.R;
     const int n = R.n;
     float t0 = 0.f, t1 = INFINITY;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (R.d[a] == 0.f) {
-            if (R.o[a] < 0.f || R.o[a] > 1.f) return 0;
+            if (R.o[a] < 0.f || R.o[a] > 1.f) return false;
             continue;
         }
         float ta = cross_t(R, a, 0), tb = cross_t(R, a, n);
         t0 = fmaxf(t0, fminf(ta, tb));
         t1 = fminf(t1, fmaxf(ta, tb));
     }
-    if (!(t1 - t0 > 0.f)) return 0;
-    int c[3];
+    if (!(t1 - t0 > 0.f)) return false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (R.d[a] == 0.f) {
-            c[a] = min(max((int)floorf(R.o[a] * (float)n), 0), n - 1);
-        } else {
-            c[a] = cell_after(R, a, t0, 0, n - 1);
-        }
-    }
-    float t = t0;
-    int nh = 0;
-    uint32_t cached = 0xFFFFFFFFu;
-    uint64_t bmask = 0;
-    int bbase = 0;
+    for (int a = 0; a < 3; ++a)
+        w.c[a] = R.d[a] == 0.f ? min(max((int)floorf(R.o[a] * (float)n), 0), n - 1)
+                               : cell_after(R, a, t0, 0, n - 1);
+    w.t = t0;
+    w.nh = 0;
+    w.steps = 0;
+    w.cached = 0xFFFFFFFFu;
+    w.bmask = 0;
+    w.bbase = 0;
+    w.pcached = 0xFFFFFFFFu;
+    w.pword = 0;
+    w.skey = 0;
+    w.svalid = 0;
+    return true;
+}
+
+// Up to `budget` steps of the walk; hits go to slot[0 .. K-1] (16 bytes each:
+// rank, packed cell, t_in, t_out). Returns true when the ray is finished (K
+// hits, left the cube, or an error was latched).
+// `stk` is this lane's ancestor stack: stk[l * stride] = node word of the
+// level-l ancestor of the cell w.skey (levels < w.svalid).
+__device__ bool walk_steps(const OctreeView &T, const uint32_t *s_nodes, int n_smem, Walk &w,
+                           int K, int4 *__restrict__ slot, int budget, uint32_t *stk, int stride) {
+    const RayState &R = w.R;
+    const int L = T.depth;
+    const int n = R.n;
     const int max_steps = 3 * n + 64;
-    for (int step = 0;; ++step) {
-        if (step >= max_steps) {
+    for (int it = 0; it < budget; ++it) {
+        if (++w.steps > max_steps) {
             raise_status(SVLF_DEV_STEP_LIMIT);
-            break;
+            return true;
         }
+        int *c = w.c;
+        TRACE_STAT(0, 1);
         const uint32_t key = (uint32_t)(c[0] >> 2) | ((uint32_t)(c[1] >> 2) << 10) |
                              ((uint32_t)(c[2] >> 2) << 20);
         int sz_log = 0;
         bool leaf = false;
         int rank = -1;
-        if (key != cached) {
+        if (key == w.cached) TRACE_STAT(6, 1);
+        if (key != w.cached) {
+            const uint32_t pkey = (uint32_t)(c[0] >> 3) | ((uint32_t)(c[1] >> 3) << 10) |
+                                  ((uint32_t)(c[2] >> 3) << 20);
             int node = 0;
             bool found = true;
-            for (int l = 0; l < T.n_node_levels; ++l) {
-                const int s = L - 1 - l;
-                const int oct = ((c[0] >> s) & 1) | (((c[1] >> s) & 1) << 1) | (((c[2] >> s) & 1) << 2);
-                uint32_t w;
-                if (node < n_smem) {
-                    w = s_nodes[node];
-                } else if (node < T.n_nodes) {
-                    w = __ldg(T.nodes + node);
-                } else {
-                    raise_status(SVLF_DEV_BAD_INDEX);
-                    return nh;
-                }
-                const uint32_t m = w >> 24;
+            if (pkey == w.pcached) {
+                TRACE_STAT(3, 1);
+                // same 8^3 region as before: one step down from the cached parent
+                const int oct = ((c[0] >> 2) & 1) | (((c[1] >> 2) & 1) << 1) | (((c[2] >> 2) & 1) << 2);
+                const uint32_t m = w.pword >> 24;
                 if (!((m >> oct) & 1u)) {
-                    sz_log = s;
+                    sz_log = 2;
                     found = false;
-                    break;
+                } else {
+                    node = (int)(w.pword & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
                 }
-                node = (int)(w & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
+            } else if (T.n_node_levels == 0) {
+                node = 0;  // depth 2: the root is the only brick
+            } else {
+                TRACE_STAT(1, 1);
+                // restart at the deepest ancestor shared with the stacked path
+                int l = 0;
+                uint32_t wd;
+                if (w.svalid > 0) {
+                    const uint32_t x = ((uint32_t)c[0] ^ (w.skey & 1023u)) |
+                                       ((uint32_t)c[1] ^ ((w.skey >> 10) & 1023u)) |
+                                       ((uint32_t)c[2] ^ ((w.skey >> 20) & 1023u));
+                    const int shared = x ? L - 1 - (31 - __clz(x)) : L;  // deepest shared level
+                    l = min(shared, w.svalid - 1);
+                    wd = stk[l * stride];
+                } else {
+                    wd = n_smem > 0 ? s_nodes[0] : __ldg(T.nodes);
+                    stk[0] = wd;
+                }
+                int reached = l;
+                for (;;) {
+                    TRACE_STAT(2, 1);
+                    const int sh = L - 1 - l;
+                    const int oct = ((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2);
+                    if (l == T.n_node_levels - 1) {
+                        w.pcached = pkey;
+                        w.pword = wd;
+                    }
+                    const uint32_t m = wd >> 24;
+                    if (!((m >> oct) & 1u)) {
+                        sz_log = sh;
+                        found = false;
+                        break;
+                    }
+                    node = (int)(wd & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
+                    if (++l == T.n_node_levels) break;  // node is a brick index
+                    if (node < n_smem) {
+                        wd = s_nodes[node];
+                    } else if (node < T.n_nodes) {
+                        wd = __ldg(T.nodes + node);
+                    } else {
+                        raise_status(SVLF_DEV_BAD_INDEX);
+                        return true;
+                    }
+                    stk[l * stride] = wd;
+                    reached = l;
+                }
+                w.svalid = reached + 1;
+                w.skey = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
             }
             if (found) {
                 if (node >= T.n_bricks) {
                     raise_status(SVLF_DEV_BAD_INDEX);
-                    return nh;
+                    return true;
                 }
+                TRACE_STAT(4, 1);
                 const uint4 b = __ldg(T.bricks + node);
-                bmask = (uint64_t)b.x | ((uint64_t)b.y << 32);
-                bbase = (int)b.z;
-                cached = key;
+                w.bmask = (uint64_t)b.x | ((uint64_t)b.y << 32);
+                w.bbase = (int)b.z;
+                w.cached = key;
             } else {
-                cached = 0xFFFFFFFFu;
+                w.cached = 0xFFFFFFFFu;
             }
         }
-        if (cached == key) {
+        if (w.cached == key) {
             const int bit = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2) |
                             (((c[0] >> 1) & 1) << 3) | (((c[1] >> 1) & 1) << 4) |
                             (((c[2] >> 1) & 1) << 5);
-            if (((bmask >> (bit & 56)) & 0xFFull) == 0) {
+            if (((w.bmask >> (bit & 56)) & 0xFFull) == 0) {
                 sz_log = 1;
-            } else if (!((bmask >> bit) & 1ull)) {
+            } else if (!((w.bmask >> bit) & 1ull)) {
                 sz_log = 0;
             } else {
                 leaf = true;
-                rank = bbase + __popcll(bmask & ((1ull << bit) - 1ull));
+                rank = w.bbase + __popcll(w.bmask & ((1ull << bit) - 1ull));
             }
         }
         const int sz = 1 << sz_log;
@@ -164,8 +253,8 @@ __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem
         }
         if (leaf) {
             const uint32_t packed = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
-            slot[nh] = make_int4(rank, (int)packed, __float_as_int(t), __float_as_int(tx));
-            if (++nh == K) break;
+            slot[w.nh] = make_int4(rank, (int)packed, __float_as_int(w.t), __float_as_int(tx));
+            if (++w.nh == K) return true;
         }
         bool out = false;
 #pragma unroll
@@ -180,122 +269,162 @@ __device__ int traverse(const OctreeView &T, const uint32_t *s_nodes, int n_smem
             }
             out |= (c[a] < 0) | (c[a] >= n);
         }
-        if (out) break;
-        t = tx;
+        if (out) return true;
+        w.t = tx;
     }
-    return nh;
+    return false;
 }
 
-// Work items are chunks of kTraceChunk rays of one scene, claimed in order
-// from a global counter (dynamic balancing; a block's consecutive chunks are
-// usually of the same scene, so its staged top levels stay valid).
-__global__ void __launch_bounds__(kTraceChunk) trace_kernel(const __grid_constant__ SceneTable T,
-                                                            Sample *__restrict__ samples,
-                                                            int4 *__restrict__ slots,
-                                                            int2 *__restrict__ ray_span,
-                                                            unsigned int *__restrict__ counter,
-                                                            int32_t *__restrict__ hits,
-                                                            float *__restrict__ t_io) {
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Each warp claims chunks of kTraceChunk rays of one scene from a global
+// counter (in order, so neighbouring warps walk neighbouring pixels). Inside
+// a chunk a lane whose ray is finished takes the chunk's next ray, so lanes
+// stay busy while other rays of the warp are still walking; rays that miss
+// the unit cube never enter the walk. Finished rays write their samples to
+// the scene's region, with one atomic per warp and round.
+__global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ SceneTable T,
+                                                    Sample *__restrict__ samples,
+                                                    int4 *__restrict__ slots,
+                                                    int2 *__restrict__ ray_span,
+                                                    unsigned int *__restrict__ counter,
+                                                    int32_t *__restrict__ hits,
+                                                    float *__restrict__ t_io) {
     extern __shared__ uint32_t s_nodes[];
-    __shared__ long long s_chunk;
+    __shared__ uint32_t s_stack[kMaxDepth * 256];  // per-lane ancestor stacks, [level][thread]
     const int lane = threadIdx.x & 31;
     const int K = T.K;
-    int staged = -1;
-    int n_smem = 0;
+    // stage the top levels of the first scene (other scenes read them through L1)
+    const int n_smem0 = min(T.s[0].tree.n_nodes, kSmemNodeWords);
+    for (int i = threadIdx.x; i < n_smem0; i += blockDim.x) s_nodes[i] = T.s[0].tree.nodes[i];
+    __syncthreads();
+    constexpr int kBudget = 16;  // walk steps per round
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
-        __syncthreads();
-        const int64_t chunk = s_chunk;
+        long long chunk = 0;
+        if (lane == 0) chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
+        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
         if (chunk >= T.total_chunks) break;
         const int sc = scene_of_chunk(T, chunk);
         const SceneDev &S = T.s[sc];
         const OctreeView &tree = S.tree;
-        if (sc != staged) {  // stage this scene's top octree levels
-            n_smem = min(tree.n_nodes, kSmemNodeWords);
-            for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_nodes[i] = tree.nodes[i];
-            staged = sc;
-        }
-        __syncthreads();
-        const int64_t r_local = (chunk - S.chunk_begin) * kTraceChunk + threadIdx.x;
-        const bool valid = r_local < S.n_rays;
-        const int64_t g = S.ray_begin + r_local;  // global ray index
-        int nh = 0;
-        int4 *slot = slots + g * K;
-        if (valid) {
-            RayState R;
-            const float2 *rp = reinterpret_cast<const float2 *>(S.rays + 6 * r_local);
-            const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
-            R.o[0] = a.x; R.o[1] = a.y; R.o[2] = b.x;
-            R.d[0] = b.y; R.d[1] = cc.x; R.d[2] = cc.y;
+        const int n_smem = sc == 0 ? n_smem0 : 0;
+        const int64_t r_begin = (chunk - S.chunk_begin) * kTraceChunk;
+        const int chunk_n = (int)min((int64_t)kTraceChunk, S.n_rays - r_begin);
+        int next = 0;        // rays of the chunk handed out so far (warp-uniform)
+        bool have = false;   // this lane walks a ray
+        int64_t g = 0;       // its global ray index
+        Walk w;
+        for (;;) {
+            // ---- hand out rays to idle lanes; rays that miss finish at once
+            bool done = false;
+            const unsigned idle = __ballot_sync(0xFFFFFFFFu, !have);
+            if (!have) {
+                const int my = next + __popc(idle & lanemask_lt());
+                if (my < chunk_n) {
+                    const int64_t rl = r_begin + my;
+                    g = S.ray_begin + rl;
+                    const float2 *rp = reinterpret_cast<const float2 *>(S.rays + 6 * rl);
+                    const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
+                    RayState &R = w.R;
+                    R.o[0] = a.x; R.o[1] = a.y; R.o[2] = b.x;
+                    R.d[0] = b.y; R.d[1] = cc.x; R.d[2] = cc.y;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float rh = 1.0f / R.d[q];  // inf for d = 0 (that axis is never crossed)
-                R.rhi[q] = rh;
-                R.rlo[q] = R.d[q] != 0.f ? fmaf(-R.d[q], rh, 1.0f) * rh : 0.f;
+                    for (int q = 0; q < 3; ++q) {
+                        const float rh = 1.0f / R.d[q];  // inf for d = 0 (that axis is never crossed)
+                        R.rhi[q] = rh;
+                        R.rlo[q] = R.d[q] != 0.f ? fmaf(-R.d[q], rh, 1.0f) * rh : 0.f;
+                    }
+                    R.n = 1 << tree.depth;
+                    R.h = ldexpf(1.0f, -tree.depth);
+                    w.nh = 0;
+                    have = walk_init(tree, w);
+                    done = !have;  // a miss: zero samples
+                    TRACE_STAT(7, 1);
+                    if (have) TRACE_STAT(5, 1);
+                }
             }
-            R.n = 1 << tree.depth;
-            R.h = ldexpf(1.0f, -tree.depth);
-            nh = traverse(tree, s_nodes, n_smem, R, K, slot);
-        }
-        // warp-aggregated reservation of nh samples per lane in the scene's region
-        int incl = nh;
+            next += __popc(idle);
+            const bool any_active = __any_sync(0xFFFFFFFFu, have);
+            if (!any_active && !__any_sync(0xFFFFFFFFu, done)) {
+                if (next >= chunk_n) break;
+                continue;
+            }
+            // ---- walk
+            if (have) {
+                int4 *slot = slots + g * K;
+                if (walk_steps(tree, n_smem ? s_nodes : nullptr, n_smem, w, K, slot, kBudget,
+                               s_stack + threadIdx.x, 256)) {
+                    have = false;
+                    done = true;
+                }
+            }
+            // ---- finished rays: reserve their samples (one atomic per warp) and copy them
+            const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
+            if (fin) {
+                const int nh = done ? w.nh : 0;
+                int incl = nh;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        unsigned int wbase = 0;
-        if (lane == 31 && total > 0) wbase = atomicAdd(counter + kCtrScene + sc, (unsigned int)total);
-        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
-        const int64_t cap = S.n_rays * (int64_t)K;  // the scene's slot region
-        const int64_t first = (int64_t)wbase + (incl - nh);
-        if (valid) {
-            int keep = nh;
-            if (first + nh > cap) {
-                raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
-                keep = (int)max((int64_t)0, cap - first);
-            }
-            const int64_t base = S.ray_begin * K + first;  // global sample index
-            ray_span[g] = make_int2((int)base, keep);
-            for (int j = 0; j < keep; ++j) {
-                const int4 h = slot[j];
-                const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
-                reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
-            }
-            if (hits || t_io) {
-                for (int j = 0; j < K; ++j) {
-                    const int4 h = j < nh ? slot[j] : make_int4(-1, 0, 0, 0);
-                    if (hits) hits[g * K + j] = h.x;
-                    if (t_io)
-                        reinterpret_cast<float2 *>(t_io)[g * K + j] =
-                            j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
-                                   : make_float2(0.f, 0.f);
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                unsigned int wbase = 0;
+                if (lane == 31 && total > 0) wbase = atomicAdd(counter + kCtrScene + sc, (unsigned int)total);
+                wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+                if (done) {
+                    const int64_t cap = S.n_rays * (int64_t)K;  // the scene's slot region
+                    const int64_t first = (int64_t)wbase + (incl - nh);
+                    int keep = nh;
+                    if (first + nh > cap) {
+                        raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
+                        keep = (int)max((int64_t)0, cap - first);
+                    }
+                    const int64_t base = S.ray_begin * K + first;  // global sample index
+                    ray_span[g] = make_int2((int)base, keep);
+                    const int4 *slot = slots + g * K;
+                    for (int j = 0; j < keep; ++j) {
+                        const int4 h = slot[j];
+                        const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
+                        reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
+                    }
+                    if (hits || t_io) {
+                        for (int j = 0; j < K; ++j) {
+                            const int4 h = j < nh ? slot[j] : make_int4(-1, 0, 0, 0);
+                            if (hits) hits[g * K + j] = h.x;
+                            if (t_io)
+                                reinterpret_cast<float2 *>(t_io)[g * K + j] =
+                                    j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
+                                           : make_float2(0.f, 0.f);
+                        }
+                    }
                 }
             }
         }
-        __syncthreads();  // s_chunk / s_nodes are rewritten next iteration
     }
 }
 
 int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float *t_io,
                  cudaStream_t s) {
     if (T.K < 1 || T.K > kMaxK) return SVLF_ERR_UNSUPPORTED;
-    int max_nodes = 0;
-    for (int i = 0; i < T.n; ++i) max_nodes = max(max_nodes, T.s[i].tree.n_nodes);
-    const size_t smem = sizeof(uint32_t) * (size_t)min(max_nodes, kSmemNodeWords);
+    const int threads = 256;
+    const size_t smem = sizeof(uint32_t) * (size_t)min(T.s[0].tree.n_nodes, kSmemNodeWords);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, kTraceChunk, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
-    int64_t blocks = T.total_chunks;
+    int64_t blocks = (T.total_chunks + threads / 32 - 1) / (threads / 32);
     const int64_t cap = (int64_t)num_sms() * per_sm;  // persistent: one wave of resident blocks
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     // the per-ray hit slots live in the network-output buffer (total_rays*K x 16 B),
     // which the network kernels only write after this kernel is done
     prof_begin("trace", s);
-    trace_kernel<<<(unsigned)blocks, kTraceChunk, smem, s>>>(T, ws.samples,
+    trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples,
                                                              reinterpret_cast<int4 *>(ws.outputs),
                                                              ws.ray_span, ws.counter, hits, t_io);
     prof_end(s);
@@ -303,3 +432,17 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
 }
 
 }  // namespace svlf
+
+#ifdef SVLF_TRACE_STATS
+// statistics build only: copy (and optionally reset) the traversal counters
+extern "C" int svlf_trace_stats(unsigned long long *out, int reset) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return SVLF_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(out, svlf::g_trace_stats, sizeof(unsigned long long) * 8) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    if (reset) {
+        unsigned long long z[8] = {0};
+        if (cudaMemcpyToSymbol(svlf::g_trace_stats, z, sizeof(z)) != cudaSuccess) return SVLF_ERR_CUDA;
+    }
+    return SVLF_OK;
+}
+#endif
