@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="step", choices=["step", "batched"],
+                   help="step: the headline render + train step; batched: 64 scenes in one "
+                        "launch per kernel under a CUDA graph")
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--render-only", action="store_true",
                    help="time only the render pass (profiling aid; not the benchmark step)")
     p.add_argument("--views", type=int, default=RENDER_VIEWS)
@@ -276,6 +280,10 @@ def run_ours(args, rank, world, local_rank):
         if not args.render_only:
             train_phase()
 
+    tuned = None
+    if not args.no_autotune and world == 1:
+        from paper_2205_07058_b300.autotune import autotune
+        tuned = autotune(step, f"step|{args.precision}|{args.views}x{args.res}|{int(args.render_only)}", repeats=3)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -421,7 +429,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "render_rays": N, "train_rays": NT, "K": K_HITS,
                        "network_precision": args.precision, "train_precision": args.train_precision or args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (features 216 MB + rays 246 MB per step)"},
+                       "l2": "inputs larger than L2 (features 216 MB + rays 246 MB per step)",
+                       "autotune": tuned},
             "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
             "train_rays_per_s": None if args.render_only else round(NT * args.steps / (train_ms / 1e3), 1),
             "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
@@ -517,6 +526,127 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 2), "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------
+# batched multi-scene workload (64 scenes, one launch per kernel, CUDA graph)
+# ----------------------------------------------------------------------------
+BATCH_SCENES = 64
+BATCH_RES = 256
+BATCH_TRAIN = 1 << 14
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    from paper_2205_07058_b300 import inputs as I
+    from paper_2205_07058_b300 import svlf
+    from paper_2205_07058_b300.autotune import autotune
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.time()
+    scenes = I.batched_scenes(1004 + 7919 * rank, BATCH_SCENES)
+    shape = I.MLPShape(FEAT, HIDDEN, N_HIDDEN)
+    rng = np.random.default_rng(1005 + rank)
+    n_leaves = [s.n_leaves for s in scenes]
+    feat_all = torch.from_numpy(I.make_features(rng, sum(n_leaves), FEAT)).to(dev)
+    par_all = torch.from_numpy(np.concatenate([I.make_mlp(rng, shape) for _ in scenes])).to(dev)
+    n_par = shape.n_params
+    net = svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.PRECISIONS[args.precision])
+    trees, rend, train = [], [], []
+    off = 0
+    r_rays, t_rays = [], []
+    for i, sc in enumerate(scenes):
+        trees.append(svlf.Octree(torch.from_numpy(sc.leaf_ijk), sc.depth))
+        az, el = I.random_view_angles(rng, 100)
+        r_rays.append(I.pinhole_rays(az[0], el[0], BATCH_RES, BATCH_RES))
+        t_rays.append(I.training_rays(rng, 100, BATCH_RES, BATCH_TRAIN, az, el))
+    r_all = torch.from_numpy(np.concatenate(r_rays)).to(dev)
+    t_all = torch.from_numpy(np.concatenate(t_rays)).to(dev)
+    NR, NT = r_all.shape[0], t_all.shape[0]
+    rgb_r = torch.empty((NR, 3), device=dev)
+    dep_r = torch.empty((NR,), device=dev)
+    rgb_t = torch.empty((NT, 3), device=dev)
+    dep_t = torch.empty((NT,), device=dev)
+    tgt_rgb = torch.rand((NT, 3), device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+    tgt_dep = torch.from_numpy(np.concatenate([I.analytic_depth(t_rays[i], scenes[i])[0] for i in range(len(scenes))])).to(dev)
+    tgt_mask = torch.from_numpy(np.concatenate([I.analytic_depth(t_rays[i], scenes[i])[1] for i in range(len(scenes))])).to(dev)
+    d_rgb = torch.empty_like(rgb_t)
+    d_dep = torch.empty_like(dep_t)
+    g_feat = torch.zeros_like(feat_all)
+    g_par = torch.zeros_like(par_all)
+    m_f, v_f, m_p, v_p = (torch.zeros_like(x) for x in (feat_all, feat_all, par_all, par_all))
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    fo = 0
+    for i, sc in enumerate(scenes):
+        f = feat_all[fo:fo + n_leaves[i]]
+        p = par_all[i * n_par:(i + 1) * n_par]
+        rs = slice(i * BATCH_RES * BATCH_RES, (i + 1) * BATCH_RES * BATCH_RES)
+        ts = slice(i * BATCH_TRAIN, (i + 1) * BATCH_TRAIN)
+        rend.append(svlf.BatchScene(trees[i], f, p, r_all[rs], rgb_r[rs], dep_r[rs]))
+        train.append(svlf.BatchScene(trees[i], f, p, t_all[ts], rgb_t[ts], dep_t[ts], d_rgb[ts], d_dep[ts],
+                                     g_feat[fo:fo + n_leaves[i]], g_par[i * n_par:(i + 1) * n_par]))
+        fo += n_leaves[i]
+    ws_r = svlf.alloc_workspace_batched(net, rend, K_HITS)
+    ws_t = svlf.alloc_workspace_batched(net, train, K_HITS)
+    adam_t = [0]
+
+    def graphed():  # render + training forward/backward of all 64 scenes
+        svlf.svlf_render_rays_batched(rend, net, K_HITS, workspace=ws_r)
+        g_feat.zero_()
+        g_par.zero_()
+        loss.zero_()
+        svlf.svlf_render_rays_batched(train, net, K_HITS, workspace=ws_t)
+        svlf.svlf_loss(rgb_t, dep_t, tgt_rgb, tgt_dep, tgt_mask, DEPTH_WEIGHT, d_rgb, d_dep, loss)
+        svlf.svlf_render_rays_backward_batched(train, net, K_HITS, (0.0, 0.0, 0.0), ws_t)
+
+    def adam():  # outside the graph: the bias correction depends on the step count
+        adam_t[0] += 1
+        svlf.svlf_adam_step(feat_all, g_feat, m_f, v_f, adam_t[0], lr=LR)
+        svlf.svlf_adam_step(par_all, g_par, m_p, v_p, adam_t[0], lr=LR)
+
+    def step():
+        graphed()
+        adam()
+
+    tuned = None if args.no_autotune else autotune(step, f"batched64|{args.precision}", repeats=3)
+    step()
+    torch.cuda.synchronize()
+    # capture the render + forward/backward in a CUDA graph; every timed step replays it
+    g = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(g, stream=cap_stream):
+            graphed()
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    for _ in range(args.warmup):
+        g.replay()
+        adam()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        g.replay()
+        adam()
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    status = svlf.svlf_get_device_status()
+    return {
+        "metric": "rays/s: 64 scenes batched (render 256^2 + train 2^14 rays each, fwd+bwd+Adam), one CUDA-graph step",
+        "value": round((NR + NT) / (ms / 1e3), 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"{BATCH_SCENES} scenes, depth in 7..10, {min(n_leaves)}..{max(n_leaves)} leaves "
+                               f"({sum(n_leaves)} total), F=32, MLP 41->3x128->4, K=8",
+                   "render_rays": NR, "train_rays": NT, "autotune": tuned, "graph": True},
+        "clocks": clk, "device_status": status, "setup_s": round(time.time() - t0, 1),
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -525,6 +655,11 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "batched":
+        out = run_batched(args, rank, world, local_rank)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     out, W = run_ours(args, rank, world, local_rank)

@@ -228,6 +228,25 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
                             const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
                             const svlf_render_opts *opts, float *rgb, float *depth, void *stream);
 
+/* ------------------------------------------------------------ tuning */
+/* Launch-shape knobs (process-wide; 0 = the library's default). The
+ * autotuner (paper_2205_07058_b300/autotune.py) times candidates on the
+ * caller's workload and sets the best. They change speed, never results.
+ *   mlp_warpgroups      tensor-core forward: tiles in flight per CTA, 1..4
+ *   mlp_epilogue_batch  tensor-core forward: TMEM loads per wait, 1 or 2
+ *                       (2 limits the CTA to 3 warpgroups)
+ *   trace_budget        traversal steps between lane refills, 1..256
+ *   trace_block         traversal threads per block, 128 or 256 */
+typedef struct {
+    int mlp_warpgroups;
+    int mlp_epilogue_batch;
+    int trace_budget;
+    int trace_block;
+} svlf_tuning;
+
+int svlf_set_tuning(const svlf_tuning *t);
+int svlf_get_tuning(svlf_tuning *t);
+
 /* ------------------------------------------------------------ measurement */
 /* Per-kernel timing (measurement aid, not part of the method). When enabled,
  * every kernel the library launches is bracketed by CUDA events on its own

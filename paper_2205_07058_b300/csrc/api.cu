@@ -22,6 +22,10 @@ int num_sms() {
     return cached[dev];
 }
 
+static svlf_tuning g_tuning = {0, 1, 16, 256};
+
+const svlf_tuning &tuning() { return g_tuning; }
+
 MlpDims make_dims(const svlf_mlp_desc &d) {
     MlpDims md;
     std::memset(&md, 0, sizeof(md));
@@ -322,6 +326,26 @@ extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc
         return SVLF_ERR_CUDA;
     const int64_t cap = n_rays * (int64_t)K;
     *n_samples = (int64_t)c < cap ? (int64_t)c : cap;
+    return SVLF_OK;
+}
+
+extern "C" int svlf_set_tuning(const svlf_tuning *t) {
+    if (!t) return SVLF_ERR_ARG;
+    svlf_tuning v = *t;
+    if (v.mlp_warpgroups < 0 || v.mlp_warpgroups > 4) return SVLF_ERR_ARG;
+    if (v.mlp_epilogue_batch == 0) v.mlp_epilogue_batch = 1;
+    if (v.mlp_epilogue_batch != 1 && v.mlp_epilogue_batch != 2) return SVLF_ERR_ARG;
+    if (v.trace_budget == 0) v.trace_budget = 16;
+    if (v.trace_budget < 1 || v.trace_budget > 256) return SVLF_ERR_ARG;
+    if (v.trace_block == 0) v.trace_block = 256;
+    if (v.trace_block != 128 && v.trace_block != 256) return SVLF_ERR_ARG;
+    g_tuning = v;
+    return SVLF_OK;
+}
+
+extern "C" int svlf_get_tuning(svlf_tuning *t) {
+    if (!t) return SVLF_ERR_ARG;
+    *t = g_tuning;
     return SVLF_OK;
 }
 

@@ -243,9 +243,12 @@ __device__ __forceinline__ void prefetch_gather(const Sample &r, const void *fea
     prefetch_l2(ray + 5);
 }
 
-template <int H>
-__global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const __grid_constant__ SceneTable T,
-                                                                const TcFwdParams P) {
+// EPI = TMEM loads (of 32 columns) issued before each wait in the hidden-layer
+// epilogue: 1 keeps registers low enough for 4 warpgroups, 2 overlaps the
+// loads and needs the register budget of at most 3 warpgroups.
+template <int H, int EPI>
+__global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
+    mlp_forward_tc_kernel(const __grid_constant__ SceneTable T, const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t s_mbar[5];  // [0..3] per warpgroup, [4] weight load
@@ -364,20 +367,25 @@ __global__ void __launch_bounds__(512, 1) mlp_forward_tc_kernel(const __grid_con
                 if (l + 1 < P.lay.n_layers) {
                     // hidden layer epilogue: bias + ReLU -> 16-bit A operand of the next layer
 #pragma unroll
-                    for (int c = 0; c < H / 32; ++c) {
-                        uint32_t v[32];
-                        tc::tmem_ld32(tmem_row + (uint32_t)(c * 32), v);
+                    for (int c0 = 0; c0 < H / 32; c0 += EPI) {
+                        uint32_t v[EPI][32];
+#pragma unroll
+                        for (int u = 0; u < EPI; ++u) tc::tmem_ld32(tmem_row + (uint32_t)((c0 + u) * 32), v[u]);
                         tc::tmem_wait_ld();
-                        uint32_t p[16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float x0 = fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f);
-                            const float x1 = fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f);
-                            p[e] = tc::pack2(x0, x1, P.fp16);
+                        for (int u = 0; u < EPI; ++u) {
+                            const int c = c0 + u;
+                            uint32_t p[16];
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const float x0 = fmaxf(__uint_as_float(v[u][2 * e]) + b[c * 32 + 2 * e], 0.f);
+                                const float x1 = fmaxf(__uint_as_float(v[u][2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f);
+                                p[e] = tc::pack2(x0, x1, P.fp16);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                st_chunk(abuf, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
                         }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            st_chunk(abuf, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
                     }
                 } else {
                     uint32_t v[4];
@@ -414,7 +422,7 @@ static int tc_forward_config(const MlpDims &md, const TcLayout &lay, int &n_wg, 
     return SVLF_OK;
 }
 
-template <int H>
+template <int H, int EPI>
 static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay,
                   cudaStream_t s, int n_wg_override) {
     TcFwdParams P = P0;
@@ -422,18 +430,15 @@ static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md,
     int rc = tc_forward_config(md, lay, P.n_wg, P.abuf_bytes, smem);
     if (rc) return rc;
     if (n_wg_override > 0 && n_wg_override < P.n_wg) P.n_wg = n_wg_override;
-    if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (EPI == 2 && P.n_wg > 3) P.n_wg = 3;
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     prof_begin("mlp_forward_tc", s);
-    mlp_forward_tc_kernel<H><<<num_sms(), 128 * P.n_wg, smem, s>>>(T, P);
+    mlp_forward_tc_kernel<H, EPI><<<num_sms(), 128 * P.n_wg, smem, s>>>(T, P);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
-
-static int g_tc_wg_override = 0;
-
-void set_tc_warpgroups(int n) { g_tc_wg_override = n; }
 
 int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
                           const Workspace &ws, cudaStream_t s) {
@@ -449,7 +454,9 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneT
     P.samples = ws.samples;
     P.counter = ws.counter;
     P.outputs = ws.outputs;
-    return fwd_tc<kHp>(T, P, md, P.lay, s, g_tc_wg_override);
+    const svlf_tuning &tu = tuning();
+    if (tu.mlp_epilogue_batch == 2) return fwd_tc<kHp, 2>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    return fwd_tc<kHp, 1>(T, P, md, P.lay, s, tu.mlp_warpgroups);
 }
 
 // ---------------------------------------------------------------- backward

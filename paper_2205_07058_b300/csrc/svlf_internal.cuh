@@ -143,6 +143,9 @@ int launch_pack_weights(const svlf_mlp_desc &mlp, const SceneTable &T, const Wor
 
 int num_sms();
 
+// process-wide launch-shape settings (svlf_set_tuning), with defaults filled in
+const svlf_tuning &tuning();
+
 // per-kernel timing (profile.cu); no-ops unless svlf_profile_enable(1)
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(cudaStream_t s);

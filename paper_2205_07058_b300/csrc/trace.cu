@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
                                                     int2 *__restrict__ ray_span,
                                                     unsigned int *__restrict__ counter,
                                                     int32_t *__restrict__ hits,
-                                                    float *__restrict__ t_io) {
+                                                    float *__restrict__ t_io, int budget) {
     extern __shared__ uint32_t s_nodes[];
     __shared__ uint32_t s_stack[kMaxDepth * 256];  // per-lane ancestor stacks, [level][thread]
     const int lane = threadIdx.x & 31;
@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
     const int n_smem0 = min(T.s[0].tree.n_nodes, kSmemNodeWords);
     for (int i = threadIdx.x; i < n_smem0; i += blockDim.x) s_nodes[i] = T.s[0].tree.nodes[i];
     __syncthreads();
-    constexpr int kBudget = 16;  // walk steps per round
     for (;;) {
         long long chunk = 0;
         if (lane == 0) chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
@@ -356,8 +355,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
             // ---- walk
             if (have) {
                 int4 *slot = slots + g * K;
-                if (walk_steps(tree, n_smem ? s_nodes : nullptr, n_smem, w, K, slot, kBudget,
-                               s_stack + threadIdx.x, 256)) {
+                if (walk_steps(tree, n_smem ? s_nodes : nullptr, n_smem, w, K, slot, budget,
+                               s_stack + threadIdx.x, blockDim.x)) {
                     have = false;
                     done = true;
                 }
@@ -411,7 +410,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
 int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float *t_io,
                  cudaStream_t s) {
     if (T.K < 1 || T.K > kMaxK) return SVLF_ERR_UNSUPPORTED;
-    const int threads = 256;
+    const int threads = tuning().trace_block;
     const size_t smem = sizeof(uint32_t) * (size_t)min(T.s[0].tree.n_nodes, kSmemNodeWords);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
@@ -426,7 +425,8 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     prof_begin("trace", s);
     trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples,
                                                              reinterpret_cast<int4 *>(ws.outputs),
-                                                             ws.ray_span, ws.counter, hits, t_io);
+                                                             ws.ray_span, ws.counter, hits, t_io,
+                                                             tuning().trace_budget);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -298,3 +298,18 @@ def full_render_workload(seed: int = 1002, views: int = 4, res: int = 1600,
     az, el = random_view_angles(rng, views)
     rays = np.concatenate([pinhole_rays(az[v], el[v], res, res) for v in range(views)])
     return Workload(f"render_d9_{views}x{res}sq", scene, shape, 8, feats, params, rays)
+
+
+def batched_scenes(seed: int = 1004, n: int = 64, min_leaves: float = 1e4, max_leaves: float = 2e6):
+    """Scenes of uneven size: depth ~ U{7, 8, 9, 10}, a target leaf count
+    log-uniform in [min_leaves, max_leaves], met by choosing how many spheres
+    and box shells to draw (about 1.3e3 * 4^(L-6) leaves per primitive)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        depth = int(rng.integers(7, 11))
+        target = math.exp(rng.uniform(math.log(min_leaves), math.log(max_leaves)))
+        n_prim = int(np.clip(round(target / (1300.0 * 4.0 ** (depth - 6))), 1, 256))
+        n_box = n_prim // 3
+        out.append(make_scene(rng, depth, n_prim - n_box, n_box))
+    return out

@@ -56,6 +56,11 @@ class SceneDesc(ctypes.Structure):
                 ("d_features", ctypes.c_void_p), ("d_mlp_params", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("mlp_warpgroups", ctypes.c_int), ("mlp_epilogue_batch", ctypes.c_int),
+                ("trace_budget", ctypes.c_int), ("trace_block", ctypes.c_int)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -66,7 +71,7 @@ EXPORTS = [
     "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma",
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
-    "svlf_render_rays_backward_batched",
+    "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
 ]
 
 _lib = None
@@ -99,6 +104,8 @@ def lib():
     L.svlf_render_rays_batched.argtypes = [P(SceneDesc), i32, P(MlpDesc), P(RenderOpts), vp, sz, vp]
     L.svlf_render_rays_backward_batched.argtypes = [P(SceneDesc), i32, P(MlpDesc), P(RenderOpts), vp, sz, vp]
     L.svlf_render_rays_static.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp, vp, vp]
+    L.svlf_set_tuning.argtypes = [P(Tuning)]
+    L.svlf_get_tuning.argtypes = [P(Tuning)]
     L.svlf_profile_enable.argtypes = [i32]
     L.svlf_profile_report.argtypes = [P(KernelStat), i32, P(i32)]
     L.svlf_workspace_samples.argtypes = [vp, P(MlpDesc), i64, i32, P(i64), vp]
@@ -354,6 +361,17 @@ def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_m
         _ptr(A), _ptr(B), _ptr(D), B.shape[0], A.shape[1], int(a_mn_major), int(b_mn_major),
         int(A.dtype == torch.bfloat16), int(flags), _stream(stream)))
     return D
+
+
+def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0):
+    t = Tuning(int(mlp_warpgroups), int(mlp_epilogue_batch), int(trace_budget), int(trace_block))
+    _check("svlf_set_tuning", lib().svlf_set_tuning(ctypes.byref(t)))
+
+
+def svlf_get_tuning() -> dict:
+    t = Tuning()
+    _check("svlf_get_tuning", lib().svlf_get_tuning(ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
 def svlf_profile_enable(on: bool = True):

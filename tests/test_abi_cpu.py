@@ -58,3 +58,16 @@ def test_host_side_argument_errors(L):
         == svlf.SVLF_ERR_ARG
     assert L.svlf_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None, None) \
         == svlf.SVLF_ERR_ARG
+
+
+def test_tuning_arguments_are_checked(L):
+    from paper_2205_07058_b300 import svlf
+    svlf.svlf_set_tuning(3, 2, 32, 128)
+    assert svlf.svlf_get_tuning() == {"mlp_warpgroups": 3, "mlp_epilogue_batch": 2, "trace_budget": 32,
+                                      "trace_block": 128}
+    with pytest.raises(svlf.SvlfError):
+        svlf.svlf_set_tuning(mlp_warpgroups=9)
+    with pytest.raises(svlf.SvlfError):
+        svlf.svlf_set_tuning(trace_block=100)
+    svlf.svlf_set_tuning()  # defaults
+    assert svlf.svlf_get_tuning()["trace_budget"] == 16

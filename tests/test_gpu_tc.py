@@ -55,3 +55,21 @@ def test_render_tensor_core_tiny(tiny, prec):
     assert e64 <= (2e-3 if prec == "fp16" else 1e-2), e64
     empty = ref64.hits.n == 0
     assert np.array_equal(rgb[empty], np.broadcast_to(np.float32(bg), (empty.sum(), 3)))
+
+
+def test_launch_shapes_do_not_change_results(tiny):
+    """Every tuning candidate gives the same image as the defaults."""
+    from paper_2205_07058_b300 import svlf
+    from paper_2205_07058_b300.autotune import MLP_CANDIDATES, TRACE_CANDIDATES
+    tree, f, p, r = gpu_inputs(tiny)
+    net = net_for(tiny, svlf.BF16)
+    svlf.svlf_set_tuning()
+    ref, dref, _, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, tiny.K)
+    try:
+        for cand in TRACE_CANDIDATES + MLP_CANDIDATES:
+            svlf.svlf_set_tuning(**cand)
+            rgb, depth, _, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, tiny.K)
+            torch.testing.assert_close(rgb, ref, rtol=0, atol=0)
+            torch.testing.assert_close(depth, dref, rtol=0, atol=0)
+    finally:
+        svlf.svlf_set_tuning()
