@@ -337,6 +337,22 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
             for (int l = 0; l < P.lay.n_layers; ++l) {
                 const int N = P.lay.w_rows[l];
                 const int Kl = P.lay.w_cols[l];
+                const bool hidden = l + 1 < P.lay.n_layers;
+                if (hidden) {
+                    // the accumulator starts at the bias: the MMAs add onto it in float32
+                    const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + P.lay.bias_l[l]);
+#pragma unroll 1
+                    for (int c = 0; c < H / 32; ++c) {
+                        uint32_t v[32];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint4 t = b4[c * 8 + q];
+                            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+                        }
+                        tc::tmem_st32(tmem_row + (uint32_t)(c * 32), v);
+                    }
+                    tc::tmem_wait_st();
+                }
                 // A operand written by all threads -> visible to the tensor core
                 tc::fence_async_smem();
                 tc::fence_before_sync();
@@ -348,7 +364,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                     for (int k = 0; k < Kl; k += 16) {
                         const uint64_t da = tc::sdesc(abuf_s + (k >> 3) * (kTcTile * 16), kTcTile * 16, 128);
                         const uint64_t db = tc::sdesc(b_base + (k >> 3) * (N * 16), N * 16, 128);
-                        tc::mma_f16(tmem_wg, da, db, idesc, k > 0 ? 1u : 0u);
+                        tc::mma_f16(tmem_wg, da, db, idesc, (hidden || k > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(mbar);
                 }
@@ -365,7 +381,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                 tc::fence_after_sync();
                 const float *b = bias + P.lay.bias_l[l];
                 if (l + 1 < P.lay.n_layers) {
-                    // hidden layer epilogue: bias + ReLU -> 16-bit A operand of the next layer
+                    // hidden layer epilogue: ReLU of (bias + W x) -> 16-bit A operand of the next layer
 #pragma unroll
                     for (int c0 = 0; c0 < H / 32; c0 += EPI) {
                         uint32_t v[EPI][32];
@@ -377,11 +393,9 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                             const int c = c0 + u;
                             uint32_t p[16];
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const float x0 = fmaxf(__uint_as_float(v[u][2 * e]) + b[c * 32 + 2 * e], 0.f);
-                                const float x1 = fmaxf(__uint_as_float(v[u][2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f);
-                                p[e] = tc::pack2(x0, x1, P.fp16);
-                            }
+                            for (int e = 0; e < 16; ++e)
+                                p[e] = tc::relu_pack2(__uint_as_float(v[u][2 * e]), __uint_as_float(v[u][2 * e + 1]),
+                                                      P.fp16);
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
                                 st_chunk(abuf, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
@@ -704,14 +718,27 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 const int Kl = l == 0 ? lay.K0 : kHp;
                 const uint32_t xa = s_base + P.x_off[l];
                 const uint32_t wb = s_base + lay.w_off[l];
+                {  // the accumulator starts at the bias
+                    const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + lay.bias_l[l]);
+#pragma unroll 1
+                    for (int c = 0; c < kHp / 32; ++c) {
+                        uint32_t v[32];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint4 t = b4[c * 8 + q];
+                            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+                        }
+                        tc::tmem_st32(tmem + lane_off + (uint32_t)(c * 32), v);
+                    }
+                    tc::tmem_wait_st();
+                }
                 if (!run([&] {
                         mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
-                                128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), false);
+                                128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), true);
                     })) {
                     aborted = true;
                     break;
                 }
-                const float *b = bias + lay.bias_l[l];
                 uint8_t *xn = smem + P.x_off[l + 1];
 #pragma unroll 1
                 for (int c = 0; c < kHp / 32; ++c) {
@@ -721,9 +748,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     uint32_t p[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
-                        p[e] = tc::pack2(fmaxf(__uint_as_float(v[2 * e]) + b[c * 32 + 2 * e], 0.f),
-                                         fmaxf(__uint_as_float(v[2 * e + 1]) + b[c * 32 + 2 * e + 1], 0.f),
-                                         P.fp16);
+                        p[e] = tc::relu_pack2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]), P.fp16);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         st_chunk(xn, row, c * 4 + q, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
@@ -764,13 +789,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
                         uint32_t o[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            // a 16-bit activation is positive iff its sign bit is clear and it is non-zero
-                            const uint32_t lo16 = xw[e] & 0xFFFFu, hi16 = xw[e] >> 16;
-                            const float g0 = (lo16 != 0u && !(lo16 & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e]) : 0.f;
-                            const float g1 = (hi16 != 0u && !(hi16 & 0x8000u)) ? __uint_as_float(v[q * 8 + 2 * e + 1]) : 0.f;
-                            o[e] = tc::pack2(g0, g1, P.fp16);
-                        }
+                        for (int e = 0; e < 4; ++e)  // delta where the activation is positive, else 0
+                            o[e] = tc::mask_pack2(__uint_as_float(v[q * 8 + 2 * e]), __uint_as_float(v[q * 8 + 2 * e + 1]),
+                                                  xw[e], P.fp16);
                         *ptr = make_uint4(o[0], o[1], o[2], o[3]);
                     }
                 }

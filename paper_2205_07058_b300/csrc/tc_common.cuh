@@ -104,6 +104,21 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                  : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+          "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]),
+          "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]),
+          "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+          "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -174,6 +189,32 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, bool fp16) {
     }
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// ReLU of two float32 values as one packed 16-bit pair: rounding first and
+// taking max(., 0) on the pair gives the same bits as the other order.
+__device__ __forceinline__ uint32_t relu_pack2(float a, float b, bool fp16) {
+    if (fp16) {
+        __half2 h = __hmax2(__floats2half2_rn(a, b), __float2half2_rn(0.f));
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(a, b), __float2bfloat162_rn(0.f));
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// (g0, g1) rounded to a 16-bit pair, each kept where the matching half of the
+// 16-bit pair x is positive and zeroed elsewhere (the ReLU derivative).
+__device__ __forceinline__ uint32_t mask_pack2(float g0, float g1, uint32_t x, bool fp16) {
+    if (fp16) {
+        const __half2 g = __floats2half2_rn(g0, g1);
+        const __half2 m = __hgt2(*reinterpret_cast<const __half2 *>(&x), __float2half2_rn(0.f));
+        __half2 r = __hmul2(g, m);
+        return *reinterpret_cast<uint32_t *>(&r);
+    }
+    const __nv_bfloat162 g = __floats2bfloat162_rn(g0, g1);
+    const __nv_bfloat162 m = __hgt2(*reinterpret_cast<const __nv_bfloat162 *>(&x), __float2bfloat162_rn(0.f));
+    __nv_bfloat162 r = __hmul2(g, m);
+    return *reinterpret_cast<uint32_t *>(&r);
 }
 
 // Byte offset of element (r, k) in a core-matrix tile with R rows.

@@ -1,0 +1,74 @@
+"""Parity at the benchmark sizes, in the benchmark's launch configuration:
+the whole workload is rendered on the GPU and a seeded sample of its rays is
+checked against the oracle ray by ray."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2205_07058_b300 import inputs as I
+from tests.gpu_common import requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def _check_sample(w, rgb, depth, hits, sample, lowp, tol):
+    tree = O.build_octree(w.scene.leaf_ijk, w.scene.depth)
+    rays = w.rays[sample]
+    feats = w.features if not w.feat_bf16 else w.features  # stored values, widened by the oracle
+    dims = O.layer_dims(w.mlp.feat_dim, w.mlp.hidden, w.mlp.n_hidden)
+    ref = O.render(tree, feats, w.params, dims, rays, w.K, bf16=lowp)
+    ok = ~ref.hits.degenerate
+    assert np.array_equal(hits[sample][ok], ref.hits.rank[ok])
+    err = np.abs(rgb[sample][ok] - ref.rgb[ok]).max()
+    derr = (np.abs(depth[sample][ok] - ref.depth[ok]) / (1 + ref.depth[ok])).max()
+    assert err <= tol and derr <= tol, (err, derr)
+    assert (ref.hits.n > 0).sum() > 500
+    return err, int(ref.hits.degenerate.sum())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_full_render_4x1600_sampled(prec):
+    from paper_2205_07058_b300 import svlf
+    w = I.full_render_workload()
+    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
+    tree = svlf.Octree(torch.from_numpy(w.scene.leaf_ijk), 9)
+    f = torch.from_numpy(w.features).cuda()
+    p = torch.from_numpy(w.params).cuda()
+    r = torch.from_numpy(w.rays).cuda()
+    rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, w.K, want_hits=True)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    sample = np.random.default_rng(17).choice(w.rays.shape[0], 8192, replace=False)
+    lowp = {"fp32": False, "bf16": "bf16", "fp16": "fp16"}[prec]
+    err, ndeg = _check_sample(w, rgb.cpu().numpy(), depth.cpu().numpy(), hits.cpu().numpy(), sample, lowp,
+                              1e-5 if prec == "fp32" else 2e-3)
+    print(prec, "max colour error", err, "near-degenerate rays in sample", ndeg)
+
+
+def test_large_scene_bf16_features_sampled():
+    """Depth 10 (7.9 M leaves), features stored as bf16, 41 -> 4x128 -> 4, K = 16,
+    8 views of 1600^2 (20.48 M rays) in one call."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(1005)
+    scene = I.make_scene(rng, 10, 128, 128)
+    shape = I.MLPShape(32, 128, 4)
+    feats32 = I.make_features(rng, scene.n_leaves, 32)
+    feats_bf = torch.from_numpy(feats32).to(torch.bfloat16)
+    params = I.make_mlp(rng, shape)
+    az, el = I.random_view_angles(rng, 8)
+    rays = np.concatenate([I.pinhole_rays(az[v], el[v], 1600, 1600) for v in range(8)])
+    w = I.Workload("large", scene, shape, 16, feats_bf.float().numpy(), params, rays, feat_bf16=True)
+    net = svlf.Network(32, 128, 4, svlf.BF16, svlf.FEAT_BF16)
+    tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), 10)
+    f = feats_bf.contiguous().cuda()
+    p = torch.from_numpy(params).cuda()
+    r = torch.from_numpy(rays).cuda()
+    rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, 16, want_hits=True)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    sample = np.random.default_rng(18).choice(rays.shape[0], 4096, replace=False)
+    err, ndeg = _check_sample(w, rgb.cpu().numpy(), depth.cpu().numpy(), hits.cpu().numpy(), sample, "bf16", 2e-3)
+    print("large bf16 max colour error vs bf16-emulating oracle", err, "near-degenerate", ndeg)
