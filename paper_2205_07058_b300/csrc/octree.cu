@@ -3,8 +3,9 @@
 //
 // The build runs once per scene on the host: Morton-encode the leaves, sort,
 // de-duplicate, then derive the 4^3-leaf bricks (level L-2) and every node
-// level above them bottom-up. The resulting arrays are uploaded once; the
-// traversal kernel (trace.cu) reads them.
+// level above them bottom-up, and a dense index over the parents of the
+// bricks. The resulting arrays are uploaded once; the traversal kernel
+// (trace.cu) reads them.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -115,6 +116,40 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
         }
     }
 
+    // Dense index over the level L-3 cells (the parents of the bricks, 8^3
+    // finest cells each), x fastest: the node word where that node exists,
+    // else (mask byte 0) log2 of the edge, in finest cells, of the largest
+    // empty octree block that contains the cell. One load then answers what a
+    // descent from the root would: the cell's brick or its empty block.
+    std::vector<uint32_t> pgrid;
+    const int pshift = n_levels > 0 ? depth - 3 : 0;
+    if (n_levels > 0 && n_leaves > 0) {
+        const int64_t P = (int64_t)1 << pshift;
+        pgrid.assign((size_t)(P * P * P), (uint32_t)depth);
+        for (int l = 0; l < n_levels; ++l) {
+            for (size_t q = 0; q < lvl_code[l].size(); ++q) {
+                uint32_t x, y, z;
+                unmorton3(lvl_code[l][q], x, y, z);
+                const uint32_t w = nodes[lvl_off[l] + q];
+                if (l == n_levels - 1) {
+                    pgrid[(size_t)(((int64_t)z * P + y) * P + x)] = w;
+                    continue;
+                }
+                const int64_t span = P >> (l + 1);  // index cells per axis under one child
+                for (int o = 0; o < 8; ++o) {
+                    if ((w >> (24 + o)) & 1u) continue;
+                    const int64_t x0 = (2 * (int64_t)x + (o & 1)) * span;
+                    const int64_t y0 = (2 * (int64_t)y + ((o >> 1) & 1)) * span;
+                    const int64_t z0 = (2 * (int64_t)z + ((o >> 2) & 1)) * span;
+                    for (int64_t k = z0; k < z0 + span; ++k)
+                        for (int64_t j = y0; j < y0 + span; ++j)
+                            std::fill_n(pgrid.begin() + (size_t)((k * P + j) * P + x0), (size_t)span,
+                                        (uint32_t)(depth - l - 1));
+                }
+            }
+        }
+    }
+
     svlf_octree_s *t = new (std::nothrow) svlf_octree_s;
     if (!t) return SVLF_ERR_CUDA;
     std::memset(t, 0, sizeof(*t));
@@ -138,7 +173,9 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     size_t nb_ijk = sizeof(int32_t) * rank_ijk.size();
     size_t nb_nodes = sizeof(uint32_t) * (nodes.size() + 1);
     size_t nb_bricks = sizeof(uint4) * (bricks.size() + 1);
+    size_t nb_pgrid = sizeof(uint32_t) * (pgrid.size() + 1);
     ok = ok && cudaMalloc(&H.leaf_ijk_dev, nb_ijk > 0 ? nb_ijk : 16) == cudaSuccess;
+    ok = ok && cudaMalloc(&H.pgrid_dev, nb_pgrid) == cudaSuccess;
     ok = ok && cudaMalloc(&H.nodes_dev, nb_nodes) == cudaSuccess;
     ok = ok && cudaMalloc(&H.bricks_dev, nb_bricks) == cudaSuccess;
     if (ok && nb_ijk)
@@ -150,9 +187,13 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     if (ok && !bricks.empty())
         ok = cudaMemcpyAsync(H.bricks_dev, bricks.data(), sizeof(uint4) * bricks.size(),
                              cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (ok && !pgrid.empty())
+        ok = cudaMemcpyAsync(H.pgrid_dev, pgrid.data(), sizeof(uint32_t) * pgrid.size(),
+                             cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
         cudaFree(H.leaf_ijk_dev);
+        cudaFree(H.pgrid_dev);
         cudaFree(H.nodes_dev);
         cudaFree(H.bricks_dev);
         delete t;
@@ -160,6 +201,8 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     }
     H.view.nodes = H.nodes_dev;
     H.view.bricks = H.bricks_dev;
+    H.view.pgrid = H.pgrid_dev;
+    H.view.pgrid_shift = pshift;
     *out = t;
     if (n_leaves_out) *n_leaves_out = n_leaves;
     return SVLF_OK;
@@ -190,6 +233,7 @@ extern "C" int svlf_free_octree(svlf_octree tree) {
     cudaFree(tree->h.leaf_ijk_dev);
     cudaFree(tree->h.nodes_dev);
     cudaFree(tree->h.bricks_dev);
+    cudaFree(tree->h.pgrid_dev);
     delete tree;
     return SVLF_OK;
 }

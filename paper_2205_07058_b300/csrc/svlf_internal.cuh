@@ -12,7 +12,6 @@ namespace svlf {
 
 constexpr int kMaxDepth = 10;
 constexpr int kMaxK = 32;
-constexpr int kSmemNodeWords = 8192;  // octree node words staged in shared memory per CTA
 
 // ---------------------------------------------------------------- octree
 // Device layout of the sparse octree (built in octree.cu):
@@ -31,6 +30,10 @@ struct OctreeView {
     int n_nodes, n_bricks;
     const uint32_t *nodes;
     const uint4 *bricks;
+    // (2^(L-3))^3 words, x fastest: node word of each level L-3 cell, or, with
+    // a zero mask byte, log2 of the edge of the largest empty block holding it
+    const uint32_t *pgrid;
+    int pgrid_shift;    // L - 3 (0 when L = 2)
     int root_is_brick;  // depth 2: the root itself is the only brick
     int empty;          // no leaves
 };
@@ -40,6 +43,7 @@ struct OctreeHost {
     int32_t *leaf_ijk_dev;  // n_leaves x 3, rank order
     uint32_t *nodes_dev;
     uint4 *bricks_dev;
+    uint32_t *pgrid_dev;
 };
 
 // ---------------------------------------------------------------- samples

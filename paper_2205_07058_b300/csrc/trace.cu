@@ -4,14 +4,13 @@
 //
 // Design (one ray per thread, stackless):
 //  * The ray is walked voxel-block by voxel-block. At every position the
-//    octree is descended from the root to find either the largest empty
-//    block containing the current finest cell, or the cell's brick (the 4^3
-//    leaves under a level L-2 node, held as a 64-bit mask). The brick of the
-//    current cell and its parent node (8^3 cells) stay cached in registers,
-//    so consecutive cells inside a brick cost no memory access and a move to
-//    a neighbouring brick of the same parent costs one brick load.
-//  * The node words of the top levels (up to kSmemNodeWords) are staged in
-//    shared memory; deeper levels and bricks come through the read-only path.
+//    octree answers either the largest empty block containing the current
+//    finest cell, or the cell's brick (the 4^3 leaves under a level L-2 node,
+//    held as a 64-bit mask). A dense index over the level L-3 nodes (the
+//    parents of the bricks) gives that answer in one load instead of a
+//    descent from the root: the parent's node word, or the size of the empty
+//    block around it. The brick of the current cell stays cached in
+//    registers, so consecutive cells inside a brick cost no memory access.
 //  * Plane crossings t = (k 2^-L - o) / d are evaluated without a division:
 //    k 2^-L - o is split exactly into hi + lo (TwoSum) and multiplied by 1/d
 //    held as a double-float (r_hi + r_lo, formed once per ray with an FMA
@@ -35,9 +34,8 @@ namespace svlf {
 __device__ unsigned int g_device_status = 0;
 
 #ifdef SVLF_TRACE_STATS
-// [0] walk steps, [1] full descents, [2] node words read in descents,
-// [3] parent-cache hits, [4] brick loads, [5] rays entering the cube,
-// [6] steps inside a cached brick, [7] rays
+// [0] walk steps, [1] parent-index loads, [2], [3] unused, [4] brick loads,
+// [5] rays entering the cube, [6] steps inside a cached brick, [7] rays
 __device__ unsigned long long g_trace_stats[8];
 #define TRACE_STAT(i, v) atomicAdd(&g_trace_stats[i], (unsigned long long)(v))
 #else
@@ -58,9 +56,19 @@ __device__ __forceinline__ float cross_t(const RayState &R, int a, int k) {
 }
 
 // Cell index along axis a occupied just after time t, searched in [lo, hi].
+// Fast path: pos = (o + t d) n is rounded once (FMA; n is a power of two), so
+// it is within 2^-24 (|o| + |t d|) n cells of the exact position at t, and a
+// crossing from cross_t is within 2^-23 |t| of the exact one, i.e. 2^-23
+// |t d| n cells. When pos is farther than that from every cell boundary
+// (eps below is 16x the sum, plus a floor for t = 0), the plane counts in the
+// loops below cannot change floor(pos), and they are skipped.
 __device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int lo, int hi) {
-    float pos = (R.o[a] + t * R.d[a]) * (float)R.n;
-    int k = (int)floorf(fminf(fmaxf(pos, -1.0f), (float)R.n));
+    const float pos = fmaf(t, R.d[a], R.o[a]) * (float)R.n;
+    const float fl = floorf(fminf(fmaxf(pos, -1.0f), (float)R.n));
+    int k = (int)fl;
+    const float fr = pos - fl;
+    const float eps = (fabsf(R.o[a]) + fabsf(t * R.d[a]) + 0x1p-10f) * (float)R.n * 0x1p-19f;
+    if (k >= lo && k <= hi && fr > eps && fr < 1.0f - eps) return k;
     k = min(max(k, lo), hi);
     if (R.d[a] > 0.f) {
         for (int it = 0; it < 64 && k > lo && cross_t(R, a, k) > t; ++it) --k;
@@ -83,10 +91,6 @@ struct Walk {
     uint32_t cached;  // brick (level L-2) of the current cell
     uint64_t bmask;
     int bbase;
-    uint32_t pcached;  // its parent node (level L-3, 8^3 cells)
-    uint32_t pword;
-    uint32_t skey;     // packed cell whose root path the ancestor stack holds
-    int svalid;        // levels 0 .. svalid-1 of the stack are valid
 };
 
 // Root clip (slab test against the unit cube) and the first cell. Returns
@@ -117,24 +121,17 @@ __device__ __forceinline__ bool walk_init(const OctreeView &T, Walk &w) {
     w.cached = 0xFFFFFFFFu;
     w.bmask = 0;
     w.bbase = 0;
-    w.pcached = 0xFFFFFFFFu;
-    w.pword = 0;
-    w.skey = 0;
-    w.svalid = 0;
     return true;
 }
 
 // Up to `budget` steps of the walk; hits go to slot[0 .. K-1] (16 bytes each:
 // rank, packed cell, t_in, t_out). Returns true when the ray is finished (K
 // hits, left the cube, or an error was latched).
-// `stk` is this lane's ancestor stack: stk[l * stride] = node word of the
-// level-l ancestor of the cell w.skey (levels < w.svalid).
-__device__ bool walk_steps(const OctreeView &T, const uint32_t *s_nodes, int n_smem, Walk &w,
-                           int K, int4 *__restrict__ slot, int budget, uint32_t *stk, int stride) {
+__device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict__ slot, int budget) {
     const RayState &R = w.R;
-    const int L = T.depth;
     const int n = R.n;
     const int max_steps = 3 * n + 64;
+    const int ps = T.pgrid_shift;
     for (int it = 0; it < budget; ++it) {
         if (++w.steps > max_steps) {
             raise_status(SVLF_DEV_STEP_LIMIT);
@@ -149,69 +146,22 @@ __device__ bool walk_steps(const OctreeView &T, const uint32_t *s_nodes, int n_s
         int rank = -1;
         if (key == w.cached) TRACE_STAT(6, 1);
         if (key != w.cached) {
-            const uint32_t pkey = (uint32_t)(c[0] >> 3) | ((uint32_t)(c[1] >> 3) << 10) |
-                                  ((uint32_t)(c[2] >> 3) << 20);
-            int node = 0;
+            int node = 0;  // depth 2: the root is the only brick
             bool found = true;
-            if (pkey == w.pcached) {
-                TRACE_STAT(3, 1);
-                // same 8^3 region as before: one step down from the cached parent
+            if (T.n_node_levels > 0) {
+                TRACE_STAT(1, 1);
+                // 0 <= c < 2^L here, so the index stays inside the (2^(L-3))^3 words
+                const uint32_t pidx = (uint32_t)(c[0] >> 3) | ((uint32_t)(c[1] >> 3) << ps) |
+                                      ((uint32_t)(c[2] >> 3) << (2 * ps));
+                const uint32_t pw = __ldg(T.pgrid + pidx);
+                const uint32_t m = pw >> 24;
                 const int oct = ((c[0] >> 2) & 1) | (((c[1] >> 2) & 1) << 1) | (((c[2] >> 2) & 1) << 2);
-                const uint32_t m = w.pword >> 24;
                 if (!((m >> oct) & 1u)) {
-                    sz_log = 2;
+                    sz_log = m ? 2 : (int)(pw & 31u);  // empty brick, or the empty block around the parent
                     found = false;
                 } else {
-                    node = (int)(w.pword & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
+                    node = (int)(pw & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
                 }
-            } else if (T.n_node_levels == 0) {
-                node = 0;  // depth 2: the root is the only brick
-            } else {
-                TRACE_STAT(1, 1);
-                // restart at the deepest ancestor shared with the stacked path
-                int l = 0;
-                uint32_t wd;
-                if (w.svalid > 0) {
-                    const uint32_t x = ((uint32_t)c[0] ^ (w.skey & 1023u)) |
-                                       ((uint32_t)c[1] ^ ((w.skey >> 10) & 1023u)) |
-                                       ((uint32_t)c[2] ^ ((w.skey >> 20) & 1023u));
-                    const int shared = x ? L - 1 - (31 - __clz(x)) : L;  // deepest shared level
-                    l = min(shared, w.svalid - 1);
-                    wd = stk[l * stride];
-                } else {
-                    wd = n_smem > 0 ? s_nodes[0] : __ldg(T.nodes);
-                    stk[0] = wd;
-                }
-                int reached = l;
-                for (;;) {
-                    TRACE_STAT(2, 1);
-                    const int sh = L - 1 - l;
-                    const int oct = ((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2);
-                    if (l == T.n_node_levels - 1) {
-                        w.pcached = pkey;
-                        w.pword = wd;
-                    }
-                    const uint32_t m = wd >> 24;
-                    if (!((m >> oct) & 1u)) {
-                        sz_log = sh;
-                        found = false;
-                        break;
-                    }
-                    node = (int)(wd & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
-                    if (++l == T.n_node_levels) break;  // node is a brick index
-                    if (node < n_smem) {
-                        wd = s_nodes[node];
-                    } else if (node < T.n_nodes) {
-                        wd = __ldg(T.nodes + node);
-                    } else {
-                        raise_status(SVLF_DEV_BAD_INDEX);
-                        return true;
-                    }
-                    stk[l * stride] = wd;
-                    reached = l;
-                }
-                w.svalid = reached + 1;
-                w.skey = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
             }
             if (found) {
                 if (node >= T.n_bricks) {
@@ -294,14 +244,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
                                                     unsigned int *__restrict__ counter,
                                                     int32_t *__restrict__ hits,
                                                     float *__restrict__ t_io, int budget) {
-    extern __shared__ uint32_t s_nodes[];
-    __shared__ uint32_t s_stack[kMaxDepth * 256];  // per-lane ancestor stacks, [level][thread]
     const int lane = threadIdx.x & 31;
     const int K = T.K;
-    // stage the top levels of the first scene (other scenes read them through L1)
-    const int n_smem0 = min(T.s[0].tree.n_nodes, kSmemNodeWords);
-    for (int i = threadIdx.x; i < n_smem0; i += blockDim.x) s_nodes[i] = T.s[0].tree.nodes[i];
-    __syncthreads();
     for (;;) {
         long long chunk = 0;
         if (lane == 0) chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
@@ -310,7 +254,6 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
         const int sc = scene_of_chunk(T, chunk);
         const SceneDev &S = T.s[sc];
         const OctreeView &tree = S.tree;
-        const int n_smem = sc == 0 ? n_smem0 : 0;
         const int64_t r_begin = (chunk - S.chunk_begin) * kTraceChunk;
         const int chunk_n = (int)min((int64_t)kTraceChunk, S.n_rays - r_begin);
         int next = 0;        // rays of the chunk handed out so far (warp-uniform)
@@ -355,8 +298,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
             // ---- walk
             if (have) {
                 int4 *slot = slots + g * K;
-                if (walk_steps(tree, n_smem ? s_nodes : nullptr, n_smem, w, K, slot, budget,
-                               s_stack + threadIdx.x, blockDim.x)) {
+                if (walk_steps(tree, w, K, slot, budget)) {
                     have = false;
                     done = true;
                 }
@@ -411,7 +353,7 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
                  cudaStream_t s) {
     if (T.K < 1 || T.K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     const int threads = tuning().trace_block;
-    const size_t smem = sizeof(uint32_t) * (size_t)min(T.s[0].tree.n_nodes, kSmemNodeWords);
+    const size_t smem = 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
             cudaSuccess || per_sm < 1)
