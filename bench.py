@@ -65,6 +65,9 @@ def parse():
                    help="step: the headline render + train step; batched: 64 scenes in one "
                         "launch per kernel under a CUDA graph")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tuning", default=None,
+                   help="fixed launch shapes instead of the search, e.g. "
+                        "mlp_warpgroups=4,mlp_epilogue_batch=1,trace_budget=16,trace_block=128")
     p.add_argument("--render-only", action="store_true",
                    help="time only the render pass (profiling aid; not the benchmark step)")
     p.add_argument("--views", type=int, default=RENDER_VIEWS)
@@ -202,6 +205,16 @@ def ncu_traffic(kernel: str):
     return ent
 
 
+def fixed_tuning(args):
+    """Apply --tuning k=v,... (launch shapes only; results do not depend on them)."""
+    if not args.tuning:
+        return None
+    from paper_2205_07058_b300 import svlf
+    kv = dict(item.split("=") for item in args.tuning.split(","))
+    svlf.svlf_set_tuning(**{k: int(v) for k, v in kv.items()})
+    return {"tuning": svlf.svlf_get_tuning(), "searched": False}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2205_07058_b300 import svlf
@@ -280,8 +293,8 @@ def run_ours(args, rank, world, local_rank):
         if not args.render_only:
             train_phase()
 
-    tuned = None
-    if not args.no_autotune and world == 1:
+    tuned = fixed_tuning(args)
+    if tuned is None and not args.no_autotune and world == 1:
         from paper_2205_07058_b300.autotune import autotune
         tuned = autotune(step, f"step|{args.precision}|{args.views}x{args.res}|{int(args.render_only)}", repeats=3)
     for _ in range(args.warmup):
@@ -607,7 +620,9 @@ def run_batched(args, rank, world, local_rank):
         graphed()
         adam()
 
-    tuned = None if args.no_autotune else autotune(step, f"batched64|{args.precision}", repeats=3)
+    tuned = fixed_tuning(args)
+    if tuned is None and not args.no_autotune:
+        tuned = autotune(step, f"batched64|{args.precision}", repeats=3)
     step()
     torch.cuda.synchronize()
     # capture the render + forward/backward in a CUDA graph; every timed step replays it

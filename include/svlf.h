@@ -273,10 +273,11 @@ int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc *mlp, int6
  * network kernels use (K-major, or MN-major when the flag is set).
  * A: device, 128 x K 16-bit values (bf16 if bf16 != 0, else f16), row-major.
  * B: device, N x K, row-major. D: device, 128 x N float32.
- * N in {32, 64, ..., 256}, K in {16, 32, ..., 256}. flags (layout diagnosis,
+ * N in {16, 32, ..., 256}, K in {16, 32, ..., 256}. flags (layout diagnosis,
  * 0 for the kernels' convention): bit 0 exchanges the two descriptor byte
  * offsets, bit 1 stages B before A, bits 2 / 3 start the B / A descriptor
- * 16 bytes later. */
+ * 16 bytes later; bit 5 reads A from tensor memory instead (row m in lane m,
+ * element pairs packed per 32-bit column; requires a_mn_major = 0). */
 int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
                       int a_mn_major, int b_mn_major, int bf16, int flags, void *stream);
 

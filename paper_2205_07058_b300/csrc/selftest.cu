@@ -1,7 +1,8 @@
 // Self-test of the tensor-core operand layouts: one 128 x N x K product
 // D = A B^T through tcgen05.mma, with either operand in K-major or MN-major
-// shared-memory layout. Test aid for the descriptor conventions the network
-// kernels rely on; not part of the rendering method.
+// shared-memory layout, or with A in tensor memory (flags bit 5). Test aid
+// for the descriptor conventions the network kernels rely on; not part of the
+// rendering method.
 #include "svlf_internal.cuh"
 #include "tc_common.cuh"
 
@@ -17,8 +18,10 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
     // flags: bit 0 swap the two descriptor byte offsets, bit 1 place B before A,
-    // bit 2 / bit 3 start the B / A descriptor 16 bytes later
+    // bit 2 / bit 3 start the B / A descriptor 16 bytes later, bit 5 A from
+    // TMEM columns 256 .. 256 + K/2 (packed pairs) instead of shared memory
     const int swap = flags & 1;
+    const bool a_tm = (flags & 32) != 0;
     const int gap = (flags >> 8) & 0xFFFF;  // bytes between the two staged operands
     uint8_t *sa = (flags & 2) ? smem + N * K * 2 + gap : smem;
     uint8_t *sb = (flags & 2) ? smem : smem + 128 * K * 2 + gap;
@@ -40,7 +43,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
         tc::mbar_init_fence();
     }
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(&s_tmem), 256);
+        tc::tmem_alloc(tc::smem_u32(&s_tmem), 512);
         tc::tmem_relinquish();
     }
     tc::fence_async_smem();
@@ -48,6 +51,23 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
+    if (a_tm) {
+        // row tid of A -> TMEM lane tid, elements (2j, 2j+1) in column 256 + j
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + 256u;
+        for (int c = 0; c < K / 2; c += 32) {
+            uint32_t v[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int j = c + e;
+                v[e] = j < K / 2 ? (uint32_t)A[tid * K + 2 * j] | ((uint32_t)A[tid * K + 2 * j + 1] << 16) : 0u;
+            }
+            tc::tmem_st32(trow + (uint32_t)c, v);
+        }
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     if (tid == 0) {
         const uint32_t idesc = tc::idesc_f16(128, N, bf16, a_mn, b_mn);
         for (int k = 0; k < K; k += 16) {
@@ -60,7 +80,10 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
             }
             const uint64_t da = tc::sdesc(tc::smem_u32(sa) + adj_a + (k >> 3) * (a_mn ? 128 : 2048), la, sa_);
             const uint64_t db = tc::sdesc(tc::smem_u32(sb) + adj_b + (k >> 3) * (b_mn ? 128 : N * 16), lb, sb_);
-            tc::mma_f16(tmem, da, db, idesc, k > 0 ? 1u : 0u);
+            if (a_tm)
+                tc::mma_f16_ta(tmem, tmem + 256u + (uint32_t)(k >> 1), db, idesc, k > 0 ? 1u : 0u);
+            else
+                tc::mma_f16(tmem, da, db, idesc, k > 0 ? 1u : 0u);
         }
         tc::mma_commit(tc::smem_u32(&s_mbar));
     }
@@ -80,7 +103,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 256);
+        tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -91,8 +114,9 @@ using namespace svlf;
 extern "C" int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
                                  int a_mn_major, int b_mn_major, int bf16, int flags,
                                  void *stream) {
-    if (!A || !B || !D || N < 32 || N > 256 || N % 32 || K < 16 || K > 256 || K % 16)
+    if (!A || !B || !D || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16)
         return SVLF_ERR_ARG;
+    if ((flags & 32) && a_mn_major) return SVLF_ERR_ARG;  // A in TMEM is K-major only
     // Generous on purpose: every read the descriptors can address stays inside
     // the allocation even if a layout were misread.
     const size_t need = (size_t)(128 + N) * K * 2 + ((flags >> 8) & 0xFFFF) + 128;

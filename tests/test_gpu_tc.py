@@ -25,6 +25,20 @@ def test_mma_operand_layouts(dtype, N, K, a_mn, b_mn):
     assert svlf.svlf_get_device_status() == 0
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("N,K", [(128, 48), (128, 128), (16, 128), (64, 144), (256, 16)])
+@pytest.mark.parametrize("b_mn", [False, True])
+def test_mma_a_operand_in_tmem(dtype, N, K, b_mn):
+    from paper_2205_07058_b300 import svlf
+    g = torch.Generator(device="cpu").manual_seed(N * 1000 + K + 7)
+    A = torch.randn(128, K, generator=g).to(dtype).cuda()
+    B = torch.randn(N, K, generator=g).to(dtype).cuda()
+    D = svlf.svlf_selftest_mma(A, B, False, b_mn, flags=32)
+    ref = A.double() @ B.double().T
+    torch.testing.assert_close(D.double(), ref, rtol=1e-5, atol=1e-4)
+    assert svlf.svlf_get_device_status() == 0
+
+
 def _render(w, precision, params, bg=(0.0, 0.0, 0.0)):
     from paper_2205_07058_b300 import svlf
     tree, f, p, r = gpu_inputs(w, params=params)
