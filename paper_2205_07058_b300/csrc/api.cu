@@ -132,6 +132,15 @@ static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_des
     T.n = n_scenes;
     T.K = K;
     int64_t rays = 0, chunks = 0;
+    // Traversal work items: kTraceChunk rays each, or fewer for small launches
+    // so that every resident warp of the traversal kernel gets work.
+    {
+        int64_t all = 0;
+        for (int i = 0; i < n_scenes; ++i) all += scenes[i].n_rays > 0 ? scenes[i].n_rays : 0;
+        const int64_t want = (int64_t)2 * num_sms() * 32;  // work items for two rounds of resident warps
+        T.chunk_rays = kTraceChunk;
+        while (T.chunk_rays > 32 && all / T.chunk_rays < want) T.chunk_rays >>= 1;
+    }
     for (int i = 0; i < n_scenes; ++i) {
         const svlf_scene &sc = scenes[i];
         if ((rc = check_scene(sc, !backward))) return rc;
@@ -151,7 +160,7 @@ static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_des
         d.n_rays = sc.n_rays;
         d.chunk_begin = chunks;
         rays += sc.n_rays;
-        chunks += (sc.n_rays + kTraceChunk - 1) / kTraceChunk;
+        chunks += (sc.n_rays + T.chunk_rays - 1) / T.chunk_rays;
     }
     T.total_rays = rays;
     T.total_chunks = chunks;

@@ -63,7 +63,7 @@ struct __align__(16) Sample {
 // as a kernel parameter, so a call needs no host-to-device copy and can be
 // captured in a CUDA graph.
 constexpr int kMaxScenes = 64;
-constexpr int kTraceChunk = 128;  // rays per traversal work item (one warp)
+constexpr int kTraceChunk = 128;  // largest number of rays per traversal work item (one warp)
 
 struct SceneDev {
     OctreeView tree;
@@ -83,6 +83,8 @@ struct SceneTable {
     int K;
     int64_t total_rays;
     int64_t total_chunks;
+    int chunk_rays;  // rays per traversal work item: 32, 64 or kTraceChunk
+    int pad_;
     SceneDev s[kMaxScenes];
 };
 

@@ -231,7 +231,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Each warp claims chunks of kTraceChunk rays of one scene from a global
+// Each warp claims chunks of T.chunk_rays rays of one scene from a global
 // counter (in order, so neighbouring warps walk neighbouring pixels). Inside
 // a chunk a lane whose ray is finished takes the chunk's next ray, so lanes
 // stay busy while other rays of the warp are still walking; rays that miss
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
         const int sc = scene_of_chunk(T, chunk);
         const SceneDev &S = T.s[sc];
         const OctreeView &tree = S.tree;
-        const int64_t r_begin = (chunk - S.chunk_begin) * kTraceChunk;
-        const int chunk_n = (int)min((int64_t)kTraceChunk, S.n_rays - r_begin);
+        const int64_t r_begin = (chunk - S.chunk_begin) * T.chunk_rays;
+        const int chunk_n = (int)min((int64_t)T.chunk_rays, S.n_rays - r_begin);
         int next = 0;        // rays of the chunk handed out so far (warp-uniform)
         bool have = false;   // this lane walks a ray
         int64_t g = 0;       // its global ray index
