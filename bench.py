@@ -38,17 +38,34 @@ TRAIN_RES = 800
 TRAIN_BATCH = 1 << 18
 K_HITS = 8
 FEAT, HIDDEN, N_HIDDEN = 32, 128, 3
+SCENE_DEPTH, N_SPHERES, N_BOXES = 9, 64, 32
+FEAT_BF16 = False  # features stored as bf16 (fp32 master copy for Adam)
 SCENE_SEED = 1002
 TEACHER_SEED = 2000
 LR = 1e-3
 DEPTH_WEIGHT = 0.1
 WORKLOAD = ("render 4x1600^2 + train 2^18 rays (100 views of 800^2); depth-9 octree over 64 "
             "spheres + 32 box shells (1.69 M leaves), F=32 fp32, MLP 41->3x128->4, K=8")
+METRIC = "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each"
+
+# The large-scene workload: depth-10 octree over 128 spheres + 128 box shells
+# (about 8 M leaves), features 32 x bf16, 41 -> 4x128 -> 4, K = 16; a step renders
+# 8 views of 1600^2 and trains on 2^20 rays.
+LARGE = dict(RENDER_VIEWS=8, TRAIN_BATCH=1 << 20, K_HITS=16, N_HIDDEN=4, SCENE_DEPTH=10, N_SPHERES=128,
+             N_BOXES=128, FEAT_BF16=True, SCENE_SEED=1005,
+             WORKLOAD=("render 8x1600^2 + train 2^20 rays (100 views of 800^2); depth-10 octree over 128 "
+                       "spheres + 128 box shells, F=32 bf16 storage (fp32 master for Adam), "
+                       "MLP 41->4x128->4, K=16"),
+             METRIC="rays/s: render 8x1600^2 + train 2^20 rays (fwd+bwd+Adam), one step each, large scene")
 
 
-def flops_per_sample(feat=FEAT, hidden=HIDDEN, n_hidden=N_HIDDEN):
-    d_in = feat + 9
-    return 2 * (d_in * hidden + (n_hidden - 1) * hidden * hidden + 4 * hidden)
+def use_profile(prof: dict):
+    globals().update(prof)
+
+
+def flops_per_sample():
+    d_in = FEAT + 9
+    return 2 * (d_in * HIDDEN + (N_HIDDEN - 1) * HIDDEN * HIDDEN + 4 * HIDDEN)
 
 
 def parse():
@@ -61,18 +78,26 @@ def parse():
     p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="step", choices=["step", "batched"],
+    p.add_argument("--workload", default="step", choices=["step", "batched", "large"],
                    help="step: the headline render + train step; batched: 64 scenes in one "
-                        "launch per kernel under a CUDA graph")
+                        "launch per kernel under a CUDA graph; large: depth-10 scene, bf16 "
+                        "features, 4x128 network, K = 16, 8 views + 2^20 training rays")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tuning", default=None,
                    help="fixed launch shapes instead of the search, e.g. "
                         "mlp_warpgroups=4,mlp_epilogue_batch=1,trace_budget=16,trace_block=128")
     p.add_argument("--render-only", action="store_true",
                    help="time only the render pass (profiling aid; not the benchmark step)")
-    p.add_argument("--views", type=int, default=RENDER_VIEWS)
-    p.add_argument("--res", type=int, default=RENDER_RES)
-    return p.parse_args()
+    p.add_argument("--views", type=int, default=None, help="render views (default: the workload's)")
+    p.add_argument("--res", type=int, default=None, help="render resolution (default: the workload's)")
+    a = p.parse_args()
+    if a.workload == "large":
+        use_profile(LARGE)
+    if a.views is None:
+        a.views = RENDER_VIEWS
+    if a.res is None:
+        a.res = RENDER_RES
+    return a
 
 
 # ----------------------------------------------------------------------------
@@ -81,7 +106,7 @@ def parse():
 def make_workload(rank: int, views: int, res: int):
     from paper_2205_07058_b300 import inputs as I
     rng = np.random.default_rng(SCENE_SEED)
-    scene = I.make_scene(rng, 9, 64, 32)
+    scene = I.make_scene(rng, SCENE_DEPTH, N_SPHERES, N_BOXES)
     shape = I.MLPShape(FEAT, HIDDEN, N_HIDDEN)
     feats = I.make_features(rng, scene.n_leaves, FEAT)
     params = I.make_mlp(rng, shape)
@@ -230,11 +255,14 @@ def run_ours(args, rank, world, local_rank):
     W = make_workload(rank, args.views, args.res)
     prec = svlf.PRECISIONS[args.precision]
     tprec = svlf.PRECISIONS[args.train_precision or args.precision]
-    net = svlf.Network(FEAT, HIDDEN, N_HIDDEN, prec)
-    tnet = svlf.Network(FEAT, HIDDEN, N_HIDDEN, tprec)
+    fdt = svlf.FEAT_BF16 if FEAT_BF16 else svlf.FEAT_F32
+    net = svlf.Network(FEAT, HIDDEN, N_HIDDEN, prec, fdt)
+    tnet = svlf.Network(FEAT, HIDDEN, N_HIDDEN, tprec, fdt)
     scene = W["scene"]
     tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), scene.depth)
-    feats = torch.from_numpy(W["feats"]).to(dev)
+    feats = torch.from_numpy(W["feats"]).to(dev)  # float32 master copy (what Adam updates)
+    # what the kernels read: the master itself, or its bf16 shadow that Adam rewrites
+    feats_k = feats.to(torch.bfloat16) if FEAT_BF16 else feats
     params = torch.from_numpy(W["params"]).to(dev)
     rays = torch.from_numpy(W["render_rays"]).to(dev)
     trays = torch.from_numpy(W["train_rays"]).to(dev)
@@ -244,8 +272,8 @@ def run_ours(args, rank, world, local_rank):
     if args.render_only:
         rgb_t = torch.zeros((NT, 3), device=dev)
     else:
-        rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats, teacher,
-                                                  svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32), trays, K_HITS)
+        rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats_k, teacher,
+                                                  svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32, fdt), trays, K_HITS)
     depth_t = torch.from_numpy(W["depth_t"]).to(dev)
     mask = torch.from_numpy(W["mask"]).to(dev)
     del teacher
@@ -268,18 +296,19 @@ def run_ours(args, rank, world, local_rank):
     ev = {}
 
     def render_phase():
-        svlf.svlf_render_rays(tree, feats, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
+        svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
 
     def train_phase():
         step_no[0] += 1
         g_feat.zero_()
         g_par.zero_()
         loss.zero_()
-        svlf.svlf_render_rays(tree, feats, params, tnet, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
+        svlf.svlf_render_rays(tree, feats_k, params, tnet, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
         svlf.svlf_loss(trgb, tdepth, rgb_t, depth_t, mask, DEPTH_WEIGHT, d_rgb, d_depth, loss)
-        svlf.svlf_render_rays_backward(tree, feats, params, tnet, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb,
+        svlf.svlf_render_rays_backward(tree, feats_k, params, tnet, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb,
                                        d_depth, g_feat, g_par, ws_t)
-        svlf.svlf_adam_step(feats, g_feat, m_feat, v_feat, step_no[0], lr=LR)
+        svlf.svlf_adam_step(feats, g_feat, m_feat, v_feat, step_no[0], lr=LR,
+                            bf16_shadow=feats_k if FEAT_BF16 else None)
         svlf.svlf_adam_step(params, g_par, m_par, v_par, step_no[0], lr=LR)
 
     def step(record=None):
@@ -296,7 +325,8 @@ def run_ours(args, rank, world, local_rank):
     tuned = fixed_tuning(args)
     if tuned is None and not args.no_autotune and world == 1:
         from paper_2205_07058_b300.autotune import autotune
-        tuned = autotune(step, f"step|{args.precision}|{args.views}x{args.res}|{int(args.render_only)}", repeats=3)
+        tuned = autotune(step, f"{args.workload}|{args.precision}|{args.views}x{args.res}|{int(args.render_only)}",
+                         repeats=3)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -425,7 +455,8 @@ def run_ours(args, rank, world, local_rank):
             achieved = work / avg_s / 1e9
         tr = ncu_traffic(dom)
         roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
-                "peak_source": f"{peak_src} ({'sustained' if bound == 'tensor' else 'copy'})",
+                "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
+                                else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
                 "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": tr["bytes_per_launch"] if tr else None,
                 "avg_launch_ms": round(ms / launches, 4)}
@@ -434,7 +465,7 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         out = {
-            "metric": "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each",
+            "metric": METRIC,
             "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
@@ -442,7 +473,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "render_rays": N, "train_rays": NT, "K": K_HITS,
                        "network_precision": args.precision, "train_precision": args.train_precision or args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (features 216 MB + rays 246 MB per step)",
+                       "l2": f"inputs larger than L2 (features {feats_k.numel() * feats_k.element_size() / 1e6:.0f} MB"
+                             f" + rays {(N + NT) * 24 / 1e6:.0f} MB per step)",
                        "autotune": tuned},
             "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
             "train_rays_per_s": None if args.render_only else round(NT * args.steps / (train_ms / 1e3), 1),
@@ -529,7 +561,7 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     v = rays / dt
     return {"impl": "reference",
-            "metric": "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each",
+            "metric": METRIC,
             "value": round(v, 2), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

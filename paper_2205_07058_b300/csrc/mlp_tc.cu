@@ -511,6 +511,12 @@ struct TcBwdParams {
     uint32_t x_off[kMaxLayers];  // X_l buffers (byte offsets after the weight image)
     uint32_t gout_off, ones_off;
     uint32_t col_dwout, col_dw[kMaxLayers], col_db[kMaxLayers], tmem_cols;
+    // Streamed weights (networks whose full image and activations do not fit
+    // together): only the image tail from w_off[nh] (output layer + biases) is
+    // resident at offset 0; hidden W_l is loaded into slot l % 2 when needed.
+    int stream;
+    uint32_t res_bytes;    // resident tail size
+    uint32_t slot_off[2];  // byte offsets of the two weight slots
 };
 
 // Shared-memory and TMEM plan of one backward pass (P.l_min, P.l_top,
@@ -527,7 +533,21 @@ static uint32_t tc_bwd_cols(const MlpDims &md, const TcLayout &lay, int l_min, i
 
 static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
     const TcLayout &lay = P.lay;
+    // activations, deltas and ones take this many bytes after the weights
+    const uint32_t act = (uint32_t)(kTcTile * lay.K0 * 2 + md.nh * kTcTile * kHp * 2 +
+                                    2 * kTcTile * kTcOutN * 2);
     uint32_t off = lay.bytes;
+    P.stream = 0;
+    if ((size_t)lay.bytes + act + 128 > 227 * 1024 - 2048) {
+        // stream the hidden layers' weights through two slots
+        P.stream = 1;
+        P.res_bytes = lay.bytes - lay.w_off[md.nh];
+        off = (P.res_bytes + 127) & ~127u;
+        const uint32_t slot = (uint32_t)(kHp * (lay.K0 > kHp ? lay.K0 : kHp) * 2);
+        P.slot_off[0] = off;
+        P.slot_off[1] = off + slot;
+        off += 2 * slot;
+    }
     P.x_off[0] = off;
     off += kTcTile * lay.K0 * 2;
     for (int l = 1; l <= md.nh; ++l) {
@@ -559,7 +579,7 @@ static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
         P.col_db[l] = col;
         col += 16;
     }
-    if (col > 512 || smem > 227 * 1024) return false;
+    if (col > 512 || smem > 227 * 1024 - 2048) return false;
     uint32_t n = 32;
     while (n < col) n <<= 1;
     P.tmem_cols = n;
@@ -591,12 +611,17 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     const MlpDims &md = P.md;
     const TcLayout &lay = P.lay;
     uint8_t *wimg = smem;
-    const float *bias = reinterpret_cast<const float *>(wimg + lay.bias_off);
+    // image offset of what sits at shared offset 0 (the whole image, or its tail)
+    const uint32_t img0 = P.stream ? lay.w_off[md.nh] : 0u;
+    const float *bias = reinterpret_cast<const float *>(wimg + lay.bias_off - img0);
     const uint32_t s_base = tc::smem_u32(smem);
+    __shared__ __align__(8) uint64_t s_wslot[2];  // streamed weight slots
 
     if (row == 0) {
         tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
         tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
+        tc::mbar_init(tc::smem_u32(&s_wslot[0]), 1);
+        tc::mbar_init(tc::smem_u32(&s_wslot[1]), 1);
         tc::mbar_init_fence();
     }
     if (warp == 0) {
@@ -650,6 +675,65 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         return !any;
     };
 
+    // ---- streamed weights: slot l % 2 holds W_l (uniform state in every thread)
+    int slot_w[2] = {-1, -1};          // layer held (or being loaded) per slot
+    bool slot_busy[2] = {false, false};  // load issued, not yet waited for
+    uint32_t slot_phase[2] = {0u, 0u};
+    const uint8_t *img_sc = nullptr;     // the current scene's packed image
+    auto issue_load = [&](int l) {
+        const int k = l & 1;
+        const uint32_t bytes = (uint32_t)(lay.w_rows[l] * lay.w_cols[l] * 2);
+        if (row == 0) {
+            const uint32_t mb = tc::smem_u32(&s_wslot[k]);
+            tc::mbar_expect_tx(mb, bytes);
+            tc::bulk_g2s(s_base + P.slot_off[k], img_sc + lay.w_off[l], bytes, mb);
+        }
+        slot_w[k] = l;
+        slot_busy[k] = true;
+    };
+    // W_l resident and complete; false on timeout
+    auto ensure = [&](int l) -> bool {
+        if (!P.stream) return true;
+        const int k = l & 1;
+        if (slot_w[k] != l) issue_load(l);
+        if (slot_busy[k]) {
+            const bool to = !tc::mbar_wait(tc::smem_u32(&s_wslot[k]), slot_phase[k]);
+            slot_phase[k] ^= 1u;
+            slot_busy[k] = false;
+            if (tc::wg_sync_or(0, to)) {
+                if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+                return false;
+            }
+        }
+        return true;
+    };
+    // start loading W_next while W_cur is in use, if they sit in different slots
+    // (the other slot's previous weights were last read by MMAs already complete)
+    auto prefetch = [&](int next, int cur) {
+        if (!P.stream || next < 0 || next >= md.nh || ((next ^ cur) & 1) == 0) return;
+        if (slot_w[next & 1] == next) return;
+        if (slot_busy[next & 1]) return;  // not reached: every issued load is waited for before reuse
+        issue_load(next);
+    };
+    // wait for every weight load still in flight (before a scene change and
+    // before the CTA exits: no bulk copy may outlive its destination); false on timeout
+    auto drain = [&]() -> bool {
+        bool to = false;
+        for (int k = 0; k < 2; ++k)
+            if (slot_busy[k]) {
+                to |= !tc::mbar_wait(tc::smem_u32(&s_wslot[k]), slot_phase[k]);
+                slot_phase[k] ^= 1u;
+                slot_busy[k] = false;
+            }
+        return !tc::wg_sync_or(0, to);
+    };
+    auto waddr = [&](int l) -> uint32_t {
+        if (!P.stream) return s_base + lay.w_off[l];
+        return l == md.nh ? s_base : s_base + P.slot_off[l & 1];
+    };
+    // does the backward at layer l form G_l = G W_l (reads W_l)?
+    auto uses_dx = [&](int l, bool feat) { return l > P.l_min || (l == 0 && feat); };
+
     const int64_t n_tiles = s_map.tile0[T.n];
     const int64_t lo = n_tiles * blockIdx.x / gridDim.x;
     const int64_t hi = n_tiles * (blockIdx.x + 1) / gridDim.x;
@@ -662,13 +746,21 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         // this scene's resident weights
         __syncthreads();
         if (row < 4) s_dbout[row] = 0.f;
-        if (row == 0) {
-            const uint32_t mb = tc::smem_u32(&s_mbar[1]);
-            const uint8_t *img = P.images + sc * P.image_stride;
-            tc::mbar_expect_tx(mb, lay.bytes);
-            for (uint32_t off = 0; off < lay.bytes; off += 32768u)
-                tc::bulk_g2s(tc::smem_u32(wimg + off), img + off, min(32768u, lay.bytes - off), mb);
+        if (!drain()) {
+            if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            aborted = true;
+            break;
         }
+        img_sc = P.images + sc * P.image_stride;
+        if (row == 0) {
+            // the whole image, or (streamed weights) its tail: output layer + biases
+            const uint32_t mb = tc::smem_u32(&s_mbar[1]);
+            const uint32_t nbytes = lay.bytes - img0;
+            tc::mbar_expect_tx(mb, nbytes);
+            for (uint32_t off = 0; off < nbytes; off += 32768u)
+                tc::bulk_g2s(tc::smem_u32(wimg + off), img_sc + img0 + off, min(32768u, nbytes - off), mb);
+        }
+        slot_w[0] = slot_w[1] = -1;  // drained above
         aborted = tc::wg_sync_or(0, !tc::mbar_wait(tc::smem_u32(&s_mbar[1]), wphase));
         wphase ^= 1u;
         tc::fence_after_sync();
@@ -717,7 +809,14 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             for (int l = 0; l < nh && !aborted; ++l) {
                 const int Kl = l == 0 ? lay.K0 : kHp;
                 const uint32_t xa = s_base + P.x_off[l];
-                const uint32_t wb = s_base + lay.w_off[l];
+                if (!ensure(l)) {
+                    aborted = true;
+                    break;
+                }
+                // next weights needed: layer l + 1 (or, after the top layer, the first
+                // backward use below it)
+                prefetch(l + 1 < nh ? l + 1 : (uses_dx(nh - 1, d_feat != nullptr) ? nh - 2 : nh - 1), l);
+                const uint32_t wb = waddr(l);
                 {  // the accumulator starts at the bias
                     const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + lay.bias_l[l]);
 #pragma unroll 1
@@ -761,7 +860,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             {
                 const uint32_t xa = s_base + P.x_off[nh];
                 const uint32_t go = s_base + P.gout_off;
-                const uint32_t wo = s_base + lay.w_off[nh];
+                const uint32_t wo = waddr(nh);
                 if (!run([&] {
                         if (P.with_out)
                             mma_seq(tmem + P.col_dwout, xa, 256, 128, kTcTile * 16, go, 256, 128, kTcTile * 16,
@@ -802,12 +901,20 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             for (int l = nh - 1; l >= P.l_min && !aborted; --l) {
                 const uint32_t g = s_base + P.x_off[l + 1];  // G_{l+1} (delta of layer l's output)
                 const uint32_t xa = s_base + P.x_off[l];
-                const uint32_t wb = s_base + lay.w_off[l];
                 const int Nin = l == 0 ? lay.K0 : kHp;
                 const bool want_dw = l <= P.l_top;
-                const bool want_dx = l > P.l_min || (l == 0 && d_feat != nullptr);
+                const bool want_dx = uses_dx(l, d_feat != nullptr);
                 const int Ndx = l > 0 ? kHp : Fn;
                 if (!want_dw && !want_dx) continue;
+                if (want_dx) {
+                    if (!ensure(l)) {
+                        aborted = true;
+                        break;
+                    }
+                    // next: the layer below if it forms a delta, else the next tile's layer 0
+                    prefetch(l - 1 >= P.l_min && uses_dx(l - 1, d_feat != nullptr) ? l - 1 : 0, l);
+                }
+                const uint32_t wb = waddr(l);
                 if (!run([&] {
                         if (want_dw) {
                             // dW_l += G^T X_l  (A: G MN-major, B: X_l MN-major)
@@ -899,6 +1006,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         tc::fence_before_sync();
         seg = seg_end;
     }
+    if (!drain() && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
@@ -932,7 +1040,20 @@ bool tc_backward_supported(const MlpDims &md) {
     if (!tc_supported(md)) return false;
     const TcLayout lay = tc_layout(md);
     int a[kMaxLayers], b[kMaxLayers], c[kMaxLayers];
-    return tc_bwd_passes(md, lay, a, b, c) > 0;
+    const int n = tc_bwd_passes(md, lay, a, b, c);
+    if (n == 0) return false;
+    for (int pass = 0; pass < n; ++pass) {
+        TcBwdParams P;
+        memset(&P, 0, sizeof(P));
+        P.md = md;
+        P.lay = lay;
+        P.l_min = a[pass];
+        P.l_top = b[pass];
+        P.with_out = c[pass];
+        size_t smem;
+        if (!tc_bwd_plan(md, P, smem)) return false;
+    }
+    return true;
 }
 
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,

@@ -13,17 +13,18 @@ pytestmark = [pytest.mark.gpu, requires_gpu]
 SHAPE = I.MLPShape(32, 128, 3)
 
 
-def _scenes(n=5, seed=40):
+def _scenes(n=5, seed=40, shape=SHAPE):
     """Scenes of depth 6..9 with different primitive counts, features,
     networks and views (a few thousand rays each, some with none)."""
     from paper_2205_07058_b300 import svlf
     rng = np.random.default_rng(seed)
+    SHAPE_ = shape
     out = []
     for i in range(n):
         depth = [6, 7, 8, 9, 7][i % 5]
         sc = I.make_scene(rng, depth, int(rng.integers(2, 10)), int(rng.integers(0, 4)))
         feats = I.make_features(rng, sc.n_leaves, 32)
-        params = I.make_mlp(rng, SHAPE, bias_std=0.2)
+        params = I.make_mlp(rng, SHAPE_, bias_std=0.2)
         az, el = I.random_view_angles(rng, 1)
         res = [48, 64, 32, 40, 0][i % 5]
         rays = I.pinhole_rays(az[0], el[0], res, res) if res else np.zeros((0, 6), np.float32)
@@ -61,11 +62,13 @@ def test_batched_render_matches_single_calls_and_oracle(prec):
         assert np.abs(b.rgb.cpu().numpy()[ok] - emu.rgb[ok]).max() <= 2e-3
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_batched_backward_matches_single_calls(prec):
+@pytest.mark.parametrize("prec,nh", [("bf16", 3), ("fp16", 3), ("bf16", 4)])
+def test_batched_backward_matches_single_calls(prec, nh):
+    """nh = 4 streams the hidden layers' weights through two shared-memory
+    slots, across scene changes inside a CTA's range of tiles."""
     from paper_2205_07058_b300 import svlf
-    scenes = _scenes(seed=41)
-    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
+    scenes = _scenes(seed=41, shape=I.MLPShape(32, 128, nh))
+    net = svlf.Network(32, 128, nh, svlf.PRECISIONS[prec])
     batch = _batch(scenes)
     ws = svlf.svlf_render_rays_batched(batch, net, 8)
     rng = np.random.default_rng(0)
