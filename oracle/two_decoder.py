@@ -1,0 +1,152 @@
+"""The paper's two-decoder SVLF in float64. TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may
+import this module. It shares no code with the CUDA path.
+
+Definitions followed (arXiv 2205.07058):
+
+* Sec. 4.1 "Scene volume": every octree vertex (corner of a leaf voxel) holds
+  one feature vector, shared by the voxels that meet there; a point p inside
+  voxel v gets psi(p; Z), the trilinear interpolation of v's eight corner
+  features.
+* Sec. 4.2: the features split into Z^T (optical thickness) and Z^C (colour).
+  For a hit voxel with intersection points x1 (entry) and x2 (exit),
+  tau, eta = F^T(r, [psi(x1; Z^T) | psi(x2; Z^T)]) (Eq. 1), the surface point
+  is x_s = eta x1 + (1 - eta) x2, and c = F^C(r, psi(x_s; Z^C)) (Eq. 2);
+  r = [p~1 | p~2] is the bounding-sphere parameterisation of Sec. 4.1.
+* Sec. 4.5 "Architecture": ReLU MLPs; ReLU on tau, sigmoid on eta and c.
+* Sec. 4.3, Eq. 3: compositing over the hits in order along the ray.
+
+Readings taken where the paper is silent: the network inputs are ordered
+[r | z]; the vertex ids are the ranks of the corner lattice points sorted by
+their Morton code (corner (a, b, c) of leaf (i, j, k) is (i+a, j+b, k+c), slot
+a + 2b + 4c); trilinear weights use the point's position inside the voxel
+clamped to [0, 1]^3; the depth of a hit is the ray parameter of x_s,
+t_s = eta t_in + (1 - eta) t_out, and the ray's depth is sum_i w_i t_s,i.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import oracle as O
+
+
+# ----------------------------------------------------------------------------
+# Vertex table (Sec. 4.1)
+# ----------------------------------------------------------------------------
+def _morton3(ijk: np.ndarray, bits: int) -> np.ndarray:
+    code = np.zeros(ijk.shape[0], dtype=np.uint64)
+    for b in range(bits):
+        for a in range(3):
+            code |= ((ijk[:, a].astype(np.uint64) >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + a)
+    return code
+
+
+CORNERS = np.array([[a, b, c] for c in (0, 1) for b in (0, 1) for a in (0, 1)], dtype=np.int64)  # slot a+2b+4c
+
+
+@dataclass
+class VertexTable:
+    leaf_vertices: np.ndarray  # (n_leaves, 8) int64: vertex id of corner slot a + 2b + 4c
+    vertex_ijk: np.ndarray     # (n_vertices, 3) int64 lattice coordinates (0 .. 2^L)
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.vertex_ijk.shape[0])
+
+
+def vertex_table(tree: O.Octree) -> VertexTable:
+    """Every corner of every leaf, de-duplicated; ids in Morton order of the
+    corner coordinates (L + 1 bits per axis)."""
+    ijk = tree.leaf_ijk()
+    corners = (ijk[:, None, :] + CORNERS[None, :, :]).reshape(-1, 3)
+    codes = _morton3(corners, tree.depth + 1)
+    uniq, inverse = np.unique(codes, return_inverse=True)
+    first = np.zeros(uniq.shape[0], dtype=np.int64)
+    first[inverse] = np.arange(codes.shape[0])
+    return VertexTable(inverse.reshape(-1, 8).astype(np.int64), corners[first])
+
+
+def trilinear_weights(p: np.ndarray, ijk: np.ndarray, depth: int) -> np.ndarray:
+    """(S, 8) weights of the eight corners of voxel ijk for points p (S, 3)."""
+    u = np.clip(p * (2.0 ** depth) - ijk.astype(np.float64), 0.0, 1.0)
+    w = np.ones((p.shape[0], 8))
+    for s, (a, b, c) in enumerate(CORNERS):
+        w[:, s] = ((u[:, 0] if a else 1.0 - u[:, 0]) * (u[:, 1] if b else 1.0 - u[:, 1]) *
+                   (u[:, 2] if c else 1.0 - u[:, 2]))
+    return w
+
+
+def psi(p: np.ndarray, rank: np.ndarray, tree: O.Octree, vt: VertexTable, Z: np.ndarray) -> np.ndarray:
+    """Trilinear interpolation of the corner features of leaf `rank` at p."""
+    ijk = tree.leaf_ijk()[rank]
+    w = trilinear_weights(p, ijk, tree.depth)
+    Zc = np.asarray(Z, dtype=np.float64)[vt.leaf_vertices[rank]]  # (S, 8, F)
+    return np.einsum("sv,svf->sf", w, Zc)
+
+
+# ----------------------------------------------------------------------------
+# Networks and rendering (Sec. 4.2, 4.3, 4.5)
+# ----------------------------------------------------------------------------
+def dims_t(feat_t: int, hidden: int, n_hidden: int):
+    d = [6 + 2 * feat_t] + [hidden] * n_hidden + [2]
+    return [(d[i + 1], d[i]) for i in range(len(d) - 1)]
+
+
+def dims_c(feat_c: int, hidden: int, n_hidden: int):
+    d = [6 + feat_c] + [hidden] * n_hidden + [3]
+    return [(d[i + 1], d[i]) for i in range(len(d) - 1)]
+
+
+@dataclass
+class Render2:
+    rgb: np.ndarray
+    depth: np.ndarray
+    hits: O.Hits
+    ray_of: np.ndarray
+    slot: np.ndarray
+    tau: np.ndarray
+    eta: np.ndarray
+    colour: np.ndarray
+    t_s: np.ndarray
+    x1: np.ndarray
+    x2: np.ndarray
+    x_s: np.ndarray
+    h_t: np.ndarray  # F^T inputs
+    h_c: np.ndarray  # F^C inputs
+    w: np.ndarray    # compositing weights (N, K)
+
+
+def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, params_t: np.ndarray,
+            params_c: np.ndarray, d_t, d_c, rays: np.ndarray, K: int, bg=(0.0, 0.0, 0.0), lowp=False,
+            hits: Optional[O.Hits] = None) -> Render2:
+    """Two-decoder render of every ray. lowp = "bf16" / "fp16" rounds each
+    layer's inputs and weights to that format (products and sums in float64)."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
+    N = rays.shape[0]
+    if hits is None:
+        hits = O.trace(tree, rays, K)
+    ray_of, slot = np.nonzero(hits.rank >= 0)
+    rank = hits.rank[ray_of, slot]
+    o = rays[ray_of, :3].astype(np.float64)
+    d = rays[ray_of, 3:].astype(np.float64)
+    t_in = hits.t_in[ray_of, slot]
+    t_out = hits.t_out[ray_of, slot]
+    c, R = O.voxel_centre_radius(tree.leaf_ijk()[rank], tree.depth)
+    p1, p2 = O.sphere_params(o, d, c, R)
+    x1 = o + t_in[:, None] * d
+    x2 = o + t_out[:, None] * d
+    h_t = np.concatenate([p1, p2, psi(x1, rank, tree, vt, z_t), psi(x2, rank, tree, vt, z_t)], axis=1)
+    _, pres_t = O.mlp_forward(h_t, O.split_params(params_t, d_t), bf16=lowp)
+    tau = np.maximum(pres_t[-1][:, 0], 0.0)
+    eta = O.sigmoid(pres_t[-1][:, 1])
+    x_s = eta[:, None] * x1 + (1.0 - eta[:, None]) * x2
+    t_s = eta * t_in + (1.0 - eta) * t_out
+    h_c = np.concatenate([p1, p2, psi(x_s, rank, tree, vt, z_c)], axis=1)
+    _, pres_c = O.mlp_forward(h_c, O.split_params(params_c, d_c), bf16=lowp)
+    colour = O.sigmoid(pres_c[-1])
+    rgb, depth, T, w = O.composite(N, K, ray_of, slot, colour, tau, t_s, bg)
+    return Render2(rgb, depth, hits, ray_of, slot, tau, eta, colour, t_s, x1, x2, x_s, h_t, h_c, w)

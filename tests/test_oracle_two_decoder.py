@@ -1,0 +1,210 @@
+"""Pins of the two-decoder oracle (vertex features, trilinear psi, Eq. 1-2)
+against closed forms, brute force and properties that fix them."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import two_decoder as T2
+from paper_2205_07058_b300 import inputs as I
+
+
+def _tree(ijk, depth):
+    return O.build_octree(np.asarray(ijk, dtype=np.int32).reshape(-1, 3), depth)
+
+
+def test_vertex_table_small_closed_forms():
+    # one leaf: its 8 corners, ids in Morton order = corner slot a + 2b + 4c
+    vt = T2.vertex_table(_tree([[0, 0, 0]], 1))
+    assert vt.n_vertices == 8
+    assert np.array_equal(vt.leaf_vertices[0], np.arange(8))
+    # two face neighbours share a face: 12 vertices
+    assert T2.vertex_table(_tree([[0, 0, 0], [1, 0, 0]], 2)).n_vertices == 12
+    # the full 2x2x2 block of depth 1: the 3^3 lattice
+    full = list(itertools.product(range(2), repeat=3))
+    assert T2.vertex_table(_tree(full, 1)).n_vertices == 27
+    # a diagonal pair sharing one corner: 15
+    assert T2.vertex_table(_tree([[0, 0, 0], [1, 1, 1]], 2)).n_vertices == 15
+
+
+def test_vertex_table_against_brute_force():
+    rng = np.random.default_rng(3)
+    ijk = np.unique(rng.integers(0, 16, size=(300, 3)), axis=0)
+    tree = _tree(ijk, 4)
+    vt = T2.vertex_table(tree)
+    leaves = tree.leaf_ijk()
+    # every corner coordinate once, via a set
+    seen = set()
+    for l in range(tree.n_leaves):
+        for a in (0, 1):
+            for b in (0, 1):
+                for c in (0, 1):
+                    seen.add((leaves[l, 0] + a, leaves[l, 1] + b, leaves[l, 2] + c))
+    assert vt.n_vertices == len(seen)
+    # the table points every (leaf, slot) at the lattice point leaf + corner(slot)
+    for l in range(tree.n_leaves):
+        for a in (0, 1):
+            for b in (0, 1):
+                for c in (0, 1):
+                    v = vt.leaf_vertices[l, a + 2 * b + 4 * c]
+                    assert tuple(vt.vertex_ijk[v]) == (leaves[l, 0] + a, leaves[l, 1] + b, leaves[l, 2] + c)
+    # ids follow Morton order of the lattice points: strictly increasing codes
+    bits = 5
+    codes = [sum(((int(x) >> i) & 1) << (3 * i + ax) for i in range(bits) for ax, x in enumerate(p))
+             for p in vt.vertex_ijk]
+    assert all(a < b for a, b in zip(codes, codes[1:]))
+
+
+def _affine_features(vt, depth, rng, F):
+    A = rng.standard_normal((F, 3))
+    b = rng.standard_normal(F)
+    pos = vt.vertex_ijk.astype(np.float64) * 2.0 ** -depth
+    return pos @ A.T + b, A, b
+
+
+def test_psi_reproduces_affine_fields_and_corners():
+    """Trilinear interpolation is exact on affine functions of position and
+    returns the corner value at a corner."""
+    rng = np.random.default_rng(4)
+    depth = 5
+    ijk = np.unique(rng.integers(0, 32, size=(200, 3)), axis=0)
+    tree = _tree(ijk, depth)
+    vt = T2.vertex_table(tree)
+    Z, A, b = _affine_features(vt, depth, rng, 6)
+    rank = rng.integers(0, tree.n_leaves, size=500)
+    p = (tree.leaf_ijk()[rank] + rng.uniform(0, 1, size=(500, 3))) * 2.0 ** -depth
+    np.testing.assert_allclose(T2.psi(p, rank, tree, vt, Z), p @ A.T + b, rtol=0, atol=1e-12)
+    # corners
+    Zr = rng.standard_normal((vt.n_vertices, 4))
+    for s, corner in enumerate(T2.CORNERS):
+        pc = (tree.leaf_ijk()[rank] + corner) * 2.0 ** -depth
+        np.testing.assert_allclose(T2.psi(pc, rank, tree, vt, Zr), Zr[vt.leaf_vertices[rank, s]], atol=1e-15)
+    # centre: the mean of the eight corners
+    pm = (tree.leaf_ijk()[rank] + 0.5) * 2.0 ** -depth
+    np.testing.assert_allclose(T2.psi(pm, rank, tree, vt, Zr), Zr[vt.leaf_vertices[rank]].mean(axis=1), atol=1e-15)
+
+
+def test_psi_is_continuous_across_shared_faces():
+    rng = np.random.default_rng(5)
+    tree = _tree([[2, 3, 4], [3, 3, 4]], 3)  # x-neighbours sharing the face x = 3
+    vt = T2.vertex_table(tree)
+    Z = rng.standard_normal((vt.n_vertices, 5))
+    yz = rng.uniform(0, 1, size=(50, 2))
+    p = np.column_stack([np.full(50, 3.0), 3.0 + yz[:, 0], 4.0 + yz[:, 1]]) / 8.0
+    ranks = {tuple(r): i for i, r in enumerate(tree.leaf_ijk())}
+    a = T2.psi(p, np.full(50, ranks[(2, 3, 4)]), tree, vt, Z)
+    b = T2.psi(p, np.full(50, ranks[(3, 3, 4)]), tree, vt, Z)
+    np.testing.assert_allclose(a, b, atol=1e-14)
+
+
+@pytest.fixture(scope="module")
+def small():
+    rng = np.random.default_rng(1006)
+    sc = I.make_scene(rng, 6, 8, 2)
+    tree = O.build_octree(sc.leaf_ijk, 6)
+    vt = T2.vertex_table(tree)
+    rays = I.pinhole_rays(np.radians(40.0), np.radians(25.0), 48, 48)
+    return sc, tree, vt, rays
+
+
+def _zero_net(dims, out_bias):
+    p = []
+    for li, (o, i) in enumerate(dims):
+        p.append(np.zeros(o * i))
+        p.append(np.asarray(out_bias, dtype=np.float64) if li + 1 == len(dims) else np.zeros(o))
+    return np.concatenate(p)
+
+
+@pytest.mark.parametrize("b_tau,b_eta,b_c", [(0.7, 0.3, -0.4), (-1.0, 2.0, 1.0), (2.5, 40.0, 0.2), (0.4, -40.0, 0.0)])
+def test_constant_networks_closed_form(small, b_tau, b_eta, b_c):
+    """All weights zero: tau = relu(b_tau), eta = sigmoid(b_eta) and c =
+    sigmoid(b_c) on every hit, so with n hits (brute-force hit lists)
+    C = c (1 - e^{-n tau}) + e^{-n tau} bg and D = sum_i T_i alpha (eta t_in,i +
+    (1 - eta) t_out,i)."""
+    sc, tree, vt, rays = small
+    K = 5
+    dt, dc = T2.dims_t(16, 32, 1), T2.dims_c(8, 32, 2)
+    pt = _zero_net(dt, [b_tau, b_eta])
+    pc = _zero_net(dc, [b_c] * 3)
+    rng = np.random.default_rng(0)
+    zt = rng.standard_normal((vt.n_vertices, 16))
+    zc = rng.standard_normal((vt.n_vertices, 8))
+    bg = (0.2, 0.5, 0.9)
+    r = T2.render2(tree, vt, zt, zc, pt, pc, dt, dc, rays, K, bg=bg)
+    brute = O.trace(tree, rays, K, mode="brute")
+    n = brute.n.astype(np.float64)
+    tau = max(b_tau, 0.0)
+    eta = 1.0 / (1.0 + np.exp(-b_eta))
+    c = 1.0 / (1.0 + np.exp(-b_c))
+    exp_rgb = c * (1.0 - np.exp(-n * tau))[:, None] + np.exp(-n * tau)[:, None] * np.asarray(bg)[None, :]
+    np.testing.assert_allclose(r.rgb, exp_rgb, rtol=0, atol=1e-12)
+    alpha = 1.0 - np.exp(-tau)
+    Ti = np.exp(-tau * np.arange(K))[None, :]
+    valid = brute.rank >= 0
+    ts = eta * brute.t_in + (1.0 - eta) * brute.t_out
+    exp_d = np.sum(np.where(valid, Ti * alpha * ts, 0.0), axis=1)
+    np.testing.assert_allclose(r.depth, exp_d, rtol=0, atol=1e-12)
+    assert (n > 0).sum() > 200
+
+
+def test_surface_point_on_segment_inside_voxel(small):
+    sc, tree, vt, rays = small
+    rng = np.random.default_rng(1)
+    dt, dc = T2.dims_t(16, 32, 1), T2.dims_c(8, 32, 2)
+
+    # He-style random networks with non-zero biases
+    def rand_net(dims):
+        out = []
+        for o, i in dims:
+            out.append(rng.standard_normal(o * i) * np.sqrt(2.0 / i))
+            out.append(rng.standard_normal(o) * 0.3)
+        return np.concatenate(out)
+    pt, pc = rand_net(dt), rand_net(dc)
+    zt = rng.standard_normal((vt.n_vertices, 16)) * 0.1
+    zc = rng.standard_normal((vt.n_vertices, 8)) * 0.1
+    r = T2.render2(tree, vt, zt, zc, pt, pc, dt, dc, rays, 6)
+    assert np.all((r.eta > 0) & (r.eta < 1))
+    # x_s on the segment [x1, x2] at parameter t_s, and inside the hit voxel
+    o = rays[r.ray_of, :3].astype(np.float64)
+    d = rays[r.ray_of, 3:].astype(np.float64)
+    np.testing.assert_allclose(r.x_s, o + r.t_s[:, None] * d, atol=1e-12)
+    rank = r.hits.rank[r.ray_of, r.slot]
+    lo = tree.leaf_ijk()[rank] * 2.0 ** -tree.depth
+    assert np.all(r.x_s >= lo - 1e-12) and np.all(r.x_s <= lo + 2.0 ** -tree.depth + 1e-12)
+    tin = r.hits.t_in[r.ray_of, r.slot]
+    tout = r.hits.t_out[r.ray_of, r.slot]
+    assert np.all((r.t_s >= tin - 1e-15) & (r.t_s <= tout + 1e-15))
+
+
+def test_network_inputs_order_by_selection(small):
+    """A network that routes one input coordinate to eta's pre-activation
+    (through a ReLU unit, with an offset keeping it positive) recovers, for
+    affine vertex features, the value of the affine field at x2 computed from
+    the brute-force exit parameter: pins the input order [r | psi(x1) |
+    psi(x2)] and the exit point."""
+    sc, tree, vt, rays = small
+    rng = np.random.default_rng(7)
+    F = 8
+    Z, A, b = _affine_features(vt, tree.depth, rng, F)
+    dt, dc = T2.dims_t(F, 32, 1), T2.dims_c(4, 32, 1)
+    f_sel = 5
+    col = 6 + F + f_sel  # psi(x2)[f_sel]
+    W0 = np.zeros((32, 6 + 2 * F))
+    W0[0, col] = 1.0
+    b0 = np.zeros(32)
+    b0[0] = 50.0  # keep the unit in the ReLU's linear part
+    W1 = np.zeros((2, 32))
+    W1[1, 0] = 1.0
+    b1 = np.array([0.0, -50.0])
+    pt = np.concatenate([W0.ravel(), b0, W1.ravel(), b1])
+    pc = _zero_net(dc, [0.0, 0.0, 0.0])
+    zc = np.zeros((vt.n_vertices, 4))
+    r = T2.render2(tree, vt, Z, zc, pt, pc, dt, dc, rays, 4)
+    brute = O.trace(tree, rays, 4, mode="brute")
+    o = rays[r.ray_of, :3].astype(np.float64)
+    d = rays[r.ray_of, 3:].astype(np.float64)
+    x2 = o + brute.t_out[r.ray_of, r.slot][:, None] * d
+    expect = x2 @ A[f_sel] + b[f_sel]
+    pre_eta = np.log(r.eta / (1.0 - r.eta))
+    np.testing.assert_allclose(pre_eta, expect, rtol=0, atol=1e-9)
