@@ -18,7 +18,10 @@ Definitions followed (arXiv 2205.07058):
 * Sec. 4.3, Eq. 3: compositing over the hits in order along the ray.
 
 Readings taken where the paper is silent: the network inputs are ordered
-[r | z]; the vertex ids are the ranks of the corner lattice points sorted by
+features first, [psi(x1) | psi(x2) | r] and [psi(x_s) | r] (the order of a
+first layer's inputs is a permutation of its weight columns; features first
+keeps feature groups aligned as in the single-network form [z | d | r]); the
+vertex ids are the ranks of the corner lattice points sorted by
 their Morton code (corner (a, b, c) of leaf (i, j, k) is (i+a, j+b, k+c), slot
 a + 2b + 4c); trilinear weights use the point's position inside the voxel
 clamped to [0, 1]^3; the depth of a hit is the ray parameter of x_s,
@@ -92,11 +95,13 @@ def psi(p: np.ndarray, rank: np.ndarray, tree: O.Octree, vt: VertexTable, Z: np.
 # Networks and rendering (Sec. 4.2, 4.3, 4.5)
 # ----------------------------------------------------------------------------
 def dims_t(feat_t: int, hidden: int, n_hidden: int):
+    """F^T: [psi(x1) | psi(x2) | p~1 | p~2] -> (tau_pre, eta_pre)."""
     d = [6 + 2 * feat_t] + [hidden] * n_hidden + [2]
     return [(d[i + 1], d[i]) for i in range(len(d) - 1)]
 
 
 def dims_c(feat_c: int, hidden: int, n_hidden: int):
+    """F^C: [psi(x_s) | p~1 | p~2] -> colour pre-activations."""
     d = [6 + feat_c] + [hidden] * n_hidden + [3]
     return [(d[i + 1], d[i]) for i in range(len(d) - 1)]
 
@@ -139,13 +144,13 @@ def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, p
     p1, p2 = O.sphere_params(o, d, c, R)
     x1 = o + t_in[:, None] * d
     x2 = o + t_out[:, None] * d
-    h_t = np.concatenate([p1, p2, psi(x1, rank, tree, vt, z_t), psi(x2, rank, tree, vt, z_t)], axis=1)
+    h_t = np.concatenate([psi(x1, rank, tree, vt, z_t), psi(x2, rank, tree, vt, z_t), p1, p2], axis=1)
     _, pres_t = O.mlp_forward(h_t, O.split_params(params_t, d_t), bf16=lowp)
     tau = np.maximum(pres_t[-1][:, 0], 0.0)
     eta = O.sigmoid(pres_t[-1][:, 1])
     x_s = eta[:, None] * x1 + (1.0 - eta[:, None]) * x2
     t_s = eta * t_in + (1.0 - eta) * t_out
-    h_c = np.concatenate([p1, p2, psi(x_s, rank, tree, vt, z_c)], axis=1)
+    h_c = np.concatenate([psi(x_s, rank, tree, vt, z_c), p1, p2], axis=1)
     _, pres_c = O.mlp_forward(h_c, O.split_params(params_c, d_c), bf16=lowp)
     colour = O.sigmoid(pres_c[-1])
     rgb, depth, T, w = O.composite(N, K, ray_of, slot, colour, tau, t_s, bg)

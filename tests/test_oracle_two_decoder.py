@@ -181,15 +181,15 @@ def test_network_inputs_order_by_selection(small):
     """A network that routes one input coordinate to eta's pre-activation
     (through a ReLU unit, with an offset keeping it positive) recovers, for
     affine vertex features, the value of the affine field at x2 computed from
-    the brute-force exit parameter: pins the input order [r | psi(x1) |
-    psi(x2)] and the exit point."""
+    the brute-force exit parameter: pins the input order [psi(x1) | psi(x2) |
+    r] and the exit point."""
     sc, tree, vt, rays = small
     rng = np.random.default_rng(7)
     F = 8
     Z, A, b = _affine_features(vt, tree.depth, rng, F)
     dt, dc = T2.dims_t(F, 32, 1), T2.dims_c(4, 32, 1)
     f_sel = 5
-    col = 6 + F + f_sel  # psi(x2)[f_sel]
+    col = F + f_sel  # psi(x2)[f_sel]
     W0 = np.zeros((32, 6 + 2 * F))
     W0[0, col] = 1.0
     b0 = np.zeros(32)
