@@ -191,6 +191,52 @@ int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
                                       const svlf_mlp_desc *mlp, const svlf_render_opts *opts,
                                       void *workspace, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------ two-decoder form (Sec. 4.1-4.2) */
+/* The paper's full SVLF: features live on octree vertices (Sec. 4.1 "Scene
+ * volume": one vector per leaf corner, shared by the voxels meeting there)
+ * and are trilinearly interpolated, psi(p; Z). For each hit voxel with
+ * entry / exit points x1, x2 (Sec. 4.2):
+ *   tau, eta = F^T([psi(x1; Z^T) | psi(x2; Z^T) | p~1 | p~2])      (Eq. 1)
+ *   x_s = eta x1 + (1 - eta) x2
+ *   c = F^C([psi(x_s; Z^C) | p~1 | p~2])                            (Eq. 2)
+ * with ReLU hidden layers, ReLU on tau, sigmoid on eta and c (Sec. 4.5), then
+ * Eq. 3 compositing; a hit's depth is the ray parameter of x_s. */
+
+/* Builds (once; later calls only report) the octree's vertex table: the
+ * corners of every leaf, de-duplicated, ids = ranks of the corner lattice
+ * points (depth + 1 bits per axis) in Morton order. Synchronises `stream`;
+ * allocates n_leaves x 8 int32 on the device, freed with the octree. */
+int svlf_octree_build_vertices(svlf_octree tree, int64_t *n_vertices, void *stream);
+/* Copies the table to out (device, n_leaves x 8 int32, rank order): entry
+ * 8 q + a + 2b + 4c is the vertex id of corner (a, b, c) of leaf q.
+ * SVLF_ERR_ARG if the table was not built. */
+int svlf_octree_leaf_vertices(svlf_octree tree, int32_t *out, void *stream);
+
+typedef struct {
+    int feat_t, feat_c;          /* Z^T and Z^C widths, 8..64, multiples of 8 (paper: 64, 32) */
+    int hidden_t, n_hidden_t;    /* F^T: hidden width 32..128 (multiple of 16), 1..4 layers (paper: 128, 1) */
+    int hidden_c, n_hidden_c;    /* F^C: the same (paper: 128, 3) */
+    int precision;               /* SVLF_BF16 or SVLF_FP16 (tensor cores); SVLF_FP32: unsupported */
+    int feat_dtype;              /* storage of Z^T and Z^C: SVLF_FEAT_F32 or SVLF_FEAT_BF16 */
+} svlf_two_decoder_desc;
+
+int svlf_workspace_size_two_decoder(const svlf_two_decoder_desc *desc, int64_t n_rays, int K,
+                                    size_t *bytes);
+
+/* Render n_rays rays with the two-decoder form. z_t: device, n_vertices x
+ * feat_t, z_c: n_vertices x feat_c (16-byte aligned rows, vertex ids of the
+ * table above). params_t / params_c: device float32, per layer W (out x in,
+ * row-major) then b; F^T maps 2 feat_t + 6 inputs to (tau_pre, eta_pre), F^C
+ * maps feat_c + 6 inputs to colour pre-activations. rays, opts, rgb, depth,
+ * hits, t_io, workspace as in svlf_render_rays. The vertex table must have
+ * been built (SVLF_ERR_ARG otherwise). */
+int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, const void *z_c,
+                                 const float *params_t, const float *params_c,
+                                 const svlf_two_decoder_desc *desc, const float *rays, int64_t n_rays,
+                                 const svlf_render_opts *opts, float *rgb, float *depth,
+                                 int32_t *hits, float *t_io, void *workspace, size_t ws_bytes,
+                                 void *stream);
+
 /* ------------------------------------------------------------ optimiser */
 /* One bias-corrected Adam step (Sec. 4.5 trains with Adam; Kingma & Ba) over
  * n float32 parameters (device): m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;

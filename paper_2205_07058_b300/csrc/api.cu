@@ -27,16 +27,21 @@ static svlf_tuning g_tuning = {0, 1, 16, 256};
 const svlf_tuning &tuning() { return g_tuning; }
 
 MlpDims make_dims(const svlf_mlp_desc &d) {
+    return make_dims_io(d.feat_dim, d.feat_dim + 9, d.hidden, d.n_hidden, 4);
+}
+
+MlpDims make_dims_io(int F, int in0, int H, int nh, int out) {
     MlpDims md;
     std::memset(&md, 0, sizeof(md));
-    md.F = d.feat_dim;
-    md.in0 = d.feat_dim + 9;
-    md.H = d.hidden;
-    md.nh = d.n_hidden;
+    md.F = F;
+    md.in0 = in0;
+    md.H = H;
+    md.nh = nh;
+    md.out = out;
     int woff = 0, poff = 0;
     for (int l = 0; l <= md.nh; ++l) {
         md.in_l[l] = l == 0 ? md.in0 : md.H;
-        md.out_l[l] = l == md.nh ? 4 : md.H;
+        md.out_l[l] = l == md.nh ? md.out : md.H;
         md.w_off[l] = woff;
         woff += md.out_l[l] * md.in_l[l] + md.out_l[l];
         md.wt_off[l] = poff;
@@ -57,7 +62,8 @@ size_t packed_weight_bytes(const svlf_mlp_desc &mlp) {
     return align256(a > b ? a : b);
 }
 
-size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K, int n_scenes) {
+// Workspace of n_rays rays with n_scenes packed weight images of `stride` bytes.
+static size_t workspace_bytes_raw(int64_t n_rays, int K, size_t stride, int n_scenes) {
     const size_t S = (size_t)n_rays * (size_t)K;
     size_t b = 0;
     b += align256(sizeof(Sample) * S);
@@ -65,12 +71,22 @@ size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K, int n_sc
     b += align256(sizeof(float4) * S);
     b += align256(sizeof(int2) * (size_t)n_rays);
     b += kCounterBytes;
-    b += (size_t)n_scenes * packed_weight_bytes(mlp);
+    b += (size_t)n_scenes * stride;
     return b;
 }
 
+size_t workspace_bytes(const svlf_mlp_desc &mlp, int64_t n_rays, int K, int n_scenes) {
+    return workspace_bytes_raw(n_rays, K, packed_weight_bytes(mlp), n_scenes);
+}
+
+static Workspace carve_workspace_raw(void *base, int64_t n_rays, int K, size_t stride, int n_scenes);
+
 Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, int K,
                           int n_scenes) {
+    return carve_workspace_raw(base, n_rays, K, packed_weight_bytes(mlp), n_scenes);
+}
+
+static Workspace carve_workspace_raw(void *base, int64_t n_rays, int K, size_t stride, int n_scenes) {
     Workspace w;
     const size_t S = (size_t)n_rays * (size_t)K;
     char *p = static_cast<char *>(base);
@@ -85,7 +101,7 @@ Workspace carve_workspace(void *base, const svlf_mlp_desc &mlp, int64_t n_rays, 
     w.counter = reinterpret_cast<unsigned int *>(p);
     p += kCounterBytes;
     w.packed_w = p;
-    w.packed_stride = packed_weight_bytes(mlp);
+    w.packed_stride = stride;
     p += (size_t)n_scenes * w.packed_stride;
     w.bytes = (size_t)(p - static_cast<char *>(base));
     return w;
@@ -119,6 +135,9 @@ static int check_scene(const svlf_scene &sc, bool need_outputs) {
 }
 
 // Validate a call and build its scene table (device-side view of the scenes).
+static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_render_opts *opts,
+                           bool backward, SceneTable &T);
+
 static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_desc *mlp,
                       const svlf_render_opts *opts, void *workspace, size_t ws_bytes,
                       bool backward, SceneTable &T) {
@@ -126,6 +145,20 @@ static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_des
     if (n_scenes > kMaxScenes) return SVLF_ERR_UNSUPPORTED;
     int rc = check_mlp(mlp);
     if (rc) return rc;
+    if ((rc = make_table_core(scenes, n_scenes, opts, backward, T))) return rc;
+    if (T.total_rays == 0) return SVLF_OK;
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes(*mlp, T.total_rays, T.K, n_scenes)) return SVLF_ERR_WORKSPACE;
+    return SVLF_OK;
+}
+
+// Scene table of a call (device-side view of the scenes), without the
+// network or workspace checks.
+static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_render_opts *opts,
+                           bool backward, SceneTable &T) {
+    if (!scenes || n_scenes < 1 || !opts) return SVLF_ERR_ARG;
+    if (n_scenes > kMaxScenes) return SVLF_ERR_UNSUPPORTED;
+    int rc = SVLF_OK;
     const int K = opts->K;
     if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     std::memset(&T, 0, sizeof(T));
@@ -165,9 +198,6 @@ static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_des
     T.total_rays = rays;
     T.total_chunks = chunks;
     if (rays * K >= ((int64_t)1 << 31)) return SVLF_ERR_UNSUPPORTED;
-    if (rays == 0) return SVLF_OK;
-    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
-    if (ws_bytes < workspace_bytes(*mlp, rays, K, n_scenes)) return SVLF_ERR_WORKSPACE;
     return SVLF_OK;
 }
 
@@ -380,4 +410,86 @@ extern "C" const char *svlf_status_string(int status) {
         case SVLF_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
         default: return "unknown status";
     }
+}
+
+// ---------------------------------------------------------------- two-decoder form
+namespace svlf {
+
+static int check_two_decoder(const svlf_two_decoder_desc *d) {
+    if (!d) return SVLF_ERR_ARG;
+    if (d->feat_t < 8 || d->feat_t > 64 || d->feat_t % 8 || d->feat_c < 8 || d->feat_c > 64 || d->feat_c % 8)
+        return SVLF_ERR_UNSUPPORTED;
+    if (d->hidden_t < 32 || d->hidden_t > 128 || d->hidden_t % 16 || d->hidden_c < 32 || d->hidden_c > 128 ||
+        d->hidden_c % 16)
+        return SVLF_ERR_UNSUPPORTED;
+    if (d->n_hidden_t < 1 || d->n_hidden_t > 4 || d->n_hidden_c < 1 || d->n_hidden_c > 4)
+        return SVLF_ERR_UNSUPPORTED;
+    if (d->precision != SVLF_BF16 && d->precision != SVLF_FP16) {
+        return d->precision == SVLF_FP32 ? SVLF_ERR_UNSUPPORTED : SVLF_ERR_ARG;
+    }
+    if (d->feat_dtype != SVLF_FEAT_F32 && d->feat_dtype != SVLF_FEAT_BF16) return SVLF_ERR_ARG;
+    return SVLF_OK;
+}
+
+static MlpDims dims_t(const svlf_two_decoder_desc &d) {
+    return make_dims_io(d.feat_t, 2 * d.feat_t + 6, d.hidden_t, d.n_hidden_t, 2);
+}
+static MlpDims dims_c(const svlf_two_decoder_desc &d) {
+    return make_dims_io(d.feat_c, d.feat_c + 6, d.hidden_c, d.n_hidden_c, 3);
+}
+// packed images: F^T at offset 0, F^C at image_c_offset
+static size_t image_c_offset(const svlf_two_decoder_desc &d) { return align256(packed_tc_bytes(dims_t(d))); }
+static size_t images_bytes(const svlf_two_decoder_desc &d) {
+    return image_c_offset(d) + align256(packed_tc_bytes(dims_c(d)));
+}
+
+}  // namespace svlf
+
+extern "C" int svlf_workspace_size_two_decoder(const svlf_two_decoder_desc *desc, int64_t n_rays, int K,
+                                               size_t *bytes) {
+    if (!bytes || n_rays < 0 || K < 1 || K > kMaxK) return SVLF_ERR_ARG;
+    int rc = check_two_decoder(desc);
+    if (rc) return rc;
+    *bytes = workspace_bytes_raw(n_rays, K, images_bytes(*desc), 1);
+    return SVLF_OK;
+}
+
+extern "C" int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, const void *z_c,
+                                            const float *params_t, const float *params_c,
+                                            const svlf_two_decoder_desc *desc, const float *rays,
+                                            int64_t n_rays, const svlf_render_opts *opts, float *rgb,
+                                            float *depth, int32_t *hits, float *t_io, void *workspace,
+                                            size_t ws_bytes, void *stream) {
+    if (!tree) return SVLF_ERR_ARG;
+    int rc = check_two_decoder(desc);
+    if (rc) return rc;
+    const OctreeView &view = octree_view(tree);
+    if (!view.leaf_vertices && view.n_leaves > 0) return SVLF_ERR_ARG;  // svlf_octree_build_vertices first
+    if (n_rays > 0 && view.n_leaves > 0 && (!z_t || !z_c || !params_t || !params_c)) return SVLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(z_c) % 16) return SVLF_ERR_ARG;
+    svlf_scene sc = one_scene(tree, z_t, params_t, rays, n_rays);
+    sc.rgb = rgb;
+    sc.depth = depth;
+    SceneTable T;
+    if ((rc = make_table_core(&sc, 1, opts, false, T))) return rc;
+    if (T.total_rays == 0) return SVLF_OK;
+    const size_t stride = images_bytes(*desc);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes_raw(T.total_rays, T.K, stride, 1)) return SVLF_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws = carve_workspace_raw(workspace, T.total_rays, T.K, stride, 1);
+    const MlpDims mt = dims_t(*desc), mc = dims_c(*desc);
+    const int fb = desc->feat_dtype == SVLF_FEAT_BF16;
+    SceneTable Tc = T;  // the colour pass: Z^C and F^C
+    Tc.s[0].feats = z_c;
+    Tc.s[0].params = params_c;
+    Workspace wc = ws;
+    wc.packed_w = static_cast<char *>(ws.packed_w) + image_c_offset(*desc);
+    if (cudaMemsetAsync(ws.counter, 0, kCounterBytes, s) != cudaSuccess) return SVLF_ERR_CUDA;
+    if ((rc = launch_pack_tc(mt, desc->precision, T, ws.packed_w, stride, s))) return rc;
+    if ((rc = launch_pack_tc(mc, desc->precision, Tc, wc.packed_w, stride, s))) return rc;
+    if ((rc = launch_trace(T, ws, hits, t_io, s))) return rc;
+    if ((rc = launch_mlp_forward_tc(mt, desc->precision, fb, T, ws, s, 1))) return rc;
+    if ((rc = launch_mlp_forward_tc(mc, desc->precision, fb, Tc, wc, s, 2))) return rc;
+    return launch_composite(T, ws, opts->bg, s);
 }

@@ -11,6 +11,7 @@ constexpr int kMaxIn = 64 + 9;    // feat_dim <= 64
 
 struct MlpDims {
     int F, in0, H, nh;
+    int out;                 // output width (4: colour + tau; two-decoder: 2 or 3)
     int in_l[kMaxLayers], out_l[kMaxLayers];
     int w_off[kMaxLayers];   // W_l in the flat parameters (b_l follows it)
     int wt_off[kMaxLayers];  // W_l^T in the packed float32 buffer
@@ -18,6 +19,8 @@ struct MlpDims {
 };
 
 MlpDims make_dims(const svlf_mlp_desc &d);
+// a network of feature width F, input width in0, nh hidden layers of H, out outputs
+MlpDims make_dims_io(int F, int in0, int H, int nh, int out);
 size_t packed_f32_floats(const MlpDims &md);
 int launch_pack_f32(const MlpDims &md, const float *params, float *packed, cudaStream_t s);
 int launch_mlp_forward_f32(const MlpDims &md, int depth, const void *feats, int fb,
@@ -80,8 +83,9 @@ size_t packed_tc_bytes(const MlpDims &md);
 void set_tc_warpgroups(int n);
 int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *packed,
                    size_t stride, cudaStream_t s);
+// mode 0: the single network; 1 / 2: the two-decoder form's F^T / F^C pass
 int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                          const Workspace &ws, cudaStream_t s);
+                          const Workspace &ws, cudaStream_t s, int mode = 0);
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
                            const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s);
 }  // namespace svlf

@@ -70,7 +70,7 @@ static TcLayout tc_layout(const MlpDims &md) {
 }
 
 bool tc_supported(const MlpDims &md) {
-    return md.H <= kHp && md.H % 16 == 0 && md.in0 <= 80 && md.nh >= 1 && md.nh <= 6;
+    return md.H <= kHp && md.H % 16 == 0 && md.in0 <= 144 && md.nh >= 1 && md.nh <= 6 && md.out <= kTcOutN;
 }
 
 size_t packed_tc_bytes(const MlpDims &md) {
@@ -124,7 +124,7 @@ struct TcFwdParams {
     int feat_bf16;
     const uint8_t *images;  // packed weights, scene i at images + i * image_stride
     size_t image_stride;
-    const Sample *samples;
+    Sample *samples;     // read; the two-decoder colour pass also rewrites each tmid
     const unsigned int *counter;
     float4 *outputs;
     int n_wg;            // warpgroups per CTA
@@ -211,6 +211,119 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
     for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
 }
 
+// ---------------------------------------------------------------- two-decoder
+// Input rows of the two-decoder form (Sec. 4.1-4.2). Each leaf corner holds a
+// feature vector (vertex table of the octree); psi(p; Z) is the trilinear
+// interpolation of the hit voxel's eight corner features at p.
+//  MODE 1 (F^T): [psi(x1; Z^T) | psi(x2; Z^T) | p~1 | p~2] with x1, x2 the
+//    ray's entry and exit points of the voxel (slab test, t clipped at 0);
+//    carries (t_in, t_out) to the output stage.
+//  MODE 2 (F^C): [psi(x_s; Z^C) | p~1 | p~2] with x_s = o + t_s d,
+//    t_s = eta t_in + (1 - eta) t_out from the F^T pass's (tau, eta, t_in,
+//    t_out) in `prev`; carries (tau, t_s).
+// Weights of the corners (slot a + 2b + 4c) of voxel `cell` at o + t d.
+__device__ __forceinline__ void corner_weights(const float o[3], const float d[3], float t, const int cell[3],
+                                               float n, float w[8]) {
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = fminf(fmaxf(fmaf(t, d[a], o[a]) * n - (float)cell[a], 0.f), 1.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        w[c] = ((c & 1) ? u[0] : 1.f - u[0]) * ((c & 2) ? u[1] : 1.f - u[1]) * ((c & 4) ? u[2] : 1.f - u[2]);
+}
+
+// Eight consecutive features (block q) of vertex v, widened to float32.
+__device__ __forceinline__ void vertex_feat8(const void *feats, int feat_bf16, int F, int v, int q, float z[8]) {
+    if (feat_bf16) {
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(feats) +
+                                                              (int64_t)v * F) + q);
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            z[2 * e] = __uint_as_float(w[e] << 16);
+            z[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+        }
+    } else {
+        const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(feats) + (int64_t)v * F) + 2 * q;
+        const float4 a = __ldg(src), b = __ldg(src + 1);
+        z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
+        z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void build_input_two_decoder(const MlpDims &md, int K0, int depth,
+                                                        const int32_t *__restrict__ leaf_vertices,
+                                                        const void *feats, int feat_bf16,
+                                                        const float *rays, int64_t ray_begin,
+                                                        const Sample &sm, bool valid, float4 prev, int fp16,
+                                                        uint8_t *abuf, int row, float &carry0, float &carry1) {
+    const int nq = md.F / 8;
+    int kb = 0;
+    if (valid) {
+        const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
+        const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
+        const float o[3] = {ra.x, ra.y, rb.x};
+        const float d[3] = {rb.y, rc.x, rc.y};
+        const int cell[3] = {(int)(sm.cell & 1023u), (int)((sm.cell >> 10) & 1023u), (int)((sm.cell >> 20) & 1023u)};
+        const float n = (float)(1 << depth);
+        const float h = ldexpf(1.0f, -depth);
+        float ta, tb;
+        if (MODE == 1) {
+            float t0 = 0.f, t1 = INFINITY;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.f) continue;
+                const float lo = ((float)cell[a] * h - o[a]) / d[a];
+                const float hi = ((float)(cell[a] + 1) * h - o[a]) / d[a];
+                t0 = fmaxf(t0, fminf(lo, hi));
+                t1 = fminf(t1, fmaxf(lo, hi));
+            }
+            ta = t0;
+            tb = t1;
+            carry0 = t0;
+            carry1 = t1;
+        } else {
+            const float ts = fmaf(prev.y, prev.z - prev.w, prev.w);  // eta t_in + (1 - eta) t_out
+            ta = tb = ts;
+            carry0 = prev.x;
+            carry1 = ts;
+        }
+        float wa[8], wb[8];
+        corner_weights(o, d, ta, cell, n, wa);
+        if (MODE == 1) corner_weights(o, d, tb, cell, n, wb);
+        const int4 *vp = reinterpret_cast<const int4 *>(leaf_vertices + 8 * (int64_t)sm.leaf);
+        const int4 va = __ldg(vp), vb = __ldg(vp + 1);
+        const int vid[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        for (int q = 0; q < nq; ++q) {
+            float acc_a[8], acc_b[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc_a[e] = acc_b[e] = 0.f;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                float z[8];
+                vertex_feat8(feats, feat_bf16, md.F, vid[v], q, z);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    acc_a[e] = fmaf(wa[v], z[e], acc_a[e]);
+                    if (MODE == 1) acc_b[e] = fmaf(wb[v], z[e], acc_b[e]);
+                }
+            }
+            st_chunk(abuf, row, q, tc::pack2(acc_a[0], acc_a[1], fp16), tc::pack2(acc_a[2], acc_a[3], fp16),
+                     tc::pack2(acc_a[4], acc_a[5], fp16), tc::pack2(acc_a[6], acc_a[7], fp16));
+            if (MODE == 1)
+                st_chunk(abuf, row, nq + q, tc::pack2(acc_b[0], acc_b[1], fp16), tc::pack2(acc_b[2], acc_b[3], fp16),
+                         tc::pack2(acc_b[4], acc_b[5], fp16), tc::pack2(acc_b[6], acc_b[7], fp16));
+        }
+        kb = (MODE == 1 ? 2 : 1) * nq;
+        float p1[3], p2[3];
+        sphere_param(o, d, sm.cell, depth, p1, p2);
+        st_chunk(abuf, row, kb++, tc::pack2(p1[0], p1[1], fp16), tc::pack2(p1[2], p2[0], fp16),
+                 tc::pack2(p2[1], p2[2], fp16), 0u);
+    }
+    for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+}
+
 // The gather of a tile is latency-bound, so each warpgroup keeps the sample
 // records of its next two tiles in registers and, one tile ahead, prefetches
 // the next tile's feature rows and rays into L2 while the current tile runs
@@ -246,7 +359,7 @@ __device__ __forceinline__ void prefetch_gather(const Sample &r, const void *fea
 // EPI = TMEM loads (of 32 columns) issued before each wait in the hidden-layer
 // epilogue: 1 keeps registers low enough for 4 warpgroups, 2 overlaps the
 // loads and needs the register budget of at most 3 warpgroups.
-template <int H, int EPI>
+template <int H, int EPI, int MODE>
 __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
     mlp_forward_tc_kernel(const __grid_constant__ SceneTable T, const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -327,13 +440,21 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
             const int64_t s = sbase + sl;
             const Sample rec = pf.cur;
             const bool valid = pf.v_cur;
-            if (pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, P.md.F, SD.rays, SD.ray_begin);
+            if (MODE == 0 && pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, P.md.F, SD.rays, SD.ray_begin);
             pf.cur = pf.nxt;
             pf.v_cur = pf.v_nxt;
             pf.v_nxt = load_record(P.samples, sbase, tile0, tile + 2 * P.n_wg, seg_end, S_sc, row, pf.nxt);
             // ---- network input row -> A operand (K0 columns)
-            build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
-                               rec, valid, P.fp16, abuf, row, nullptr);
+            float carry0 = 0.f, carry1 = 0.f;
+            if (MODE == 0) {
+                build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                                   rec, valid, P.fp16, abuf, row, nullptr);
+            } else {
+                const float4 prev = (MODE == 2 && valid) ? P.outputs[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                build_input_two_decoder<MODE>(P.md, P.lay.K0, depth, SD.tree.leaf_vertices, SD.feats, P.feat_bf16,
+                                              SD.rays, SD.ray_begin, rec, valid, prev, P.fp16, abuf, row, carry0,
+                                              carry1);
+            }
             for (int l = 0; l < P.lay.n_layers; ++l) {
                 const int N = P.lay.w_rows[l];
                 const int Kl = P.lay.w_cols[l];
@@ -405,9 +526,18 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                     uint32_t v[4];
                     tc::tmem_ld4(tmem_row, v);
                     tc::tmem_wait_ld();
-                    if (sl < S_sc)
-                        P.outputs[s] = output_activation(__uint_as_float(v[0]) + b[0], __uint_as_float(v[1]) + b[1],
-                                                         __uint_as_float(v[2]) + b[2], __uint_as_float(v[3]) + b[3]);
+                    if (sl < S_sc) {
+                        const float o0 = __uint_as_float(v[0]) + b[0], o1 = __uint_as_float(v[1]) + b[1];
+                        const float o2 = __uint_as_float(v[2]) + b[2], o3 = __uint_as_float(v[3]) + b[3];
+                        if (MODE == 0) {
+                            P.outputs[s] = output_activation(o0, o1, o2, o3);
+                        } else if (MODE == 1) {  // (tau, eta, t_in, t_out) for the colour pass
+                            P.outputs[s] = make_float4(fmaxf(o0, 0.f), sigmoidf_(o1), carry0, carry1);
+                        } else {                 // (colour, tau); the sample's depth parameter becomes t_s
+                            P.outputs[s] = make_float4(sigmoidf_(o0), sigmoidf_(o1), sigmoidf_(o2), carry0);
+                            P.samples[s].tmid = carry1;
+                        }
+                    }
                 }
             }
             // all TMEM reads of this tile are done before the next tile's MMAs
@@ -436,7 +566,7 @@ static int tc_forward_config(const MlpDims &md, const TcLayout &lay, int &n_wg, 
     return SVLF_OK;
 }
 
-template <int H, int EPI>
+template <int H, int EPI, int MODE>
 static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md, const TcLayout &lay,
                   cudaStream_t s, int n_wg_override) {
     TcFwdParams P = P0;
@@ -445,17 +575,17 @@ static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md,
     if (rc) return rc;
     if (n_wg_override > 0 && n_wg_override < P.n_wg) P.n_wg = n_wg_override;
     if (EPI == 2 && P.n_wg > 3) P.n_wg = 3;
-    if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H, EPI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
-    prof_begin("mlp_forward_tc", s);
-    mlp_forward_tc_kernel<H, EPI><<<num_sms(), 128 * P.n_wg, smem, s>>>(T, P);
+    prof_begin(MODE == 0 ? "mlp_forward_tc" : MODE == 1 ? "two_decoder_ft_tc" : "two_decoder_fc_tc", s);
+    mlp_forward_tc_kernel<H, EPI, MODE><<<num_sms(), 128 * P.n_wg, smem, s>>>(T, P);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
 int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                          const Workspace &ws, cudaStream_t s) {
+                          const Workspace &ws, cudaStream_t s, int mode) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcFwdParams P;
     memset(&P, 0, sizeof(P));
@@ -469,8 +599,10 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneT
     P.counter = ws.counter;
     P.outputs = ws.outputs;
     const svlf_tuning &tu = tuning();
-    if (tu.mlp_epilogue_batch == 2) return fwd_tc<kHp, 2>(T, P, md, P.lay, s, tu.mlp_warpgroups);
-    return fwd_tc<kHp, 1>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    if (mode == 1) return fwd_tc<kHp, 1, 1>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    if (mode == 2) return fwd_tc<kHp, 1, 2>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    if (tu.mlp_epilogue_batch == 2) return fwd_tc<kHp, 2, 0>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    return fwd_tc<kHp, 1, 0>(T, P, md, P.lay, s, tu.mlp_warpgroups);
 }
 
 // ---------------------------------------------------------------- backward

@@ -234,8 +234,69 @@ extern "C" int svlf_free_octree(svlf_octree tree) {
     cudaFree(tree->h.nodes_dev);
     cudaFree(tree->h.bricks_dev);
     cudaFree(tree->h.pgrid_dev);
+    cudaFree(tree->h.vtx_dev);
     delete tree;
     return SVLF_OK;
+}
+
+// Vertex table of the two-decoder form (Sec. 4.1: one feature vector per
+// octree vertex, shared by the voxels meeting there). Built on the host once
+// per octree: every leaf corner as a lattice point (depth + 1 bits per axis),
+// Morton-encoded, sorted and de-duplicated; a vertex id is the rank of its
+// lattice point in that order.
+extern "C" int svlf_octree_build_vertices(svlf_octree tree, int64_t *n_vertices, void *stream) {
+    if (!tree) return SVLF_ERR_ARG;
+    OctreeHost &H = tree->h;
+    if (H.vtx_dev) {
+        if (n_vertices) *n_vertices = H.view.n_vertices;
+        return SVLF_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = H.view.n_leaves;
+    std::vector<int32_t> ijk((size_t)n * 3);
+    if (n > 0) {
+        if (cudaMemcpyAsync(ijk.data(), H.leaf_ijk_dev, sizeof(int32_t) * 3 * (size_t)n,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return SVLF_ERR_CUDA;
+    }
+    std::vector<uint64_t> code((size_t)n * 8);
+    for (int64_t q = 0; q < n; ++q)
+        for (int c = 0; c < 8; ++c)
+            code[(size_t)q * 8 + c] = morton3((uint32_t)ijk[3 * q] + (c & 1), (uint32_t)ijk[3 * q + 1] + ((c >> 1) & 1),
+                                              (uint32_t)ijk[3 * q + 2] + ((c >> 2) & 1));
+    std::vector<uint64_t> uniq(code);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    if ((int64_t)uniq.size() >= ((int64_t)1 << 31)) return SVLF_ERR_UNSUPPORTED;
+    std::vector<int32_t> vid(code.size());
+    for (size_t i = 0; i < code.size(); ++i)
+        vid[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), code[i]) - uniq.begin());
+    int32_t *dev = nullptr;
+    const size_t nb = sizeof(int32_t) * (vid.size() > 0 ? vid.size() : 8);
+    if (cudaMalloc(&dev, nb) != cudaSuccess) return SVLF_ERR_CUDA;
+    if (!vid.empty() &&
+        (cudaMemcpyAsync(dev, vid.data(), sizeof(int32_t) * vid.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+        cudaFree(dev);
+        return SVLF_ERR_CUDA;
+    }
+    H.vtx_dev = dev;
+    H.view.leaf_vertices = dev;
+    H.view.n_vertices = (int64_t)uniq.size();
+    if (n_vertices) *n_vertices = H.view.n_vertices;
+    return SVLF_OK;
+}
+
+extern "C" int svlf_octree_leaf_vertices(svlf_octree tree, int32_t *out, void *stream) {
+    if (!tree || !out) return SVLF_ERR_ARG;
+    if (!tree->h.vtx_dev) return SVLF_ERR_ARG;
+    const size_t nb = sizeof(int32_t) * 8 * (size_t)tree->h.view.n_leaves;
+    if (nb == 0) return SVLF_OK;
+    return cudaMemcpyAsync(out, tree->h.vtx_dev, nb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? SVLF_OK
+               : SVLF_ERR_CUDA;
 }
 
 namespace svlf {

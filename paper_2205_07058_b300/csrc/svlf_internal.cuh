@@ -36,6 +36,10 @@ struct OctreeView {
     int pgrid_shift;    // L - 3 (0 when L = 2)
     int root_is_brick;  // depth 2: the root itself is the only brick
     int empty;          // no leaves
+    // vertex table (two-decoder form, built on request): vertex id of corner
+    // (a, b, c) of leaf q at leaf_vertices[8 q + a + 2b + 4c]; null until built
+    const int32_t *leaf_vertices;
+    int64_t n_vertices;
 };
 
 struct OctreeHost {
@@ -44,6 +48,7 @@ struct OctreeHost {
     uint32_t *nodes_dev;
     uint4 *bricks_dev;
     uint32_t *pgrid_dev;
+    int32_t *vtx_dev;       // n_leaves x 8 vertex ids, or null
 };
 
 // ---------------------------------------------------------------- samples

@@ -45,6 +45,12 @@ class MlpDesc(ctypes.Structure):
                 ("out_dim", ctypes.c_int), ("precision", ctypes.c_int), ("feat_dtype", ctypes.c_int)]
 
 
+class TwoDecoderDescC(ctypes.Structure):
+    _fields_ = [("feat_t", ctypes.c_int), ("feat_c", ctypes.c_int), ("hidden_t", ctypes.c_int),
+                ("n_hidden_t", ctypes.c_int), ("hidden_c", ctypes.c_int), ("n_hidden_c", ctypes.c_int),
+                ("precision", ctypes.c_int), ("feat_dtype", ctypes.c_int)]
+
+
 class RenderOpts(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3)]
 
@@ -72,6 +78,8 @@ EXPORTS = [
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
+    "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_workspace_size_two_decoder",
+    "svlf_render_rays_two_decoder",
 ]
 
 _lib = None
@@ -169,6 +177,19 @@ class Octree:
         _check("svlf_octree_leaf_ijk", lib().svlf_octree_leaf_ijk(self.handle, _ptr(out), _stream(stream)))
         return out
 
+    def build_vertices(self, stream=None) -> int:
+        """Vertex table of the two-decoder form; returns the vertex count."""
+        n = ctypes.c_int64()
+        _check("svlf_octree_build_vertices", lib().svlf_octree_build_vertices(self.handle, ctypes.byref(n),
+                                                                               _stream(stream)))
+        self.n_vertices = int(n.value)
+        return self.n_vertices
+
+    def leaf_vertices(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n_leaves, 8), dtype=torch.int32, device="cuda")
+        _check("svlf_octree_leaf_vertices", lib().svlf_octree_leaf_vertices(self.handle, _ptr(out), _stream(stream)))
+        return out
+
     def free(self):
         if self.handle:
             lib().svlf_free_octree(self.handle)
@@ -242,6 +263,56 @@ def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor,
     _check("svlf_render_rays", lib().svlf_render_rays(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
         _ptr(rgb), _ptr(depth), _ptr(hits), _ptr(t_io), wp, wb, _stream(stream)))
+    return rgb, depth, hits, t_io, workspace
+
+
+@dataclass
+class TwoDecoder:
+    """Shapes of the two-decoder form (defaults: the paper's Sec. 4.5 sizes)."""
+    feat_t: int = 64
+    feat_c: int = 32
+    hidden_t: int = 128
+    n_hidden_t: int = 1
+    hidden_c: int = 128
+    n_hidden_c: int = 3
+    precision: int = BF16
+    feat_dtype: int = FEAT_F32
+
+    def desc(self) -> TwoDecoderDescC:
+        return TwoDecoderDescC(self.feat_t, self.feat_c, self.hidden_t, self.n_hidden_t, self.hidden_c,
+                               self.n_hidden_c, self.precision, self.feat_dtype)
+
+
+def workspace_size_two_decoder(net: TwoDecoder, n_rays: int, K: int) -> int:
+    b = ctypes.c_size_t()
+    d = net.desc()
+    _check("svlf_workspace_size_two_decoder",
+           lib().svlf_workspace_size_two_decoder(ctypes.byref(d), int(n_rays), int(K), ctypes.byref(b)))
+    return int(b.value)
+
+
+def svlf_render_rays_two_decoder(tree: Octree, z_t: torch.Tensor, z_c: torch.Tensor, params_t: torch.Tensor,
+                                 params_c: torch.Tensor, net: TwoDecoder, rays: torch.Tensor, K: int,
+                                 bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
+                                 want_hits: bool = False, out: Optional[tuple] = None, stream=None):
+    """Two-decoder render (the octree's vertex table must be built).
+    Returns (rgb, depth, hits or None, t_io or None, workspace)."""
+    N = rays.shape[0]
+    if workspace is None:
+        workspace = torch.empty(workspace_size_two_decoder(net, N, K) + 256, dtype=torch.uint8, device="cuda")
+    if out is None:
+        rgb = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+        depth = torch.empty((N,), dtype=torch.float32, device="cuda")
+    else:
+        rgb, depth = out
+    hits = torch.empty((N, K), dtype=torch.int32, device="cuda") if want_hits else None
+    t_io = torch.empty((N, K, 2), dtype=torch.float32, device="cuda") if want_hits else None
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays_two_decoder", lib().svlf_render_rays_two_decoder(
+        tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays), N,
+        ctypes.byref(o), _ptr(rgb), _ptr(depth), _ptr(hits), _ptr(t_io), wp, wb, _stream(stream)))
     return rgb, depth, hits, t_io, workspace
 
 

@@ -1,0 +1,151 @@
+"""The paper's two-decoder SVLF (vertex features, trilinear interpolation,
+F^T -> tau, eta; F^C at the surface point) on the GPU against the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import two_decoder as T2
+from paper_2205_07058_b300 import inputs as I
+from tests.gpu_common import compare_hits, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def _net(rng, dims, bias_std=0.2):
+    out = []
+    for o, i in dims:
+        out.append(rng.standard_normal(o * i) * math.sqrt(2.0 / i))
+        out.append(rng.standard_normal(o) * bias_std)
+    return np.concatenate(out).astype(np.float32)
+
+
+def _setup(seed, depth, n_sph, n_box, views, res, ft=64, fc=32, ht=128, nt=1, hc=128, nc=3):
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(seed)
+    sc = I.make_scene(rng, depth, n_sph, n_box)
+    tree_o = O.build_octree(sc.leaf_ijk, depth)
+    vt = T2.vertex_table(tree_o)
+    zt = I.make_features(rng, vt.n_vertices, ft)
+    zc = I.make_features(rng, vt.n_vertices, fc)
+    dt, dc = T2.dims_t(ft, ht, nt), T2.dims_c(fc, hc, nc)
+    pt, pc = _net(rng, dt), _net(rng, dc)
+    az, el = I.random_view_angles(rng, views)
+    rays = np.concatenate([I.pinhole_rays(az[v], el[v], res, res) for v in range(views)])
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), depth)
+    return dict(sc=sc, tree_o=tree_o, vt=vt, zt=zt, zc=zc, dt=dt, dc=dc, pt=pt, pc=pc, rays=rays, tree=tree,
+                shape=(ft, fc, ht, nt, hc, nc))
+
+
+@pytest.fixture(scope="module")
+def small():
+    return _setup(1007, 7, 10, 4, 2, 96)
+
+
+def test_vertex_table_matches_oracle(small):
+    n = small["tree"].build_vertices()
+    assert n == small["vt"].n_vertices
+    lv = small["tree"].leaf_vertices().cpu().numpy()
+    assert np.array_equal(lv, small["vt"].leaf_vertices)
+
+
+def _gpu(w, prec, K, bg=(0.0, 0.0, 0.0), feat_bf16=False, params=None):
+    from paper_2205_07058_b300 import svlf
+    w["tree"].build_vertices()
+    ft, fc, ht, nt, hc, nc = w["shape"]
+    net = svlf.TwoDecoder(ft, fc, ht, nt, hc, nc, svlf.PRECISIONS[prec],
+                          svlf.FEAT_BF16 if feat_bf16 else svlf.FEAT_F32)
+    cast = (lambda a: torch.from_numpy(a).to(torch.bfloat16).cuda()) if feat_bf16 else (lambda a: torch.from_numpy(a).cuda())
+    pt, pc = params if params is not None else (w["pt"], w["pc"])
+    rgb, depth, hits, tio, _ = svlf.svlf_render_rays_two_decoder(
+        w["tree"], cast(w["zt"]), cast(w["zc"]), torch.from_numpy(pt).cuda(), torch.from_numpy(pc).cuda(),
+        net, torch.from_numpy(w["rays"]).cuda(), K, bg=bg, want_hits=True)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    return rgb.cpu().numpy(), depth.cpu().numpy(), hits.cpu().numpy(), tio.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,feat_bf16", [("bf16", False), ("fp16", False), ("bf16", True)])
+def test_render_matches_emulating_oracle(small, prec, feat_bf16):
+    w = small
+    K = 6
+    bg = (0.1, 0.2, 0.3)
+    rgb, depth, hits, tio = _gpu(w, prec, K, bg, feat_bf16)
+    zt, zc = w["zt"], w["zc"]
+    if feat_bf16:  # the stored values the GPU reads
+        zt = torch.from_numpy(zt).to(torch.bfloat16).float().numpy()
+        zc = torch.from_numpy(zc).to(torch.bfloat16).float().numpy()
+    ref = T2.render2(w["tree_o"], w["vt"], zt, zc, w["pt"], w["pc"], w["dt"], w["dc"], w["rays"], K, bg=bg,
+                     lowp=prec)
+    n_ok, n_deg, _ = compare_hits(ref.hits, hits, tio)
+    ok = ~ref.hits.degenerate
+    assert (ref.hits.n[ok] > 0).sum() > 1500
+    err = np.abs(rgb[ok] - ref.rgb[ok]).max(axis=1)
+    derr = np.abs(depth[ok] - ref.depth[ok]) / (1 + ref.depth[ok])
+    f64 = T2.render2(w["tree_o"], w["vt"], zt, zc, w["pt"], w["pc"], w["dt"], w["dc"], w["rays"], K, bg=bg,
+                     hits=ref.hits)
+    print(prec, "bf16 storage" if feat_bf16 else "fp32 storage", "colour max / p99", err.max(), np.quantile(err, 0.99),
+          "depth max", derr.max(), "| vs FP64: colour max", np.abs(rgb[ok] - f64.rgb[ok]).max())
+    assert err.max() <= 2e-3 and derr.max() <= 2e-3
+    assert np.quantile(err, 0.99) <= 2e-4
+
+
+def test_constant_networks_closed_form(small):
+    """Zero weights: every hit has tau = relu(b_tau), eta = sigmoid(b_eta),
+    c = sigmoid(b_c), so the image depends only on the hit segments."""
+    w = small
+    K = 5
+    def zero_net(dims, out_b):
+        parts = []
+        for li, (o, i) in enumerate(dims):
+            parts.append(np.zeros(o * i, np.float32))
+            parts.append(np.asarray(out_b, np.float32) if li + 1 == len(dims) else np.zeros(o, np.float32))
+        return np.concatenate(parts)
+    pt = zero_net(w["dt"], [0.8, -0.7])
+    pc = zero_net(w["dc"], [0.3, -1.2, 2.0])
+    bg = (0.5, 0.5, 0.5)
+    rgb, depth, hits, tio = _gpu(w, "bf16", K, bg, params=(pt, pc))
+    ref = T2.render2(w["tree_o"], w["vt"], w["zt"], w["zc"], pt, pc, w["dt"], w["dc"], w["rays"], K, bg=bg)
+    ok = ~ref.hits.degenerate
+    np.testing.assert_allclose(rgb[ok], ref.rgb[ok], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=0, atol=2e-6 * (1 + ref.depth[ok].max()))
+
+
+def test_many_tiles_per_cta_sampled():
+    """Depth 9 scene, 2 views of 800^2 (1.28 M rays): every CTA runs many
+    tiles; 3000 sampled rays against the bf16-emulating oracle."""
+    w = _setup(1008, 9, 48, 24, 2, 800)
+    K = 8
+    rgb, depth, hits, tio = _gpu(w, "bf16", K)
+    sample = np.random.default_rng(3).choice(w["rays"].shape[0], 3000, replace=False)
+    ref = T2.render2(w["tree_o"], w["vt"], w["zt"], w["zc"], w["pt"], w["pc"], w["dt"], w["dc"],
+                     w["rays"][sample], K, lowp="bf16")
+    ok = ~ref.hits.degenerate
+    assert np.array_equal(hits[sample][ok], ref.hits.rank[ok])
+    assert (ref.hits.n[ok] > 0).sum() > 300
+    err = np.abs(rgb[sample][ok] - ref.rgb[ok]).max()
+    derr = (np.abs(depth[sample][ok] - ref.depth[ok]) / (1 + ref.depth[ok])).max()
+    assert err <= 2e-3 and derr <= 2e-3, (err, derr)
+
+
+def test_argument_errors():
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(9)
+    ijk = torch.from_numpy(np.unique(rng.integers(0, 8, size=(40, 3)), axis=0).astype(np.int32))
+    tree = svlf.Octree(ijk, 3)
+    net = svlf.TwoDecoder(16, 8, 32, 1, 32, 1)
+    z = torch.zeros((1000, 16), device="cuda")
+    p = torch.zeros(10000, device="cuda")
+    rays = torch.from_numpy(I.pinhole_rays(0.3, 0.2, 8, 8)).cuda()
+    with pytest.raises(svlf.SvlfError) as e:  # vertex table not built
+        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, net, rays, 4)
+    assert e.value.code == svlf.SVLF_ERR_ARG
+    tree.build_vertices()
+    with pytest.raises(svlf.SvlfError) as e:
+        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, svlf.TwoDecoder(16, 8, 32, 1, 32, 1, svlf.FP32), rays, 4)
+    assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
+    with pytest.raises(svlf.SvlfError) as e:
+        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, svlf.TwoDecoder(12, 8, 32, 1, 32, 1), rays, 4)
+    assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
