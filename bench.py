@@ -78,10 +78,11 @@ def parse():
     p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="step", choices=["step", "batched", "large"],
+    p.add_argument("--workload", default="step", choices=["step", "batched", "large", "twodec"],
                    help="step: the headline render + train step; batched: 64 scenes in one "
                         "launch per kernel under a CUDA graph; large: depth-10 scene, bf16 "
-                        "features, 4x128 network, K = 16, 8 views + 2^20 training rays")
+                        "features, 4x128 network, K = 16, 8 views + 2^20 training rays; twodec: "
+                        "the paper's two-decoder form (vertex features), render of 4 views of 1600^2")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tuning", default=None,
                    help="fixed launch shapes instead of the search, e.g. "
@@ -694,6 +695,162 @@ def run_batched(args, rank, world, local_rank):
     }
 
 
+# ----------------------------------------------------------------------------
+# two-decoder form (Sec. 4.1-4.2): render only
+# ----------------------------------------------------------------------------
+TD_FT, TD_FC, TD_H, TD_NT, TD_NC = 64, 32, 128, 1, 3  # the paper's Sec. 4.5 sizes
+TD_WORKLOAD = ("two-decoder render 4x1600^2: depth-9 octree over 64 spheres + 32 box shells, vertex features "
+               "Z^T 64 + Z^C 32 fp32, F^T 134->128->2, F^C 38->3x128->3, K=8")
+
+
+def td_flops_per_sample():
+    ft = 2 * ((2 * TD_FT + 6) * TD_H + (TD_NT - 1) * TD_H * TD_H + 2 * TD_H)
+    fc = 2 * ((TD_FC + 6) * TD_H + (TD_NC - 1) * TD_H * TD_H + 3 * TD_H)
+    return ft, fc
+
+
+def td_bytes_per_sample():
+    """Algorithmic bytes of the two passes per sample (vertex rows counted once
+    per sample, not deduplicated): record 16 + ray 24 + 8 vertex ids 32 + the
+    rows, + 16 B output; the colour pass also reads the first pass's output."""
+    ft = 16 + 24 + 32 + 8 * TD_FT * 4 + 16
+    fc = 16 + 24 + 32 + 8 * TD_FC * 4 + 16 + 16
+    return ft, fc
+
+
+def run_twodec(args, rank, world, local_rank):
+    import torch
+    from paper_2205_07058_b300 import inputs as I
+    from paper_2205_07058_b300 import svlf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t_setup = time.time()
+    rng = np.random.default_rng(SCENE_SEED)
+    scene = I.make_scene(rng, 9, 64, 32)
+    tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), 9)
+    n_vert = tree.build_vertices()
+    zt = torch.from_numpy(I.make_features(rng, n_vert, TD_FT)).to(dev)
+    zc = torch.from_numpy(I.make_features(rng, n_vert, TD_FC)).to(dev)
+    d_t = [(TD_H, 2 * TD_FT + 6)] + [(TD_H, TD_H)] * (TD_NT - 1) + [(2, TD_H)]
+    d_c = [(TD_H, TD_FC + 6)] + [(TD_H, TD_H)] * (TD_NC - 1) + [(3, TD_H)]
+    pt = torch.from_numpy(I.make_mlp_dims(rng, d_t, 0.1)).to(dev)
+    pc = torch.from_numpy(I.make_mlp_dims(rng, d_c, 0.1)).to(dev)
+    az, el = I.random_view_angles(np.random.default_rng(SCENE_SEED + 7919 * rank), args.views)
+    rays_h = np.concatenate([I.pinhole_rays(az[v], el[v], args.res, args.res) for v in range(args.views)])
+    rays = torch.from_numpy(rays_h).to(dev)
+    N = rays.shape[0]
+    net = svlf.TwoDecoder(TD_FT, TD_FC, TD_H, TD_NT, TD_H, TD_NC, svlf.PRECISIONS[args.precision])
+    ws = torch.empty(svlf.workspace_size_two_decoder(net, N, K_HITS) + 256, dtype=torch.uint8, device=dev)
+    rgb = torch.empty((N, 3), device=dev)
+    depth = torch.empty((N,), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws, out=(rgb, depth))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    svlf.svlf_profile_enable(True)
+    svlf.svlf_profile_report()
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kstats = svlf.svlf_profile_report()
+    svlf.svlf_profile_enable(False)
+    status = svlf.svlf_get_device_status()
+    ms = e0.elapsed_time(e1)
+    value = N * world * args.steps / (ms / 1e3)
+    # samples: count the hits of one render through the hit lists
+    _, _, hits, _, _ = svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws,
+                                                          want_hits=True)
+    S = int((hits >= 0).sum().item())
+    peaks, peak_src = measured_peaks()
+    total = sum(v[1] for v in kstats.values())
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / total, 4)}
+                  for k, v in sorted(kstats.items(), key=lambda x: -x[1][1])}
+    dom = max(kstats.items(), key=lambda x: x[1][1])[0]
+    launches, kms = kstats[dom]
+    avg_s = kms / launches / 1e3
+    bft, bfc = td_bytes_per_sample()
+    roof = None
+    if dom in ("two_decoder_ft_tc", "two_decoder_fc_tc"):
+        work = S * (bft if dom == "two_decoder_ft_tc" else bfc)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],
+                "peak_source": f"{peak_src} (copy)", "unit": "GB/s",
+                "frac": round(work / avg_s / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                "avg_launch_ms": round(kms / launches, 4),
+                "work": f"{S} samples x {bft if dom == 'two_decoder_ft_tc' else bfc} B (vertex rows not deduplicated)"}
+    elif dom == "trace":
+        work = (N * 32.0 + S * 16.0)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],
+                "peak_source": f"{peak_src} (copy)", "unit": "GB/s",
+                "frac": round(work / avg_s / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                "avg_launch_ms": round(kms / launches, 4)}
+    fft, ffc = td_flops_per_sample()
+    tensor = {k: round(S * f / (kstats[k][1] / kstats[k][0] / 1e3) / 1e12, 2)
+              for k, f in (("two_decoder_ft_tc", fft), ("two_decoder_fc_tc", ffc)) if k in kstats}
+    # end to end: rays from pinned host memory, image back
+    e2e = None
+    if not args.no_e2e:
+        h_rays = torch.from_numpy(rays_h).pin_memory()
+        h_rgb = torch.empty((N, 3)).pin_memory()
+        h_depth = torch.empty((N,)).pin_memory()
+
+        def e2e_step():
+            rays.copy_(h_rays, non_blocking=True)
+            step()
+            h_rgb.copy_(rgb, non_blocking=True)
+            h_depth.copy_(depth, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": N * world * args.steps / (a.elapsed_time(b) / 1e3), "unit": "rays/s",
+               "h2d_bytes_per_step": int(h_rays.numel() * 4), "d2h_bytes_per_step": int((h_rgb.numel() + N) * 4)}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import oracle as O
+        from oracle import two_decoder as T2
+        tree_o = O.build_octree(scene.leaf_ijk, 9)
+        vt = T2.vertex_table(tree_o)
+        sample = rays_h[np.random.default_rng(5).choice(N, 4096, replace=False)]
+        zt_h, zc_h = zt.cpu().numpy(), zc.cpu().numpy()
+        pt_h, pc_h = pt.cpu().numpy(), pc.cpu().numpy()
+        dt_o, dc_o = T2.dims_t(TD_FT, TD_H, TD_NT), T2.dims_c(TD_FC, TD_H, TD_NC)
+        T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, sample[:256], K_HITS)
+        t0 = time.perf_counter()
+        T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, sample, K_HITS)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(4096 / dt, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": "4096 random rays of the same views through the FP64 two-decoder oracle (vertex table "
+                         "built outside the timed region)"}
+    return {
+        "metric": "rays/s: two-decoder render 4x1600^2 (vertex features, F^T + F^C)",
+        "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic (seeded sphere/box-shell scene, pinhole views; stands in for RTMV)",
+        "config": {"workload": TD_WORKLOAD, "render_rays": N, "K": K_HITS, "vertices": n_vert, "samples": S,
+                   "l2": f"inputs larger than L2 (vertex features {n_vert * (TD_FT + TD_FC) * 4 / 1e6:.0f} MB)"},
+        "e2e": e2e, "gpu_launches": int(sum(v[0] for v in kstats.values())), "kernels": per_kernel,
+        "tensor_tflops": tensor, "roofline": roof, "clocks": clk, "device_status": status, "cpu_baseline": cpu,
+        "setup_s": round(time.time() - t_setup, 1),
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -702,6 +859,11 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "twodec":
+        out = run_twodec(args, rank, world, local_rank)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     if args.workload == "batched":

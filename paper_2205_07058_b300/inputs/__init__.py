@@ -138,6 +138,16 @@ def make_mlp(rng: np.random.Generator, shape: MLPShape, bias_std: float = 0.0) -
     return np.concatenate(parts).astype(np.float32)
 
 
+def make_mlp_dims(rng: np.random.Generator, dims, bias_std: float = 0.0) -> np.ndarray:
+    """Flat fp32 parameters for layers given as (out, in) pairs, initialised as
+    make_mlp does."""
+    parts = []
+    for o, i in dims:
+        parts.append((rng.standard_normal((o, i)) * math.sqrt(2.0 / i)).reshape(-1))
+        parts.append(rng.standard_normal(o) * bias_std if bias_std > 0 else np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def split_mlp(flat: np.ndarray, shape: MLPShape):
     """Views (W_l, b_l) into a flat parameter vector."""
     out, off = [], 0

@@ -117,6 +117,11 @@ def lib():
     L.svlf_profile_enable.argtypes = [i32]
     L.svlf_profile_report.argtypes = [P(KernelStat), i32, P(i32)]
     L.svlf_workspace_samples.argtypes = [vp, P(MlpDesc), i64, i32, P(i64), vp]
+    L.svlf_octree_build_vertices.argtypes = [vp, P(i64), vp]
+    L.svlf_octree_leaf_vertices.argtypes = [vp, vp, vp]
+    L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
+    L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
+                                               vp, vp, vp, vp, vp, sz, vp]
     L.svlf_status_string.argtypes = [i32]
     L.svlf_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:

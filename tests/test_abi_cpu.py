@@ -38,6 +38,14 @@ def test_binding_names_cover_the_abi():
     assert _declared() <= set(svlf.EXPORTS)
 
 
+def test_every_binding_declares_argument_types(L):
+    """Without argtypes ctypes passes Python ints as 32-bit C ints, leaving the
+    upper half of an int64_t / size_t argument undefined."""
+    from paper_2205_07058_b300 import svlf
+    for n in svlf.EXPORTS:
+        assert getattr(L, n).argtypes is not None, n
+
+
 def test_host_side_argument_errors(L):
     from paper_2205_07058_b300 import svlf
     assert svlf.status_string(0) == "ok"
