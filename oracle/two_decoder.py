@@ -123,6 +123,15 @@ class Render2:
     h_t: np.ndarray  # F^T inputs
     h_c: np.ndarray  # F^C inputs
     w: np.ndarray    # compositing weights (N, K)
+    T: np.ndarray    # transmittance (N, K + 1)
+    rank: np.ndarray
+    t_in: np.ndarray
+    t_out: np.ndarray
+    xs_t: list       # every F^T layer's input
+    pres_t: list     # every F^T layer's pre-activation
+    xs_c: list
+    pres_c: list
+    dirs: np.ndarray  # ray direction of every sample
 
 
 def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, params_t: np.ndarray,
@@ -145,13 +154,113 @@ def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, p
     x1 = o + t_in[:, None] * d
     x2 = o + t_out[:, None] * d
     h_t = np.concatenate([psi(x1, rank, tree, vt, z_t), psi(x2, rank, tree, vt, z_t), p1, p2], axis=1)
-    _, pres_t = O.mlp_forward(h_t, O.split_params(params_t, d_t), bf16=lowp)
+    xs_t, pres_t = O.mlp_forward(h_t, O.split_params(params_t, d_t), bf16=lowp)
     tau = np.maximum(pres_t[-1][:, 0], 0.0)
     eta = O.sigmoid(pres_t[-1][:, 1])
     x_s = eta[:, None] * x1 + (1.0 - eta[:, None]) * x2
     t_s = eta * t_in + (1.0 - eta) * t_out
     h_c = np.concatenate([psi(x_s, rank, tree, vt, z_c), p1, p2], axis=1)
-    _, pres_c = O.mlp_forward(h_c, O.split_params(params_c, d_c), bf16=lowp)
+    xs_c, pres_c = O.mlp_forward(h_c, O.split_params(params_c, d_c), bf16=lowp)
     colour = O.sigmoid(pres_c[-1])
     rgb, depth, T, w = O.composite(N, K, ray_of, slot, colour, tau, t_s, bg)
-    return Render2(rgb, depth, hits, ray_of, slot, tau, eta, colour, t_s, x1, x2, x_s, h_t, h_c, w)
+    return Render2(rgb, depth, hits, ray_of, slot, tau, eta, colour, t_s, x1, x2, x_s, h_t, h_c, w, T, rank,
+                   t_in, t_out, xs_t, pres_t, xs_c, pres_c, d)
+
+
+# ----------------------------------------------------------------------------
+# Adjoint (derived by hand from the definitions above, Eq. 3 and the loss)
+# ----------------------------------------------------------------------------
+def trilinear_weight_gradients(p: np.ndarray, ijk: np.ndarray, depth: int) -> np.ndarray:
+    """(S, 8, 3): d w_corner / d p inside the voxel (0 along an axis where the
+    position is clamped)."""
+    n = 2.0 ** depth
+    u_raw = p * n - ijk.astype(np.float64)
+    u = np.clip(u_raw, 0.0, 1.0)
+    inside = (u_raw > 0.0) & (u_raw < 1.0)
+    g = np.zeros((p.shape[0], 8, 3))
+    for s, corner in enumerate(CORNERS):
+        f = [u[:, a] if corner[a] else 1.0 - u[:, a] for a in range(3)]
+        for a in range(3):
+            sign = 1.0 if corner[a] else -1.0
+            others = f[(a + 1) % 3] * f[(a + 2) % 3]
+            g[:, s, a] = np.where(inside[:, a], sign * others * n, 0.0)
+    return g
+
+
+def _mlp_backward(delta, xs, pres, layers, lowp):
+    """Returns (flat dparams, dL/d(network input))."""
+    rnd = O._rounder(lowp)
+    grads = []
+    dx = None
+    for li in range(len(layers) - 1, -1, -1):
+        W, b = layers[li]
+        xin = rnd(xs[li]) if rnd else xs[li]
+        Wl = rnd(W) if rnd else W
+        grads.append((delta.T @ xin, delta.sum(axis=0)))
+        dx = delta @ Wl
+        if li > 0:
+            delta = dx * (pres[li - 1] > 0)
+    grads.reverse()
+    return np.concatenate([np.concatenate([g[0].reshape(-1), g[1]]) for g in grads]), dx
+
+
+def backward2(tree: O.Octree, vt: VertexTable, r: Render2, z_c: np.ndarray, params_t, params_c, d_t, d_c,
+              rgb_t, depth_t, mask, bg, feat_t: int, feat_c: int, lowp=False):
+    """Gradient of loss(render2(...)) (the loss of the single-network form:
+    mean over rays of the squared colour error + 0.1 masked |D - D*|).
+    Returns (dZ^T (n_vertices x feat_t), dZ^C, dparams_t, dparams_c, dC, dD)."""
+    N, K = r.hits.rank.shape
+    bg = np.asarray(bg, dtype=np.float64)
+    dC = 2.0 * (r.rgb - rgb_t) / N
+    dD = O.DEPTH_WEIGHT * mask * np.sign(r.depth - depth_t) / N
+    col_k = np.zeros((N, K, 3))
+    ts_k = np.zeros((N, K))
+    col_k[r.ray_of, r.slot] = r.colour
+    ts_k[r.ray_of, r.slot] = r.t_s
+    wc = r.w[:, :, None] * col_k
+    wt = r.w * ts_k
+    S = np.zeros((N, K, 3))
+    U = np.zeros((N, K))
+    accS = r.T[:, K:K + 1] * bg[None, :]
+    accU = np.zeros(N)
+    for i in range(K - 1, -1, -1):
+        S[:, i] = accS
+        U[:, i] = accU
+        accS = accS + wc[:, i]
+        accU = accU + wt[:, i]
+    Tn = r.T[:, 1:]
+    dcol = (r.w[:, :, None] * dC[:, None, :])[r.ray_of, r.slot]
+    dtau = (np.sum(dC[:, None, :] * (Tn[:, :, None] * col_k - S), axis=2) + dD[:, None] * (Tn * ts_k - U))[r.ray_of, r.slot]
+    dts = (r.w * dD[:, None])[r.ray_of, r.slot]  # D = sum_i w_i t_s,i
+    # F^C
+    ijk = tree.leaf_ijk()[r.rank]
+    dparams_c, dhc = _mlp_backward(dcol * r.colour * (1.0 - r.colour), r.xs_c, r.pres_c,
+                                   O.split_params(params_c, d_c), lowp)
+    dpsi_c = dhc[:, :feat_c]
+    wgt_s = trilinear_weights(r.x_s, ijk, tree.depth)
+    dzc = np.zeros((vt.n_vertices, feat_c))
+    np.add.at(dzc, vt.leaf_vertices[r.rank].reshape(-1),
+              (wgt_s[:, :, None] * dpsi_c[:, None, :]).reshape(-1, feat_c))
+    # through x_s = o + t_s d: d psi / d x_s from the corner weights' gradients
+    gw = trilinear_weight_gradients(r.x_s, ijk, tree.depth)                  # (S, 8, 3)
+    zdot = np.einsum("svf,sf->sv", np.asarray(z_c, np.float64)[vt.leaf_vertices[r.rank]], dpsi_c)
+    dxs = np.einsum("sv,sva->sa", zdot, gw)
+    dts = dts + np.einsum("sa,sa->s", dxs, r.dirs)  # x_s = o + t_s d
+    deta = dts * (r.t_in - r.t_out)                # t_s = eta t_in + (1 - eta) t_out
+    # F^T
+    delta_t = np.stack([dtau * (r.pres_t[-1][:, 0] > 0), deta * r.eta * (1.0 - r.eta)], axis=1)
+    dparams_t, dht = _mlp_backward(delta_t, r.xs_t, r.pres_t, O.split_params(params_t, d_t), lowp)
+    w1 = trilinear_weights(r.x1, ijk, tree.depth)
+    w2 = trilinear_weights(r.x2, ijk, tree.depth)
+    contrib = w1[:, :, None] * dht[:, None, :feat_t] + w2[:, :, None] * dht[:, None, feat_t:2 * feat_t]
+    dzt = np.zeros((vt.n_vertices, feat_t))
+    np.add.at(dzt, vt.leaf_vertices[r.rank].reshape(-1), contrib.reshape(-1, feat_t))
+    return dzt, dzc, dparams_t, dparams_c, dC, dD
+
+
+def kink_pattern2(r: Render2, depth_t, mask):
+    """Every hidden ReLU of both networks, the tau ReLU and the sign of D - D*."""
+    parts = [(p > 0) for p in r.pres_t[:-1]] + [(p > 0) for p in r.pres_c[:-1]]
+    parts.append(r.pres_t[-1][:, 0] > 0)
+    parts.append(np.sign(r.depth - depth_t) * (mask > 0))
+    return parts

@@ -208,3 +208,74 @@ def test_network_inputs_order_by_selection(small):
     expect = x2 @ A[f_sel] + b[f_sel]
     pre_eta = np.log(r.eta / (1.0 - r.eta))
     np.testing.assert_allclose(pre_eta, expect, rtol=0, atol=1e-9)
+
+
+def test_two_decoder_adjoint_matches_central_differences(small):
+    """The hand-derived adjoint (through Eq. 3, both networks, the trilinear
+    scatter and the surface point x_s = o + t_s d) against central
+    differences in float64, h = 1e-3, on 64 parameters: Z^T and Z^C entries
+    of hit voxels' corners, weights of both networks, and always eta's output
+    bias and weights (the path through x_s). Perturbations that flip a ReLU,
+    the tau ReLU or the sign of D - D* are resampled."""
+    sc, tree, vt, rays = small
+    K = 4
+    ft, fc = 8, 8
+    dt, dc = T2.dims_t(ft, 32, 1), T2.dims_c(fc, 32, 2)
+    rng = np.random.default_rng(21)
+
+    def rand_net(dims):
+        out = []
+        for o, i in dims:
+            out.append(rng.standard_normal(o * i) * np.sqrt(2.0 / i))
+            out.append(rng.standard_normal(o) * 0.3)
+        return np.concatenate(out)
+    pt, pc = rand_net(dt), rand_net(dc)
+    zt = rng.standard_normal((vt.n_vertices, ft)) * 0.5
+    zc = rng.standard_normal((vt.n_vertices, fc)) * 0.5
+    rgb_t = rng.uniform(0, 1, size=(rays.shape[0], 3))
+    depth_t, mask = I.analytic_depth(rays, sc)
+    depth_t, mask = depth_t.astype(np.float64), mask.astype(np.float64)
+    bg = np.array([0.3, 0.2, 0.1])
+    hits = O.trace(tree, rays, K)
+
+    def run(zt_, zc_, pt_, pc_):
+        r = T2.render2(tree, vt, zt_, zc_, pt_, pc_, dt, dc, rays, K, bg=bg, hits=hits)
+        return O.loss(r.rgb, r.depth, rgb_t, depth_t, mask), r
+
+    L0, r0 = run(zt, zc, pt, pc)
+    dzt, dzc, dpt, dpc, _, _ = T2.backward2(tree, vt, r0, zc, pt, pc, dt, dc, rgb_t, depth_t, mask, bg, ft, fc)
+    pat0 = T2.kink_pattern2(r0, depth_t, mask)
+    hit_vertices = np.unique(vt.leaf_vertices[r0.rank])
+    # eta's output row of F^T: the last layer is (2 x 32) then its bias (2)
+    n_t = pt.size
+    eta_idx = [n_t - 1] + [n_t - 2 - 32 + j for j in range(0, 32, 7)]
+    h = 1e-3
+    fd, ad, flips, k = [], [], 0, 0
+    while len(fd) < 64:
+        kind = ["zt", "zc", "pt", "pc"][k % 4]
+        if k < len(eta_idx):
+            kind, idx = "pt", eta_idx[k]
+        elif kind in ("zt", "zc"):
+            idx = (rng.choice(hit_vertices), rng.integers(ft if kind == "zt" else fc))
+        else:
+            idx = rng.integers((pt if kind == "pt" else pc).size)
+        k += 1
+        vals, ok = [], True
+        for sgn in (+1, -1):
+            a = {"zt": zt.copy(), "zc": zc.copy(), "pt": pt.copy(), "pc": pc.copy()}
+            a[kind][idx] += sgn * h
+            Ls, rs = run(a["zt"], a["zc"], a["pt"], a["pc"])
+            ok &= O.same_pattern(T2.kink_pattern2(rs, depth_t, mask), pat0)
+            vals.append(Ls)
+        if not ok:
+            flips += 1
+            continue
+        fd.append((vals[0] - vals[1]) / (2 * h))
+        ad.append({"zt": dzt, "zc": dzc, "pt": dpt, "pc": dpc}[kind][idx])
+    fd, ad = np.array(fd), np.array(ad)
+    scale = np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+    rel = np.abs(ad - fd) / scale
+    assert rel.max() <= 1e-4, (rel.max(), flips)
+    assert np.linalg.norm(ad - fd) / np.linalg.norm(fd) <= 1e-5
+    # eta carries gradient: its output bias derivative is not negligible
+    assert abs(dpt[n_t - 1]) > 1e-3 * np.abs(dpt).max()
