@@ -237,6 +237,23 @@ int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, const void *
                                  int32_t *hits, float *t_io, void *workspace, size_t ws_bytes,
                                  void *stream);
 
+/* Backward of svlf_render_rays_two_decoder with the workspace of that render
+ * (same inputs; it reuses the render's samples, outputs and per-sample
+ * (tau, eta, t_in, t_out)). Accumulates (+=) into d_z_t (n_vertices x feat_t
+ * float32), d_z_c (n_vertices x feat_c), d_params_t, d_params_c (layouts of
+ * z_t, z_c, params_t, params_c); any of them may be NULL. The adjoint runs
+ * through Eq. 3, F^C, the trilinear scatter to the corners, the surface point
+ * (x_s depends on eta: dL/deta = (dL/dx_s . d + w dL/dD)(t_in - t_out)) and
+ * F^T. Float16 operands scale the deltas by a power of two as in
+ * svlf_render_rays_backward. */
+int svlf_render_rays_backward_two_decoder(svlf_octree tree, const void *z_t, const void *z_c,
+                                          const float *params_t, const float *params_c,
+                                          const svlf_two_decoder_desc *desc, const float *rays,
+                                          int64_t n_rays, const svlf_render_opts *opts,
+                                          const float *d_rgb, const float *d_depth, float *d_z_t,
+                                          float *d_z_c, float *d_params_t, float *d_params_c,
+                                          void *workspace, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------ optimiser */
 /* One bias-corrected Adam step (Sec. 4.5 trains with Adam; Kingma & Ba) over
  * n float32 parameters (device): m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;

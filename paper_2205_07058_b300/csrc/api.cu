@@ -442,6 +442,18 @@ static size_t image_c_offset(const svlf_two_decoder_desc &d) { return align256(p
 static size_t images_bytes(const svlf_two_decoder_desc &d) {
     return image_c_offset(d) + align256(packed_tc_bytes(dims_c(d)));
 }
+// after the images: aux (tau, eta, t_in, t_out per sample) and w dL/dD per sample
+static size_t two_decoder_stride(const svlf_two_decoder_desc &d, int64_t n_rays, int K) {
+    const size_t S = (size_t)n_rays * (size_t)K;
+    return images_bytes(d) + align256(sizeof(float4) * S) + align256(sizeof(float) * S);
+}
+static float4 *aux_of(const Workspace &ws, const svlf_two_decoder_desc &d) {
+    return reinterpret_cast<float4 *>(static_cast<char *>(ws.packed_w) + images_bytes(d));
+}
+static float *w_dD_of(const Workspace &ws, const svlf_two_decoder_desc &d, int64_t n_rays, int K) {
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(aux_of(ws, d)) +
+                                     align256(sizeof(float4) * (size_t)n_rays * (size_t)K));
+}
 
 }  // namespace svlf
 
@@ -450,7 +462,7 @@ extern "C" int svlf_workspace_size_two_decoder(const svlf_two_decoder_desc *desc
     if (!bytes || n_rays < 0 || K < 1 || K > kMaxK) return SVLF_ERR_ARG;
     int rc = check_two_decoder(desc);
     if (rc) return rc;
-    *bytes = workspace_bytes_raw(n_rays, K, images_bytes(*desc), 1);
+    *bytes = workspace_bytes_raw(n_rays, K, two_decoder_stride(*desc, n_rays, K), 1);
     return SVLF_OK;
 }
 
@@ -473,7 +485,7 @@ extern "C" int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, c
     SceneTable T;
     if ((rc = make_table_core(&sc, 1, opts, false, T))) return rc;
     if (T.total_rays == 0) return SVLF_OK;
-    const size_t stride = images_bytes(*desc);
+    const size_t stride = two_decoder_stride(*desc, T.total_rays, T.K);
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
     if (ws_bytes < workspace_bytes_raw(T.total_rays, T.K, stride, 1)) return SVLF_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -489,7 +501,57 @@ extern "C" int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, c
     if ((rc = launch_pack_tc(mt, desc->precision, T, ws.packed_w, stride, s))) return rc;
     if ((rc = launch_pack_tc(mc, desc->precision, Tc, wc.packed_w, stride, s))) return rc;
     if ((rc = launch_trace(T, ws, hits, t_io, s))) return rc;
-    if ((rc = launch_mlp_forward_tc(mt, desc->precision, fb, T, ws, s, 1))) return rc;
-    if ((rc = launch_mlp_forward_tc(mc, desc->precision, fb, Tc, wc, s, 2))) return rc;
+    float4 *aux = aux_of(ws, *desc);
+    if ((rc = launch_mlp_forward_tc(mt, desc->precision, fb, T, ws, s, 1, aux))) return rc;
+    if ((rc = launch_mlp_forward_tc(mc, desc->precision, fb, Tc, wc, s, 2, aux))) return rc;
     return launch_composite(T, ws, opts->bg, s);
+}
+
+extern "C" int svlf_render_rays_backward_two_decoder(
+    svlf_octree tree, const void *z_t, const void *z_c, const float *params_t, const float *params_c,
+    const svlf_two_decoder_desc *desc, const float *rays, int64_t n_rays, const svlf_render_opts *opts,
+    const float *d_rgb, const float *d_depth, float *d_z_t, float *d_z_c, float *d_params_t, float *d_params_c,
+    void *workspace, size_t ws_bytes, void *stream) {
+    if (!tree) return SVLF_ERR_ARG;
+    int rc = check_two_decoder(desc);
+    if (rc) return rc;
+    const OctreeView &view = octree_view(tree);
+    if (!view.leaf_vertices && view.n_leaves > 0) return SVLF_ERR_ARG;
+    if (n_rays > 0 && view.n_leaves > 0 && (!z_t || !z_c || !params_t || !params_c)) return SVLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(z_c) % 16) return SVLF_ERR_ARG;
+    svlf_scene sc = one_scene(tree, z_t, params_t, rays, n_rays);
+    sc.d_rgb = d_rgb;
+    sc.d_depth = d_depth;
+    sc.d_features = d_z_t;
+    sc.d_mlp_params = d_params_t;
+    SceneTable T;
+    if ((rc = make_table_core(&sc, 1, opts, true, T))) return rc;
+    if (T.total_rays == 0 || (!d_z_t && !d_z_c && !d_params_t && !d_params_c)) return SVLF_OK;
+    const size_t stride = two_decoder_stride(*desc, T.total_rays, T.K);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes_raw(T.total_rays, T.K, stride, 1)) return SVLF_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws = carve_workspace_raw(workspace, T.total_rays, T.K, stride, 1);
+    const MlpDims mt = dims_t(*desc), mc = dims_c(*desc);
+    const int fb = desc->feat_dtype == SVLF_FEAT_BF16;
+    SceneTable Tc = T;
+    Tc.s[0].feats = z_c;
+    Tc.s[0].params = params_c;
+    Tc.s[0].d_feat = d_z_c;
+    Tc.s[0].d_params = d_params_c;
+    Workspace wc = ws;
+    wc.packed_w = static_cast<char *>(ws.packed_w) + image_c_offset(*desc);
+    float4 *aux = aux_of(ws, *desc);
+    float *w_dD = w_dD_of(ws, *desc, T.total_rays, T.K);
+    if (cudaMemsetAsync(ws.counter + kCtrMaxAbsDout, 0, sizeof(unsigned int), s) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    if ((rc = launch_composite_backward(T, ws, opts->bg, s, w_dD))) return rc;
+    // the colour pass runs whenever anything is wanted: it forms dL/d(eta) for the
+    // optical-thickness pass
+    if ((rc = launch_mlp_backward_tc(mc, desc->precision, fb, Tc, wc, d_z_c != nullptr, d_params_c != nullptr, s,
+                                     2, aux, w_dD)))
+        return rc;
+    if (!d_z_t && !d_params_t) return SVLF_OK;
+    return launch_mlp_backward_tc(mt, desc->precision, fb, T, ws, d_z_t != nullptr, d_params_t != nullptr, s, 1,
+                                  aux, w_dD);
 }

@@ -48,7 +48,8 @@ __global__ void composite_backward_kernel(const __grid_constant__ SceneTable Tb,
                                           const Sample *__restrict__ samples,
                                           const float4 *__restrict__ outputs, float bg0,
                                           float bg1, float bg2, float4 *__restrict__ dout,
-                                          unsigned int *__restrict__ max_abs_bits) {
+                                          unsigned int *__restrict__ max_abs_bits,
+                                          float *__restrict__ w_dD) {
     float gmax = 0.f;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Tb.total_rays;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -77,6 +78,7 @@ __global__ void composite_backward_kernel(const __grid_constant__ SceneTable Tb,
             g.z = w * g2 * o.z * (1.f - o.z);
             g.w = o.w > 0.f ? dtau : 0.f;
             dout[sp.x + j] = g;
+            if (w_dD) w_dD[sp.x + j] = w * gD;  // dL/d(depth parameter of the sample): D = sum_i w_i t_i
             gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(g.x), fabsf(g.y)), fmaxf(fabsf(g.z), fabsf(g.w))));
             S0 = fmaf(w, o.x, S0);
             S1 = fmaf(w, o.y, S1);
@@ -141,11 +143,11 @@ int launch_composite(const SceneTable &T, const Workspace &ws, const float bg[3]
 }
 
 int launch_composite_backward(const SceneTable &T, const Workspace &ws, const float bg[3],
-                              cudaStream_t s) {
+                              cudaStream_t s, float *w_dD) {
     prof_begin("composite_backward", s);
     composite_backward_kernel<<<grid_for(T.total_rays, 256), 256, 0, s>>>(
         T, ws.ray_span, ws.samples, ws.outputs, bg[0], bg[1], bg[2], ws.dout,
-        ws.counter + kCtrMaxAbsDout);
+        ws.counter + kCtrMaxAbsDout, w_dD);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

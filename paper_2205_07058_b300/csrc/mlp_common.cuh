@@ -84,8 +84,10 @@ void set_tc_warpgroups(int n);
 int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *packed,
                    size_t stride, cudaStream_t s);
 // mode 0: the single network; 1 / 2: the two-decoder form's F^T / F^C pass
+// (aux: per-sample (tau, eta, t_in, t_out), written by mode 1, read by mode 2)
 int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                          const Workspace &ws, cudaStream_t s, int mode = 0);
+                          const Workspace &ws, cudaStream_t s, int mode = 0, float4 *aux = nullptr);
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s);
+                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s,
+                           int mode = 0, float4 *aux = nullptr, const float *w_dD = nullptr);
 }  // namespace svlf

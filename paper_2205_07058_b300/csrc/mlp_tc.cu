@@ -127,6 +127,7 @@ struct TcFwdParams {
     Sample *samples;     // read; the two-decoder colour pass also rewrites each tmid
     const unsigned int *counter;
     float4 *outputs;
+    float4 *aux;         // two-decoder: (tau, eta, t_in, t_out) per sample, F^T pass -> F^C pass
     int n_wg;            // warpgroups per CTA
     uint32_t abuf_bytes; // activation buffer per warpgroup
 };
@@ -230,6 +231,29 @@ __device__ __forceinline__ void corner_weights(const float o[3], const float d[3
 #pragma unroll
     for (int c = 0; c < 8; ++c)
         w[c] = ((c & 1) ? u[0] : 1.f - u[0]) * ((c & 2) ? u[1] : 1.f - u[1]) * ((c & 4) ? u[2] : 1.f - u[2]);
+}
+
+// d w_c / d p (c = a + 2b + 4c') for the corners of voxel `cell` at p = o + t d;
+// zero along an axis where the position is clamped to the voxel.
+__device__ __forceinline__ void corner_weight_grads(const float o[3], const float d[3], float t, const int cell[3],
+                                                    float n, float g[8][3]) {
+    float u[3];
+    bool in[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float r = fmaf(t, d[a], o[a]) * n - (float)cell[a];
+        in[a] = r > 0.f && r < 1.f;
+        u[a] = fminf(fmaxf(r, 0.f), 1.f);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float f0 = (c & 1) ? u[0] : 1.f - u[0];
+        const float f1 = (c & 2) ? u[1] : 1.f - u[1];
+        const float f2 = (c & 4) ? u[2] : 1.f - u[2];
+        g[c][0] = in[0] ? ((c & 1) ? n : -n) * f1 * f2 : 0.f;
+        g[c][1] = in[1] ? ((c & 2) ? n : -n) * f0 * f2 : 0.f;
+        g[c][2] = in[2] ? ((c & 4) ? n : -n) * f0 * f1 : 0.f;
+    }
 }
 
 // Eight consecutive features (block q) of vertex v, widened to float32.
@@ -450,7 +474,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                 build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
                                    rec, valid, P.fp16, abuf, row, nullptr);
             } else {
-                const float4 prev = (MODE == 2 && valid) ? P.outputs[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 prev = (MODE == 2 && valid) ? P.aux[s] : make_float4(0.f, 0.f, 0.f, 0.f);
                 build_input_two_decoder<MODE>(P.md, P.lay.K0, depth, SD.tree.leaf_vertices, SD.feats, P.feat_bf16,
                                               SD.rays, SD.ray_begin, rec, valid, prev, P.fp16, abuf, row, carry0,
                                               carry1);
@@ -532,7 +556,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                         if (MODE == 0) {
                             P.outputs[s] = output_activation(o0, o1, o2, o3);
                         } else if (MODE == 1) {  // (tau, eta, t_in, t_out) for the colour pass
-                            P.outputs[s] = make_float4(fmaxf(o0, 0.f), sigmoidf_(o1), carry0, carry1);
+                            P.aux[s] = make_float4(fmaxf(o0, 0.f), sigmoidf_(o1), carry0, carry1);
                         } else {                 // (colour, tau); the sample's depth parameter becomes t_s
                             P.outputs[s] = make_float4(sigmoidf_(o0), sigmoidf_(o1), sigmoidf_(o2), carry0);
                             P.samples[s].tmid = carry1;
@@ -585,7 +609,7 @@ static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md,
 }
 
 int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                          const Workspace &ws, cudaStream_t s, int mode) {
+                          const Workspace &ws, cudaStream_t s, int mode, float4 *aux) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcFwdParams P;
     memset(&P, 0, sizeof(P));
@@ -598,6 +622,7 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneT
     P.samples = ws.samples;
     P.counter = ws.counter;
     P.outputs = ws.outputs;
+    P.aux = aux;
     const svlf_tuning &tu = tuning();
     if (mode == 1) return fwd_tc<kHp, 1, 1>(T, P, md, P.lay, s, tu.mlp_warpgroups);
     if (mode == 2) return fwd_tc<kHp, 1, 2>(T, P, md, P.lay, s, tu.mlp_warpgroups);
@@ -640,6 +665,12 @@ struct TcBwdParams {
     const Sample *samples;
     const unsigned int *counter;
     const float4 *dout;
+    // two-decoder form: per-sample (tau, eta, t_in, t_out) from the render, replaced by
+    // the colour pass's (dL/dtau_pre, dL/deta_pre) for the optical-thickness pass;
+    // dL/d(depth parameter) per sample; the running max |dL/d(output)| (fp16 scaling)
+    float4 *aux;
+    const float *w_dD;
+    unsigned int *gmax;
     uint32_t x_off[kMaxLayers];  // X_l buffers (byte offsets after the weight image)
     uint32_t gout_off, ones_off;
     uint32_t col_dwout, col_dw[kMaxLayers], col_db[kMaxLayers], tmem_cols;
@@ -718,6 +749,86 @@ static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
     return true;
 }
 
+// Layer-0 epilogue of the two-decoder backward: dL/dpsi (fp32 in TMEM columns
+// [0, F) and, for F^T, [F, 2F) for the exit point) spread to the hit voxel's
+// corner features by their trilinear weights (one float atomic each). The
+// colour pass (MODE 2) also carries dL/dpsi through the surface point:
+// dL/dx_s = sum_c (Z^C_c . dL/dpsi) grad w_c(x_s), dL/dt_s = w dL/dD + dL/dx_s . d,
+// dL/deta = dL/dt_s (t_in - t_out), and leaves (dL/dtau_pre, dL/deta_pre) in
+// aux for the optical-thickness pass. Every lane runs the TMEM loads; rows
+// without a sample skip the rest.
+template <int MODE>
+__device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev &SD, const Sample &rec, bool valid,
+                                               int64_t s, float carry0, float carry1, float4 prev,
+                                               float *__restrict__ dZ, uint32_t trow, float ginv,
+                                               const TcBwdParams &P) {
+    const int F = md.F;
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
+    int cell[3] = {0, 0, 0};
+    int vid[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float wa[8], wb[8];
+    float gw[8][3];
+    const float n = (float)(1 << SD.tree.depth);
+    if (valid) {
+        const float2 *rp = reinterpret_cast<const float2 *>(SD.rays + 6 * ((int64_t)rec.ray - SD.ray_begin));
+        const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
+        o[0] = ra.x; o[1] = ra.y; o[2] = rb.x;
+        d[0] = rb.y; d[1] = rc.x; d[2] = rc.y;
+        cell[0] = (int)(rec.cell & 1023u);
+        cell[1] = (int)((rec.cell >> 10) & 1023u);
+        cell[2] = (int)((rec.cell >> 20) & 1023u);
+        const int4 *vp = reinterpret_cast<const int4 *>(SD.tree.leaf_vertices + 8 * (int64_t)rec.leaf);
+        const int4 va = __ldg(vp), vb = __ldg(vp + 1);
+        vid[0] = va.x; vid[1] = va.y; vid[2] = va.z; vid[3] = va.w;
+        vid[4] = vb.x; vid[5] = vb.y; vid[6] = vb.z; vid[7] = vb.w;
+        if (MODE == 1) {  // carry = (t_in, t_out)
+            corner_weights(o, d, carry0, cell, n, wa);
+            corner_weights(o, d, carry1, cell, n, wb);
+        } else {          // carry = (tau, t_s)
+            corner_weights(o, d, carry1, cell, n, wa);
+            corner_weight_grads(o, d, carry1, cell, n, gw);
+        }
+    }
+    float zdot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < F; c += 16) {
+        uint32_t a[16], b[16];
+        tc::tmem_ld16(trow + (uint32_t)c, a);
+        if (MODE == 1) tc::tmem_ld16(trow + (uint32_t)(F + c), b);
+        tc::tmem_wait_ld();
+        if (!valid) continue;
+        const int ne = min(16, F - c);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            if (MODE == 2) {
+                float z[16];
+                vertex_feat8(SD.feats, P.feat_bf16, F, vid[v], c >> 3, z);
+                if (ne > 8) vertex_feat8(SD.feats, P.feat_bf16, F, vid[v], (c >> 3) + 1, z + 8);
+                for (int e = 0; e < ne; ++e) zdot[v] = fmaf(z[e], __uint_as_float(a[e]) * ginv, zdot[v]);
+            }
+            if (dZ) {
+                float *dst = dZ + (int64_t)vid[v] * F + c;
+                for (int e = 0; e < ne; ++e) {
+                    float gv = wa[v] * __uint_as_float(a[e]);
+                    if (MODE == 1) gv = fmaf(wb[v], __uint_as_float(b[e]), gv);
+                    atomicAdd(dst + e, gv * ginv);
+                }
+            }
+        }
+    }
+    if (MODE == 2 && valid) {
+        float dx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dx[a] = fmaf(zdot[v], gw[v][a], dx[a]);
+        const float dts = P.w_dD[s] + dx[0] * d[0] + dx[1] * d[1] + dx[2] * d[2];
+        const float eta = prev.y;
+        const float geta = dts * (prev.z - prev.w) * eta * (1.f - eta);
+        P.aux[s] = make_float4(P.dout[s].w, geta, 0.f, 0.f);
+        if (geta != 0.f) atomicMax(P.gmax, __float_as_uint(fabsf(geta)));
+    }
+}
+
 __device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32_t a_kstep,
                                         uint32_t a_lbo, uint32_t a_sbo, uint32_t b_base,
                                         uint32_t b_kstep, uint32_t b_lbo, uint32_t b_sbo, int K,
@@ -729,6 +840,7 @@ __device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_constant__ SceneTable T,
                                                                  const TcBwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -774,7 +886,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     const uint32_t mbar = tc::smem_u32(&s_mbar[0]);
     const int bf16 = P.fp16 ? 0 : 1;
     const int nh = md.nh;
-    const int Fn = (md.F + 15) & ~15;
+    // columns of dL/d(network input) formed at layer 0: the features (both
+    // interpolated blocks in the two-decoder optical-thickness pass)
+    const int Fn = ((MODE == 1 ? 2 * md.F : md.F) + 15) & ~15;
     uint32_t phase = 0, wphase = 0;
     bool aborted = false;
 
@@ -904,6 +1018,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         const int64_t sbase = SD.ray_begin * T.K;
         const int depth = SD.tree.depth;
         float *d_feat = (P.want_feat && P.l_min == 0) ? SD.d_feat : nullptr;
+        // the colour pass always forms dL/dpsi at layer 0: it carries the surface
+        // point's gradient to eta
+        const bool form_dz = MODE == 2 ? P.l_min == 0 : d_feat != nullptr;
         int tiles_done = 0;
         const int64_t tile0 = s_map.tile0[sc];
         TilePrefetch pf;
@@ -914,16 +1031,34 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             const int64_t s = sbase + sl;
             const Sample rec = pf.cur;
             const bool valid = pf.v_cur;
-            if (pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, md.F, SD.rays, SD.ray_begin);
+            if (MODE == 0 && pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, md.F, SD.rays, SD.ray_begin);
             pf.cur = pf.nxt;
             pf.v_cur = pf.v_nxt;
             pf.v_nxt = load_record(P.samples, sbase, tile0, tile + 2, seg_end, S_sc, row, pf.nxt);
             int leaf = -1;
+            float carry0 = 0.f, carry1 = 0.f;
+            float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
             // ---- 1. X_0 and G_out
             {
-                build_input_chunks(md, lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
-                                   rec, valid, P.fp16, smem + P.x_off[0], row, &leaf);
-                const float4 g = valid ? P.dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (MODE == 0) {
+                    build_input_chunks(md, lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                                       rec, valid, P.fp16, smem + P.x_off[0], row, &leaf);
+                    if (valid) g = P.dout[s];
+                } else {
+                    if (valid) prev = P.aux[s];
+                    build_input_two_decoder<MODE>(md, lay.K0, depth, SD.tree.leaf_vertices, SD.feats, P.feat_bf16,
+                                                  SD.rays, SD.ray_begin, rec, valid, prev, P.fp16, smem + P.x_off[0],
+                                                  row, carry0, carry1);
+                    if (valid) {
+                        if (MODE == 2) {  // colour: the compositing gradients of the three colour outputs
+                            const float4 d4 = P.dout[s];
+                            g = make_float4(d4.x, d4.y, d4.z, 0.f);
+                        } else {          // optical thickness: (dL/dtau_pre, dL/deta_pre) from the colour pass
+                            g = make_float4(prev.x, prev.y, 0.f, 0.f);
+                        }
+                    }
+                }
                 uint8_t *go = smem + P.gout_off;
                 st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
                          tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
@@ -947,7 +1082,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 }
                 // next weights needed: layer l + 1 (or, after the top layer, the first
                 // backward use below it)
-                prefetch(l + 1 < nh ? l + 1 : (uses_dx(nh - 1, d_feat != nullptr) ? nh - 2 : nh - 1), l);
+                prefetch(l + 1 < nh ? l + 1 : (uses_dx(nh - 1, form_dz) ? nh - 2 : nh - 1), l);
                 const uint32_t wb = waddr(l);
                 {  // the accumulator starts at the bias
                     const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + lay.bias_l[l]);
@@ -1035,7 +1170,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 const uint32_t xa = s_base + P.x_off[l];
                 const int Nin = l == 0 ? lay.K0 : kHp;
                 const bool want_dw = l <= P.l_top;
-                const bool want_dx = uses_dx(l, d_feat != nullptr);
+                const bool want_dx = uses_dx(l, form_dz);
                 const int Ndx = l > 0 ? kHp : Fn;
                 if (!want_dw && !want_dx) continue;
                 if (want_dx) {
@@ -1044,7 +1179,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         break;
                     }
                     // next: the layer below if it forms a delta, else the next tile's layer 0
-                    prefetch(l - 1 >= P.l_min && uses_dx(l - 1, d_feat != nullptr) ? l - 1 : 0, l);
+                    prefetch(l - 1 >= P.l_min && uses_dx(l - 1, form_dz) ? l - 1 : 0, l);
                 }
                 const uint32_t wb = waddr(l);
                 if (!run([&] {
@@ -1067,6 +1202,10 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 }
                 if (l > 0) {
                     if (want_dx) mask_epilogue(l);
+                } else if (MODE != 0) {
+                    if (form_dz)
+                        two_decoder_dz<MODE>(md, SD, rec, valid && sl < S_sc, s, carry0, carry1, prev, d_feat,
+                                             tmem + lane_off, ginv, P);
                 } else if (d_feat) {
                     // dL/dz: stage rows in shared memory (X_1's buffer is free now)
                     float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
@@ -1113,9 +1252,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 tc::tmem_wait_ld();
                 if (row < H) {
                     float *dW = dpar + md.w_off[nh];
-                    for (int j = 0; j < 4; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
+                    for (int j = 0; j < md.out; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
                 }
-                if (row < 4) atomicAdd(dpar + md.w_off[nh] + 4 * H + row, s_dbout[row]);
+                if (row < md.out) atomicAdd(dpar + md.w_off[nh] + md.out * H + row, s_dbout[row]);
             }
             for (int l = P.l_min; l <= P.l_top; ++l) {
                 const int in = md.in_l[l];
@@ -1189,7 +1328,8 @@ bool tc_backward_supported(const MlpDims &md) {
 }
 
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
-                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s) {
+                           const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s, int mode,
+                           float4 *aux, const float *w_dD) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcBwdParams P;
     memset(&P, 0, sizeof(P));
@@ -1207,6 +1347,9 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
     P.samples = ws.samples;
     P.counter = ws.counter;
     P.dout = ws.dout;
+    P.aux = aux;
+    P.w_dD = w_dD;
+    P.gmax = ws.counter + kCtrMaxAbsDout;
     for (int pass = 0; pass < n_pass; ++pass) {
         if (pl_min[pass] > 0 && !want_params) continue;  // only the last pass forms dL/dz
         P.l_min = pl_min[pass];
@@ -1215,11 +1358,22 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
         size_t smem;
         if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
         if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
-        if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+        if (mode == 0) {
+            if (cudaFuncSetAttribute(mlp_backward_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SVLF_ERR_CUDA;
+        } else if (mode == 1) {
+            if (cudaFuncSetAttribute(mlp_backward_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SVLF_ERR_CUDA;
+        } else if (cudaFuncSetAttribute(mlp_backward_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem) != cudaSuccess) {
             return SVLF_ERR_CUDA;
-        prof_begin("mlp_backward_tc", s);
-        mlp_backward_tc_kernel<<<num_sms(), 128, smem, s>>>(T, P);
+        }
+        prof_begin(mode == 0 ? "mlp_backward_tc" : mode == 1 ? "two_decoder_ft_bwd_tc" : "two_decoder_fc_bwd_tc", s);
+        if (mode == 0) mlp_backward_tc_kernel<0><<<num_sms(), 128, smem, s>>>(T, P);
+        else if (mode == 1) mlp_backward_tc_kernel<1><<<num_sms(), 128, smem, s>>>(T, P);
+        else mlp_backward_tc_kernel<2><<<num_sms(), 128, smem, s>>>(T, P);
         prof_end(s);
         if (cudaGetLastError() != cudaSuccess) return SVLF_ERR_CUDA;
     }

@@ -148,7 +148,7 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
                  cudaStream_t s);
 int launch_composite(const SceneTable &T, const Workspace &ws, const float bg[3], cudaStream_t s);
 int launch_composite_backward(const SceneTable &T, const Workspace &ws, const float bg[3],
-                              cudaStream_t s);
+                              cudaStream_t s, float *w_dD = nullptr);
 int launch_pack_weights(const svlf_mlp_desc &mlp, const SceneTable &T, const Workspace &ws,
                         cudaStream_t s);
 

@@ -79,7 +79,7 @@ EXPORTS = [
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
     "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_workspace_size_two_decoder",
-    "svlf_render_rays_two_decoder",
+    "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder",
 ]
 
 _lib = None
@@ -122,6 +122,8 @@ def lib():
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
     L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
                                                vp, vp, vp, vp, vp, sz, vp]
+    L.svlf_render_rays_backward_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64,
+                                                        P(RenderOpts), vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.svlf_status_string.argtypes = [i32]
     L.svlf_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -319,6 +321,21 @@ def svlf_render_rays_two_decoder(tree: Octree, z_t: torch.Tensor, z_c: torch.Ten
         tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays), N,
         ctypes.byref(o), _ptr(rgb), _ptr(depth), _ptr(hits), _ptr(t_io), wp, wb, _stream(stream)))
     return rgb, depth, hits, t_io, workspace
+
+
+def svlf_render_rays_backward_two_decoder(tree: Octree, z_t, z_c, params_t, params_c, net: TwoDecoder,
+                                          rays: torch.Tensor, K: int, bg, d_rgb: torch.Tensor, d_depth: torch.Tensor,
+                                          d_z_t=None, d_z_c=None, d_params_t=None, d_params_c=None,
+                                          workspace: torch.Tensor = None, stream=None):
+    """Accumulates the gradients (those passed) of the two-decoder render whose
+    workspace is given."""
+    d = net.desc()
+    o = _opts(K, bg)
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_render_rays_backward_two_decoder", lib().svlf_render_rays_backward_two_decoder(
+        tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays),
+        rays.shape[0], ctypes.byref(o), _ptr(d_rgb), _ptr(d_depth), _ptr(d_z_t), _ptr(d_z_c), _ptr(d_params_t),
+        _ptr(d_params_c), wp, wb, _stream(stream)))
 
 
 def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,

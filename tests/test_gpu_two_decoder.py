@@ -149,3 +149,71 @@ def test_argument_errors():
     with pytest.raises(svlf.SvlfError) as e:
         svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, svlf.TwoDecoder(12, 8, 32, 1, 32, 1), rays, 4)
     assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
+
+
+def _rel(g, r):
+    return float(np.linalg.norm(g - r) / np.linalg.norm(r))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_backward_matches_oracle_adjoint(prec):
+    """Gradients of Z^T, Z^C and both networks through the GPU render + loss +
+    backward against the oracle's adjoint with the same operand rounding.
+    Near-degenerate rays are dropped and the L1 depth term is masked where
+    |D - D*| is within float32 noise (its kink)."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(1009)
+    sc = I.make_scene(rng, 7, 10, 4)
+    tree_o = O.build_octree(sc.leaf_ijk, 7)
+    vt = T2.vertex_table(tree_o)
+    ft, fc = 32, 16
+    dt, dc = T2.dims_t(ft, 64, 1), T2.dims_c(fc, 64, 2)
+    zt = (rng.standard_normal((vt.n_vertices, ft)) * 0.3).astype(np.float32)
+    zc = (rng.standard_normal((vt.n_vertices, fc)) * 0.3).astype(np.float32)
+    pt, pc = _net(rng, dt, 0.3), _net(rng, dc, 0.3)
+    az, el = I.random_view_angles(rng, 40)
+    rays = I.training_rays(np.random.default_rng(2), 40, 200, 10000, az, el)
+    K = 6
+    rays = rays[~O.trace(tree_o, rays, K).degenerate]
+    rgb_t = np.random.default_rng(3).uniform(0, 1, size=(rays.shape[0], 3)).astype(np.float32)
+    depth_t, mask = I.analytic_depth(rays, sc)
+    ref64 = T2.render2(tree_o, vt, zt, zc, pt, pc, dt, dc, rays, K)
+    mask = np.where(np.abs(ref64.depth - depth_t) < 1e-4, 0.0, mask).astype(np.float32)
+    assert (ref64.hits.n > 0).sum() > 1000
+    # GPU
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), 7)
+    tree.build_vertices()
+    net = svlf.TwoDecoder(ft, fc, 64, 1, 64, 2, svlf.PRECISIONS[prec])
+    g = {k: torch.from_numpy(v).cuda() for k, v in dict(zt=zt, zc=zc, pt=pt, pc=pc, rays=rays).items()}
+    rgb, depth, _, _, ws = svlf.svlf_render_rays_two_decoder(tree, g["zt"], g["zc"], g["pt"], g["pc"], net,
+                                                             g["rays"], K)
+    d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    svlf.svlf_loss(rgb, depth, torch.from_numpy(rgb_t).cuda(), torch.from_numpy(depth_t).cuda(),
+                   torch.from_numpy(mask).cuda(), 0.1, d_rgb, d_depth, loss)
+    grads = {k: torch.zeros_like(g[k]) for k in ("zt", "zc", "pt", "pc")}
+    svlf.svlf_render_rays_backward_two_decoder(tree, g["zt"], g["zc"], g["pt"], g["pc"], net, g["rays"], K,
+                                               (0.0, 0.0, 0.0), d_rgb, d_depth, grads["zt"], grads["zc"],
+                                               grads["pt"], grads["pc"], ws)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    gpu = {k: v.cpu().numpy() for k, v in grads.items()}
+    # oracle adjoint with the same rounding, and in FP64
+    res = {}
+    for lowp in (prec, False):
+        r = T2.render2(tree_o, vt, zt, zc, pt, pc, dt, dc, rays, K, lowp=lowp, hits=ref64.hits)
+        res[lowp] = T2.backward2(tree_o, vt, r, zc, pt, pc, dt, dc, rgb_t, depth_t, mask, (0, 0, 0), ft, fc,
+                                 lowp=lowp)
+    names = ["zt", "zc", "pt", "pc"]
+    errs = {n: _rel(gpu[n], res[prec][i]) for i, n in enumerate(names)}
+    errs64 = {n: _rel(gpu[n], res[False][i]) for i, n in enumerate(names)}
+    print(prec, "two-decoder gradients vs emulating oracle", errs, "| vs FP64", errs64)
+    for n in names:
+        assert errs[n] <= 2e-2, (n, errs[n])
+    # every layer of both networks
+    for flat, ref, dims in ((gpu["pt"], res[prec][2], dt), (gpu["pc"], res[prec][3], dc)):
+        off = 0
+        for o, i in dims:
+            for m in (o * i, o):
+                assert _rel(flat[off:off + m], ref[off:off + m]) <= 5e-2
+                off += m
