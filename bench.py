@@ -699,8 +699,8 @@ def run_batched(args, rank, world, local_rank):
 # two-decoder form (Sec. 4.1-4.2): render only
 # ----------------------------------------------------------------------------
 TD_FT, TD_FC, TD_H, TD_NT, TD_NC = 64, 32, 128, 1, 3  # the paper's Sec. 4.5 sizes
-TD_WORKLOAD = ("two-decoder render 4x1600^2: depth-9 octree over 64 spheres + 32 box shells, vertex features "
-               "Z^T 64 + Z^C 32 fp32, F^T 134->128->2, F^C 38->3x128->3, K=8")
+TD_WORKLOAD = ("two-decoder render 4x1600^2 + train 2^18 rays (100 views of 800^2): depth-9 octree over 64 spheres + "
+               "32 box shells, vertex features Z^T 64 + Z^C 32 fp32, F^T 134->128->2, F^C 38->3x128->3, K=8")
 
 
 def td_flops_per_sample():
@@ -745,9 +745,56 @@ def run_twodec(args, rank, world, local_rank):
     rgb = torch.empty((N, 3), device=dev)
     depth = torch.empty((N,), device=dev)
     stream = torch.cuda.current_stream()
+    # training batch: 2^18 rays from 100 views of 800^2; targets from a teacher with other
+    # weights (colour) and the analytic surface depth
+    trng = np.random.default_rng(SCENE_SEED + 1 + 7919 * rank)
+    taz, tel = I.random_view_angles(trng, TRAIN_VIEWS)
+    trays_h = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel)
+    dt_h, mask_h = I.analytic_depth(trays_h, scene)
+    trays = torch.from_numpy(trays_h).to(dev)
+    NT = trays.shape[0]
+    teach_rng = np.random.default_rng(TEACHER_SEED)
+    tpt = torch.from_numpy(I.make_mlp_dims(teach_rng, d_t, 0.1)).to(dev)
+    tpc = torch.from_numpy(I.make_mlp_dims(teach_rng, d_c, 0.1)).to(dev)
+    ws_t = torch.empty(svlf.workspace_size_two_decoder(net, NT, K_HITS) + 256, dtype=torch.uint8, device=dev)
+    rgb_t, _, _, _, _ = svlf.svlf_render_rays_two_decoder(tree, zt, zc, tpt, tpc, net, trays, K_HITS, workspace=ws_t)
+    depth_t = torch.from_numpy(dt_h).to(dev)
+    mask = torch.from_numpy(mask_h).to(dev)
+    trgb = torch.empty((NT, 3), device=dev)
+    tdepth = torch.empty((NT,), device=dev)
+    d_rgb, d_depth = torch.empty_like(trgb), torch.empty_like(tdepth)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    opt = {k: (v, torch.zeros_like(v), torch.zeros_like(v), torch.zeros_like(v))
+           for k, v in (("zt", zt), ("zc", zc), ("pt", pt), ("pc", pc))}  # param, grad, m, v
+    step_no = [0]
 
-    def step():
+    def render_phase():
         svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws, out=(rgb, depth))
+
+    def train_phase():
+        step_no[0] += 1
+        for _, g, _, _ in opt.values():
+            g.zero_()
+        loss.zero_()
+        svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
+        svlf.svlf_loss(trgb, tdepth, rgb_t, depth_t, mask, DEPTH_WEIGHT, d_rgb, d_depth, loss)
+        svlf.svlf_render_rays_backward_two_decoder(tree, zt, zc, pt, pc, net, trays, K_HITS, (0.0, 0.0, 0.0),
+                                                   d_rgb, d_depth, opt["zt"][1], opt["zc"][1], opt["pt"][1],
+                                                   opt["pc"][1], ws_t)
+        for p_, g, m, v in opt.values():
+            svlf.svlf_adam_step(p_, g, m, v, step_no[0], lr=LR)
+
+    marks = []
+
+    def step(record=False):
+        if record:
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(stream)
+        render_phase()
+        if record:
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(stream)
+        train_phase()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -760,7 +807,7 @@ def run_twodec(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(record=True)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -768,11 +815,16 @@ def run_twodec(args, rank, world, local_rank):
     svlf.svlf_profile_enable(False)
     status = svlf.svlf_get_device_status()
     ms = e0.elapsed_time(e1)
-    value = N * world * args.steps / (ms / 1e3)
+    render_ms = sum(marks[2 * i].elapsed_time(marks[2 * i + 1]) for i in range(args.steps))
+    train_ms = ms - render_ms
+    value = (N + NT) * world * args.steps / (ms / 1e3)
     # samples: count the hits of one render through the hit lists
     _, _, hits, _, _ = svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws,
                                                           want_hits=True)
     S = int((hits >= 0).sum().item())
+    _, _, thits, _, _ = svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, trays, K_HITS, workspace=ws_t,
+                                                           want_hits=True)
+    ST = int((thits >= 0).sum().item())
     peaks, peak_src = measured_peaks()
     total = sum(v[1] for v in kstats.values())
     per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / total, 4)}
@@ -782,22 +834,33 @@ def run_twodec(args, rank, world, local_rank):
     avg_s = kms / launches / 1e3
     bft, bfc = td_bytes_per_sample()
     roof = None
-    if dom in ("two_decoder_ft_tc", "two_decoder_fc_tc"):
-        work = S * (bft if dom == "two_decoder_ft_tc" else bfc)
+    fft, ffc = td_flops_per_sample()
+    if dom in ("two_decoder_ft_bwd_tc", "two_decoder_fc_bwd_tc"):
+        work = ST * 3.0 * (fft if dom == "two_decoder_ft_bwd_tc" else ffc)
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        roof = {"kernel": dom, "bound": "tensor", "achieved": round(work / avg_s / 1e12, 3), "peak": peak,
+                "peak_source": f"{peak_src} (sustained)", "unit": "TFLOP/s",
+                "frac": round(work / avg_s / 1e12 / peak, 4), "traffic": None,
+                "avg_launch_ms": round(kms / launches, 4)}
+    elif dom in ("two_decoder_ft_tc", "two_decoder_fc_tc"):
+        # one launch renders, one trains: average over both
+        work = (S + ST) / 2.0 * (bft if dom == "two_decoder_ft_tc" else bfc)
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],
                 "peak_source": f"{peak_src} (copy)", "unit": "GB/s",
                 "frac": round(work / avg_s / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
                 "avg_launch_ms": round(kms / launches, 4),
-                "work": f"{S} samples x {bft if dom == 'two_decoder_ft_tc' else bfc} B (vertex rows not deduplicated)"}
+                "work": f"({S} + {ST}) / 2 samples x {bft if dom == 'two_decoder_ft_tc' else bfc} B per launch "
+                        f"(vertex rows not deduplicated)"}
     elif dom == "trace":
-        work = (N * 32.0 + S * 16.0)
+        work = ((N + NT) * 32.0 + (S + ST) * 16.0) / 2.0
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],
                 "peak_source": f"{peak_src} (copy)", "unit": "GB/s",
                 "frac": round(work / avg_s / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
                 "avg_launch_ms": round(kms / launches, 4)}
-    fft, ffc = td_flops_per_sample()
-    tensor = {k: round(S * f / (kstats[k][1] / kstats[k][0] / 1e3) / 1e12, 2)
+    tensor = {k: round((S + ST) / 2.0 * f / (kstats[k][1] / kstats[k][0] / 1e3) / 1e12, 2)
               for k, f in (("two_decoder_ft_tc", fft), ("two_decoder_fc_tc", ffc)) if k in kstats}
+    tensor.update({k: round(ST * 3.0 * f / (kstats[k][1] / kstats[k][0] / 1e3) / 1e12, 2)
+                   for k, f in (("two_decoder_ft_bwd_tc", fft), ("two_decoder_fc_bwd_tc", ffc)) if k in kstats})
     # end to end: rays from pinned host memory, image back
     e2e = None
     if not args.no_e2e:
@@ -805,11 +868,16 @@ def run_twodec(args, rank, world, local_rank):
         h_rgb = torch.empty((N, 3)).pin_memory()
         h_depth = torch.empty((N,)).pin_memory()
 
+        h_trays = torch.from_numpy(trays_h).pin_memory()
+        h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+
         def e2e_step():
             rays.copy_(h_rays, non_blocking=True)
+            trays.copy_(h_trays, non_blocking=True)
             step()
             h_rgb.copy_(rgb, non_blocking=True)
             h_depth.copy_(depth, non_blocking=True)
+            h_loss.copy_(loss, non_blocking=True)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -819,8 +887,9 @@ def run_twodec(args, rank, world, local_rank):
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
-        e2e = {"value": N * world * args.steps / (a.elapsed_time(b) / 1e3), "unit": "rays/s",
-               "h2d_bytes_per_step": int(h_rays.numel() * 4), "d2h_bytes_per_step": int((h_rgb.numel() + N) * 4)}
+        e2e = {"value": (N + NT) * world * args.steps / (a.elapsed_time(b) / 1e3), "unit": "rays/s",
+               "h2d_bytes_per_step": int((h_rays.numel() + h_trays.numel()) * 4),
+               "d2h_bytes_per_step": int((h_rgb.numel() + N) * 4 + 8)}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O
@@ -831,19 +900,41 @@ def run_twodec(args, rank, world, local_rank):
         zt_h, zc_h = zt.cpu().numpy(), zc.cpu().numpy()
         pt_h, pc_h = pt.cpu().numpy(), pc.cpu().numpy()
         dt_o, dc_o = T2.dims_t(TD_FT, TD_H, TD_NT), T2.dims_c(TD_FC, TD_H, TD_NC)
-        T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, sample[:256], K_HITS)
+        tsel = np.random.default_rng(6).choice(NT, 128, replace=False)
+        tr, dts, msk = trays_h[tsel], dt_h[tsel].astype(np.float64), mask_h[tsel].astype(np.float64)
+        tgt = rgb_t.cpu().numpy()[tsel].astype(np.float64)
+        adam_state = {k: [v.astype(np.float64), np.zeros(v.size), np.zeros(v.size)]
+                      for k, v in (("zt", zt_h.reshape(-1)), ("zc", zc_h.reshape(-1)), ("pt", pt_h), ("pc", pc_h))}
+
+        def oracle_step(t):
+            T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, sample, K_HITS)
+            r = T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, tr, K_HITS)
+            gzt, gzc, gpt, gpc, _, _ = T2.backward2(tree_o, vt, r, zc_h, pt_h, pc_h, dt_o, dc_o, tgt, dts, msk,
+                                                    (0, 0, 0), TD_FT, TD_FC)
+            for k, g_ in (("zt", gzt.reshape(-1)), ("zc", gzc.reshape(-1)), ("pt", gpt), ("pc", gpc)):
+                st = adam_state[k]
+                st[0], st[1], st[2] = O.adam(st[0], g_, st[1], st[2], t, lr=LR)
+
+        oracle_step(1)
         t0 = time.perf_counter()
-        T2.render2(tree_o, vt, zt_h, zc_h, pt_h, pc_h, dt_o, dc_o, sample, K_HITS)
+        oracle_step(2)
         dt = time.perf_counter() - t0
-        cpu = {"value": round(4096 / dt, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
-               "sample": "4096 random rays of the same views through the FP64 two-decoder oracle (vertex table "
-                         "built outside the timed region)"}
+        cpu = {"value": round((4096 + 128) / dt, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": "per step: 4096 random render rays of the same views + a training step on 128 random "
+                         "training rays (adjoint through both decoders) with Adam over all "
+                         f"{sum(v[0].size for v in adam_state.values())} parameters, FP64 two-decoder oracle; "
+                         "1 step timed after 1 untimed (vertex table built outside the timed region)"}
     return {
-        "metric": "rays/s: two-decoder render 4x1600^2 (vertex features, F^T + F^C)",
+        "metric": "rays/s: two-decoder render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each",
         "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
+        "train_rays_per_s": round(NT * args.steps / (train_ms / 1e3), 1),
+        "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
         "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic (seeded sphere/box-shell scene, pinhole views; stands in for RTMV)",
-        "config": {"workload": TD_WORKLOAD, "render_rays": N, "K": K_HITS, "vertices": n_vert, "samples": S,
+        "config": {"workload": TD_WORKLOAD, "render_rays": N, "train_rays": NT, "K": K_HITS, "vertices": n_vert,
+                   "render_samples": S, "train_samples": ST,
+                   "parameters": int(sum(v[0].numel() for v in opt.values())),
                    "l2": f"inputs larger than L2 (vertex features {n_vert * (TD_FT + TD_FC) * 4 / 1e6:.0f} MB)"},
         "e2e": e2e, "gpu_launches": int(sum(v[0] for v in kstats.values())), "kernels": per_kernel,
         "tensor_tflops": tensor, "roofline": roof, "clocks": clk, "device_status": status, "cpu_baseline": cpu,
