@@ -134,21 +134,32 @@ class Render2:
     dirs: np.ndarray  # ray direction of every sample
 
 
-def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, params_t: np.ndarray,
-            params_c: np.ndarray, d_t, d_c, rays: np.ndarray, K: int, bg=(0.0, 0.0, 0.0), lowp=False,
-            hits: Optional[O.Hits] = None) -> Render2:
-    """Two-decoder render of every ray. lowp = "bf16" / "fp16" rounds each
-    layer's inputs and weights to that format (products and sums in float64)."""
-    rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
-    N = rays.shape[0]
-    if hits is None:
-        hits = O.trace(tree, rays, K)
-    ray_of, slot = np.nonzero(hits.rank >= 0)
-    rank = hits.rank[ray_of, slot]
-    o = rays[ray_of, :3].astype(np.float64)
-    d = rays[ray_of, 3:].astype(np.float64)
-    t_in = hits.t_in[ray_of, slot]
-    t_out = hits.t_out[ray_of, slot]
+@dataclass
+class Eval2:
+    """The two decoders on a list of (ray, voxel, segment) samples."""
+    rank: np.ndarray
+    t_in: np.ndarray
+    t_out: np.ndarray
+    dirs: np.ndarray
+    x1: np.ndarray
+    x2: np.ndarray
+    tau: np.ndarray
+    eta: np.ndarray
+    x_s: np.ndarray
+    t_s: np.ndarray
+    colour: np.ndarray
+    h_t: np.ndarray
+    h_c: np.ndarray
+    xs_t: list
+    pres_t: list
+    xs_c: list
+    pres_c: list
+
+
+def eval_samples(tree: O.Octree, vt: VertexTable, z_t, z_c, params_t, params_c, d_t, d_c, o, d, rank, t_in,
+                 t_out, lowp=False) -> Eval2:
+    """Eq. 1-2 on samples: ray origin o and direction d (S x 3), hit leaf rank,
+    segment [t_in, t_out]."""
     c, R = O.voxel_centre_radius(tree.leaf_ijk()[rank], tree.depth)
     p1, p2 = O.sphere_params(o, d, c, R)
     x1 = o + t_in[:, None] * d
@@ -162,9 +173,27 @@ def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, p
     h_c = np.concatenate([psi(x_s, rank, tree, vt, z_c), p1, p2], axis=1)
     xs_c, pres_c = O.mlp_forward(h_c, O.split_params(params_c, d_c), bf16=lowp)
     colour = O.sigmoid(pres_c[-1])
-    rgb, depth, T, w = O.composite(N, K, ray_of, slot, colour, tau, t_s, bg)
-    return Render2(rgb, depth, hits, ray_of, slot, tau, eta, colour, t_s, x1, x2, x_s, h_t, h_c, w, T, rank,
-                   t_in, t_out, xs_t, pres_t, xs_c, pres_c, d)
+    return Eval2(rank, t_in, t_out, d, x1, x2, tau, eta, x_s, t_s, colour, h_t, h_c, xs_t, pres_t, xs_c, pres_c)
+
+
+def render2(tree: O.Octree, vt: VertexTable, z_t: np.ndarray, z_c: np.ndarray, params_t: np.ndarray,
+            params_c: np.ndarray, d_t, d_c, rays: np.ndarray, K: int, bg=(0.0, 0.0, 0.0), lowp=False,
+            hits: Optional[O.Hits] = None) -> Render2:
+    """Two-decoder render of every ray. lowp = "bf16" / "fp16" rounds each
+    layer's inputs and weights to that format (products and sums in float64)."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
+    N = rays.shape[0]
+    if hits is None:
+        hits = O.trace(tree, rays, K)
+    ray_of, slot = np.nonzero(hits.rank >= 0)
+    rank = hits.rank[ray_of, slot]
+    o = rays[ray_of, :3].astype(np.float64)
+    d = rays[ray_of, 3:].astype(np.float64)
+    e = eval_samples(tree, vt, z_t, z_c, params_t, params_c, d_t, d_c, o, d, rank, hits.t_in[ray_of, slot],
+                     hits.t_out[ray_of, slot], lowp)
+    rgb, depth, T, w = O.composite(N, K, ray_of, slot, e.colour, e.tau, e.t_s, bg)
+    return Render2(rgb, depth, hits, ray_of, slot, e.tau, e.eta, e.colour, e.t_s, e.x1, e.x2, e.x_s, e.h_t, e.h_c,
+                   w, T, rank, e.t_in, e.t_out, e.xs_t, e.pres_t, e.xs_c, e.pres_c, d)
 
 
 # ----------------------------------------------------------------------------
@@ -204,10 +233,40 @@ def _mlp_backward(delta, xs, pres, layers, lowp):
     return np.concatenate([np.concatenate([g[0].reshape(-1), g[1]]) for g in grads]), dx
 
 
+def adjoint_core(tree: O.Octree, vt: VertexTable, e, z_c, params_t, params_c, d_t, d_c, dcol, dtau, dts,
+                 deta_direct, feat_t: int, feat_c: int, lowp=False):
+    """Adjoint of the two decoders on samples `e` (Eval2 or Render2) given the
+    loss's gradients w.r.t. every sample's colour (S x 3), tau, depth
+    parameter t_s and (directly) eta. Returns (dZ^T, dZ^C, dparams_t, dparams_c)."""
+    ijk = tree.leaf_ijk()[e.rank]
+    dparams_c, dhc = _mlp_backward(dcol * e.colour * (1.0 - e.colour), e.xs_c, e.pres_c,
+                                   O.split_params(params_c, d_c), lowp)
+    dpsi_c = dhc[:, :feat_c]
+    wgt_s = trilinear_weights(e.x_s, ijk, tree.depth)
+    dzc = np.zeros((vt.n_vertices, feat_c))
+    np.add.at(dzc, vt.leaf_vertices[e.rank].reshape(-1),
+              (wgt_s[:, :, None] * dpsi_c[:, None, :]).reshape(-1, feat_c))
+    # through x_s = o + t_s d: d psi / d x_s from the corner weights' gradients
+    gw = trilinear_weight_gradients(e.x_s, ijk, tree.depth)                  # (S, 8, 3)
+    zdot = np.einsum("svf,sf->sv", np.asarray(z_c, np.float64)[vt.leaf_vertices[e.rank]], dpsi_c)
+    dxs = np.einsum("sv,sva->sa", zdot, gw)
+    dts = dts + np.einsum("sa,sa->s", dxs, e.dirs)  # x_s = o + t_s d
+    deta = dts * (e.t_in - e.t_out) + deta_direct  # t_s = eta t_in + (1 - eta) t_out
+    delta_t = np.stack([dtau * (e.pres_t[-1][:, 0] > 0), deta * e.eta * (1.0 - e.eta)], axis=1)
+    dparams_t, dht = _mlp_backward(delta_t, e.xs_t, e.pres_t, O.split_params(params_t, d_t), lowp)
+    w1 = trilinear_weights(e.x1, ijk, tree.depth)
+    w2 = trilinear_weights(e.x2, ijk, tree.depth)
+    contrib = w1[:, :, None] * dht[:, None, :feat_t] + w2[:, :, None] * dht[:, None, feat_t:2 * feat_t]
+    dzt = np.zeros((vt.n_vertices, feat_t))
+    np.add.at(dzt, vt.leaf_vertices[e.rank].reshape(-1), contrib.reshape(-1, feat_t))
+    return dzt, dzc, dparams_t, dparams_c
+
+
 def backward2(tree: O.Octree, vt: VertexTable, r: Render2, z_c: np.ndarray, params_t, params_c, d_t, d_c,
-              rgb_t, depth_t, mask, bg, feat_t: int, feat_c: int, lowp=False):
+              rgb_t, depth_t, mask, bg, feat_t: int, feat_c: int, lowp=False, deta_direct=None):
     """Gradient of loss(render2(...)) (the loss of the single-network form:
-    mean over rays of the squared colour error + 0.1 masked |D - D*|).
+    mean over rays of the squared colour error + 0.1 masked |D - D*|), plus
+    an optional direct gradient w.r.t. each sample's eta.
     Returns (dZ^T (n_vertices x feat_t), dZ^C, dparams_t, dparams_c, dC, dD)."""
     N, K = r.hits.rank.shape
     bg = np.asarray(bg, dtype=np.float64)
@@ -232,30 +291,10 @@ def backward2(tree: O.Octree, vt: VertexTable, r: Render2, z_c: np.ndarray, para
     dcol = (r.w[:, :, None] * dC[:, None, :])[r.ray_of, r.slot]
     dtau = (np.sum(dC[:, None, :] * (Tn[:, :, None] * col_k - S), axis=2) + dD[:, None] * (Tn * ts_k - U))[r.ray_of, r.slot]
     dts = (r.w * dD[:, None])[r.ray_of, r.slot]  # D = sum_i w_i t_s,i
-    # F^C
-    ijk = tree.leaf_ijk()[r.rank]
-    dparams_c, dhc = _mlp_backward(dcol * r.colour * (1.0 - r.colour), r.xs_c, r.pres_c,
-                                   O.split_params(params_c, d_c), lowp)
-    dpsi_c = dhc[:, :feat_c]
-    wgt_s = trilinear_weights(r.x_s, ijk, tree.depth)
-    dzc = np.zeros((vt.n_vertices, feat_c))
-    np.add.at(dzc, vt.leaf_vertices[r.rank].reshape(-1),
-              (wgt_s[:, :, None] * dpsi_c[:, None, :]).reshape(-1, feat_c))
-    # through x_s = o + t_s d: d psi / d x_s from the corner weights' gradients
-    gw = trilinear_weight_gradients(r.x_s, ijk, tree.depth)                  # (S, 8, 3)
-    zdot = np.einsum("svf,sf->sv", np.asarray(z_c, np.float64)[vt.leaf_vertices[r.rank]], dpsi_c)
-    dxs = np.einsum("sv,sva->sa", zdot, gw)
-    dts = dts + np.einsum("sa,sa->s", dxs, r.dirs)  # x_s = o + t_s d
-    deta = dts * (r.t_in - r.t_out)                # t_s = eta t_in + (1 - eta) t_out
-    # F^T
-    delta_t = np.stack([dtau * (r.pres_t[-1][:, 0] > 0), deta * r.eta * (1.0 - r.eta)], axis=1)
-    dparams_t, dht = _mlp_backward(delta_t, r.xs_t, r.pres_t, O.split_params(params_t, d_t), lowp)
-    w1 = trilinear_weights(r.x1, ijk, tree.depth)
-    w2 = trilinear_weights(r.x2, ijk, tree.depth)
-    contrib = w1[:, :, None] * dht[:, None, :feat_t] + w2[:, :, None] * dht[:, None, feat_t:2 * feat_t]
-    dzt = np.zeros((vt.n_vertices, feat_t))
-    np.add.at(dzt, vt.leaf_vertices[r.rank].reshape(-1), contrib.reshape(-1, feat_t))
-    return dzt, dzc, dparams_t, dparams_c, dC, dD
+    dd = np.zeros(r.rank.shape[0]) if deta_direct is None else deta_direct
+    dzt, dzc, dpt, dpc = adjoint_core(tree, vt, r, z_c, params_t, params_c, d_t, d_c, dcol, dtau, dts, dd,
+                                      feat_t, feat_c, lowp)
+    return dzt, dzc, dpt, dpc, dC, dD
 
 
 def kink_pattern2(r: Render2, depth_t, mask):
@@ -264,3 +303,96 @@ def kink_pattern2(r: Render2, depth_t, mask):
     parts.append(r.pres_t[-1][:, 0] > 0)
     parts.append(np.sign(r.depth - depth_t) * (mask > 0))
     return parts
+
+
+# ----------------------------------------------------------------------------
+# Staged training (Sec. 4.4, Eq. 4)
+# ----------------------------------------------------------------------------
+def eta_target(t_in, t_out, t_star):
+    """Within-voxel depth of the true surface point o + t* d on the segment
+    [t_in, t_out]: x* = eta x1 + (1 - eta) x2 (clamped to [0, 1])."""
+    return np.clip((t_out - t_star) / (t_out - t_in), 0.0, 1.0)
+
+
+@dataclass
+class SurfaceSamples:
+    ray: np.ndarray
+    rank: np.ndarray
+    t_in: np.ndarray
+    t_out: np.ndarray
+    eta_gt: np.ndarray
+
+
+def surface_samples(tree: O.Octree, rays: np.ndarray, depth_t: np.ndarray, mask: np.ndarray) -> SurfaceSamples:
+    """Stage 1 ("voxel training"): for each ray with a known surface depth D*,
+    the voxel containing the surface point x* = o + D* d (floor of x* 2^L),
+    kept when it is a leaf and the ray's segment through it has positive
+    length."""
+    rays = np.asarray(rays, dtype=np.float32).reshape(-1, 6)
+    n = 1 << tree.depth
+    sel = np.nonzero((np.asarray(mask) > 0) & np.isfinite(depth_t))[0]
+    o = rays[sel, :3].astype(np.float64)
+    d = rays[sel, 3:].astype(np.float64)
+    t_star = np.asarray(depth_t, np.float64)[sel]
+    xs = o + t_star[:, None] * d
+    ijk = np.clip(np.floor(xs * n).astype(np.int64), 0, n - 1)
+    leaves = tree.leaf_ijk()
+    lookup = {tuple(v): i for i, v in enumerate(leaves)}
+    rank = np.array([lookup.get(tuple(v), -1) for v in ijk], dtype=np.int64)
+    h = 1.0 / n
+    lo = ijk * h
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo - o) / d
+        tb = (lo + h - o) / d
+    ta = np.where(d == 0, -np.inf, ta)
+    tb = np.where(d == 0, np.inf, tb)
+    t_in = np.maximum(np.max(np.minimum(ta, tb), axis=1), 0.0)
+    t_out = np.min(np.maximum(ta, tb), axis=1)
+    keep = (rank >= 0) & (t_out > t_in)
+    return SurfaceSamples(sel[keep], rank[keep], t_in[keep], t_out[keep],
+                          eta_target(t_in[keep], t_out[keep], t_star[keep]))
+
+
+def surface_loss(tree, vt, z_t, z_c, params_t, params_c, d_t, d_c, rays, rgb_t, depth_t, mask, lam_eta, lam_tau,
+                 feat_t, feat_c, lowp=False, with_grad=True):
+    """Eq. 4 on the surface voxels of a batch of N rays, divided by N:
+    (1/N) sum_v |c_v - c*|^2 + lam_eta (eta_v - eta*)^2 + lam_tau exp(-tau_v)^2.
+    Returns (loss, samples, eval, grads or None)."""
+    rays = np.asarray(rays, dtype=np.float32).reshape(-1, 6)
+    N = rays.shape[0]
+    ss = surface_samples(tree, rays, depth_t, mask)
+    o = rays[ss.ray, :3].astype(np.float64)
+    d = rays[ss.ray, 3:].astype(np.float64)
+    e = eval_samples(tree, vt, z_t, z_c, params_t, params_c, d_t, d_c, o, d, ss.rank, ss.t_in, ss.t_out, lowp)
+    ct = np.asarray(rgb_t, np.float64)[ss.ray]
+    et = np.exp(-e.tau)
+    L = float(np.sum(np.sum((e.colour - ct) ** 2, axis=1) + lam_eta * (e.eta - ss.eta_gt) ** 2
+                     + lam_tau * et * et) / N)
+    if not with_grad:
+        return L, ss, e, None
+    dcol = 2.0 * (e.colour - ct) / N
+    dtau = -2.0 * lam_tau * et * et / N
+    deta = 2.0 * lam_eta * (e.eta - ss.eta_gt) / N
+    grads = adjoint_core(tree, vt, e, z_c, params_t, params_c, d_t, d_c, dcol, dtau, np.zeros(ss.ray.size), deta,
+                         feat_t, feat_c, lowp)
+    return L, ss, e, grads
+
+
+def eta_term(r: Render2, depth_t, mask, lam_eta):
+    """Stages 2-3: lam_eta (eta_v - eta*)^2 / N over each ray's surface voxel
+    among its hits (the hit whose segment contains D*). Returns (loss term,
+    per-sample direct dL/deta)."""
+    N = r.hits.rank.shape[0]
+    t_star = np.asarray(depth_t, np.float64)[r.ray_of]
+    on = (np.asarray(mask)[r.ray_of] > 0) & (r.t_in <= t_star) & (t_star <= r.t_out) & (r.t_out > r.t_in)
+    # one surface voxel per ray: the first hit containing D*
+    first = np.zeros_like(on)
+    seen = set()
+    for i in np.nonzero(on)[0]:
+        if r.ray_of[i] not in seen:
+            seen.add(r.ray_of[i])
+            first[i] = True
+    eg = eta_target(r.t_in, r.t_out, t_star)
+    L = float(lam_eta * np.sum(((r.eta - eg) ** 2)[first]) / N)
+    deta = np.where(first, 2.0 * lam_eta * (r.eta - eg) / N, 0.0)
+    return L, deta

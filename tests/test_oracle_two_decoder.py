@@ -279,3 +279,158 @@ def test_two_decoder_adjoint_matches_central_differences(small):
     assert np.linalg.norm(ad - fd) / np.linalg.norm(fd) <= 1e-5
     # eta carries gradient: its output bias derivative is not negligible
     assert abs(dpt[n_t - 1]) > 1e-3 * np.abs(dpt).max()
+
+
+# ---------------------------------------------------------------- staged training (Sec. 4.4, Eq. 4)
+def test_surface_voxel_is_a_hit_of_the_ray(small):
+    """The stage-1 voxel (the leaf containing o + D* d) is one of the ray's
+    hits in the brute-force list, with the same segment; eta* is 1 at the
+    entry and 0 at the exit."""
+    sc, tree, vt, rays = small
+    depth_t, mask = I.analytic_depth(rays, sc)
+    ss = T2.surface_samples(tree, rays, depth_t, mask)
+    assert ss.ray.size > 0.9 * (mask > 0).sum()
+    brute = O.trace(tree, rays[ss.ray], 64, mode="brute")
+    for i in range(ss.ray.size):
+        j = np.nonzero(brute.rank[i] == ss.rank[i])[0]
+        assert j.size == 1
+        assert abs(brute.t_in[i, j[0]] - ss.t_in[i]) < 1e-12 and abs(brute.t_out[i, j[0]] - ss.t_out[i]) < 1e-12
+    assert np.all((ss.eta_gt >= 0) & (ss.eta_gt <= 1))
+    np.testing.assert_allclose(T2.eta_target(ss.t_in, ss.t_out, ss.t_in), 1.0)
+    np.testing.assert_allclose(T2.eta_target(ss.t_in, ss.t_out, ss.t_out), 0.0, atol=1e-15)
+
+
+def test_surface_loss_constant_networks_closed_form(small):
+    sc, tree, vt, rays = small
+    depth_t, mask = I.analytic_depth(rays, sc)
+    rng = np.random.default_rng(31)
+    rgb_t = rng.uniform(0, 1, size=(rays.shape[0], 3))
+    dt, dc = T2.dims_t(8, 32, 1), T2.dims_c(8, 32, 2)
+    b_tau, b_eta, b_c = 0.6, -0.3, np.array([0.2, -0.5, 1.1])
+    pt = _zero_net(dt, [b_tau, b_eta])
+    pc = _zero_net(dc, b_c)
+    zt = rng.standard_normal((vt.n_vertices, 8))
+    zc = rng.standard_normal((vt.n_vertices, 8))
+    lam_eta, lam_tau = 0.7, 0.3
+    L, ss, _, _ = T2.surface_loss(tree, vt, zt, zc, pt, pc, dt, dc, rays, rgb_t, depth_t, mask, lam_eta, lam_tau,
+                                  8, 8, with_grad=False)
+    c = 1.0 / (1.0 + np.exp(-b_c))
+    eta = 1.0 / (1.0 + np.exp(-b_eta))
+    brute = O.trace(tree, rays[ss.ray], 64, mode="brute")
+    t_in = np.array([brute.t_in[i, np.nonzero(brute.rank[i] == ss.rank[i])[0][0]] for i in range(ss.ray.size)])
+    t_out = np.array([brute.t_out[i, np.nonzero(brute.rank[i] == ss.rank[i])[0][0]] for i in range(ss.ray.size)])
+    eg = np.clip((t_out - depth_t[ss.ray]) / (t_out - t_in), 0, 1)
+    expect = (np.sum((c[None, :] - rgb_t[ss.ray]) ** 2) + lam_eta * np.sum((eta - eg) ** 2)
+              + lam_tau * ss.ray.size * np.exp(-2.0 * b_tau)) / rays.shape[0]
+    assert abs(L - expect) <= 1e-12 * max(1.0, abs(expect))
+
+
+def _fd_check(loss_fn, grads, params, rng, kinds, n=48, h=1e-3):
+    fd, ad, flips = [], [], 0
+    L0, pat0 = loss_fn(params)
+    k = 0
+    while len(fd) < n:
+        kind = kinds[k % len(kinds)]
+        k += 1
+        a = params[kind]
+        idx = tuple(rng.integers(s) for s in a.shape)
+        vals, ok = [], True
+        for sgn in (+1, -1):
+            p2 = {kk: v.copy() for kk, v in params.items()}
+            p2[kind][idx] += sgn * h
+            Ls, pat = loss_fn(p2)
+            ok &= O.same_pattern(pat, pat0)
+            vals.append(Ls)
+        if not ok:
+            flips += 1
+            continue
+        fd.append((vals[0] - vals[1]) / (2 * h))
+        ad.append(grads[kind][idx])
+    fd, ad = np.array(fd), np.array(ad)
+    scale = np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+    return np.abs(ad - fd) / scale, fd, ad
+
+
+def test_surface_loss_adjoint_matches_central_differences(small):
+    """Eq. 4's adjoint (colour, tau and eta terms; eta also through x_s)."""
+    sc, tree, vt, rays = small
+    depth_t, mask = I.analytic_depth(rays, sc)
+    rng = np.random.default_rng(41)
+    rgb_t = rng.uniform(0, 1, size=(rays.shape[0], 3))
+    ft, fc = 8, 8
+    dt, dc = T2.dims_t(ft, 32, 1), T2.dims_c(fc, 32, 2)
+
+    def rand_net(dims):
+        return np.concatenate([np.concatenate([rng.standard_normal(o * i) * np.sqrt(2.0 / i),
+                                               rng.standard_normal(o) * 0.3]) for o, i in dims])
+    P = {"zt": rng.standard_normal((vt.n_vertices, ft)) * 0.5, "zc": rng.standard_normal((vt.n_vertices, fc)) * 0.5,
+         "pt": rand_net(dt), "pc": rand_net(dc)}
+    lam = (0.8, 0.5)
+
+    def loss_fn(p):
+        L, ss, e, _ = T2.surface_loss(tree, vt, p["zt"], p["zc"], p["pt"], p["pc"], dt, dc, rays, rgb_t, depth_t,
+                                      mask, lam[0], lam[1], ft, fc, with_grad=False)
+        return L, [(x > 0) for x in e.pres_t[:-1]] + [(x > 0) for x in e.pres_c[:-1]] + [e.pres_t[-1][:, 0] > 0]
+    L, ss, e, (gzt, gzc, gpt, gpc) = T2.surface_loss(tree, vt, P["zt"], P["zc"], P["pt"], P["pc"], dt, dc, rays,
+                                                     rgb_t, depth_t, mask, lam[0], lam[1], ft, fc)
+    G = {"zt": gzt, "zc": gzc, "pt": gpt, "pc": gpc}
+    # perturb only vertices of surface voxels (others have zero gradient and zero FD)
+    verts = np.unique(vt.leaf_vertices[ss.rank])
+    sub = {"zt": P["zt"], "zc": P["zc"], "pt": P["pt"], "pc": P["pc"]}
+    rel, fd, ad = _fd_check(loss_fn, G, sub, np.random.default_rng(5), ["pt", "pc", "pt", "pc"])
+    assert rel.max() <= 1e-4, rel.max()
+    # vertex features of surface voxels
+    fd2, ad2 = [], []
+    for i in range(24):
+        kind = "zt" if i % 2 == 0 else "zc"
+        v = verts[(i * 7919) % verts.size]
+        f = i % (ft if kind == "zt" else fc)
+        vals = []
+        for sgn in (+1, -1):
+            p2 = {kk: vv.copy() for kk, vv in P.items()}
+            p2[kind][v, f] += sgn * 1e-3
+            vals.append(loss_fn(p2)[0])
+        fd2.append((vals[0] - vals[1]) / 2e-3)
+        ad2.append(G[kind][v, f])
+    fd2, ad2 = np.array(fd2), np.array(ad2)
+    assert np.abs(ad2 - fd2).max() <= 1e-4 * max(np.abs(fd2).max(), 1e-12) + 1e-9
+
+
+def test_volume_stage_eta_term_adjoint(small):
+    """Stages 2-3: the composited loss plus lam_eta (eta_v - eta*)^2 on each
+    ray's surface voxel among its hits; the eta term's direct gradient flows
+    through the same adjoint."""
+    sc, tree, vt, rays = small
+    depth_t, mask = I.analytic_depth(rays, sc)
+    depth_t, mask = depth_t.astype(np.float64), mask.astype(np.float64)
+    rng = np.random.default_rng(51)
+    rgb_t = rng.uniform(0, 1, size=(rays.shape[0], 3))
+    ft, fc = 8, 8
+    dt, dc = T2.dims_t(ft, 32, 1), T2.dims_c(fc, 32, 2)
+
+    def rand_net(dims):
+        return np.concatenate([np.concatenate([rng.standard_normal(o * i) * np.sqrt(2.0 / i),
+                                               rng.standard_normal(o) * 0.3]) for o, i in dims])
+    P = {"zt": rng.standard_normal((vt.n_vertices, ft)) * 0.5, "zc": rng.standard_normal((vt.n_vertices, fc)) * 0.5,
+         "pt": rand_net(dt), "pc": rand_net(dc)}
+    K = 4
+    hits = O.trace(tree, rays, K)
+    lam_eta = 0.9
+
+    def loss_fn(p):
+        r = T2.render2(tree, vt, p["zt"], p["zc"], p["pt"], p["pc"], dt, dc, rays, K, hits=hits)
+        Le, _ = T2.eta_term(r, depth_t, mask, lam_eta)
+        return O.loss(r.rgb, r.depth, rgb_t, depth_t, mask) + Le, T2.kink_pattern2(r, depth_t, mask)
+    r = T2.render2(tree, vt, P["zt"], P["zc"], P["pt"], P["pc"], dt, dc, rays, K, hits=hits)
+    Le, deta = T2.eta_term(r, depth_t, mask, lam_eta)
+    assert np.count_nonzero(deta) > 100
+    gzt, gzc, gpt, gpc, _, _ = T2.backward2(tree, vt, r, P["zc"], P["pt"], P["pc"], dt, dc, rgb_t, depth_t, mask,
+                                            (0, 0, 0), ft, fc, deta_direct=deta)
+    G = {"zt": gzt, "zc": gzc, "pt": gpt, "pc": gpc}
+    rel, fd, ad = _fd_check(loss_fn, G, P, np.random.default_rng(6), ["pt", "pc"])
+    assert rel.max() <= 1e-4, rel.max()
+    # eta's output bias carries the eta term's gradient
+    n_t = P["pt"].size
+    r0 = T2.render2(tree, vt, P["zt"], P["zc"], P["pt"], P["pc"], dt, dc, rays, K, hits=hits)
+    g_no = T2.backward2(tree, vt, r0, P["zc"], P["pt"], P["pc"], dt, dc, rgb_t, depth_t, mask, (0, 0, 0), ft, fc)[2]
+    assert abs(gpt[n_t - 1] - g_no[n_t - 1]) > 1e-6
