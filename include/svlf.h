@@ -254,6 +254,36 @@ int svlf_render_rays_backward_two_decoder(svlf_octree tree, const void *z_t, con
                                           float *d_z_c, float *d_params_t, float *d_params_c,
                                           void *workspace, size_t ws_bytes, void *stream);
 
+/* Staged training of the two-decoder form (Sec. 4.4, Eq. 4).
+ * Stage 1 (voxel training): every ray with mask > 0 (mask may be NULL = all)
+ * and a finite surface depth D* (depth_target, device, n_rays float32) is
+ * evaluated at one voxel, the leaf containing o + D* d (skipped if that cell
+ * is empty or the ray's segment through it is empty); with
+ * eta* = (t_out - D*) / (t_out - t_in) clamped to [0, 1] (the within-voxel
+ * depth of the surface point), it adds to *loss_accum (device double)
+ *   (1/n_rays) sum_v |c_v - c*|^2 + lambda_eta (eta_v - eta*)^2
+ *                    + lambda_tau exp(-tau_v)^2
+ * (rgb_target: device, n_rays x 3 float32) and accumulates the gradients
+ * (any may be NULL). Workspace: svlf_workspace_size_two_decoder(desc, n_rays,
+ * 1). The paper gives no values for lambda_eta, lambda_tau. */
+int svlf_surface_loss_two_decoder(svlf_octree tree, const void *z_t, const void *z_c,
+                                  const float *params_t, const float *params_c,
+                                  const svlf_two_decoder_desc *desc, const float *rays, int64_t n_rays,
+                                  const float *rgb_target, const float *depth_target, const float *mask,
+                                  float lambda_eta, float lambda_tau, double *loss_accum, float *d_z_t,
+                                  float *d_z_c, float *d_params_t, float *d_params_c, void *workspace,
+                                  size_t ws_bytes, void *stream);
+/* Stages 2-3 (volumetric training): after svlf_render_rays_two_decoder and
+ * before its backward, on the same workspace and rays: adds
+ * lambda_eta (eta_v - eta*)^2 / n_rays over each ray's surface voxel among
+ * its hits (the first hit whose segment contains D*) to *loss_accum and
+ * records the term's gradient for the backward. (Stage 2 freezes Z^C and F^C:
+ * pass NULL for their gradients to the backward.) */
+int svlf_eta_loss_two_decoder(svlf_octree tree, const svlf_two_decoder_desc *desc, const float *rays,
+                              int64_t n_rays, const svlf_render_opts *opts, const float *depth_target,
+                              const float *mask, float lambda_eta, double *loss_accum, void *workspace,
+                              size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------ optimiser */
 /* One bias-corrected Adam step (Sec. 4.5 trains with Adam; Kingma & Ba) over
  * n float32 parameters (device): m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;

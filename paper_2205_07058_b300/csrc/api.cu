@@ -136,7 +136,7 @@ static int check_scene(const svlf_scene &sc, bool need_outputs) {
 
 // Validate a call and build its scene table (device-side view of the scenes).
 static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_render_opts *opts,
-                           bool backward, SceneTable &T);
+                           bool backward, SceneTable &T, bool per_ray_io = true);
 
 static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_desc *mlp,
                       const svlf_render_opts *opts, void *workspace, size_t ws_bytes,
@@ -154,8 +154,10 @@ static int make_table(const svlf_scene *scenes, int n_scenes, const svlf_mlp_des
 
 // Scene table of a call (device-side view of the scenes), without the
 // network or workspace checks.
+// per_ray_io = false: the call reads and writes no per-ray images or image
+// gradients (the surface loss of the staged training)
 static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_render_opts *opts,
-                           bool backward, SceneTable &T) {
+                           bool backward, SceneTable &T, bool per_ray_io) {
     if (!scenes || n_scenes < 1 || !opts) return SVLF_ERR_ARG;
     if (n_scenes > kMaxScenes) return SVLF_ERR_UNSUPPORTED;
     int rc = SVLF_OK;
@@ -176,8 +178,8 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
     }
     for (int i = 0; i < n_scenes; ++i) {
         const svlf_scene &sc = scenes[i];
-        if ((rc = check_scene(sc, !backward))) return rc;
-        if (backward && sc.n_rays > 0 && (!sc.d_rgb || !sc.d_depth)) return SVLF_ERR_ARG;
+        if ((rc = check_scene(sc, per_ray_io && !backward))) return rc;
+        if (per_ray_io && backward && sc.n_rays > 0 && (!sc.d_rgb || !sc.d_depth)) return SVLF_ERR_ARG;
         SceneDev &d = T.s[i];
         d.tree = octree_view(sc.tree);
         d.feats = sc.features;
@@ -442,10 +444,11 @@ static size_t image_c_offset(const svlf_two_decoder_desc &d) { return align256(p
 static size_t images_bytes(const svlf_two_decoder_desc &d) {
     return image_c_offset(d) + align256(packed_tc_bytes(dims_c(d)));
 }
-// after the images: aux (tau, eta, t_in, t_out per sample) and w dL/dD per sample
+// after the images: aux (tau, eta, t_in, t_out per sample), w dL/dD per sample and
+// a direct dL/d(eta) per sample (a loss term on eta; zero unless one is added)
 static size_t two_decoder_stride(const svlf_two_decoder_desc &d, int64_t n_rays, int K) {
     const size_t S = (size_t)n_rays * (size_t)K;
-    return images_bytes(d) + align256(sizeof(float4) * S) + align256(sizeof(float) * S);
+    return images_bytes(d) + align256(sizeof(float4) * S) + 2 * align256(sizeof(float) * S);
 }
 static float4 *aux_of(const Workspace &ws, const svlf_two_decoder_desc &d) {
     return reinterpret_cast<float4 *>(static_cast<char *>(ws.packed_w) + images_bytes(d));
@@ -453,6 +456,10 @@ static float4 *aux_of(const Workspace &ws, const svlf_two_decoder_desc &d) {
 static float *w_dD_of(const Workspace &ws, const svlf_two_decoder_desc &d, int64_t n_rays, int K) {
     return reinterpret_cast<float *>(reinterpret_cast<char *>(aux_of(ws, d)) +
                                      align256(sizeof(float4) * (size_t)n_rays * (size_t)K));
+}
+static float *deta_of(const Workspace &ws, const svlf_two_decoder_desc &d, int64_t n_rays, int K) {
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(w_dD_of(ws, d, n_rays, K)) +
+                                     align256(sizeof(float) * (size_t)n_rays * (size_t)K));
 }
 
 }  // namespace svlf
@@ -498,6 +505,9 @@ extern "C" int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, c
     Workspace wc = ws;
     wc.packed_w = static_cast<char *>(ws.packed_w) + image_c_offset(*desc);
     if (cudaMemsetAsync(ws.counter, 0, kCounterBytes, s) != cudaSuccess) return SVLF_ERR_CUDA;
+    if (cudaMemsetAsync(deta_of(ws, *desc, T.total_rays, T.K), 0, sizeof(float) * (size_t)T.total_rays * T.K, s) !=
+        cudaSuccess)
+        return SVLF_ERR_CUDA;
     if ((rc = launch_pack_tc(mt, desc->precision, T, ws.packed_w, stride, s))) return rc;
     if ((rc = launch_pack_tc(mc, desc->precision, Tc, wc.packed_w, stride, s))) return rc;
     if ((rc = launch_trace(T, ws, hits, t_io, s))) return rc;
@@ -549,9 +559,106 @@ extern "C" int svlf_render_rays_backward_two_decoder(
     // the colour pass runs whenever anything is wanted: it forms dL/d(eta) for the
     // optical-thickness pass
     if ((rc = launch_mlp_backward_tc(mc, desc->precision, fb, Tc, wc, d_z_c != nullptr, d_params_c != nullptr, s,
-                                     2, aux, w_dD)))
+                                     2, aux, w_dD, deta_of(ws, *desc, T.total_rays, T.K))))
         return rc;
     if (!d_z_t && !d_params_t) return SVLF_OK;
     return launch_mlp_backward_tc(mt, desc->precision, fb, T, ws, d_z_t != nullptr, d_params_t != nullptr, s, 1,
                                   aux, w_dD);
+}
+
+// ---------------------------------------------------------------- staged training (Sec. 4.4)
+namespace svlf {
+int launch_surface_samples(const SceneTable &T, const float *depth_t, const float *mask, Sample *samples,
+                           float *eta_gt, unsigned int *counter, cudaStream_t s);
+int launch_surface_loss(const Sample *samples, const unsigned int *counter, const float4 *outputs,
+                        const float4 *aux, const float *rgb_t, int64_t n_rays, float lam_eta, float lam_tau,
+                        float4 *dout, float *deta, float *w_dD, unsigned int *max_abs_bits, double *loss_accum,
+                        cudaStream_t s);
+int launch_eta_term(const SceneTable &T, const int2 *ray_span, const float4 *aux, const float *depth_t,
+                    const float *mask, float lam_eta, float *deta, double *loss_accum, cudaStream_t s);
+}  // namespace svlf
+
+extern "C" int svlf_surface_loss_two_decoder(
+    svlf_octree tree, const void *z_t, const void *z_c, const float *params_t, const float *params_c,
+    const svlf_two_decoder_desc *desc, const float *rays, int64_t n_rays, const float *rgb_target,
+    const float *depth_target, const float *mask, float lambda_eta, float lambda_tau, double *loss_accum,
+    float *d_z_t, float *d_z_c, float *d_params_t, float *d_params_c, void *workspace, size_t ws_bytes,
+    void *stream) {
+    if (!tree) return SVLF_ERR_ARG;
+    int rc = check_two_decoder(desc);
+    if (rc) return rc;
+    const OctreeView &view = octree_view(tree);
+    if (!view.leaf_vertices && view.n_leaves > 0) return SVLF_ERR_ARG;
+    if (n_rays > 0 && (!rgb_target || !depth_target || !loss_accum)) return SVLF_ERR_ARG;
+    if (n_rays > 0 && view.n_leaves > 0 && (!z_t || !z_c || !params_t || !params_c)) return SVLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(z_c) % 16) return SVLF_ERR_ARG;
+    svlf_render_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    opts.K = 1;  // one sample (the surface voxel) per ray
+    svlf_scene sc = one_scene(tree, z_t, params_t, rays, n_rays);
+    SceneTable T;
+    if ((rc = make_table_core(&sc, 1, &opts, false, T, false))) return rc;
+    if (T.total_rays == 0 || view.n_leaves == 0) return SVLF_OK;
+    const size_t stride = two_decoder_stride(*desc, T.total_rays, 1);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes_raw(T.total_rays, 1, stride, 1)) return SVLF_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws = carve_workspace_raw(workspace, T.total_rays, 1, stride, 1);
+    const MlpDims mt = dims_t(*desc), mc = dims_c(*desc);
+    const int fb = desc->feat_dtype == SVLF_FEAT_BF16;
+    SceneTable Tc = T;
+    Tc.s[0].feats = z_c;
+    Tc.s[0].params = params_c;
+    Tc.s[0].d_feat = d_z_c;
+    Tc.s[0].d_params = d_params_c;
+    T.s[0].d_feat = d_z_t;
+    T.s[0].d_params = d_params_t;
+    Workspace wc = ws;
+    wc.packed_w = static_cast<char *>(ws.packed_w) + image_c_offset(*desc);
+    float4 *aux = aux_of(ws, *desc);
+    float *w_dD = w_dD_of(ws, *desc, T.total_rays, 1);
+    float *deta = deta_of(ws, *desc, T.total_rays, 1);
+    if (cudaMemsetAsync(ws.counter, 0, kCounterBytes, s) != cudaSuccess) return SVLF_ERR_CUDA;
+    if ((rc = launch_pack_tc(mt, desc->precision, T, ws.packed_w, stride, s))) return rc;
+    if ((rc = launch_pack_tc(mc, desc->precision, Tc, wc.packed_w, stride, s))) return rc;
+    if ((rc = launch_surface_samples(T, depth_target, mask, ws.samples, deta, ws.counter, s))) return rc;
+    if ((rc = launch_mlp_forward_tc(mt, desc->precision, fb, T, ws, s, 1, aux))) return rc;
+    if ((rc = launch_mlp_forward_tc(mc, desc->precision, fb, Tc, wc, s, 2, aux))) return rc;
+    if ((rc = launch_surface_loss(ws.samples, ws.counter, ws.outputs, aux, rgb_target, T.total_rays, lambda_eta,
+                                  lambda_tau, ws.dout, deta, w_dD, ws.counter + kCtrMaxAbsDout, loss_accum, s)))
+        return rc;
+    if (!d_z_t && !d_z_c && !d_params_t && !d_params_c) return SVLF_OK;
+    if ((rc = launch_mlp_backward_tc(mc, desc->precision, fb, Tc, wc, d_z_c != nullptr, d_params_c != nullptr, s,
+                                     2, aux, w_dD, deta)))
+        return rc;
+    if (!d_z_t && !d_params_t) return SVLF_OK;
+    return launch_mlp_backward_tc(mt, desc->precision, fb, T, ws, d_z_t != nullptr, d_params_t != nullptr, s, 1,
+                                  aux, w_dD, nullptr);
+}
+
+extern "C" int svlf_eta_loss_two_decoder(svlf_octree tree, const svlf_two_decoder_desc *desc, const float *rays,
+                                         int64_t n_rays, const svlf_render_opts *opts, const float *depth_target,
+                                         const float *mask, float lambda_eta, double *loss_accum, void *workspace,
+                                         size_t ws_bytes, void *stream) {
+    if (!tree) return SVLF_ERR_ARG;
+    int rc = check_two_decoder(desc);
+    if (rc) return rc;
+    if (n_rays > 0 && (!depth_target || !loss_accum)) return SVLF_ERR_ARG;
+    SceneTable T;
+    std::memset(&T, 0, sizeof(T));
+    if (!opts || opts->K < 1 || opts->K > kMaxK) return opts ? SVLF_ERR_UNSUPPORTED : SVLF_ERR_ARG;
+    if (n_rays < 0) return SVLF_ERR_ARG;
+    if (n_rays == 0) return SVLF_OK;
+    T.n = 1;
+    T.K = opts->K;
+    T.s[0].tree = octree_view(tree);
+    T.s[0].rays = rays;
+    T.s[0].n_rays = n_rays;
+    T.total_rays = n_rays;
+    const size_t stride = two_decoder_stride(*desc, n_rays, T.K);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
+    if (ws_bytes < workspace_bytes_raw(n_rays, T.K, stride, 1)) return SVLF_ERR_WORKSPACE;
+    Workspace ws = carve_workspace_raw(workspace, n_rays, T.K, stride, 1);
+    return launch_eta_term(T, ws.ray_span, aux_of(ws, *desc), depth_target, mask, lambda_eta,
+                           deta_of(ws, *desc, n_rays, T.K), loss_accum, (cudaStream_t)stream);
 }

@@ -89,5 +89,6 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneT
                           const Workspace &ws, cudaStream_t s, int mode = 0, float4 *aux = nullptr);
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
                            const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s,
-                           int mode = 0, float4 *aux = nullptr, const float *w_dD = nullptr);
+                           int mode = 0, float4 *aux = nullptr, const float *w_dD = nullptr,
+                           const float *deta = nullptr);
 }  // namespace svlf

@@ -670,6 +670,7 @@ struct TcBwdParams {
     // dL/d(depth parameter) per sample; the running max |dL/d(output)| (fp16 scaling)
     float4 *aux;
     const float *w_dD;
+    const float *deta;   // direct dL/d(eta) per sample (a loss term on eta), or null
     unsigned int *gmax;
     uint32_t x_off[kMaxLayers];  // X_l buffers (byte offsets after the weight image)
     uint32_t gout_off, ones_off;
@@ -823,7 +824,8 @@ __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev
             for (int a = 0; a < 3; ++a) dx[a] = fmaf(zdot[v], gw[v][a], dx[a]);
         const float dts = P.w_dD[s] + dx[0] * d[0] + dx[1] * d[1] + dx[2] * d[2];
         const float eta = prev.y;
-        const float geta = dts * (prev.z - prev.w) * eta * (1.f - eta);
+        const float deta = fmaf(dts, prev.z - prev.w, P.deta ? P.deta[s] : 0.f);
+        const float geta = deta * eta * (1.f - eta);
         P.aux[s] = make_float4(P.dout[s].w, geta, 0.f, 0.f);
         if (geta != 0.f) atomicMax(P.gmax, __float_as_uint(fabsf(geta)));
     }
@@ -1329,7 +1331,7 @@ bool tc_backward_supported(const MlpDims &md) {
 
 int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const SceneTable &T,
                            const Workspace &ws, bool want_feat, bool want_params, cudaStream_t s, int mode,
-                           float4 *aux, const float *w_dD) {
+                           float4 *aux, const float *w_dD, const float *deta) {
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     TcBwdParams P;
     memset(&P, 0, sizeof(P));
@@ -1349,6 +1351,7 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
     P.dout = ws.dout;
     P.aux = aux;
     P.w_dD = w_dD;
+    P.deta = deta;
     P.gmax = ws.counter + kCtrMaxAbsDout;
     for (int pass = 0; pass < n_pass; ++pass) {
         if (pl_min[pass] > 0 && !want_params) continue;  // only the last pass forms dL/dz

@@ -79,7 +79,8 @@ EXPORTS = [
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
     "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_workspace_size_two_decoder",
-    "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder",
+    "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
+    "svlf_eta_loss_two_decoder",
 ]
 
 _lib = None
@@ -124,6 +125,10 @@ def lib():
                                                vp, vp, vp, vp, vp, sz, vp]
     L.svlf_render_rays_backward_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64,
                                                         P(RenderOpts), vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.svlf_surface_loss_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, vp, vp, vp, f32,
+                                                f32, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.svlf_eta_loss_two_decoder.argtypes = [vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts), vp, vp, f32, vp, vp,
+                                            sz, vp]
     L.svlf_status_string.argtypes = [i32]
     L.svlf_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -336,6 +341,37 @@ def svlf_render_rays_backward_two_decoder(tree: Octree, z_t, z_c, params_t, para
         tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays),
         rays.shape[0], ctypes.byref(o), _ptr(d_rgb), _ptr(d_depth), _ptr(d_z_t), _ptr(d_z_c), _ptr(d_params_t),
         _ptr(d_params_c), wp, wb, _stream(stream)))
+
+
+def svlf_surface_loss_two_decoder(tree: Octree, z_t, z_c, params_t, params_c, net: TwoDecoder, rays, rgb_target,
+                                  depth_target, mask, lambda_eta: float, lambda_tau: float, loss: torch.Tensor,
+                                  d_z_t=None, d_z_c=None, d_params_t=None, d_params_c=None, workspace=None,
+                                  stream=None):
+    """Stage 1 of the staged training (Eq. 4 on the rays' surface voxels);
+    adds to `loss` (1-element float64) and accumulates the given gradients.
+    Returns the workspace."""
+    N = rays.shape[0]
+    if workspace is None:
+        workspace = torch.empty(workspace_size_two_decoder(net, N, 1) + 256, dtype=torch.uint8, device="cuda")
+    d = net.desc()
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_surface_loss_two_decoder", lib().svlf_surface_loss_two_decoder(
+        tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays), N,
+        _ptr(rgb_target), _ptr(depth_target), _ptr(mask), float(lambda_eta), float(lambda_tau), _ptr(loss),
+        _ptr(d_z_t), _ptr(d_z_c), _ptr(d_params_t), _ptr(d_params_c), wp, wb, _stream(stream)))
+    return workspace
+
+
+def svlf_eta_loss_two_decoder(tree: Octree, net: TwoDecoder, rays, K: int, depth_target, mask, lambda_eta: float,
+                              loss: torch.Tensor, workspace: torch.Tensor, stream=None):
+    """Stages 2-3: the eta term on the surface voxels among the hits of the
+    render whose workspace is given (call before its backward)."""
+    d = net.desc()
+    o = _opts(K, (0.0, 0.0, 0.0))
+    wp, wb = _ws_ptr(workspace)
+    _check("svlf_eta_loss_two_decoder", lib().svlf_eta_loss_two_decoder(
+        tree.handle, ctypes.byref(d), _ptr(rays), rays.shape[0], ctypes.byref(o), _ptr(depth_target), _ptr(mask),
+        float(lambda_eta), _ptr(loss), wp, wb, _stream(stream)))
 
 
 def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,

@@ -217,3 +217,97 @@ def test_backward_matches_oracle_adjoint(prec):
             for m in (o * i, o):
                 assert _rel(flat[off:off + m], ref[off:off + m]) <= 5e-2
                 off += m
+
+
+# ---------------------------------------------------------------- staged training (Sec. 4.4, Eq. 4)
+def _staged_setup(seed=1010):
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(seed)
+    sc = I.make_scene(rng, 7, 10, 4)
+    tree_o = O.build_octree(sc.leaf_ijk, 7)
+    vt = T2.vertex_table(tree_o)
+    ft, fc = 32, 16
+    dt, dc = T2.dims_t(ft, 64, 1), T2.dims_c(fc, 64, 2)
+    zt = (rng.standard_normal((vt.n_vertices, ft)) * 0.3).astype(np.float32)
+    zc = (rng.standard_normal((vt.n_vertices, fc)) * 0.3).astype(np.float32)
+    pt, pc = _net(rng, dt, 0.3), _net(rng, dc, 0.3)
+    az, el = I.random_view_angles(rng, 40)
+    rays = I.training_rays(np.random.default_rng(2), 40, 200, 12000, az, el)
+    rgb_t = np.random.default_rng(3).uniform(0, 1, size=(rays.shape[0], 3)).astype(np.float32)
+    depth_t, mask = I.analytic_depth(rays, sc)
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), 7)
+    tree.build_vertices()
+    return dict(sc=sc, tree_o=tree_o, vt=vt, ft=ft, fc=fc, dt=dt, dc=dc, zt=zt, zc=zc, pt=pt, pc=pc, rays=rays,
+                rgb_t=rgb_t, depth_t=depth_t, mask=mask, tree=tree)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_surface_loss_matches_oracle(prec):
+    """Stage 1: Eq. 4 over the rays' surface voxels (point lookup) and its
+    gradients, against the oracle with the same operand rounding."""
+    from paper_2205_07058_b300 import svlf
+    w = _staged_setup()
+    lam_eta, lam_tau = 0.8, 0.4
+    net = svlf.TwoDecoder(w["ft"], w["fc"], 64, 1, 64, 2, svlf.PRECISIONS[prec])
+    g = {k: torch.from_numpy(w[k]).cuda() for k in ("zt", "zc", "pt", "pc", "rays", "rgb_t", "depth_t", "mask")}
+    grads = {k: torch.zeros_like(g[k]) for k in ("zt", "zc", "pt", "pc")}
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = svlf.svlf_surface_loss_two_decoder(w["tree"], g["zt"], g["zc"], g["pt"], g["pc"], net, g["rays"], g["rgb_t"],
+                                            g["depth_t"], g["mask"], lam_eta, lam_tau, loss, grads["zt"], grads["zc"],
+                                            grads["pt"], grads["pc"])
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    n_gpu = svlf.svlf_workspace_samples(ws, svlf.Network(32, 64, 1, svlf.BF16), w["rays"].shape[0], 1)
+    L, ss, _, ref = T2.surface_loss(w["tree_o"], w["vt"], w["zt"], w["zc"], w["pt"], w["pc"], w["dt"], w["dc"],
+                                    w["rays"], w["rgb_t"], w["depth_t"], w["mask"], lam_eta, lam_tau, w["ft"], w["fc"],
+                                    lowp=prec)
+    assert ss.ray.size > 1000
+    assert abs(n_gpu - ss.ray.size) <= max(2, ss.ray.size // 500)  # surface points on a voxel face may round apart
+    print(prec, "surface samples", n_gpu, ss.ray.size, "loss", loss.item(), L)
+    assert abs(loss.item() - L) <= 2e-3 * abs(L)
+    for i, k in enumerate(("zt", "zc", "pt", "pc")):
+        e = _rel(grads[k].cpu().numpy(), ref[i])
+        print(prec, k, e)
+        assert e <= 2e-2, (k, e)
+
+
+@pytest.mark.parametrize("prec", ["bf16"])
+def test_volume_stage_eta_term_matches_oracle(prec):
+    """Stages 2-3: two-decoder render + the workload loss + the eta term on
+    each ray's surface voxel among its hits; loss and gradients against the
+    oracle (Z^C and F^C frozen as in stage 2: their gradients not asked for)."""
+    from paper_2205_07058_b300 import svlf
+    w = _staged_setup(1011)
+    K = 6
+    lam_eta = 0.7
+    rays = w["rays"][~O.trace(w["tree_o"], w["rays"], K).degenerate]
+    rgb_t = w["rgb_t"][:rays.shape[0]]
+    depth_t, mask = I.analytic_depth(rays, w["sc"])
+    ref64 = T2.render2(w["tree_o"], w["vt"], w["zt"], w["zc"], w["pt"], w["pc"], w["dt"], w["dc"], rays, K)
+    mask = np.where(np.abs(ref64.depth - depth_t) < 1e-4, 0.0, mask).astype(np.float32)
+    net = svlf.TwoDecoder(w["ft"], w["fc"], 64, 1, 64, 2, svlf.PRECISIONS[prec])
+    g = {k: torch.from_numpy(v).cuda() for k, v in dict(zt=w["zt"], zc=w["zc"], pt=w["pt"], pc=w["pc"], rays=rays,
+                                                        rgb_t=rgb_t, depth_t=depth_t, mask=mask).items()}
+    rgb, depth, _, _, ws = svlf.svlf_render_rays_two_decoder(w["tree"], g["zt"], g["zc"], g["pt"], g["pc"], net,
+                                                             g["rays"], K)
+    d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    svlf.svlf_loss(rgb, depth, g["rgb_t"], g["depth_t"], g["mask"], 0.1, d_rgb, d_depth, loss)
+    svlf.svlf_eta_loss_two_decoder(w["tree"], net, g["rays"], K, g["depth_t"], g["mask"], lam_eta, loss, ws)
+    gzt, gpt = torch.zeros_like(g["zt"]), torch.zeros_like(g["pt"])
+    svlf.svlf_render_rays_backward_two_decoder(w["tree"], g["zt"], g["zc"], g["pt"], g["pc"], net, g["rays"], K,
+                                               (0.0, 0.0, 0.0), d_rgb, d_depth, gzt, None, gpt, None, ws)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    r = T2.render2(w["tree_o"], w["vt"], w["zt"], w["zc"], w["pt"], w["pc"], w["dt"], w["dc"], rays, K, lowp=prec,
+                   hits=ref64.hits)
+    Le, deta = T2.eta_term(r, depth_t, mask, lam_eta)
+    L = O.loss(r.rgb, r.depth, rgb_t, depth_t, mask) + Le
+    assert np.count_nonzero(deta) > 500
+    print(prec, "loss", loss.item(), L, "eta term", Le)
+    assert abs(loss.item() - L) <= 2e-3 * abs(L)
+    ref = T2.backward2(w["tree_o"], w["vt"], r, w["zc"], w["pt"], w["pc"], w["dt"], w["dc"], rgb_t, depth_t, mask,
+                       (0, 0, 0), w["ft"], w["fc"], lowp=prec, deta_direct=deta)
+    ez, ep = _rel(gzt.cpu().numpy(), ref[0]), _rel(gpt.cpu().numpy(), ref[2])
+    print(prec, "gradients: Z^T", ez, "F^T", ep)
+    assert ez <= 2e-2 and ep <= 2e-2
