@@ -890,6 +890,53 @@ def run_twodec(args, rank, world, local_rank):
         e2e = {"value": (N + NT) * world * args.steps / (a.elapsed_time(b) / 1e3), "unit": "rays/s",
                "h2d_bytes_per_step": int((h_rays.numel() + h_trays.numel()) * 4),
                "d2h_bytes_per_step": int((h_rgb.numel() + N) * 4 + 8)}
+    # ---- the paper's staged schedule (Sec. 4.4) on the same 2^18-ray batch: per stage one
+    # training step (loss, backward, Adam on the parameters the stage trains), device-timed
+    lam_eta, lam_tau = 1.0, 1.0
+    ws_s = torch.empty(svlf.workspace_size_two_decoder(net, NT, 1) + 256, dtype=torch.uint8, device=dev)
+
+    def stage_step(stage):
+        for _, g_, _, _ in opt.values():
+            g_.zero_()
+        loss.zero_()
+        if stage == 1:  # surface rendering, Eq. 4, everything trained
+            svlf.svlf_surface_loss_two_decoder(tree, zt, zc, pt, pc, net, trays, rgb_t, depth_t, mask, lam_eta,
+                                               lam_tau, loss, opt["zt"][1], opt["zc"][1], opt["pt"][1],
+                                               opt["pc"][1], workspace=ws_s)
+            names = ("zt", "zc", "pt", "pc")
+        else:           # volumetric: photometric + eta term; stage 2 freezes Z^C and F^C
+            svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, trays, K_HITS, workspace=ws_t,
+                                              out=(trgb, tdepth))
+            svlf.svlf_loss(trgb, tdepth, rgb_t, depth_t, mask, 0.0, d_rgb, d_depth, loss)
+            svlf.svlf_eta_loss_two_decoder(tree, net, trays, K_HITS, depth_t, mask, lam_eta, loss, ws_t)
+            frozen = stage == 2
+            svlf.svlf_render_rays_backward_two_decoder(
+                tree, zt, zc, pt, pc, net, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb, d_depth, opt["zt"][1],
+                None if frozen else opt["zc"][1], opt["pt"][1], None if frozen else opt["pc"][1], ws_t)
+            names = ("zt", "pt") if frozen else ("zt", "zc", "pt", "pc")
+        step_no[0] += 1
+        for k in names:
+            p_, g_, m_, v_ = opt[k]
+            svlf.svlf_adam_step(p_, g_, m_, v_, step_no[0], lr=LR if stage < 3 else 2e-4)
+
+    staged = {}
+    for stage in (1, 2, 3):
+        for _ in range(3):
+            stage_step(stage)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            stage_step(stage)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / args.steps
+        staged[f"stage{stage}"] = {"ms_per_step": round(t, 4), "train_rays_per_s": round(NT / (t / 1e3), 1)}
+    staged["note"] = ("Sec. 4.4: stage 1 surface rendering with Eq. 4 (lambda_eta = lambda_tau = 1; the paper gives "
+                      "no values), stage 2 volumetric with Z^C and F^C frozen, stage 3 all parameters at lr 2e-4; "
+                      "one training step on the 2^18-ray batch each")
+    assert svlf.svlf_get_device_status() == 0
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O
@@ -938,6 +985,7 @@ def run_twodec(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 (vertex features {n_vert * (TD_FT + TD_FC) * 4 / 1e6:.0f} MB)"},
         "e2e": e2e, "gpu_launches": int(sum(v[0] for v in kstats.values())), "kernels": per_kernel,
         "tensor_tflops": tensor, "roofline": roof, "clocks": clk, "device_status": status, "cpu_baseline": cpu,
+        "staged_training": staged,
         "setup_s": round(time.time() - t_setup, 1),
     }
 
