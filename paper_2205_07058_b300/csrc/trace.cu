@@ -19,10 +19,11 @@
 //    current t. A voxel is therefore entered at the t its slab test gives as
 //    t_in and left at its t_out, every visited voxel has t_out > t_in, and no
 //    voxel with a positive segment is skipped.
-//  * Hits go straight to the ray's K slots in a scratch area (the network
-//    output buffer, not yet in use), keeping registers free for occupancy; at
-//    the end each warp reserves space for its rays' samples with one atomic
-//    and copies them contiguously per ray from the (cache-hot) slots.
+//  * Hits go to the lane's K slots, in shared memory (interleaved by thread)
+//    for K <= 16, else in a global scratch area (the network output buffer,
+//    not yet in use), keeping registers free for occupancy; at the end each
+//    warp reserves space for its rays' samples with one atomic and copies them
+//    contiguously per ray from the slots.
 //  * Many scenes can be traced in one launch (see SceneTable).
 //  * Warps fetch their own chunks of rays and refill lanes as rays finish
 //    (persistent warps), so no lane waits for the longest ray of its warp
@@ -124,10 +125,10 @@ __device__ __forceinline__ bool walk_init(const OctreeView &T, Walk &w) {
     return true;
 }
 
-// Up to `budget` steps of the walk; hits go to slot[0 .. K-1] (16 bytes each:
+// Up to `budget` steps of the walk; hit j goes to slot[j * stride] (16 bytes:
 // rank, packed cell, t_in, t_out). Returns true when the ray is finished (K
 // hits, left the cube, or an error was latched).
-__device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict__ slot, int budget) {
+__device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict__ slot, int stride, int budget) {
     const RayState &R = w.R;
     const int n = R.n;
     const int max_steps = 3 * n + 64;
@@ -203,7 +204,7 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
         }
         if (leaf) {
             const uint32_t packed = (uint32_t)c[0] | ((uint32_t)c[1] << 10) | ((uint32_t)c[2] << 20);
-            slot[w.nh] = make_int4(rank, (int)packed, __float_as_int(w.t), __float_as_int(tx));
+            slot[w.nh * stride] = make_int4(rank, (int)packed, __float_as_int(w.t), __float_as_int(tx));
             if (++w.nh == K) return true;
         }
         bool out = false;
@@ -243,7 +244,10 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
                                                     int2 *__restrict__ ray_span,
                                                     unsigned int *__restrict__ counter,
                                                     int32_t *__restrict__ hits,
-                                                    float *__restrict__ t_io, int budget) {
+                                                    float *__restrict__ t_io, int budget, int smem_slots) {
+    // a lane's hit slots: in shared memory, interleaved [hit][thread] (conflict-free
+    // warp stores), when they fit; else its ray's K slots in the global scratch
+    extern __shared__ int4 s_slots[];
     const int lane = threadIdx.x & 31;
     const int K = T.K;
     for (;;) {
@@ -297,8 +301,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
             }
             // ---- walk
             if (have) {
-                int4 *slot = slots + g * K;
-                if (walk_steps(tree, w, K, slot, budget)) {
+                int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
+                if (walk_steps(tree, w, K, slot, smem_slots ? (int)blockDim.x : 1, budget)) {
                     have = false;
                     done = true;
                 }
@@ -327,15 +331,16 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
                     }
                     const int64_t base = S.ray_begin * K + first;  // global sample index
                     ray_span[g] = make_int2((int)base, keep);
-                    const int4 *slot = slots + g * K;
+                    const int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
+                    const int ss = smem_slots ? (int)blockDim.x : 1;
                     for (int j = 0; j < keep; ++j) {
-                        const int4 h = slot[j];
+                        const int4 h = slot[j * ss];
                         const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
                         reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
                     }
                     if (hits || t_io) {
                         for (int j = 0; j < K; ++j) {
-                            const int4 h = j < nh ? slot[j] : make_int4(-1, 0, 0, 0);
+                            const int4 h = j < nh ? slot[j * ss] : make_int4(-1, 0, 0, 0);
                             if (hits) hits[g * K + j] = h.x;
                             if (t_io)
                                 reinterpret_cast<float2 *>(t_io)[g * K + j] =
@@ -353,7 +358,12 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
                  cudaStream_t s) {
     if (T.K < 1 || T.K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     const int threads = tuning().trace_block;
-    const size_t smem = 0;
+    // hit slots in shared memory up to K = 16 (32-64 KB per block of 256)
+    const int smem_slots = T.K <= 16 ? 1 : 0;
+    const size_t smem = smem_slots ? sizeof(int4) * (size_t)threads * T.K : 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SVLF_ERR_CUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
             cudaSuccess || per_sm < 1)
@@ -368,7 +378,7 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples,
                                                              reinterpret_cast<int4 *>(ws.outputs),
                                                              ws.ray_span, ws.counter, hits, t_io,
-                                                             tuning().trace_budget);
+                                                             tuning().trace_budget, smem_slots);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
