@@ -63,6 +63,33 @@ def use_profile(prof: dict):
     globals().update(prof)
 
 
+# ----------------------------------------------------------------------------
+# multi-rank host logic (one independent replica per rank; no data-path collective)
+# ----------------------------------------------------------------------------
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's time (the job's time): an all-reduce MAX of one
+    float64, or `ms` itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step: int, world: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank has its own fixed work)."""
+    return units_per_rank_step * world * steps / (t_max_ms / 1e3)
+
+
+def replica_views(rank: int, views: int):
+    """Camera angles of replica `rank` >= 1: its own seeded views of the same
+    scene (rank 0 renders the workload's views)."""
+    from paper_2205_07058_b300 import inputs as I
+    return I.random_view_angles(np.random.default_rng(SCENE_SEED + 7919 * rank), views)
+
+
 def flops_per_sample():
     d_in = FEAT + 9
     return 2 * (d_in * HIDDEN + (N_HIDDEN - 1) * HIDDEN * HIDDEN + 4 * HIDDEN)
@@ -113,7 +140,7 @@ def make_workload(rank: int, views: int, res: int):
     params = I.make_mlp(rng, shape)
     az, el = I.random_view_angles(rng, views)
     if rank > 0:  # replicas render their own views of the same scene
-        az, el = I.random_view_angles(np.random.default_rng(SCENE_SEED + 7919 * rank), views)
+        az, el = replica_views(rank, views)
     render_rays = np.concatenate([I.pinhole_rays(az[v], el[v], res, res) for v in range(views)])
     trng = np.random.default_rng(SCENE_SEED + 1 + 7919 * rank)
     taz, tel = I.random_view_angles(trng, TRAIN_VIEWS)
@@ -363,13 +390,9 @@ def run_ours(args, rank, world, local_rank):
     render_ms = sum(marks[2 * i].elapsed_time(marks[2 * i + 1]) for i in range(args.steps))
     train_ms = total_ms - render_ms
     status = svlf.svlf_get_device_status()
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, dist, dev)
     rays_per_step = N + (0 if args.render_only else NT)
-    value = rays_per_step * world * args.steps / (t_max / 1e3)
+    value = job_value(rays_per_step, world, args.steps, t_max)
 
     # ---- end-to-end through host buffers (H2D of the step's inputs, D2H of its results)
     e2e = None
@@ -407,12 +430,8 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
-        te = a.elapsed_time(b)
-        if dist is not None:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": rays_per_step * world * args.steps / (te / 1e3), "unit": "rays/s",
+        te = max_over_ranks(a.elapsed_time(b), dist, dev)
+        e2e = {"value": job_value(rays_per_step, world, args.steps, te), "unit": "rays/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel
