@@ -97,6 +97,17 @@ int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *strea
                       svlf_octree *out, int64_t *n_leaves_out);
 
 /* Leaf coordinates in rank order. out_ijk: device, n_leaves x 3 int32. */
+/* Builds the octree on the GPU from depth maps (Sec. 4.1: the voxel grid
+ * comes from the dataset's depth maps; Sec. 4.5: 128^3, i.e. depth 7). Pixel
+ * p (rays: device n x 6 float32, origin and unit direction; depth: device n
+ * float32) marks the leaf floor((o + D d) 2^depth_levels) (clamped to the
+ * grid; the point is formed as the product D d rounded, then the sum rounded);
+ * pixels with a non-finite or non-positive depth are skipped. The result is
+ * the same octree svlf_build_octree gives for those leaves. Synchronises
+ * `stream`; allocates 2^(3 depth_levels) bits of temporary device memory
+ * (128 MB at depth 10). */
+int svlf_build_octree_from_depth(const float *rays, const float *depth, int64_t n, int depth_levels,
+                                 void *stream, svlf_octree *out, int64_t *n_leaves_out);
 int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *stream);
 
 /* Sizes: depth, leaves, internal node words, leaf bricks (host outputs, any

@@ -302,3 +302,341 @@ extern "C" int svlf_octree_leaf_vertices(svlf_octree tree, int32_t *out, void *s
 namespace svlf {
 const OctreeView &octree_view(svlf_octree t) { return t->h.view; }
 }  // namespace svlf
+
+// ============================================================================
+// Octree built on the GPU from depth maps (Sec. 4.1: the scene's voxel grid
+// comes from the dataset's depth maps; Sec. 4.5 builds it at 128^3).
+//
+// No sort is needed: a pixel's surface point x = o + D d marks bit
+// Morton(floor(x 2^L)) of an occupancy bitmap, and in Morton order the 64
+// leaves of one brick (level L-2 node) are one 64-bit word of that bitmap.
+// So the bricks are the non-zero words, a leaf's rank is the exclusive
+// prefix sum of the words' popcounts plus its rank inside the word, and each
+// node level above is one pass over groups of 8 child-existence flags. The
+// arrays produced are exactly those of svlf_build_octree for the same leaves.
+// ============================================================================
+namespace svlf {
+namespace {
+
+__device__ __forceinline__ uint64_t spread3_dev(uint32_t v) {
+    uint64_t x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x1F00000000FFFFull;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+__device__ __forceinline__ uint32_t compact3_dev(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10C30C30C30C30C3ull;
+    x = (x ^ (x >> 4)) & 0x100F00F00F00F00Full;
+    x = (x ^ (x >> 8)) & 0x1F0000FF0000FFull;
+    x = (x ^ (x >> 16)) & 0x1F00000000FFFFull;
+    x = (x ^ (x >> 32)) & 0x1FFFFFull;
+    return (uint32_t)x;
+}
+
+__global__ void backproject_kernel(const float *__restrict__ rays, const float *__restrict__ depth, int64_t n,
+                                   int L, unsigned long long *__restrict__ bitmap) {
+    const int nc = 1 << L;
+    const float fn = (float)nc;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const float D = depth[p];
+        if (!(D > 0.f) || !isfinite(D)) continue;
+        uint32_t c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // the product rounded, then the sum rounded (no contraction into an FMA)
+            const float x = __fadd_rn(rays[6 * p + a], __fmul_rn(D, rays[6 * p + 3 + a]));
+            c[a] = (uint32_t)min(max((int)floorf(x * fn), 0), nc - 1);
+        }
+        const uint64_t code = spread3_dev(c[0]) | (spread3_dev(c[1]) << 1) | (spread3_dev(c[2]) << 2);
+        atomicOr(bitmap + (code >> 6), 1ull << (code & 63));
+    }
+}
+
+__global__ void word_stats_kernel(const unsigned long long *__restrict__ bitmap, int64_t W,
+                                  uint32_t *__restrict__ flag, uint32_t *__restrict__ cnt) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long m = bitmap[w];
+        flag[w] = m != 0ull;
+        cnt[w] = (uint32_t)__popcll(m);
+    }
+}
+
+// Exclusive scan of up to 1024 * gridDim values per launch: each block scans
+// its 1024 (4 per thread), writes its total to sums[block].
+__global__ void scan_block_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                                  uint32_t *__restrict__ sums) {
+    __shared__ uint32_t s[256];
+    const int64_t base = (int64_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t v[4], t = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        v[e] = base + e < n ? in[base + e] : 0u;
+        t += v[e];
+    }
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {  // inclusive Hillis-Steele over the thread totals
+        const uint32_t x = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += x;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - t;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (base + e < n) out[base + e] = run;
+        run += v[e];
+    }
+    if (threadIdx.x == 255) sums[blockIdx.x] = s[255];
+}
+
+__global__ void scan_add_kernel(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ offs) {
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (i + e < n) out[i + e] += offs[blockIdx.x];
+}
+
+__global__ void bricks_kernel(const unsigned long long *__restrict__ bitmap, int64_t W,
+                              const uint32_t *__restrict__ brick_idx, const uint32_t *__restrict__ leaf_base,
+                              uint4 *__restrict__ bricks, int32_t *__restrict__ leaf_ijk) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long m = bitmap[w];
+        if (!m) continue;
+        const uint32_t base = leaf_base[w];
+        bricks[brick_idx[w]] = make_uint4((uint32_t)m, (uint32_t)(m >> 32), base, 0u);
+        unsigned long long r = m;
+        uint32_t k = 0;
+        while (r) {
+            const int b = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            const uint64_t code = ((uint64_t)w << 6) | (uint64_t)b;
+            leaf_ijk[3 * (int64_t)(base + k)] = (int32_t)compact3_dev(code);
+            leaf_ijk[3 * (int64_t)(base + k) + 1] = (int32_t)compact3_dev(code >> 1);
+            leaf_ijk[3 * (int64_t)(base + k) + 2] = (int32_t)compact3_dev(code >> 2);
+            ++k;
+        }
+    }
+}
+
+// Parent level from child-existence flags (8 children per parent, Morton order).
+__global__ void level_mask_kernel(const uint32_t *__restrict__ child_flag, int64_t n_parent,
+                                  uint8_t *__restrict__ mask, uint32_t *__restrict__ flag) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m |= (child_flag[8 * p + c] ? 1u : 0u) << c;
+        mask[p] = (uint8_t)m;
+        flag[p] = m != 0u;
+    }
+}
+
+// Node words of one level: mask << 24 | absolute index of the first child
+// (the child level's compact index of child 8p + lowest set bit, plus the
+// child level's offset in the node array; 0 offset when the children are bricks).
+__global__ void node_words_kernel(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ idx,
+                                  int64_t n_cells, const uint32_t *__restrict__ child_idx, uint32_t child_off,
+                                  uint32_t *__restrict__ nodes) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_cells;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = mask[p];
+        if (!m) continue;
+        const int first = __ffs((int)m) - 1;
+        nodes[idx[p]] = (m << 24) | (child_off + child_idx[8 * p + first]);
+    }
+}
+
+struct LevelPtrs {
+    const uint32_t *flag[kMaxDepth];  // existence per cell of level l (Morton order)
+};
+
+// Dense parent index: per level-(L-3) cell (x fastest), its node word, or (mask
+// 0) log2 of the edge of the largest empty block around it: the child, at
+// level l + 1, of its deepest existing ancestor l.
+__global__ void pgrid_kernel(const __grid_constant__ LevelPtrs lv, int L, const uint32_t *__restrict__ node_idx,
+                             const uint32_t *__restrict__ nodes, uint32_t off_top, uint32_t *__restrict__ pgrid) {
+    const int top = L - 3;
+    const int64_t P = (int64_t)1 << top;
+    const int64_t n = P * P * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(i % P), y = (uint32_t)((i / P) % P), z = (uint32_t)(i / (P * P));
+        const uint64_t m = spread3_dev(x) | (spread3_dev(y) << 1) | (spread3_dev(z) << 2);
+        uint32_t v = (uint32_t)L;
+        if (lv.flag[top][m]) {
+            v = nodes[off_top + node_idx[m]];
+        } else {
+            for (int l = top - 1; l >= 0; --l)
+                if (lv.flag[l][m >> (3 * (top - l))]) {
+                    v = (uint32_t)(L - l - 1);
+                    break;
+                }
+        }
+        pgrid[i] = v;
+    }
+}
+
+unsigned grid_for_n(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 32;
+    return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// Exclusive scan of n uint32 values (device) into out; returns the total
+// (synchronises s). tmp: scratch of at least scan_tmp_words(n) words.
+int64_t scan_tmp_words(int64_t n) {
+    int64_t w = 0;
+    while (n > 1) {
+        n = (n + 1023) / 1024;
+        w += 2 * n + 2;
+    }
+    return w + 4;
+}
+
+int exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s, uint32_t *total) {
+    if (n <= 0) {
+        *total = 0;
+        return SVLF_OK;
+    }
+    const int64_t nb = (n + 1023) / 1024;
+    uint32_t *sums = tmp, *sums_scan = tmp + nb;
+    scan_block_kernel<<<(unsigned)nb, 256, 0, s>>>(in, out, n, sums);
+    if (nb > 1) {
+        uint32_t t = 0;
+        int rc = exclusive_scan(sums, sums_scan, nb, tmp + 2 * nb, s, &t);
+        if (rc) return rc;
+        scan_add_kernel<<<(unsigned)nb, 256, 0, s>>>(out, n, sums_scan);
+        *total = t;
+    } else {
+        if (cudaMemcpyAsync(total, sums, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return SVLF_ERR_CUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace svlf
+
+extern "C" int svlf_build_octree_from_depth(const float *rays, const float *depth, int64_t n, int L, void *stream,
+                                            svlf_octree *out, int64_t *n_leaves_out) {
+    if (!out || n < 0 || (n > 0 && (!rays || !depth))) return SVLF_ERR_ARG;
+    if (L < 2 || L > kMaxDepth) return SVLF_ERR_UNSUPPORTED;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n_levels = L - 2;
+    const int64_t W = (int64_t)1 << (3 * L - 6);  // bitmap words = level L-2 cells
+    std::vector<void *> scratch;
+    auto dalloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) return nullptr;
+        scratch.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (void *p : scratch) cudaFree(p);
+        scratch.clear();
+    };
+    // per level: flags, compact index, masks; level n_levels = the bricks
+    std::vector<uint32_t *> flag(n_levels + 1), idx(n_levels + 1);
+    std::vector<uint8_t *> mask(n_levels + 1, nullptr);
+    std::vector<uint32_t> count(n_levels + 1, 0);
+    unsigned long long *bitmap = (unsigned long long *)dalloc(sizeof(unsigned long long) * (size_t)W);
+    uint32_t *cnt = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)W);
+    uint32_t *leaf_base = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)W);
+    uint32_t *tmp = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)scan_tmp_words(W));
+    flag[n_levels] = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)W);
+    idx[n_levels] = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)W);
+    if (!bitmap || !cnt || !leaf_base || !tmp || !flag[n_levels] || !idx[n_levels]) {
+        cleanup();
+        return SVLF_ERR_CUDA;
+    }
+    int rc = SVLF_OK;
+    uint32_t n_leaves = 0;
+    if (cudaMemsetAsync(bitmap, 0, sizeof(unsigned long long) * (size_t)W, s) != cudaSuccess) rc = SVLF_ERR_CUDA;
+    if (!rc && n > 0) backproject_kernel<<<grid_for_n(n), 256, 0, s>>>(rays, depth, n, L, bitmap);
+    if (!rc) word_stats_kernel<<<grid_for_n(W), 256, 0, s>>>(bitmap, W, flag[n_levels], cnt);
+    if (!rc) rc = exclusive_scan(flag[n_levels], idx[n_levels], W, tmp, s, &count[n_levels]);
+    if (!rc) rc = exclusive_scan(cnt, leaf_base, W, tmp, s, &n_leaves);
+    if (!rc && count[n_levels] >= (1u << 24)) rc = SVLF_ERR_UNSUPPORTED;
+    // node levels bottom-up
+    for (int l = n_levels - 1; l >= 0 && !rc; --l) {
+        const int64_t cells = (int64_t)1 << (3 * l);
+        mask[l] = (uint8_t *)dalloc((size_t)cells);
+        flag[l] = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)cells);
+        idx[l] = (uint32_t *)dalloc(sizeof(uint32_t) * (size_t)cells);
+        if (!mask[l] || !flag[l] || !idx[l]) {
+            rc = SVLF_ERR_CUDA;
+            break;
+        }
+        level_mask_kernel<<<grid_for_n(cells), 256, 0, s>>>(flag[l + 1], cells, mask[l], flag[l]);
+        rc = exclusive_scan(flag[l], idx[l], cells, tmp, s, &count[l]);
+    }
+    std::vector<uint32_t> off(n_levels + 1, 0);
+    for (int l = 0; l < n_levels; ++l) off[l + 1] = off[l] + count[l];
+    const uint32_t n_nodes = n_levels > 0 ? off[n_levels] : 0;
+    if (!rc && n_nodes >= (1u << 24)) rc = SVLF_ERR_UNSUPPORTED;
+    svlf_octree_s *t = nullptr;
+    if (!rc) {
+        t = new (std::nothrow) svlf_octree_s;
+        if (!t) rc = SVLF_ERR_CUDA;
+    }
+    if (!rc) {
+        std::memset(t, 0, sizeof(*t));
+        OctreeHost &H = t->h;
+        const int64_t P = n_levels > 0 ? (int64_t)1 << (L - 3) : 0;
+        const int64_t n_pgrid = P * P * P;
+        bool ok = cudaMalloc(&H.leaf_ijk_dev, sizeof(int32_t) * 3 * ((size_t)n_leaves + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&H.bricks_dev, sizeof(uint4) * ((size_t)count[n_levels] + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&H.nodes_dev, sizeof(uint32_t) * ((size_t)n_nodes + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&H.pgrid_dev, sizeof(uint32_t) * ((size_t)n_pgrid + 1)) == cudaSuccess;
+        if (!ok) {
+            rc = SVLF_ERR_CUDA;
+        } else {
+            bricks_kernel<<<grid_for_n(W), 256, 0, s>>>(bitmap, W, idx[n_levels], leaf_base, H.bricks_dev,
+                                                        H.leaf_ijk_dev);
+            for (int l = 0; l < n_levels; ++l) {
+                const int64_t cells = (int64_t)1 << (3 * l);
+                const uint32_t child_off = l + 1 < n_levels ? off[l + 1] : 0u;  // bricks are indexed from 0
+                node_words_kernel<<<grid_for_n(cells), 256, 0, s>>>(mask[l], idx[l], cells, idx[l + 1], child_off,
+                                                                    H.nodes_dev + off[l]);
+            }
+            if (n_levels > 0 && n_leaves > 0) {
+                LevelPtrs lv;
+                std::memset(&lv, 0, sizeof(lv));
+                for (int l = 0; l < n_levels; ++l) lv.flag[l] = flag[l];
+                pgrid_kernel<<<grid_for_n(n_pgrid), 256, 0, s>>>(lv, L, idx[n_levels - 1], H.nodes_dev,
+                                                                 off[n_levels - 1], H.pgrid_dev);
+            }
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = SVLF_ERR_CUDA;
+        }
+        H.view.depth = L;
+        H.view.n_node_levels = n_levels;
+        H.view.n_leaves = n_leaves;
+        H.view.n_nodes = (int)n_nodes;
+        H.view.n_bricks = (int)count[n_levels];
+        H.view.root_is_brick = n_levels == 0;
+        H.view.empty = n_leaves == 0;
+        H.view.nodes = H.nodes_dev;
+        H.view.bricks = H.bricks_dev;
+        H.view.pgrid = H.pgrid_dev;
+        H.view.pgrid_shift = n_levels > 0 ? L - 3 : 0;
+        if (rc) {
+            cudaFree(H.leaf_ijk_dev);
+            cudaFree(H.bricks_dev);
+            cudaFree(H.nodes_dev);
+            cudaFree(H.pgrid_dev);
+            delete t;
+            t = nullptr;
+        }
+    }
+    cleanup();
+    if (rc) return rc;
+    *out = t;
+    if (n_leaves_out) *n_leaves_out = n_leaves;
+    return SVLF_OK;
+}

@@ -80,7 +80,7 @@ EXPORTS = [
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
     "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
-    "svlf_eta_loss_two_decoder",
+    "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth",
 ]
 
 _lib = None
@@ -98,6 +98,7 @@ def lib():
     P = ctypes.POINTER
     L.svlf_build_octree.argtypes = [vp, i64, i32, vp, P(vp), P(i64)]
     L.svlf_octree_leaf_ijk.argtypes = [vp, vp, vp]
+    L.svlf_build_octree_from_depth.argtypes = [vp, vp, i64, i32, vp, P(vp), P(i64)]
     L.svlf_octree_info.argtypes = [vp, P(i32), P(i64), P(i64), P(i64)]
     L.svlf_free_octree.argtypes = [vp]
     L.svlf_workspace_size.argtypes = [P(MlpDesc), i64, i32, P(sz)]
@@ -177,6 +178,21 @@ class Octree:
         self.handle = h
         self.depth = int(depth)
         self.n_leaves = int(n.value)
+
+    @classmethod
+    def from_depth(cls, rays: torch.Tensor, depth: torch.Tensor, depth_levels: int, stream=None) -> "Octree":
+        """Octree of the voxels the depth maps' surface points fall in, built on the GPU."""
+        r = rays.to(device="cuda", dtype=torch.float32).contiguous()
+        d = depth.to(device="cuda", dtype=torch.float32).contiguous()
+        h = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check("svlf_build_octree_from_depth", lib().svlf_build_octree_from_depth(
+            _ptr(r), _ptr(d), r.shape[0], int(depth_levels), _stream(stream), ctypes.byref(h), ctypes.byref(n)))
+        t = cls.__new__(cls)
+        t.handle = h
+        t.depth = int(depth_levels)
+        t.n_leaves = int(n.value)
+        return t
 
     def info(self):
         d, nl, nn, nb = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
