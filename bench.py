@@ -105,11 +105,12 @@ def parse():
     p.add_argument("--train-precision", default=None, choices=["bf16", "fp16", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="step", choices=["step", "batched", "large", "twodec"],
+    p.add_argument("--workload", default="step", choices=["step", "batched", "large", "twodec", "octree"],
                    help="step: the headline render + train step; batched: 64 scenes in one "
                         "launch per kernel under a CUDA graph; large: depth-10 scene, bf16 "
                         "features, 4x128 network, K = 16, 8 views + 2^20 training rays; twodec: "
-                        "the paper's two-decoder form (vertex features), render of 4 views of 1600^2")
+                        "the paper's two-decoder form (vertex features), render of 4 views of 1600^2; octree: "
+                        "octree construction on the GPU from depth maps")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tuning", default=None,
                    help="fixed launch shapes instead of the search, e.g. "
@@ -1009,6 +1010,49 @@ def run_twodec(args, rank, world, local_rank):
     }
 
 
+# ----------------------------------------------------------------------------
+# octree construction from depth maps (Sec. 4.1, 4.5)
+# ----------------------------------------------------------------------------
+def run_octree(args, rank, world, local_rank):
+    import torch
+    from paper_2205_07058_b300 import inputs as I
+    from paper_2205_07058_b300 import svlf
+    torch.cuda.set_device(local_rank)
+    rng = np.random.default_rng(SCENE_SEED)
+    scene = I.make_scene(rng, 9, 64, 32)
+    views, res = 16, 512
+    az, el = I.random_view_angles(np.random.default_rng(SCENE_SEED + 3), views)
+    rays_h = np.concatenate([I.pinhole_rays(az[v], el[v], res, res) for v in range(views)])
+    depth_h, mask_h = I.analytic_depth(rays_h, scene)
+    depth_h = np.where(mask_h > 0, depth_h, np.nan).astype(np.float32)
+    rays = torch.from_numpy(rays_h).cuda()
+    depth = torch.from_numpy(depth_h).cuda()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for L in (7, 9, 10):  # 128^3 (the paper's resolution), 512^3, 1024^3
+        for _ in range(2):
+            svlf.Octree.from_depth(rays, depth, L).free()
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 20))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            t = svlf.Octree.from_depth(rays, depth, L)
+            n = t.n_leaves
+            t.free()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"L{L}"] = {"ms_per_build": round(ms, 3), "leaves": n, "pixels_per_s": round(rays.shape[0] / (ms / 1e3), 1)}
+    return {"metric": "pixels/s: octree construction from 16 depth maps of 512^2 (host-synchronised build)",
+            "value": out["L7"]["pixels_per_s"], "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (analytic depth of the seeded scene)",
+            "config": {"workload": "octree from depth maps, 16 views of 512^2, depth-9 scene's analytic depths",
+                       "pixels": int(rays.shape[0])},
+            "builds": out, "device_status": svlf.svlf_get_device_status()}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -1017,6 +1061,11 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "octree":
+        out = run_octree(args, rank, world, local_rank)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     if args.workload == "twodec":
