@@ -11,9 +11,12 @@
 //    the warpgroup's activation buffer (the A operand).
 //  * One thread issues the layer's tcgen05.mma instructions (M = 128 samples,
 //    N = layer width, K = 16 each) into the warpgroup's 128 TMEM columns and
-//    commits them to an mbarrier; the warpgroup waits, reads its row of the
-//    accumulator (tcgen05.ld, lane = sample), adds the bias, applies ReLU,
-//    rounds to 16 bits and writes the next layer's A operand in place.
+//    commits them to an mbarrier. A hidden layer's first MMA multiplies a
+//    block of ones by the bias split into 16-bit pieces, so the accumulator
+//    starts at the bias with no TMEM store on the tile's critical path. The
+//    warpgroup waits, reads its row of the accumulator (tcgen05.ld, lane =
+//    sample), applies ReLU, rounds to 16 bits and writes the next layer's A
+//    operand in place.
 //  * The last layer (N padded 4 -> 16) writes sigmoid colour and ReLU optical
 //    thickness per sample.
 //  Warpgroups run independently, so the tensor core works on one tile while
@@ -43,7 +46,16 @@ struct TcLayout {
     uint32_t w_cols[kMaxLayers]; // columns (K) of each B tile
     uint32_t bias_off;           // byte offset of the float32 biases
     uint32_t bias_l[kMaxLayers]; // float index of each layer's bias within the bias block
-    uint32_t bytes;              // total image size (multiple of 16)
+    uint32_t bytes;              // weights + float32 biases (multiple of 16): what the backward copies
+    // Forward-only tail: each hidden layer's bias as the B operand of one extra
+    // K = 16 MMA against a block of ones, so the accumulator starts at the bias
+    // without a TMEM store. B tile l holds the 8-column K group 0 of an N = 128
+    // tile: columns 0..2 = the bias split into three 16-bit pieces (hi + mid +
+    // lo, exact for BF16), 3..7 = 0; its K group 1 (leading byte offset 2 KB) is
+    // the next region, which the zero half of the ones block multiplies away.
+    uint32_t bias_b_off[kMaxLayers];
+    uint32_t ones_off;           // 2 KB of 16-bit 1.0 (A rows, K group 0), then 2 KB of zeros (group 1)
+    uint32_t fwd_bytes;          // total image size, forward tail included
 };
 
 static TcLayout tc_layout(const MlpDims &md) {
@@ -66,6 +78,13 @@ static TcLayout tc_layout(const MlpDims &md) {
     }
     off += nb * 4;
     t.bytes = (off + 15) & ~15u;
+    off = (t.bytes + 127) & ~127u;
+    for (int l = 0; l < md.nh; ++l) {
+        t.bias_b_off[l] = off;
+        off += kHp * 16;
+    }
+    t.ones_off = off;
+    t.fwd_bytes = off + 2 * kTcTile * 16;
     return t;
 }
 
@@ -75,7 +94,7 @@ bool tc_supported(const MlpDims &md) {
 
 size_t packed_tc_bytes(const MlpDims &md) {
     if (!tc_supported(md)) return 0;
-    return tc_layout(md).bytes;
+    return tc_layout(md).fwd_bytes;
 }
 
 // ---------------------------------------------------------------- packing
@@ -101,7 +120,35 @@ __global__ void pack_tc_kernel(MlpDims md, TcLayout lay, int fp16, const float *
         }
         float *bias = reinterpret_cast<float *>(image + lay.bias_off) + lay.bias_l[l];
         for (int r = tid; r < R; r += nthr) bias[r] = r < out ? W[out * in + r] : 0.f;
+        if (l < md.nh) {
+            // forward tail: the bias as three 16-bit pieces (K columns 0..2 of B)
+            for (int r = tid; r < kHp; r += nthr) {
+                const float b = r < out ? W[out * in + r] : 0.f;
+                float piece[3];
+                float rem = b;
+                for (int j = 0; j < 3; ++j) {
+                    piece[j] = fp16 ? __half2float(__float2half_rn(rem))
+                                    : __bfloat162float(__float2bfloat16_rn(rem));
+                    rem -= piece[j];
+                }
+                for (int k = 0; k < 8; ++k) {
+                    const float v = k < 3 ? piece[k] : 0.f;
+                    uint16_t bits;
+                    if (fp16) {
+                        __half h = __float2half_rn(v);
+                        bits = *reinterpret_cast<uint16_t *>(&h);
+                    } else {
+                        __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        bits = *reinterpret_cast<uint16_t *>(&h);
+                    }
+                    *reinterpret_cast<uint16_t *>(image + lay.bias_b_off[l] + tc::cm_offset(r, k, kHp)) = bits;
+                }
+            }
+        }
     }
+    const uint16_t one = fp16 ? 0x3C00u : 0x3F80u;
+    uint16_t *ones = reinterpret_cast<uint16_t *>(image + lay.ones_off);
+    for (int e = tid; e < 2 * kTcTile * 8; e += nthr) ones[e] = e < kTcTile * 8 ? one : 0u;
 }
 
 int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *packed,
@@ -130,6 +177,9 @@ struct TcFwdParams {
     float4 *aux;         // two-decoder: (tau, eta, t_in, t_out) per sample, F^T pass -> F^C pass
     int n_wg;            // warpgroups per CTA
     uint32_t abuf_bytes; // activation buffer per warpgroup
+    int bias_mma;        // 1: hidden biases enter through the MMA (image copied with its forward tail);
+                         // 0: they are stored into TMEM before each layer (tail left out, to save shared memory)
+    uint32_t wbytes;     // bytes of the image copied into shared memory: fwd_bytes or bytes
 };
 
 // Per-CTA view of the global tile list: scene s owns global tiles
@@ -399,7 +449,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
     const int warp = tid >> 5;
     const uint32_t ncols = P.n_wg <= 2 ? 256u : 512u;
     uint8_t *wimg = smem;
-    uint8_t *abuf = smem + P.lay.bytes + wg * P.abuf_bytes;
+    uint8_t *abuf = smem + P.wbytes + wg * P.abuf_bytes;
     const float *bias = reinterpret_cast<const float *>(wimg + P.lay.bias_off);
 
     if (tid == 0) {
@@ -439,9 +489,9 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
         if (tid == 0) {
             const uint32_t mb = tc::smem_u32(&s_mbar[4]);
             const uint8_t *img = P.images + sc * P.image_stride;
-            tc::mbar_expect_tx(mb, P.lay.bytes);
-            for (uint32_t off = 0; off < P.lay.bytes; off += 32768u)
-                tc::bulk_g2s(tc::smem_u32(wimg + off), img + off, min(32768u, P.lay.bytes - off), mb);
+            tc::mbar_expect_tx(mb, P.wbytes);
+            for (uint32_t off = 0; off < P.wbytes; off += 32768u)
+                tc::bulk_g2s(tc::smem_u32(wimg + off), img + off, min(32768u, P.wbytes - off), mb);
         }
         if (!tc::mbar_wait(tc::smem_u32(&s_mbar[4]), wphase)) {
             raise_status(SVLF_DEV_WAIT_TIMEOUT);
@@ -483,7 +533,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                 const int N = P.lay.w_rows[l];
                 const int Kl = P.lay.w_cols[l];
                 const bool hidden = l + 1 < P.lay.n_layers;
-                if (hidden) {
+                if (hidden && !P.bias_mma) {
                     // the accumulator starts at the bias: the MMAs add onto it in float32
                     const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + P.lay.bias_l[l]);
 #pragma unroll 1
@@ -506,6 +556,12 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                     tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(kTcTile, N, bf16, 0, 0);
                     const uint32_t b_base = wimg_s + P.lay.w_off[l];
+                    if (hidden && P.bias_mma) {
+                        // the accumulator starts at the bias (ones x bias pieces); the layer's MMAs add onto it
+                        const uint64_t da = tc::sdesc(wimg_s + P.lay.ones_off, kTcTile * 16, 128);
+                        const uint64_t db = tc::sdesc(wimg_s + P.lay.bias_b_off[l], N * 16, 128);
+                        tc::mma_f16(tmem_wg, da, db, idesc, 0u);
+                    }
                     for (int k = 0; k < Kl; k += 16) {
                         const uint64_t da = tc::sdesc(abuf_s + (k >> 3) * (kTcTile * 16), kTcTile * 16, 128);
                         const uint64_t db = tc::sdesc(b_base + (k >> 3) * (N * 16), N * 16, 128);
@@ -576,16 +632,30 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
     }
 }
 
-static int tc_forward_config(const MlpDims &md, const TcLayout &lay, int &n_wg, uint32_t &abuf,
-                             size_t &smem) {
-    const int kmax = lay.K0 > kHp ? lay.K0 : kHp;
-    abuf = (uint32_t)(kTcTile * kmax * 2);
-    const size_t limit = 227 * 1024 - 256;
-    for (n_wg = 4; n_wg >= 1; --n_wg) {
-        smem = lay.bytes + (size_t)n_wg * abuf + 128;  // + alignment slack
-        if (smem <= limit) break;
+// Warpgroups that fit next to `wbytes` of resident image (0 if none does).
+static int tc_forward_wgs(uint32_t wbytes, uint32_t abuf, size_t &smem) {
+    const size_t limit = 227 * 1024 - sizeof(TileMap) - 256;  // static shared memory comes off the top
+    for (int n_wg = 4; n_wg >= 1; --n_wg) {
+        smem = wbytes + (size_t)n_wg * abuf + 128;  // + alignment slack
+        if (smem <= limit) return n_wg;
     }
-    if (n_wg < 1) return SVLF_ERR_UNSUPPORTED;
+    return 0;
+}
+
+// Launch shape: the biases go through the MMA unless the image's forward tail
+// would cost a warpgroup (or the whole launch), in which case they are stored
+// into TMEM and the tail stays in global memory.
+static int tc_forward_config(const MlpDims &md, const TcLayout &lay, TcFwdParams &P, size_t &smem) {
+    const int kmax = lay.K0 > kHp ? lay.K0 : kHp;
+    P.abuf_bytes = (uint32_t)(kTcTile * kmax * 2);
+    size_t smem_mma, smem_st;
+    const int wg_mma = tc_forward_wgs(lay.fwd_bytes, P.abuf_bytes, smem_mma);
+    const int wg_st = tc_forward_wgs(lay.bytes, P.abuf_bytes, smem_st);
+    if (wg_st < 1) return SVLF_ERR_UNSUPPORTED;
+    P.bias_mma = wg_mma == wg_st ? 1 : 0;
+    P.n_wg = P.bias_mma ? wg_mma : wg_st;
+    P.wbytes = P.bias_mma ? lay.fwd_bytes : lay.bytes;
+    smem = P.bias_mma ? smem_mma : smem_st;
     if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: it owns all TMEM columns it asks for
     return SVLF_OK;
 }
@@ -595,7 +665,7 @@ static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md,
                   cudaStream_t s, int n_wg_override) {
     TcFwdParams P = P0;
     size_t smem;
-    int rc = tc_forward_config(md, lay, P.n_wg, P.abuf_bytes, smem);
+    int rc = tc_forward_config(md, lay, P, smem);
     if (rc) return rc;
     if (n_wg_override > 0 && n_wg_override < P.n_wg) P.n_wg = n_wg_override;
     if (EPI == 2 && P.n_wg > 3) P.n_wg = 3;
