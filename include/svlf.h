@@ -96,7 +96,6 @@ typedef struct {
 int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
                       svlf_octree *out, int64_t *n_leaves_out);
 
-/* Leaf coordinates in rank order. out_ijk: device, n_leaves x 3 int32. */
 /* Builds the octree on the GPU from depth maps (Sec. 4.1: the voxel grid
  * comes from the dataset's depth maps; Sec. 4.5: 128^3, i.e. depth 7). Pixel
  * p (rays: device n x 6 float32, origin and unit direction; depth: device n
@@ -108,6 +107,8 @@ int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *strea
  * (128 MB at depth 10). */
 int svlf_build_octree_from_depth(const float *rays, const float *depth, int64_t n, int depth_levels,
                                  void *stream, svlf_octree *out, int64_t *n_leaves_out);
+
+/* Leaf coordinates in rank order. out_ijk: device, n_leaves x 3 int32. */
 int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *stream);
 
 /* Sizes: depth, leaves, internal node words, leaf bricks (host outputs, any
@@ -340,12 +341,17 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
  *   mlp_epilogue_batch  tensor-core forward: TMEM loads per wait, 1 or 2
  *                       (2 limits the CTA to 3 warpgroups)
  *   trace_budget        traversal steps between lane refills, 1..256
- *   trace_block         traversal threads per block, 128 or 256 */
+ *   trace_block         traversal threads per block, 128 or 256
+ *   trace_refill        traversal: idle lanes a warp needs before it claims
+ *                       a new chunk of rays while rays of its current chunks
+ *                       still walk, 1..32 (32: only once all lanes are idle;
+ *                       default 32 for large launches, 16 for small ones) */
 typedef struct {
     int mlp_warpgroups;
     int mlp_epilogue_batch;
     int trace_budget;
     int trace_block;
+    int trace_refill;
 } svlf_tuning;
 
 int svlf_set_tuning(const svlf_tuning *t);

@@ -22,7 +22,7 @@ int num_sms() {
     return cached[dev];
 }
 
-static svlf_tuning g_tuning = {0, 1, 16, 256};
+static svlf_tuning g_tuning = {0, 1, 16, 256, 0};
 
 const svlf_tuning &tuning() { return g_tuning; }
 
@@ -380,6 +380,7 @@ extern "C" int svlf_set_tuning(const svlf_tuning *t) {
     if (v.trace_budget < 1 || v.trace_budget > 256) return SVLF_ERR_ARG;
     if (v.trace_block == 0) v.trace_block = 256;
     if (v.trace_block != 128 && v.trace_block != 256) return SVLF_ERR_ARG;
+    if (v.trace_refill < 0 || v.trace_refill > 32) return SVLF_ERR_ARG;
     g_tuning = v;
     return SVLF_OK;
 }

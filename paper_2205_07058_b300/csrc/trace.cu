@@ -25,9 +25,10 @@
 //    warp reserves space for its rays' samples with one atomic and copies them
 //    contiguously per ray from the slots.
 //  * Many scenes can be traced in one launch (see SceneTable).
-//  * Warps fetch their own chunks of rays and refill lanes as rays finish
-//    (persistent warps), so no lane waits for the longest ray of its warp
-//    and no warp waits for the rest of its block.
+//  * Warps fetch their own chunks of rays and refill lanes as rays finish,
+//    claiming the next chunk as soon as the current one runs dry (persistent
+//    warps), so no lane waits for the longest ray of its warp and no warp
+//    waits for the rest of its block.
 #include "svlf_internal.cuh"
 
 namespace svlf {
@@ -232,47 +233,65 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Each warp claims chunks of T.chunk_rays rays of one scene from a global
-// counter (in order, so neighbouring warps walk neighbouring pixels). Inside
-// a chunk a lane whose ray is finished takes the chunk's next ray, so lanes
-// stay busy while other rays of the warp are still walking; rays that miss
-// the unit cube never enter the walk. Finished rays write their samples to
-// the scene's region, with one atomic per warp and round.
+// Each warp claims chunks of T.chunk_rays rays from a global counter (in
+// order, so neighbouring warps walk neighbouring pixels). A lane whose ray is
+// finished takes the next ray of the warp's current chunk; once that chunk is
+// handed out, the warp claims another one when at least `refill` lanes are
+// idle (32: only when all are), so lanes may hold rays of different chunks
+// and scenes. Rays that miss the unit cube never enter the walk. Finished rays
+// write their samples to their scene's region, with one atomic per warp,
+// scene and round.
+// MULTI = false: a single-scene table (scene 0 is then addressed statically).
+template <bool MULTI>
 __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ SceneTable T,
                                                     Sample *__restrict__ samples,
                                                     int4 *__restrict__ slots,
                                                     int2 *__restrict__ ray_span,
                                                     unsigned int *__restrict__ counter,
                                                     int32_t *__restrict__ hits,
-                                                    float *__restrict__ t_io, int budget, int smem_slots) {
+                                                    float *__restrict__ t_io, int budget, int smem_slots,
+                                                    int refill) {
     // a lane's hit slots: in shared memory, interleaved [hit][thread] (conflict-free
     // warp stores), when they fit; else its ray's K slots in the global scratch
     extern __shared__ int4 s_slots[];
     const int lane = threadIdx.x & 31;
     const int K = T.K;
+    const int ss = smem_slots ? (int)blockDim.x : 1;
+    // warp-uniform: the chunk being handed out
+    int64_t r_begin = 0;
+    int chunk_n = 0, next = 0, csc = 0;
+    bool exhausted = false;  // the launch has no chunk left
+    // per lane: the ray it walks
+    bool have = false;
+    int64_t g = 0;
+    int sc = 0;
+    Walk w;
     for (;;) {
-        long long chunk = 0;
-        if (lane == 0) chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
-        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
-        if (chunk >= T.total_chunks) break;
-        const int sc = scene_of_chunk(T, chunk);
-        const SceneDev &S = T.s[sc];
-        const OctreeView &tree = S.tree;
-        const int64_t r_begin = (chunk - S.chunk_begin) * T.chunk_rays;
-        const int chunk_n = (int)min((int64_t)T.chunk_rays, S.n_rays - r_begin);
-        int next = 0;        // rays of the chunk handed out so far (warp-uniform)
-        bool have = false;   // this lane walks a ray
-        int64_t g = 0;       // its global ray index
-        Walk w;
-        for (;;) {
-            // ---- hand out rays to idle lanes; rays that miss finish at once
-            bool done = false;
+        // ---- refill idle lanes (warp-uniform loop); rays that miss finish here
+        for (int round = 0; round < 64; ++round) {
             const unsigned idle = __ballot_sync(0xFFFFFFFFu, !have);
+            if (!idle || exhausted) break;
+            if (next >= chunk_n) {
+                if (__popc(idle) < refill) break;  // keep walking the rays in hand
+                long long chunk = 0;
+                if (lane == 0) chunk = (long long)atomicAdd(counter + kCtrTraceChunks, 1u);
+                chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+                if (chunk >= T.total_chunks) {
+                    exhausted = true;
+                    break;
+                }
+                csc = MULTI ? scene_of_chunk(T, chunk) : 0;
+                r_begin = (chunk - T.s[csc].chunk_begin) * T.chunk_rays;
+                chunk_n = (int)min((int64_t)T.chunk_rays, T.s[csc].n_rays - r_begin);
+                next = 0;
+            }
             if (!have) {
                 const int my = next + __popc(idle & lanemask_lt());
                 if (my < chunk_n) {
+                    const SceneDev &S = T.s[csc];
                     const int64_t rl = r_begin + my;
                     g = S.ray_begin + rl;
+                    sc = csc;
                     const float2 *rp = reinterpret_cast<const float2 *>(S.rays + 6 * rl);
                     const float2 a = __ldg(rp), b = __ldg(rp + 1), cc = __ldg(rp + 2);
                     RayState &R = w.R;
@@ -284,69 +303,75 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ S
                         R.rhi[q] = rh;
                         R.rlo[q] = R.d[q] != 0.f ? fmaf(-R.d[q], rh, 1.0f) * rh : 0.f;
                     }
-                    R.n = 1 << tree.depth;
-                    R.h = ldexpf(1.0f, -tree.depth);
+                    R.n = 1 << S.tree.depth;
+                    R.h = ldexpf(1.0f, -S.tree.depth);
                     w.nh = 0;
-                    have = walk_init(tree, w);
-                    done = !have;  // a miss: zero samples
+                    have = walk_init(S.tree, w);
                     TRACE_STAT(7, 1);
-                    if (have) TRACE_STAT(5, 1);
+                    if (have) {
+                        TRACE_STAT(5, 1);
+                    } else {  // a miss: zero samples
+                        ray_span[g] = make_int2((int)(S.ray_begin * K), 0);
+                        for (int j = 0; hits && j < K; ++j) hits[g * K + j] = -1;
+                        for (int j = 0; t_io && j < K; ++j)
+                            reinterpret_cast<float2 *>(t_io)[g * K + j] = make_float2(0.f, 0.f);
+                    }
                 }
             }
-            next += __popc(idle);
-            const bool any_active = __any_sync(0xFFFFFFFFu, have);
-            if (!any_active && !__any_sync(0xFFFFFFFFu, done)) {
-                if (next >= chunk_n) break;
-                continue;
+            next = min(next + __popc(idle), chunk_n);
+        }
+        if (exhausted && !__any_sync(0xFFFFFFFFu, have)) break;
+        // ---- walk
+        bool done = false;
+        if (have) {
+            int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
+            if (walk_steps(T.s[MULTI ? sc : 0].tree, w, K, slot, ss, budget)) {
+                have = false;
+                done = true;
             }
-            // ---- walk
-            if (have) {
-                int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
-                if (walk_steps(tree, w, K, slot, smem_slots ? (int)blockDim.x : 1, budget)) {
-                    have = false;
-                    done = true;
-                }
-            }
-            // ---- finished rays: reserve their samples (one atomic per warp) and copy them
-            const unsigned fin = __ballot_sync(0xFFFFFFFFu, done);
-            if (fin) {
-                const int nh = done ? w.nh : 0;
-                int incl = nh;
+        }
+        // ---- finished rays: reserve their samples (one atomic per scene present) and copy them
+        unsigned pending = __ballot_sync(0xFFFFFFFFu, done);
+        while (pending) {
+            const int lsc = MULTI ? __shfl_sync(0xFFFFFFFFu, sc, __ffs(pending) - 1) : 0;
+            const bool mine = done && (!MULTI || sc == lsc);
+            pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
+            const int nh = mine ? w.nh : 0;
+            int incl = nh;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-                    if (lane >= off) incl += v;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            unsigned int wbase = 0;
+            if (lane == 31 && total > 0) wbase = atomicAdd(counter + kCtrScene + lsc, (unsigned int)total);
+            wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+            if (mine) {
+                const SceneDev &S = T.s[lsc];
+                const int64_t cap = S.n_rays * (int64_t)K;  // the scene's slot region
+                const int64_t first = (int64_t)wbase + (incl - nh);
+                int keep = nh;
+                if (first + nh > cap) {
+                    raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
+                    keep = (int)max((int64_t)0, cap - first);
                 }
-                const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                unsigned int wbase = 0;
-                if (lane == 31 && total > 0) wbase = atomicAdd(counter + kCtrScene + sc, (unsigned int)total);
-                wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
-                if (done) {
-                    const int64_t cap = S.n_rays * (int64_t)K;  // the scene's slot region
-                    const int64_t first = (int64_t)wbase + (incl - nh);
-                    int keep = nh;
-                    if (first + nh > cap) {
-                        raise_status(SVLF_DEV_SAMPLE_OVERFLOW);
-                        keep = (int)max((int64_t)0, cap - first);
-                    }
-                    const int64_t base = S.ray_begin * K + first;  // global sample index
-                    ray_span[g] = make_int2((int)base, keep);
-                    const int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
-                    const int ss = smem_slots ? (int)blockDim.x : 1;
-                    for (int j = 0; j < keep; ++j) {
-                        const int4 h = slot[j * ss];
-                        const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
-                        reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
-                    }
-                    if (hits || t_io) {
-                        for (int j = 0; j < K; ++j) {
-                            const int4 h = j < nh ? slot[j * ss] : make_int4(-1, 0, 0, 0);
-                            if (hits) hits[g * K + j] = h.x;
-                            if (t_io)
-                                reinterpret_cast<float2 *>(t_io)[g * K + j] =
-                                    j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
-                                           : make_float2(0.f, 0.f);
-                        }
+                const int64_t base = S.ray_begin * K + first;  // global sample index
+                ray_span[g] = make_int2((int)base, keep);
+                const int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
+                for (int j = 0; j < keep; ++j) {
+                    const int4 h = slot[j * ss];
+                    const float tm = 0.5f * (__int_as_float(h.z) + __int_as_float(h.w));
+                    reinterpret_cast<int4 *>(samples)[base + j] = make_int4(h.x, (int)g, h.y, __float_as_int(tm));
+                }
+                if (hits || t_io) {
+                    for (int j = 0; j < K; ++j) {
+                        const int4 h = j < nh ? slot[j * ss] : make_int4(-1, 0, 0, 0);
+                        if (hits) hits[g * K + j] = h.x;
+                        if (t_io)
+                            reinterpret_cast<float2 *>(t_io)[g * K + j] =
+                                j < nh ? make_float2(__int_as_float(h.z), __int_as_float(h.w))
+                                       : make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -361,11 +386,12 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     // hit slots in shared memory up to K = 16 (32-64 KB per block of 256)
     const int smem_slots = T.K <= 16 ? 1 : 0;
     const size_t smem = smem_slots ? sizeof(int4) * (size_t)threads * T.K : 0;
+    const auto kernel = T.n > 1 ? trace_kernel<true> : trace_kernel<false>;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (T.total_chunks + threads / 32 - 1) / (threads / 32);
@@ -374,11 +400,13 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     if (blocks < 1) blocks = 1;
     // the per-ray hit slots live in the network-output buffer (total_rays*K x 16 B),
     // which the network kernels only write after this kernel is done
+    // lanes wait for the whole warp before a new chunk on coherent (large)
+    // launches, and refill at half a warp on small, incoherent ones
+    const int refill = tuning().trace_refill ? tuning().trace_refill : T.chunk_rays >= kTraceChunk ? 32 : 16;
     prof_begin("trace", s);
-    trace_kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples,
-                                                             reinterpret_cast<int4 *>(ws.outputs),
-                                                             ws.ray_span, ws.counter, hits, t_io,
-                                                             tuning().trace_budget, smem_slots);
+    kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples, reinterpret_cast<int4 *>(ws.outputs),
+                                                   ws.ray_span, ws.counter, hits, t_io, tuning().trace_budget,
+                                                   smem_slots, refill);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -64,7 +64,8 @@ class SceneDesc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("mlp_warpgroups", ctypes.c_int), ("mlp_epilogue_batch", ctypes.c_int),
-                ("trace_budget", ctypes.c_int), ("trace_block", ctypes.c_int)]
+                ("trace_budget", ctypes.c_int), ("trace_block", ctypes.c_int),
+                ("trace_refill", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -508,8 +509,9 @@ def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_m
     return D
 
 
-def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0):
-    t = Tuning(int(mlp_warpgroups), int(mlp_epilogue_batch), int(trace_budget), int(trace_block))
+def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0, trace_refill=0):
+    t = Tuning(int(mlp_warpgroups), int(mlp_epilogue_batch), int(trace_budget), int(trace_block),
+               int(trace_refill))
     _check("svlf_set_tuning", lib().svlf_set_tuning(ctypes.byref(t)))
 
 

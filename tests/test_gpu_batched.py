@@ -117,3 +117,25 @@ def test_batched_render_under_cuda_graph():
         torch.cuda.synchronize()
         for b, r in zip(batch, ref):
             torch.testing.assert_close(b.rgb, r, rtol=0, atol=1e-6)
+
+
+def test_batched_trace_refill_shapes_agree():
+    """Warps that mix rays of several chunks and scenes (refill below 32) give
+    the same images, bit for bit, as warps that finish a chunk first."""
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes(seed=41)
+    net = svlf.Network(32, 128, 3, svlf.BF16)
+    out = {}
+    try:
+        for refill in (32, 16, 1, 0):
+            svlf.svlf_set_tuning(trace_refill=refill, trace_budget=4)
+            batch = _batch(scenes)
+            svlf.svlf_render_rays_batched(batch, net, 8)
+            torch.cuda.synchronize()
+            assert svlf.svlf_get_device_status() == 0
+            out[refill] = [(b.rgb.clone(), b.depth.clone()) for b in batch]
+    finally:
+        svlf.svlf_set_tuning()
+    for refill in (16, 1, 0):
+        for (c0, d0), (c1, d1) in zip(out[32], out[refill]):
+            assert torch.equal(c0, c1) and torch.equal(d0, d1)

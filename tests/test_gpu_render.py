@@ -59,6 +59,26 @@ def test_hit_lists_bit_exact_tiny(tiny, K):
     assert svlf.svlf_get_device_status() == 0
 
 
+@pytest.mark.parametrize("refill", [1, 16])
+def test_hit_lists_independent_of_lane_refill(tiny, refill):
+    """Lanes refilled across chunk boundaries give the same hit lists."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(4)
+    rays = np.concatenate([tiny.rays, random_rays(rng, 20000)])
+    tree, f, p, r = gpu_inputs(tiny, rays=rays)
+    net = net_for(tiny, svlf.FP32)
+    try:
+        svlf.svlf_set_tuning(trace_refill=32)
+        _, _, h0, t0, _ = svlf.svlf_render_rays(tree, f, p, net, r, 8, want_hits=True)
+        svlf.svlf_set_tuning(trace_refill=refill, trace_budget=2)
+        _, _, h1, t1, _ = svlf.svlf_render_rays(tree, f, p, net, r, 8, want_hits=True)
+        torch.cuda.synchronize()
+    finally:
+        svlf.svlf_set_tuning()
+    assert torch.equal(h0, h1) and torch.equal(t0, t1)
+    assert svlf.svlf_get_device_status() == 0
+
+
 def test_render_fp32_matches_oracle_tiny(tiny):
     from paper_2205_07058_b300 import svlf
     rng = np.random.default_rng(4)
