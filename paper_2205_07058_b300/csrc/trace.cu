@@ -51,35 +51,45 @@ struct RayState {
     int n;  // 2^L
 };
 
-__device__ __forceinline__ float cross_t(const RayState &R, int a, int k) {
+__device__ __forceinline__ float cross_t1(int k, float h, float o, float rhi, float rlo) {
     float xh, xl;
-    two_sum((float)k * R.h, -R.o[a], xh, xl);  // k 2^-L exact; difference split exactly
-    return fmaf(xh, R.rhi[a], fmaf(xh, R.rlo[a], xl * R.rhi[a]));
+    two_sum((float)k * h, -o, xh, xl);  // k 2^-L exact; difference split exactly
+    return fmaf(xh, rhi, fmaf(xh, rlo, xl * rhi));
 }
 
-// Cell index along axis a occupied just after time t, searched in [lo, hi].
-// Fast path: pos = (o + t d) n is rounded once (FMA; n is a power of two), so
-// it is within 2^-24 (|o| + |t d|) n cells of the exact position at t, and a
-// crossing from cross_t is within 2^-23 |t| of the exact one, i.e. 2^-23
-// |t d| n cells. When pos is farther than that from every cell boundary
-// (eps below is 16x the sum, plus a floor for t = 0), the plane counts in the
-// loops below cannot change floor(pos), and they are skipped.
-__device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int lo, int hi) {
-    const float pos = fmaf(t, R.d[a], R.o[a]) * (float)R.n;
-    const float fl = floorf(fminf(fmaxf(pos, -1.0f), (float)R.n));
-    int k = (int)fl;
-    const float fr = pos - fl;
-    const float eps = (fabsf(R.o[a]) + fabsf(t * R.d[a]) + 0x1p-10f) * (float)R.n * 0x1p-19f;
-    if (k >= lo && k <= hi && fr > eps && fr < 1.0f - eps) return k;
+__device__ __forceinline__ float cross_t(const RayState &R, int a, int k) {
+    return cross_t1(k, R.h, R.o[a], R.rhi[a], R.rlo[a]);
+}
+
+// Cell index along axis a occupied just after time t, searched in [lo, hi],
+// by counting the planes whose crossing is <= t. (Kept inline: a call would
+// make the walk state spill around it.)
+__device__ __forceinline__ int cell_after_exact(float h, float o, float d, float rhi, float rlo, float t, int k,
+                                             int lo, int hi) {
     k = min(max(k, lo), hi);
-    if (R.d[a] > 0.f) {
-        for (int it = 0; it < 64 && k > lo && cross_t(R, a, k) > t; ++it) --k;
-        for (int it = 0; it < 64 && k < hi && cross_t(R, a, k + 1) <= t; ++it) ++k;
+    if (d > 0.f) {
+        for (int it = 0; it < 64 && k > lo && cross_t1(k, h, o, rhi, rlo) > t; ++it) --k;
+        for (int it = 0; it < 64 && k < hi && cross_t1(k + 1, h, o, rhi, rlo) <= t; ++it) ++k;
     } else {
-        for (int it = 0; it < 64 && k < hi && cross_t(R, a, k + 1) > t; ++it) ++k;
-        for (int it = 0; it < 64 && k > lo && cross_t(R, a, k) <= t; ++it) --k;
+        for (int it = 0; it < 64 && k < hi && cross_t1(k + 1, h, o, rhi, rlo) > t; ++it) ++k;
+        for (int it = 0; it < 64 && k > lo && cross_t1(k, h, o, rhi, rlo) <= t; ++it) --k;
     }
     return k;
+}
+
+// The same, with a fast path: pos = (o + t d) n is rounded once (FMA; n is a
+// power of two), so it is within 2^-24 (|o| + |t d|) n cells of the exact
+// position at t, and a crossing from cross_t is within 2^-23 |t| of the exact
+// one, i.e. 2^-23 |t d| n cells. `eps` (per ray, see walk_init) is at least
+// 16x the sum for every t of the walk; when pos is farther than that from
+// every cell boundary, the plane counts cannot change floor(pos).
+__device__ __forceinline__ int cell_after(const RayState &R, int a, float t, int lo, int hi, float eps) {
+    const float pos = fmaf(t, R.d[a], R.o[a]) * (float)R.n;
+    const float fl = floorf(fminf(fmaxf(pos, -1.0f), (float)R.n));
+    const int k = (int)fl;
+    const float fr = pos - fl;
+    if (k >= lo && k <= hi && fr > eps && fr < 1.0f - eps) return k;
+    return cell_after_exact(R.h, R.o[a], R.d[a], R.rhi[a], R.rlo[a], t, k, lo, hi);
 }
 
 // Traversal state of one ray, kept in registers across the rounds of the
@@ -88,6 +98,7 @@ struct Walk {
     RayState R;
     int c[3];        // current finest cell
     float t;         // entry t of the current cell
+    float eps;       // fast-path margin of cell_after, in cells (valid for t up to the cube exit)
     int nh;          // hits so far
     int steps;
     uint32_t cached;  // brick (level L-2) of the current cell
@@ -113,10 +124,14 @@ __device__ __forceinline__ bool walk_init(const OctreeView &T, Walk &w) {
         t1 = fminf(t1, fmaxf(ta, tb));
     }
     if (!(t1 - t0 > 0.f)) return false;
+    // margin for every t <= t1: (|o_a| + t |d_a| + 2^-10) n 2^-19 over the axes
+    const float om = fmaxf(fabsf(R.o[0]), fmaxf(fabsf(R.o[1]), fabsf(R.o[2])));
+    const float dm = fmaxf(fabsf(R.d[0]), fmaxf(fabsf(R.d[1]), fabsf(R.d[2])));
+    w.eps = (om + t1 * dm + 0x1p-10f) * (float)n * 0x1p-19f;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         w.c[a] = R.d[a] == 0.f ? min(max((int)floorf(R.o[a] * (float)n), 0), n - 1)
-                               : cell_after(R, a, t0, 0, n - 1);
+                               : cell_after(R, a, t0, 0, n - 1, w.eps);
     w.t = t0;
     w.nh = 0;
     w.steps = 0;
@@ -217,9 +232,9 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
             } else if (sz > 1) {
                 const int lo = R.d[a] > 0.f ? c[a] : B[a];
                 const int hi = R.d[a] > 0.f ? B[a] + sz - 1 : c[a];
-                c[a] = cell_after(R, a, tx, lo, hi);
+                c[a] = cell_after(R, a, tx, lo, hi, w.eps);
             }
-            out |= (c[a] < 0) | (c[a] >= n);
+            out |= (unsigned)c[a] >= (unsigned)n;
         }
         if (out) return true;
         w.t = tx;
@@ -241,9 +256,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // and scenes. Rays that miss the unit cube never enter the walk. Finished rays
 // write their samples to their scene's region, with one atomic per warp,
 // scene and round.
+#ifndef SVLF_TRACE_MIN_BLOCKS
+#define SVLF_TRACE_MIN_BLOCKS 4  // resident blocks of 256 per SM the register budget is sized for
+#endif
+
 // MULTI = false: a single-scene table (scene 0 is then addressed statically).
 template <bool MULTI>
-__global__ void __launch_bounds__(256, 4) trace_kernel(const __grid_constant__ SceneTable T,
+__global__ void __launch_bounds__(256, SVLF_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ SceneTable T,
                                                     Sample *__restrict__ samples,
                                                     int4 *__restrict__ slots,
                                                     int2 *__restrict__ ray_span,
