@@ -223,20 +223,37 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
             slot[w.nh * stride] = make_int4(rank, (int)packed, __float_as_int(w.t), __float_as_int(tx));
             if (++w.nh == K) return true;
         }
-        bool out = false;
+        // the cell after tx on every axis, without a branch per axis: exit axes
+        // step into the neighbouring block, the others stay inside the block at
+        // floor(pos) where that is provably exact (cell_after's fast path), else
+        // by plane counting (rare: one branch for the warp)
+        int slow = 0;
+        const float fn = (float)n;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (R.d[a] == 0.f) continue;
-            if (ta[a] <= tx) {
-                c[a] = R.d[a] > 0.f ? B[a] + sz : B[a] - 1;
-            } else if (sz > 1) {
-                const int lo = R.d[a] > 0.f ? c[a] : B[a];
-                const int hi = R.d[a] > 0.f ? B[a] + sz - 1 : c[a];
-                c[a] = cell_after(R, a, tx, lo, hi, w.eps);
-            }
-            out |= (unsigned)c[a] >= (unsigned)n;
+            const bool up = R.d[a] > 0.f;
+            const float p = fmaf(tx, R.d[a], R.o[a]) * fn;
+            const float fl = floorf(fminf(fmaxf(p, -1.0f), fn));
+            const int k = (int)fl;
+            const float fr = p - fl;
+            const int lo = up ? c[a] : B[a];
+            const int hi = up ? B[a] + sz - 1 : c[a];
+            const bool ok = k >= lo && k <= hi && fr > w.eps && fr < 1.0f - w.eps;
+            const bool ex = ta[a] <= tx;
+            const bool stay = !ex && sz > 1 && R.d[a] != 0.f;
+            slow |= (stay && !ok) ? (1 << a) : 0;
+            c[a] = ex ? (up ? B[a] + sz : B[a] - 1) : stay ? k : c[a];
         }
-        if (out) return true;
+        if (slow) {
+            // searched over the whole block: the plane counts cannot move below the
+            // (exact) cell held before the step, whose entry crossing is <= tx
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if ((slow >> a) & 1)
+                    c[a] = cell_after_exact(R.h, R.o[a], R.d[a], R.rhi[a], R.rlo[a], tx, c[a], B[a], B[a] + sz - 1);
+        }
+        if (((unsigned)c[0] >= (unsigned)n) | ((unsigned)c[1] >= (unsigned)n) | ((unsigned)c[2] >= (unsigned)n))
+            return true;
         w.t = tx;
     }
     return false;
