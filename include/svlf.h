@@ -111,6 +111,18 @@ int svlf_build_octree_from_depth(const float *rays, const float *depth, int64_t 
 /* Leaf coordinates in rank order. out_ijk: device, n_leaves x 3 int32. */
 int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *stream);
 
+/* The dense parent index the traversal reads (inspection and tests): one
+ * entry of two uint32 per level L-3 cell, (2^(L-3))^3 entries, x fastest.
+ * Entry = (node word, 0) where the cell's node exists (bits 24..31 = child
+ * mask, bits 0..23 = index of its first child brick); else (lo, hi), an
+ * empty box of level L-3 cells around the cell, lo = x | y << 8 | z << 16
+ * inclusive, hi exclusive, with bits 24..31 zero. The box is the largest
+ * empty octree block holding the cell, grown face by face (x, y, z; low face
+ * then high) while the added layer holds no leaf, until no face can grow.
+ * out: device, 2 x *n_entries uint32, or NULL to query *n_entries (host; 0
+ * for depths below 3 or an empty tree). */
+int svlf_octree_parent_index(svlf_octree tree, uint32_t *out, int64_t *n_entries, void *stream);
+
 /* Sizes: depth, leaves, internal node words, leaf bricks (host outputs, any
  * may be NULL). */
 int svlf_octree_info(svlf_octree tree, int *depth, int64_t *n_leaves, int64_t *n_nodes,

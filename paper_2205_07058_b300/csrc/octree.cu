@@ -34,6 +34,54 @@ static void unmorton3(uint64_t c, uint32_t &i, uint32_t &j, uint32_t &k) {
     }
 }
 
+// Occupied cells in the box [l, h) of a G^3 grid, from its summed-volume
+// table S ((G+1)^3 entries, x fastest): S(x, y, z) counts the occupied cells
+// whose coordinates are all below (x, y, z).
+__host__ __device__ inline int64_t svt_at(const int32_t *S, int64_t W, int x, int y, int z) {
+    return S[((int64_t)z * W + y) * W + x];
+}
+
+__host__ __device__ inline int64_t svt_count(const int32_t *S, int G, const int l[3], const int h[3]) {
+    const int64_t W = G + 1;
+    return svt_at(S, W, h[0], h[1], h[2]) - svt_at(S, W, l[0], h[1], h[2]) - svt_at(S, W, h[0], l[1], h[2]) -
+           svt_at(S, W, h[0], h[1], l[2]) + svt_at(S, W, l[0], l[1], h[2]) + svt_at(S, W, l[0], h[1], l[2]) +
+           svt_at(S, W, h[0], l[1], l[2]) - svt_at(S, W, l[0], l[1], l[2]);
+}
+
+// Grows the empty box [lo, hi) of a G^3 grid face by face (axes x, y, z in
+// turn, low face then high face) while the layer it would add is empty, until
+// no face can grow. Deterministic, so the host and the GPU builds agree. A ray
+// inside the box can jump to where it leaves the box: it meets no occupied
+// cell on the way.
+__host__ __device__ inline void grow_empty_box(const int32_t *S, int G, int lo[3], int hi[3]) {
+    for (int round = 0; round <= 6 * G; ++round) {
+        bool grown = false;
+        for (int a = 0; a < 3; ++a) {
+            for (int side = 0; side < 2; ++side) {
+                int l[3] = {lo[0], lo[1], lo[2]}, h[3] = {hi[0], hi[1], hi[2]};
+                if (side == 0) {
+                    if (lo[a] == 0) continue;
+                    l[a] = lo[a] - 1;
+                    h[a] = lo[a];
+                } else {
+                    if (hi[a] == G) continue;
+                    l[a] = hi[a];
+                    h[a] = hi[a] + 1;
+                }
+                if (svt_count(S, G, l, h) == 0) {
+                    if (side == 0) --lo[a]; else ++hi[a];
+                    grown = true;
+                }
+            }
+        }
+        if (!grown) break;
+    }
+}
+
+__host__ __device__ inline uint32_t pack_corner(const int v[3]) {
+    return (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16);
+}
+
 }  // namespace svlf
 
 using namespace svlf;
@@ -119,8 +167,10 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     // Dense index over the level L-3 cells (the parents of the bricks, 8^3
     // finest cells each), x fastest: the node word where that node exists,
     // else (mask byte 0) log2 of the edge, in finest cells, of the largest
-    // empty octree block that contains the cell. One load then answers what a
-    // descent from the root would: the cell's brick or its empty block.
+    // empty octree block that contains the cell; then each empty block is
+    // grown into a larger empty box (OctreeView::pgrid). One load then answers
+    // what a descent from the root would: the cell's brick or an empty region
+    // around it.
     std::vector<uint32_t> pgrid;
     const int pshift = n_levels > 0 ? depth - 3 : 0;
     if (n_levels > 0 && n_leaves > 0) {
@@ -150,6 +200,44 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
         }
     }
 
+    std::vector<uint2> pgrid2(pgrid.size());
+    if (!pgrid.empty()) {
+        const int G = 1 << pshift;
+        const int64_t W = G + 1;
+        std::vector<int32_t> S((size_t)(W * W * W), 0);
+        for (int z = 0; z < G; ++z)
+            for (int y = 0; y < G; ++y)
+                for (int x = 0; x < G; ++x) {
+                    const int64_t i = ((int64_t)z * G + y) * G + x;
+                    const int32_t o = (pgrid[(size_t)i] >> 24) ? 1 : 0;
+                    S[(size_t)(((z + 1) * W + y + 1) * W + x + 1)] =
+                        o + S[(size_t)(((z + 1) * W + y + 1) * W + x)] + S[(size_t)(((z + 1) * W + y) * W + x + 1)] +
+                        S[(size_t)((z * W + y + 1) * W + x + 1)] - S[(size_t)(((z + 1) * W + y) * W + x)] -
+                        S[(size_t)((z * W + y + 1) * W + x)] - S[(size_t)((z * W + y) * W + x + 1)] +
+                        S[(size_t)((z * W + y) * W + x)];
+                }
+        for (int z = 0; z < G; ++z)
+            for (int y = 0; y < G; ++y)
+                for (int x = 0; x < G; ++x) {
+                    const size_t i = (size_t)(((int64_t)z * G + y) * G + x);
+                    const uint32_t w = pgrid[i];
+                    if (w >> 24) {
+                        pgrid2[i] = make_uint2(w, 0u);
+                        continue;
+                    }
+                    const int e = 1 << ((int)(w & 31u) - 3);  // block edge in level L-3 cells
+                    int lo[3] = {x & ~(e - 1), y & ~(e - 1), z & ~(e - 1)};
+                    const size_t corner = (size_t)(((int64_t)lo[2] * G + lo[1]) * G + lo[0]);
+                    if (corner != i) {  // the block's corner comes first in x-fastest order
+                        pgrid2[i] = pgrid2[corner];
+                        continue;
+                    }
+                    int hi[3] = {lo[0] + e, lo[1] + e, lo[2] + e};
+                    grow_empty_box(S.data(), G, lo, hi);
+                    pgrid2[i] = make_uint2(pack_corner(lo), pack_corner(hi));
+                }
+    }
+
     svlf_octree_s *t = new (std::nothrow) svlf_octree_s;
     if (!t) return SVLF_ERR_CUDA;
     std::memset(t, 0, sizeof(*t));
@@ -173,7 +261,7 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     size_t nb_ijk = sizeof(int32_t) * rank_ijk.size();
     size_t nb_nodes = sizeof(uint32_t) * (nodes.size() + 1);
     size_t nb_bricks = sizeof(uint4) * (bricks.size() + 1);
-    size_t nb_pgrid = sizeof(uint32_t) * (pgrid.size() + 1);
+    size_t nb_pgrid = sizeof(uint2) * (pgrid2.size() + 1);
     ok = ok && cudaMalloc(&H.leaf_ijk_dev, nb_ijk > 0 ? nb_ijk : 16) == cudaSuccess;
     ok = ok && cudaMalloc(&H.pgrid_dev, nb_pgrid) == cudaSuccess;
     ok = ok && cudaMalloc(&H.nodes_dev, nb_nodes) == cudaSuccess;
@@ -187,8 +275,8 @@ extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, 
     if (ok && !bricks.empty())
         ok = cudaMemcpyAsync(H.bricks_dev, bricks.data(), sizeof(uint4) * bricks.size(),
                              cudaMemcpyHostToDevice, s) == cudaSuccess;
-    if (ok && !pgrid.empty())
-        ok = cudaMemcpyAsync(H.pgrid_dev, pgrid.data(), sizeof(uint32_t) * pgrid.size(),
+    if (ok && !pgrid2.empty())
+        ok = cudaMemcpyAsync(H.pgrid_dev, pgrid2.data(), sizeof(uint2) * pgrid2.size(),
                              cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
@@ -213,6 +301,18 @@ extern "C" int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *st
     size_t nb = sizeof(int32_t) * 3 * (size_t)tree->h.view.n_leaves;
     if (nb == 0) return SVLF_OK;
     return cudaMemcpyAsync(out_ijk, tree->h.leaf_ijk_dev, nb, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? SVLF_OK
+               : SVLF_ERR_CUDA;
+}
+
+extern "C" int svlf_octree_parent_index(svlf_octree tree, uint32_t *out, int64_t *n_entries, void *stream) {
+    if (!tree || !n_entries) return SVLF_ERR_ARG;
+    const OctreeView &v = tree->h.view;
+    const int64_t G = v.n_node_levels > 0 && !v.empty ? (int64_t)1 << v.pgrid_shift : 0;
+    *n_entries = G * G * G;
+    if (!out || *n_entries == 0) return SVLF_OK;
+    return cudaMemcpyAsync(out, tree->h.pgrid_dev, sizeof(uint2) * (size_t)*n_entries, cudaMemcpyDeviceToDevice,
                            (cudaStream_t)stream) == cudaSuccess
                ? SVLF_OK
                : SVLF_ERR_CUDA;
@@ -457,9 +557,10 @@ struct LevelPtrs {
 
 // Dense parent index: per level-(L-3) cell (x fastest), its node word, or (mask
 // 0) log2 of the edge of the largest empty block around it: the child, at
-// level l + 1, of its deepest existing ancestor l.
+// level l + 1, of its deepest existing ancestor l. (box_grow_kernel and
+// box_fill_kernel then turn the empty blocks into grown boxes.)
 __global__ void pgrid_kernel(const __grid_constant__ LevelPtrs lv, int L, const uint32_t *__restrict__ node_idx,
-                             const uint32_t *__restrict__ nodes, uint32_t off_top, uint32_t *__restrict__ pgrid) {
+                             const uint32_t *__restrict__ nodes, uint32_t off_top, uint2 *__restrict__ pgrid) {
     const int top = L - 3;
     const int64_t P = (int64_t)1 << top;
     const int64_t n = P * P * P;
@@ -476,7 +577,64 @@ __global__ void pgrid_kernel(const __grid_constant__ LevelPtrs lv, int L, const 
                     break;
                 }
         }
-        pgrid[i] = v;
+        pgrid[i] = make_uint2(v, 0u);
+    }
+}
+
+// Summed-volume table of the occupied parents (S zeroed before; (G+1)^3, x
+// fastest), one axis per launch: pass 0 writes the running count along x,
+// passes 1 and 2 accumulate it along y and then z in place.
+__global__ void svt_kernel(const uint2 *__restrict__ pgrid, int G, int pass, int32_t *__restrict__ S) {
+    const int64_t W = G + 1;
+    const int64_t rows = (int64_t)G * G;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(r % G), v = (int)(r / G);
+        int32_t acc = 0;
+        for (int k = 0; k < G; ++k) {
+            const int x = pass == 0 ? k : u;
+            const int y = pass == 0 ? u : pass == 1 ? k : v;
+            const int z = pass == 2 ? k : v;
+            const int64_t o = ((int64_t)(z + 1) * W + y + 1) * W + x + 1;
+            acc += pass == 0 ? ((pgrid[((int64_t)z * G + y) * G + x].x >> 24) ? 1 : 0) : S[o];
+            S[o] = acc;
+        }
+    }
+}
+
+// Empty parent cell -> the corner of its empty block, in level L-3 cells.
+__device__ __forceinline__ void empty_block_corner(uint32_t w, int G, int64_t i, int lo[3], int &e) {
+    e = 1 << ((int)(w & 31u) - 3);
+    lo[0] = (int)(i % G) & ~(e - 1);
+    lo[1] = (int)((i / G) % G) & ~(e - 1);
+    lo[2] = (int)(i / ((int64_t)G * G)) & ~(e - 1);
+}
+
+// The corner cell of each empty block grows the block into its empty box
+// (written to `boxes` at the corner's index; pgrid is left as it is).
+__global__ void box_grow_kernel(const uint2 *__restrict__ pgrid, int G, const int32_t *__restrict__ S,
+                                uint2 *__restrict__ boxes) {
+    const int64_t n = (int64_t)G * G * G;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = pgrid[i].x;
+        if (w >> 24) continue;
+        int lo[3], e;
+        empty_block_corner(w, G, i, lo, e);
+        if (((int64_t)lo[2] * G + lo[1]) * G + lo[0] != i) continue;
+        int hi[3] = {lo[0] + e, lo[1] + e, lo[2] + e};
+        grow_empty_box(S, G, lo, hi);
+        boxes[i] = make_uint2(pack_corner(lo), pack_corner(hi));
+    }
+}
+
+// Every cell of each empty block (its corner included) takes the block's box.
+__global__ void box_fill_kernel(uint2 *__restrict__ pgrid, int G, const uint2 *__restrict__ boxes) {
+    const int64_t n = (int64_t)G * G * G;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = pgrid[i].x;
+        if (w >> 24) continue;
+        int lo[3], e;
+        empty_block_corner(w, G, i, lo, e);
+        pgrid[i] = boxes[((int64_t)lo[2] * G + lo[1]) * G + lo[0]];
     }
 }
 
@@ -593,7 +751,13 @@ extern "C" int svlf_build_octree_from_depth(const float *rays, const float *dept
         bool ok = cudaMalloc(&H.leaf_ijk_dev, sizeof(int32_t) * 3 * ((size_t)n_leaves + 1)) == cudaSuccess;
         ok = ok && cudaMalloc(&H.bricks_dev, sizeof(uint4) * ((size_t)count[n_levels] + 1)) == cudaSuccess;
         ok = ok && cudaMalloc(&H.nodes_dev, sizeof(uint32_t) * ((size_t)n_nodes + 1)) == cudaSuccess;
-        ok = ok && cudaMalloc(&H.pgrid_dev, sizeof(uint32_t) * ((size_t)n_pgrid + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&H.pgrid_dev, sizeof(uint2) * ((size_t)n_pgrid + 1)) == cudaSuccess;
+        const int G = (int)P;
+        const size_t svt_bytes = sizeof(int32_t) * (size_t)((G + 1) * (G + 1) * (G + 1));
+        const bool want_boxes = n_levels > 0 && n_leaves > 0;
+        int32_t *svt = want_boxes ? (int32_t *)dalloc(svt_bytes) : nullptr;
+        uint2 *boxes = want_boxes ? (uint2 *)dalloc(sizeof(uint2) * (size_t)n_pgrid) : nullptr;
+        ok = ok && ((svt && boxes) || !want_boxes);
         if (!ok) {
             rc = SVLF_ERR_CUDA;
         } else {
@@ -611,6 +775,11 @@ extern "C" int svlf_build_octree_from_depth(const float *rays, const float *dept
                 for (int l = 0; l < n_levels; ++l) lv.flag[l] = flag[l];
                 pgrid_kernel<<<grid_for_n(n_pgrid), 256, 0, s>>>(lv, L, idx[n_levels - 1], H.nodes_dev,
                                                                  off[n_levels - 1], H.pgrid_dev);
+                if (cudaMemsetAsync(svt, 0, svt_bytes, s) != cudaSuccess) rc = SVLF_ERR_CUDA;
+                for (int pass = 0; pass < 3; ++pass)
+                    svt_kernel<<<grid_for_n((int64_t)G * G), 256, 0, s>>>(H.pgrid_dev, G, pass, svt);
+                box_grow_kernel<<<grid_for_n(n_pgrid), 256, 0, s>>>(H.pgrid_dev, G, svt, boxes);
+                box_fill_kernel<<<grid_for_n(n_pgrid), 256, 0, s>>>(H.pgrid_dev, G, boxes);
             }
             if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = SVLF_ERR_CUDA;
         }

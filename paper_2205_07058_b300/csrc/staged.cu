@@ -26,7 +26,7 @@ __device__ __forceinline__ int leaf_of_cell(const OctreeView &T, const int c[3])
     if (T.n_node_levels > 0) {
         const int ps = T.pgrid_shift;
         const uint32_t pidx = (uint32_t)(c[0] >> 3) | ((uint32_t)(c[1] >> 3) << ps) | ((uint32_t)(c[2] >> 3) << (2 * ps));
-        const uint32_t pw = __ldg(T.pgrid + pidx);
+        const uint32_t pw = __ldg(&T.pgrid[pidx].x);
         const uint32_t m = pw >> 24;
         const int oct = ((c[0] >> 2) & 1) | (((c[1] >> 2) & 1) << 1) | (((c[2] >> 2) & 1) << 2);
         if (!((m >> oct) & 1u)) return -1;

@@ -30,9 +30,13 @@ struct OctreeView {
     int n_nodes, n_bricks;
     const uint32_t *nodes;
     const uint4 *bricks;
-    // (2^(L-3))^3 words, x fastest: node word of each level L-3 cell, or, with
-    // a zero mask byte, log2 of the edge of the largest empty block holding it
-    const uint32_t *pgrid;
+    // (2^(L-3))^3 entries, x fastest, one per level L-3 cell (a parent of
+    // bricks). .x: the cell's node word where that node exists. Else .x has a
+    // zero mask byte and the low corner of an empty box around the cell, in
+    // level L-3 cells (x | y << 8 | z << 16), and .y its exclusive high
+    // corner: the largest empty octree block holding the cell, grown face by
+    // face while it stays empty (grow_empty_box)
+    const uint2 *pgrid;
     int pgrid_shift;    // L - 3 (0 when L = 2)
     int root_is_brick;  // depth 2: the root itself is the only brick
     int empty;          // no leaves
@@ -47,7 +51,7 @@ struct OctreeHost {
     int32_t *leaf_ijk_dev;  // n_leaves x 3, rank order
     uint32_t *nodes_dev;
     uint4 *bricks_dev;
-    uint32_t *pgrid_dev;
+    uint2 *pgrid_dev;
     int32_t *vtx_dev;       // n_leaves x 8 vertex ids, or null
 };
 

@@ -3,14 +3,16 @@
 // intersected voxels"; slab test of Sec. 4.2).
 //
 // Design (one ray per thread, stackless):
-//  * The ray is walked voxel-block by voxel-block. At every position the
-//    octree answers either the largest empty block containing the current
-//    finest cell, or the cell's brick (the 4^3 leaves under a level L-2 node,
-//    held as a 64-bit mask). A dense index over the level L-3 nodes (the
-//    parents of the bricks) gives that answer in one load instead of a
-//    descent from the root: the parent's node word, or the size of the empty
-//    block around it. The brick of the current cell stays cached in
-//    registers, so consecutive cells inside a brick cost no memory access.
+//  * The ray is walked region by region. At every position the octree
+//    answers either an empty region containing the current finest cell, or
+//    the cell's brick (the 4^3 leaves under a level L-2 node, held as a 64-bit
+//    mask). A dense index over the level L-3 nodes (the parents of the
+//    bricks) gives that answer in one load instead of a descent from the
+//    root: the parent's node word, or an empty box around it (the largest
+//    empty octree block holding it, grown face by face while it stays empty,
+//    which takes about a third fewer steps than the octree blocks alone). The
+//    brick of the current cell stays cached in registers, so consecutive
+//    cells inside a brick cost no memory access.
 //  * Plane crossings t = (k 2^-L - o) / d are evaluated without a division:
 //    k 2^-L - o is split exactly into hi + lo (TwoSum) and multiplied by 1/d
 //    held as a double-float (r_hi + r_lo, formed once per ray with an FMA
@@ -161,6 +163,7 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
         int sz_log = 0;
         bool leaf = false;
         int rank = -1;
+        uint32_t box_lo = 0, box_hi = 0;  // nonzero box_hi: an empty box around the parent (level L-3 cells)
         if (key == w.cached) TRACE_STAT(6, 1);
         if (key != w.cached) {
             int node = 0;  // depth 2: the root is the only brick
@@ -170,11 +173,14 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
                 // 0 <= c < 2^L here, so the index stays inside the (2^(L-3))^3 words
                 const uint32_t pidx = (uint32_t)(c[0] >> 3) | ((uint32_t)(c[1] >> 3) << ps) |
                                       ((uint32_t)(c[2] >> 3) << (2 * ps));
-                const uint32_t pw = __ldg(T.pgrid + pidx);
+                const uint2 pe = __ldg(T.pgrid + pidx);
+                const uint32_t pw = pe.x;
                 const uint32_t m = pw >> 24;
                 const int oct = ((c[0] >> 2) & 1) | (((c[1] >> 2) & 1) << 1) | (((c[2] >> 2) & 1) << 2);
                 if (!((m >> oct) & 1u)) {
-                    sz_log = m ? 2 : (int)(pw & 31u);  // empty brick, or the empty block around the parent
+                    sz_log = 2;  // empty brick (unless the whole parent is empty: its box below)
+                    box_lo = pw;
+                    box_hi = m ? 0u : pe.y;
                     found = false;
                 } else {
                     node = (int)(pw & 0xFFFFFFu) + __popc(m & ((1u << oct) - 1u));
@@ -207,15 +213,22 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
                 rank = w.bbase + __popcll(w.bmask & ((1ull << bit) - 1ull));
             }
         }
+        // the empty (or leaf) region the ray is in: [blo, bhi) per axis, finest cells
         const int sz = 1 << sz_log;
-        int B[3];
+        int blo[3], bhi[3];
         float ta[3];
         float tx = INFINITY;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            B[a] = c[a] & ~(sz - 1);
-            ta[a] = R.d[a] > 0.f ? cross_t(R, a, B[a] + sz)
-                  : R.d[a] < 0.f ? cross_t(R, a, B[a]) : INFINITY;
+            if (box_hi) {
+                blo[a] = (int)((box_lo >> (8 * a)) & 0xFFu) << 3;
+                bhi[a] = (int)((box_hi >> (8 * a)) & 0xFFu) << 3;
+            } else {
+                blo[a] = c[a] & ~(sz - 1);
+                bhi[a] = blo[a] + sz;
+            }
+            ta[a] = R.d[a] > 0.f ? cross_t(R, a, bhi[a])
+                  : R.d[a] < 0.f ? cross_t(R, a, blo[a]) : INFINITY;
             tx = fminf(tx, ta[a]);
         }
         if (leaf) {
@@ -236,13 +249,13 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
             const float fl = floorf(fminf(fmaxf(p, -1.0f), fn));
             const int k = (int)fl;
             const float fr = p - fl;
-            const int lo = up ? c[a] : B[a];
-            const int hi = up ? B[a] + sz - 1 : c[a];
+            const int lo = up ? c[a] : blo[a];
+            const int hi = up ? bhi[a] - 1 : c[a];
             const bool ok = k >= lo && k <= hi && fr > w.eps && fr < 1.0f - w.eps;
             const bool ex = ta[a] <= tx;
-            const bool stay = !ex && sz > 1 && R.d[a] != 0.f;
+            const bool stay = !ex && bhi[a] - blo[a] > 1 && R.d[a] != 0.f;
             slow |= (stay && !ok) ? (1 << a) : 0;
-            c[a] = ex ? (up ? B[a] + sz : B[a] - 1) : stay ? k : c[a];
+            c[a] = ex ? (up ? bhi[a] : blo[a] - 1) : stay ? k : c[a];
         }
         if (slow) {
             // searched over the whole block: the plane counts cannot move below the
@@ -250,7 +263,7 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 if ((slow >> a) & 1)
-                    c[a] = cell_after_exact(R.h, R.o[a], R.d[a], R.rhi[a], R.rlo[a], tx, c[a], B[a], B[a] + sz - 1);
+                    c[a] = cell_after_exact(R.h, R.o[a], R.d[a], R.rhi[a], R.rlo[a], tx, c[a], blo[a], bhi[a] - 1);
         }
         if (((unsigned)c[0] >= (unsigned)n) | ((unsigned)c[1] >= (unsigned)n) | ((unsigned)c[2] >= (unsigned)n))
             return true;

@@ -79,7 +79,8 @@ EXPORTS = [
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
-    "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_workspace_size_two_decoder",
+    "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_octree_parent_index",
+    "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
     "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth",
 ]
@@ -122,6 +123,7 @@ def lib():
     L.svlf_workspace_samples.argtypes = [vp, P(MlpDesc), i64, i32, P(i64), vp]
     L.svlf_octree_build_vertices.argtypes = [vp, P(i64), vp]
     L.svlf_octree_leaf_vertices.argtypes = [vp, vp, vp]
+    L.svlf_octree_parent_index.argtypes = [vp, vp, P(i64), vp]
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
     L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
                                                vp, vp, vp, vp, vp, sz, vp]
@@ -204,6 +206,17 @@ class Octree:
     def leaf_ijk(self, stream=None) -> torch.Tensor:
         out = torch.empty((self.n_leaves, 3), dtype=torch.int32, device="cuda")
         _check("svlf_octree_leaf_ijk", lib().svlf_octree_leaf_ijk(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def parent_index(self, stream=None) -> torch.Tensor:
+        """The dense parent index (n_entries x 2 int32 on the device; the uint32
+        words reinterpreted): node words, or empty boxes (lo, hi)."""
+        n = ctypes.c_int64()
+        _check("svlf_octree_parent_index", lib().svlf_octree_parent_index(self.handle, None, ctypes.byref(n), None))
+        out = torch.empty((n.value, 2), dtype=torch.int32, device="cuda")
+        if n.value:
+            _check("svlf_octree_parent_index", lib().svlf_octree_parent_index(self.handle, _ptr(out), ctypes.byref(n),
+                                                                               _stream(stream)))
         return out
 
     def build_vertices(self, stream=None) -> int:

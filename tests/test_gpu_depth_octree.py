@@ -43,6 +43,7 @@ def test_leaves_nodes_and_traversal(L, views, res):
     # the same structure as the host build of those leaves
     host = svlf.Octree(torch.from_numpy(ref.astype(np.int32)), L)
     assert tree.info() == host.info()
+    assert torch.equal(tree.parent_index(), host.parent_index())
     # hit lists on the GPU-built tree, bit-exact against the oracle's walk
     rng = np.random.default_rng(L)
     probe = np.concatenate([rays[rng.choice(rays.shape[0], min(4000, rays.shape[0]), replace=False)],
