@@ -587,8 +587,10 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                     for (int c0 = 0; c0 < H / 32; c0 += EPI) {
                         uint32_t v[EPI][32];
 #pragma unroll
-                        for (int u = 0; u < EPI; ++u) tc::tmem_ld32(tmem_row + (uint32_t)((c0 + u) * 32), v[u]);
-                        tc::tmem_wait_ld();
+                        if (EPI == 2)
+                            tc::tmem_ld64_wait(tmem_row + (uint32_t)(c0 * 32), reinterpret_cast<uint32_t(&)[64]>(v));
+                        else
+                            tc::tmem_ld32_wait(tmem_row + (uint32_t)(c0 * 32), reinterpret_cast<uint32_t(&)[32]>(v));
 #pragma unroll
                         for (int u = 0; u < EPI; ++u) {
                             const int c = c0 + u;
@@ -604,8 +606,7 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                     }
                 } else {
                     uint32_t v[4];
-                    tc::tmem_ld4(tmem_row, v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld4_wait(tmem_row, v);
                     if (sl < S_sc) {
                         const float o0 = __uint_as_float(v[0]) + b[0], o1 = __uint_as_float(v[1]) + b[1];
                         const float o2 = __uint_as_float(v[2]) + b[2], o3 = __uint_as_float(v[3]) + b[3];
@@ -863,9 +864,10 @@ __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev
     float zdot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int c = 0; c < F; c += 16) {
         uint32_t a[16], b[16];
-        tc::tmem_ld16(trow + (uint32_t)c, a);
-        if (MODE == 1) tc::tmem_ld16(trow + (uint32_t)(F + c), b);
-        tc::tmem_wait_ld();
+        if (MODE == 1)
+            tc::tmem_ld16x2_wait(trow + (uint32_t)c, trow + (uint32_t)(F + c), a, b);
+        else
+            tc::tmem_ld16_wait(trow + (uint32_t)c, a);
         if (!valid) continue;
         const int ne = min(16, F - c);
 #pragma unroll
@@ -1181,8 +1183,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
 #pragma unroll 1
                 for (int c = 0; c < kHp / 32; ++c) {
                     uint32_t v[32];
-                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld32_wait(tmem + lane_off + (uint32_t)(c * 32), v);
                     uint32_t p[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
@@ -1217,8 +1218,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
 #pragma unroll 1
                 for (int c = 0; c < kHp / 32; ++c) {
                     uint32_t v[32];
-                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld32_wait(tmem + lane_off + (uint32_t)(c * 32), v);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         uint4 *ptr = reinterpret_cast<uint4 *>(x + (c * 4 + q) * (kTcTile * 16) +
@@ -1284,8 +1284,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     const int F = md.F;
                     for (int c = 0; c < Fn; c += 16) {
                         uint32_t v[16];
-                        tc::tmem_ld16(tmem + lane_off + (uint32_t)c, v);
-                        tc::tmem_wait_ld();
+                        tc::tmem_ld16_wait(tmem + lane_off + (uint32_t)c, v);
                         for (int e = 0; e < 16 && c + e < F; ++e) stage[row * F + c + e] = __uint_as_float(v[e]) * ginv;
                     }
                     tc::fence_before_sync();
@@ -1320,8 +1319,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             // dW_out^T: lane = input feature k, columns = output j (< 4)
             if (P.with_out) {
                 uint32_t v[16];
-                tc::tmem_ld16(tmem + lane_off + P.col_dwout, v);
-                tc::tmem_wait_ld();
+                tc::tmem_ld16_wait(tmem + lane_off + P.col_dwout, v);
                 if (row < H) {
                     float *dW = dpar + md.w_off[nh];
                     for (int j = 0; j < md.out; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
@@ -1334,15 +1332,13 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 float *dW = dpar + md.w_off[l];
                 for (int c = 0; c < ncol; c += 16) {
                     uint32_t v[16];
-                    tc::tmem_ld16(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld16_wait(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
                     if (row < H)
                         for (int e = 0; e < 16; ++e)
                             if (c + e < in) atomicAdd(dW + row * in + c + e, __uint_as_float(v[e]) * ginv);
                 }
                 uint32_t v[4];
-                tc::tmem_ld4(tmem + lane_off + P.col_db[l], v);
-                tc::tmem_wait_ld();
+                tc::tmem_ld4_wait(tmem + lane_off + P.col_db[l], v);
                 if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
             }
         }

@@ -94,8 +94,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *__
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c = 0; c < N; c += 32) {
             uint32_t v[32];
-            tc::tmem_ld32(trow + c, v);
-            tc::tmem_wait_ld();
+            tc::tmem_ld32_wait(trow + c, v);
             for (int e = 0; e < 32 && c + e < N; ++e) D[tid * N + c + e] = __uint_as_float(v[e]);
         }
     }

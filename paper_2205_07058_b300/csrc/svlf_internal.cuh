@@ -175,27 +175,31 @@ void prof_end(cudaStream_t s);
 // arithmetic (Dekker 1971: exact TwoSum / TwoProduct with FMA): o - c exactly,
 // t_f = -(d.(o-c)) / |d|^2 and q = (o - c) + t_f d to about 1e-12 absolute.
 // The half chord and the normalisation are then plain float32.
+// Every product and sum is written with an explicit rounding (fmaf, __fmul_rn,
+// __fadd_rn), which the compiler never fuses or reassociates: each inlined
+// copy computes the same bits (TwoProduct also needs its product rounded on
+// its own, not fused into a following sum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = a * b;
+    p = __fmul_rn(a, b);
     e = fmaf(a, b, -p);
 }
 
 __device__ __forceinline__ void sphere_param(const float o[3], const float d[3], uint32_t cell,
                                              int depth, float p1[3], float p2[3]) {
     const float h = ldexpf(1.0f, -depth);
-    const float R = 0.8660254037844386f * h;
+    const float R = __fmul_rn(0.8660254037844386f, h);
     float oc_hi[3], oc_lo[3];
     {
         int ijk[3] = {(int)(cell & 1023u), (int)((cell >> 10) & 1023u), (int)((cell >> 20) & 1023u)};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float c = ((float)ijk[a] + 0.5f) * h;  // exact
+            const float c = __fmul_rn(__fadd_rn((float)ijk[a], 0.5f), h);  // exact
             two_sum(o[a], -c, oc_hi[a], oc_lo[a]);
         }
     }
@@ -207,11 +211,11 @@ __device__ __forceinline__ void sphere_param(const float o[3], const float d[3],
         two_prod(d[a], oc_hi[a], p, pe);
         two_sum(b_hi, p, s, se);
         b_hi = s;
-        b_lo += se + pe + d[a] * oc_lo[a];
+        b_lo = __fadd_rn(b_lo, fmaf(d[a], oc_lo[a], __fadd_rn(se, pe)));
         two_prod(d[a], d[a], p, pe);
         two_sum(dd_hi, p, s, se);
         dd_hi = s;
-        dd_lo += se + pe;
+        dd_lo = __fadd_rn(dd_lo, __fadd_rn(se, pe));
     }
     {
         float s, se;
@@ -220,33 +224,33 @@ __device__ __forceinline__ void sphere_param(const float o[3], const float d[3],
         b_lo = se;
     }
     // 1/dd = 1 + e + O(e^2) with e = 1 - dd (|e| ~ 1e-7 for a float32 unit vector)
-    const float e = (1.0f - dd_hi) - dd_lo;
+    const float e = __fsub_rn(__fsub_rn(1.0f, dd_hi), dd_lo);
     // t_f = -b (1 + e) as (tf_hi, tf_lo)
     const float tf_hi = -b_hi;
-    const float tf_lo = -b_lo - b_hi * e;
+    const float tf_lo = fmaf(-b_hi, e, -b_lo);
     float q[3];
     float qq = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float p, pe;
         two_prod(tf_hi, d[a], p, pe);
-        q[a] = (oc_hi[a] + p) + (oc_lo[a] + pe + tf_lo * d[a]);
+        q[a] = __fadd_rn(__fadd_rn(oc_hi[a], p), fmaf(tf_lo, d[a], __fadd_rn(oc_lo[a], pe)));
         qq = fmaf(q[a], q[a], qq);
     }
-    const float half = sqrtf(fmaxf(R * R - qq, 0.0f) * (1.0f + e));
+    const float half = sqrtf(__fmul_rn(fmaxf(fmaf(R, R, -qq), 0.0f), __fadd_rn(1.0f, e)));
     float n1 = 0.f, n2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        p1[a] = q[a] - half * d[a];
-        p2[a] = q[a] + half * d[a];
+        p1[a] = fmaf(-half, d[a], q[a]);
+        p2[a] = fmaf(half, d[a], q[a]);
         n1 = fmaf(p1[a], p1[a], n1);
         n2 = fmaf(p2[a], p2[a], n2);
     }
     const float i1 = rsqrtf(n1), i2 = rsqrtf(n2);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        p1[a] *= i1;
-        p2[a] *= i2;
+        p1[a] = __fmul_rn(p1[a], i1);
+        p2[a] = __fmul_rn(p2[a], i2);
     }
 }
 

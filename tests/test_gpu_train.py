@@ -112,5 +112,8 @@ def test_autograd_function_matches_direct_calls(tiny):
     svlf.svlf_render_rays_backward(tree, f.detach(), p.detach(), net, r, tiny.K, (0, 0, 0), d_rgb,
                                    d_depth, df, dp, ws)
     torch.cuda.synchronize()
-    torch.testing.assert_close(f.grad, df, rtol=1e-5, atol=1e-7)
-    torch.testing.assert_close(p.grad, dp, rtol=1e-5, atol=1e-7)
+    # both calls accumulate per-sample contributions with float atomics, in
+    # an order that differs from call to call: agreement to rounding of the
+    # sums, scaled by the gradient's magnitude
+    torch.testing.assert_close(f.grad, df, rtol=1e-5, atol=1e-6 * float(df.abs().max()))
+    torch.testing.assert_close(p.grad, dp, rtol=1e-5, atol=1e-6 * float(dp.abs().max()))
