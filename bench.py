@@ -242,9 +242,14 @@ KERNEL_SOURCES = {
 }
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per unit for `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+def workload_tag(views: int, res: int, precision: str) -> str:
+    """Name of the step workload in the profiles/ summaries."""
+    return f"render{views}x{res}_train2e{TRAIN_BATCH.bit_length() - 1}_{precision}"
+
+
+def ncu_traffic(kernel: str, tag: str):
+    """DRAM bytes per launch for `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source and on this workload; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -255,6 +260,8 @@ def ncu_traffic(kernel: str):
     if not ent or kernel not in KERNEL_SOURCES:
         return None
     if ent.get("source_hash") != kernel_source_hash(KERNEL_SOURCES[kernel]):
+        return None
+    if ent.get("workload") != tag:
         return None
     return ent
 
@@ -474,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
             bound, unit = "hbm", "GB/s"
             peak = peaks["hbm_gbs"]
             achieved = work / avg_s / 1e9
-        tr = ncu_traffic(dom)
+        tr = ncu_traffic(dom, workload_tag(args.views, args.res, args.precision))
         roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
                 "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
                                 else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
