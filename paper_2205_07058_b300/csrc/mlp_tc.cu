@@ -879,11 +879,17 @@ __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev
                 for (int e = 0; e < ne; ++e) zdot[v] = fmaf(z[e], __uint_as_float(a[e]) * ginv, zdot[v]);
             }
             if (dZ) {
-                float *dst = dZ + (int64_t)vid[v] * F + c;
-                for (int e = 0; e < ne; ++e) {
-                    float gv = wa[v] * __uint_as_float(a[e]);
-                    if (MODE == 1) gv = fmaf(wb[v], __uint_as_float(b[e]), gv);
-                    atomicAdd(dst + e, gv * ginv);
+                // 16-byte vector atomics (rows are F floats, F a multiple of 8)
+                float4 *dst = reinterpret_cast<float4 *>(dZ + (int64_t)vid[v] * F + c);
+                for (int e = 0; e < ne; e += 4) {
+                    float g[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float gv = wa[v] * __uint_as_float(a[e + q]);
+                        if (MODE == 1) gv = fmaf(wb[v], __uint_as_float(b[e + q]), gv);
+                        g[q] = gv * ginv;
+                    }
+                    atomicAdd(dst + (e >> 2), make_float4(g[0], g[1], g[2], g[3]));
                 }
             }
         }
