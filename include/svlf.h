@@ -350,8 +350,10 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
  * autotuner (paper_2205_07058_b300/autotune.py) times candidates on the
  * caller's workload and sets the best. They change speed, never results.
  *   mlp_warpgroups      tensor-core forward: tiles in flight per CTA, 1..4
- *   mlp_epilogue_batch  tensor-core forward: TMEM loads per wait, 1 or 2
- *                       (2 limits the CTA to 3 warpgroups)
+ *   mlp_epilogue_batch  tensor-core forward, hidden-layer epilogue: 1 = 32
+ *                       TMEM columns per load and wait, 2 = 64 (limits the
+ *                       CTA to 3 warpgroups), 3 = 16 with the next load in
+ *                       flight while a chunk is packed
  *   trace_budget        traversal steps between lane refills, 1..256
  *   trace_block         traversal threads per block, 128 or 256
  *   trace_refill        traversal: idle lanes a warp needs before it claims

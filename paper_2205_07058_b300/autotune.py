@@ -7,7 +7,7 @@ later run applies it without searching again. Shapes never change results.
 
 The search is coordinate-wise: traversal shape first (steps between lane
 refills, block size), then the tensor-core forward (tiles in flight per CTA,
-TMEM loads per wait).
+form of the hidden-layer epilogue).
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ import torch
 from . import svlf
 
 TRACE_CANDIDATES = [dict(trace_budget=b, trace_block=t) for b in (8, 16, 32, 64) for t in (128, 256)]
-MLP_CANDIDATES = [dict(mlp_warpgroups=w, mlp_epilogue_batch=e) for w in (2, 3, 4) for e in (1, 2)
+MLP_CANDIDATES = [dict(mlp_warpgroups=w, mlp_epilogue_batch=e) for w in (2, 3, 4) for e in (1, 2, 3)
                   if not (e == 2 and w > 3)]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "svlf_autotune.json")

@@ -375,7 +375,7 @@ extern "C" int svlf_set_tuning(const svlf_tuning *t) {
     svlf_tuning v = *t;
     if (v.mlp_warpgroups < 0 || v.mlp_warpgroups > 4) return SVLF_ERR_ARG;
     if (v.mlp_epilogue_batch == 0) v.mlp_epilogue_batch = 1;
-    if (v.mlp_epilogue_batch != 1 && v.mlp_epilogue_batch != 2) return SVLF_ERR_ARG;
+    if (v.mlp_epilogue_batch < 1 || v.mlp_epilogue_batch > 3) return SVLF_ERR_ARG;
     if (v.trace_budget == 0) v.trace_budget = 16;
     if (v.trace_budget < 1 || v.trace_budget > 256) return SVLF_ERR_ARG;
     if (v.trace_block == 0) v.trace_block = 256;

@@ -225,30 +225,44 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
     int kb = 0;
     if (valid) {
         if (leaf_out) *leaf_out = sm.leaf;
+        // every load of the row is issued before the first use (up to 128 bytes of
+        // features per batch, F <= 32 float32 or F <= 64 bfloat16 in one batch), so
+        // the row costs one memory latency, not one per chunk
         const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
         const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
-        if (feat_bf16) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const __nv_bfloat16 *>(feats) + (int64_t)sm.leaf * F);
-            for (int q = 0; q < F / 8; ++q, ++kb) {
-                uint4 v = __ldg(src + q);
-                if (fp16) {
-                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-                    uint32_t o[4];
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(feats) +
+                                                           (int64_t)sm.leaf * F * (feat_bf16 ? 2 : 4));
+        const int nq = feat_bf16 ? F / 8 : F / 4;  // 16-byte loads in the row
+        for (int q0 = 0; q0 < nq; q0 += 8) {
+            uint4 buf[8];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        o[e] = tc::pack2(__uint_as_float(w[e] << 16), __uint_as_float(w[e] & 0xFFFF0000u), true);
-                    v = make_uint4(o[0], o[1], o[2], o[3]);
+            for (int q = 0; q < 8; ++q)
+                if (q0 + q < nq) buf[q] = __ldg(src + q0 + q);
+            if (feat_bf16) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q0 + q >= nq) break;
+                    uint4 v = buf[q];
+                    if (fp16) {
+                        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                        uint32_t o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            o[e] = tc::pack2(__uint_as_float(w[e] << 16), __uint_as_float(w[e] & 0xFFFF0000u), true);
+                        v = make_uint4(o[0], o[1], o[2], o[3]);
+                    }
+                    st_chunk(abuf, row, kb++, v.x, v.y, v.z, v.w);
                 }
-                st_chunk(abuf, row, kb, v.x, v.y, v.z, v.w);
-            }
-        } else {
-            const float4 *src = reinterpret_cast<const float4 *>(
-                reinterpret_cast<const float *>(feats) + (int64_t)sm.leaf * F);
-            for (int q = 0; q < F / 8; ++q, ++kb) {
-                const float4 a = __ldg(src + 2 * q), b = __ldg(src + 2 * q + 1);
-                st_chunk(abuf, row, kb, tc::pack2(a.x, a.y, fp16), tc::pack2(a.z, a.w, fp16),
-                         tc::pack2(b.x, b.y, fp16), tc::pack2(b.z, b.w, fp16));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q += 2) {
+                    if (q0 + q >= nq) break;
+                    const uint4 a = buf[q], b = buf[q + 1];
+                    st_chunk(abuf, row, kb++, tc::pack2(__uint_as_float(a.x), __uint_as_float(a.y), fp16),
+                             tc::pack2(__uint_as_float(a.z), __uint_as_float(a.w), fp16),
+                             tc::pack2(__uint_as_float(b.x), __uint_as_float(b.y), fp16),
+                             tc::pack2(__uint_as_float(b.z), __uint_as_float(b.w), fp16));
+                }
             }
         }
         const float o[3] = {ra.x, ra.y, rb.x};
@@ -430,11 +444,22 @@ __device__ __forceinline__ void prefetch_gather(const Sample &r, const void *fea
     prefetch_l2(ray + 5);
 }
 
-// EPI = TMEM loads (of 32 columns) issued before each wait in the hidden-layer
-// epilogue: 1 keeps registers low enough for 4 warpgroups, 2 overlaps the
-// loads and needs the register budget of at most 3 warpgroups.
+// ReLU, 16-bit packing and A-operand store of 16 accumulator columns (two
+// 8-column chunks starting at chunk kb).
+__device__ __forceinline__ void epi_chunk16(const uint32_t (&v)[16], uint8_t *abuf, int row, int kb, int fp16) {
+    uint32_t p[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) p[e] = tc::relu_pack2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]), fp16);
+    st_chunk(abuf, row, kb, p[0], p[1], p[2], p[3]);
+    st_chunk(abuf, row, kb + 1, p[4], p[5], p[6], p[7]);
+}
+
+// EPI = hidden-layer epilogue form: 1 loads 32 TMEM columns per wait (registers
+// low enough for 4 warpgroups); 2 loads 64 per wait (at most 3 warpgroups);
+// 3 loads 16 columns at a time with the next load in flight while a chunk is
+// packed.
 template <int H, int EPI, int MODE>
-__global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
+__global__ void __launch_bounds__(EPI == 2 ? 384 : 512, 1)
     mlp_forward_tc_kernel(const __grid_constant__ SceneTable T, const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
@@ -583,16 +608,31 @@ __global__ void __launch_bounds__(EPI == 1 ? 512 : 384, 1)
                 const float *b = bias + P.lay.bias_l[l];
                 if (l + 1 < P.lay.n_layers) {
                     // hidden layer epilogue: ReLU of (bias + W x) -> 16-bit A operand of the next layer
+                    if (EPI == 3) {
+                        // 16-column chunks, the next chunk's TMEM load in flight while one is packed
+                        uint32_t va[16], vb[16];
+                        tc::tmem_ld16_async(tmem_row, va);
+                        tc::tmem_wait_ld16(va);
 #pragma unroll
-                    for (int c0 = 0; c0 < H / 32; c0 += EPI) {
-                        uint32_t v[EPI][32];
+                        for (int c = 0; c < H / 16; c += 2) {
+                            tc::tmem_ld16_async(tmem_row + (uint32_t)((c + 1) * 16), vb);
+                            epi_chunk16(va, abuf, row, 2 * c, P.fp16);
+                            tc::tmem_wait_ld16(vb);
+                            if (c + 2 < H / 16) tc::tmem_ld16_async(tmem_row + (uint32_t)((c + 2) * 16), va);
+                            epi_chunk16(vb, abuf, row, 2 * c + 2, P.fp16);
+                            if (c + 2 < H / 16) tc::tmem_wait_ld16(va);
+                        }
+                    }
+#pragma unroll
+                    for (int c0 = 0; EPI != 3 && c0 < H / 32; c0 += EPI) {
+                        uint32_t v[EPI == 2 ? 2 : 1][32];
 #pragma unroll
                         if (EPI == 2)
                             tc::tmem_ld64_wait(tmem_row + (uint32_t)(c0 * 32), reinterpret_cast<uint32_t(&)[64]>(v));
                         else
                             tc::tmem_ld32_wait(tmem_row + (uint32_t)(c0 * 32), reinterpret_cast<uint32_t(&)[32]>(v));
 #pragma unroll
-                        for (int u = 0; u < EPI; ++u) {
+                        for (int u = 0; u < (EPI == 2 ? 2 : 1); ++u) {
                             const int c = c0 + u;
                             uint32_t p[16];
 #pragma unroll
@@ -698,6 +738,7 @@ int launch_mlp_forward_tc(const MlpDims &md, int precision, int fb, const SceneT
     if (mode == 1) return fwd_tc<kHp, 1, 1>(T, P, md, P.lay, s, tu.mlp_warpgroups);
     if (mode == 2) return fwd_tc<kHp, 1, 2>(T, P, md, P.lay, s, tu.mlp_warpgroups);
     if (tu.mlp_epilogue_batch == 2) return fwd_tc<kHp, 2, 0>(T, P, md, P.lay, s, tu.mlp_warpgroups);
+    if (tu.mlp_epilogue_batch == 3) return fwd_tc<kHp, 3, 0>(T, P, md, P.lay, s, tu.mlp_warpgroups);
     return fwd_tc<kHp, 1, 0>(T, P, md, P.lay, s, tu.mlp_warpgroups);
 }
 
@@ -1316,7 +1357,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             }
             if (!aborted) ++tiles_done;
         }
-        // ---- flush this scene's TMEM gradient accumulators (one atomic per element)
+        // ---- flush this scene's TMEM gradient accumulators (one atomic per element, or per 4
+        // where a row is 16-byte aligned)
         __syncthreads();
         tc::fence_after_sync();
         if (!aborted && tiles_done > 0 && P.want_params) {
@@ -1339,9 +1381,19 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 for (int c = 0; c < ncol; c += 16) {
                     uint32_t v[16];
                     tc::tmem_ld16_wait(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
-                    if (row < H)
-                        for (int e = 0; e < 16; ++e)
-                            if (c + e < in) atomicAdd(dW + row * in + c + e, __uint_as_float(v[e]) * ginv);
+                    if (row < H) {
+                        float *dst = dW + row * in + c;
+                        for (int e = 0; e < 16; e += 4) {
+                            if (c + e + 4 <= in && ((uintptr_t)(dst + e) & 15u) == 0) {  // 16-byte vector atomic
+                                atomicAdd(reinterpret_cast<float4 *>(dst + e),
+                                          make_float4(__uint_as_float(v[e]) * ginv, __uint_as_float(v[e + 1]) * ginv,
+                                                      __uint_as_float(v[e + 2]) * ginv, __uint_as_float(v[e + 3]) * ginv));
+                            } else {
+                                for (int q = e; q < e + 4; ++q)
+                                    if (c + q < in) atomicAdd(dst + q, __uint_as_float(v[q]) * ginv);
+                            }
+                        }
+                    }
                 }
                 uint32_t v[4];
                 tc::tmem_ld4_wait(tmem + lane_off + P.col_db[l], v);

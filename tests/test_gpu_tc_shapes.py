@@ -40,18 +40,19 @@ def test_launch_shapes_agree_and_match_oracle(scene, prec, F, H, nh):
     net = svlf.Network(F, H, nh, svlf.PRECISIONS[prec])
     K = 6
     out = {}
+    shapes = [(4, 1), (2, 1), (3, 1), (4, 3), (3, 2)]  # (warpgroups, epilogue form)
     try:
-        for wgs in (4, 2, 3):
-            svlf.svlf_set_tuning(mlp_warpgroups=wgs)
+        for wgs, epi in shapes:
+            svlf.svlf_set_tuning(mlp_warpgroups=wgs, mlp_epilogue_batch=epi)
             rgb, depth, _, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, K)
             torch.cuda.synchronize()
             assert svlf.svlf_get_device_status() == 0
-            out[wgs] = (rgb.cpu().numpy(), depth.cpu().numpy())
+            out[(wgs, epi)] = (rgb.cpu().numpy(), depth.cpu().numpy())
     finally:
         svlf.svlf_set_tuning()
-    for wgs in (2, 3):
-        assert np.array_equal(out[wgs][0], out[4][0]) and np.array_equal(out[wgs][1], out[4][1])
-    rgb, depth = out[4]
+    for key in shapes[1:]:
+        assert np.array_equal(out[key][0], out[shapes[0]][0]) and np.array_equal(out[key][1], out[shapes[0]][1])
+    rgb, depth = out[shapes[0]]
     sample = np.random.default_rng(5).choice(rays.shape[0], 4000, replace=False)
     ref = O.render(O.build_octree(sc.leaf_ijk, sc.depth), feats, params, O.layer_dims(F, H, nh),
                    rays[sample], K, bf16=prec)
