@@ -331,10 +331,10 @@ def run_ours(args, rank, world, local_rank):
     step_no = [0]
     ev = {}
 
-    def render_phase():
+    def render_phase(rays=rays, rgb=rgb, depth=depth):
         svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
 
-    def train_phase():
+    def train_phase(trays=trays, loss=loss):
         step_no[0] += 1
         g_feat.zero_()
         g_par.zero_()
@@ -402,45 +402,83 @@ def run_ours(args, rank, world, local_rank):
     rays_per_step = N + (0 if args.render_only else NT)
     value = job_value(rays_per_step, world, args.steps, t_max)
 
-    # ---- end-to-end through host buffers (H2D of the step's inputs, D2H of its results)
+    # ---- end-to-end through host buffers: every step copies its inputs in from
+    # pinned host memory and its results out. Steps are pipelined over two sets of
+    # device buffers and three streams: step k+1's inputs go in and step k-1's
+    # results come out (the link is full duplex) while step k computes.
     e2e = None
     if not args.no_e2e and not args.render_only:
         h_rays = torch.from_numpy(W["render_rays"]).pin_memory()
         h_trays = torch.from_numpy(W["train_rays"]).pin_memory()
         h_tgt = torch.cat([rgb_t.cpu(), depth_t.cpu()[:, None], mask.cpu()[:, None]], dim=1).contiguous().pin_memory()
-        d_tgt = torch.empty(h_tgt.shape, device=dev)
-        h_rgb = torch.empty((N, 3)).pin_memory()
-        h_depth = torch.empty((N,)).pin_memory()
-        h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        sets = []
+        for _ in range(2):
+            sets.append(dict(rays=torch.empty_like(rays), trays=torch.empty_like(trays),
+                             tgt=torch.empty(h_tgt.shape, device=dev), rgb=torch.empty_like(rgb),
+                             depth=torch.empty_like(depth), loss=torch.zeros_like(loss),
+                             h_rgb=torch.empty((N, 3)).pin_memory(), h_depth=torch.empty((N,)).pin_memory(),
+                             h_loss=torch.empty(1, dtype=torch.float64).pin_memory(),
+                             in_ready=torch.cuda.Event(), used=torch.cuda.Event(), done=torch.cuda.Event(),
+                             copied=torch.cuda.Event()))
         h2d = h_rays.numel() * 4 + h_trays.numel() * 4 + h_tgt.numel() * 4
-        d2h = h_rgb.numel() * 4 + h_depth.numel() * 4 + 8
+        d2h = sets[0]["h_rgb"].numel() * 4 + sets[0]["h_depth"].numel() * 4 + 8
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        for b in sets:  # every buffer set starts free
+            b["used"].record(stream)
+            b["copied"].record(stream)
 
-        def e2e_step():
-            rays.copy_(h_rays, non_blocking=True)
-            trays.copy_(h_trays, non_blocking=True)
-            d_tgt.copy_(h_tgt, non_blocking=True)
-            rgb_t.copy_(d_tgt[:, :3])
-            depth_t.copy_(d_tgt[:, 3])
-            mask.copy_(d_tgt[:, 4])
-            step()
-            h_rgb.copy_(rgb, non_blocking=True)
-            h_depth.copy_(depth, non_blocking=True)
-            h_loss.copy_(loss, non_blocking=True)
+        def copy_in(b):
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(b["used"])  # the step that last read this set is done with it
+                b["rays"].copy_(h_rays, non_blocking=True)
+                b["trays"].copy_(h_trays, non_blocking=True)
+                b["tgt"].copy_(h_tgt, non_blocking=True)
+                b["in_ready"].record(s_in)
 
-        e2e_step()
+        def compute(b):
+            stream.wait_event(b["in_ready"])
+            stream.wait_event(b["copied"])  # the previous results of this set have left the device
+            rgb_t.copy_(b["tgt"][:, :3])
+            depth_t.copy_(b["tgt"][:, 3])
+            mask.copy_(b["tgt"][:, 4])
+            render_phase(b["rays"], b["rgb"], b["depth"])
+            train_phase(b["trays"], b["loss"])
+            b["used"].record(stream)
+            b["done"].record(stream)
+
+        def copy_out(b):
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(b["done"])
+                b["h_rgb"].copy_(b["rgb"], non_blocking=True)
+                b["h_depth"].copy_(b["depth"], non_blocking=True)
+                b["h_loss"].copy_(b["loss"], non_blocking=True)
+                b["copied"].record(s_out)
+
+        def e2e_run(n):
+            copy_in(sets[0])
+            for k in range(n):
+                if k + 1 < n:
+                    copy_in(sets[(k + 1) % 2])
+                compute(sets[k % 2])
+                copy_out(sets[k % 2])
+
+        e2e_run(2)
         torch.cuda.synchronize()
         barrier()
         a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        b.record(stream)
+        s_in.wait_stream(stream)  # no copy starts before the timed region
+        e2e_run(args.steps)
+        for st in (s_in, s_out):
+            stream.wait_stream(st)
+        b_.record(stream)
         torch.cuda.synchronize()
         barrier()
-        te = max_over_ranks(a.elapsed_time(b), dist, dev)
+        te = max_over_ranks(a.elapsed_time(b_), dist, dev)
         e2e = {"value": job_value(rays_per_step, world, args.steps, te), "unit": "rays/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "pipelined": "2 buffer sets; H2D of step k+1 and D2H of step k-1 overlap step k"}
 
     # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
