@@ -487,45 +487,51 @@ def run_ours(args, rank, world, local_rank):
                   for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
     dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
     roof = None
-    if dom:
-        launches, ms = kstats[dom]
+    S_r, S_t = n_samples_render, n_samples_train
+    tag = workload_tag(args.views, args.res, args.precision)
+
+    def kernel_roofline(name):
+        """Algorithmic work per launch (launches alternate render / training
+        where a kernel runs in both) over the live average launch time."""
+        launches, ms = kstats[name]
         avg_s = ms / launches / 1e3
-        S_r, S_t = n_samples_render, n_samples_train
-        if dom == "mlp_forward_tc":
-            # one launch per render and one per training forward, alternating
-            work = (S_r + S_t) * fps / 2.0
-            bound, unit = "tensor", "TFLOP/s"
-            peak = peaks.get("bf16_tflops_sustained", 1400.0)
-            achieved = work / avg_s / 1e12
-        elif dom == "mlp_backward_tc":
-            work = S_t * 3.0 * fps
-            bound, unit = "tensor", "TFLOP/s"
-            peak = peaks.get("bf16_tflops_sustained", 1400.0)
-            achieved = work / avg_s / 1e12
-        elif dom in ("mlp_forward_f32", "mlp_backward_f32"):
-            mult = 1.0 if dom == "mlp_forward_f32" else 3.0
-            work = ((S_r + S_t) / 2.0 if dom == "mlp_forward_f32" else S_t) * mult * fps
+        tensor_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        if name == "mlp_forward_tc":
+            work, bound, unit, peak = (S_r + S_t) * fps / 2.0, "tensor", "TFLOP/s", tensor_peak
+        elif name == "mlp_backward_tc":
+            work, bound, unit, peak = S_t * 3.0 * fps, "tensor", "TFLOP/s", tensor_peak
+        elif name in ("mlp_forward_f32", "mlp_backward_f32"):
+            mult = 1.0 if name == "mlp_forward_f32" else 3.0
+            work = ((S_r + S_t) / 2.0 if name == "mlp_forward_f32" else S_t) * mult * fps
             bound, unit = "alu", "TFLOP/s"
             peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-            achieved = work / avg_s / 1e12
-        elif dom == "adam":
+        elif name == "adam":
             n_par = feats.numel() + params.numel()
-            work = n_par * 28.0 / 2.0  # two launches per step (features, network)
-            bound, unit = "hbm", "GB/s"
-            peak = peaks["hbm_gbs"]
-            achieved = work / avg_s / 1e9
-        else:  # trace / composite: bytes of their own inputs and outputs
-            work = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0
-            bound, unit = "hbm", "GB/s"
-            peak = peaks["hbm_gbs"]
-            achieved = work / avg_s / 1e9
-        tr = ncu_traffic(dom, workload_tag(args.views, args.res, args.precision))
-        roof = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+            work, bound, unit, peak = n_par * 28.0 / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]  # features, network
+        elif name == "trace":  # ray in (24 B), span out (8 B), a 16-byte record per sample
+            work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+        elif name == "composite":  # span in, colour + depth out (16 B) per ray; record + output per sample
+            work, bound, unit, peak = ((N + NT) * 24.0 + (S_r + S_t) * 32.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+        else:
+            return None
+        achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
+        tr = ncu_traffic(name, tag)
+        return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
                 "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
                                 else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
                 "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": tr["bytes_per_launch"] if tr else None,
                 "avg_launch_ms": round(ms / launches, 4)}
+
+    if dom:
+        roof = kernel_roofline(dom)
+    # the same for every kernel whose algorithmic work is defined (each row of the path)
+    kernel_rooflines = {}
+    for k in kstats:
+        r = kernel_roofline(k)
+        if r is not None:
+            kernel_rooflines[k] = {key: r[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic",
+                                                         "avg_launch_ms")}
 
     gpu_launches = int(sum(v[0] for v in kstats.values()))
     out = None
@@ -547,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
             "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
             "samples_per_step": {"render": n_samples_render, "train": n_samples_train},
             "e2e": e2e, "gpu_launches": gpu_launches, "kernels": per_kernel,
-            "roofline": roof, "clocks": clk, "device_status": status,
+            "roofline": roof, "kernel_rooflines": kernel_rooflines, "clocks": clk, "device_status": status,
         }
     if dist is not None:
         dist.destroy_process_group()
