@@ -366,6 +366,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # FP32 SIMT roofline denominator: this GPU's measured FMA rate
+    ffma_tf = svlf.svlf_measure_ffma_tflops() if "fp32" in (args.precision, args.train_precision) else None
     n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
     n_samples_train = 0 if args.render_only else svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
     loss_first = None
@@ -504,7 +506,7 @@ def run_ours(args, rank, world, local_rank):
             mult = 1.0 if name == "mlp_forward_f32" else 3.0
             work = ((S_r + S_t) / 2.0 if name == "mlp_forward_f32" else S_t) * mult * fps
             bound, unit = "alu", "TFLOP/s"
-            peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+            peak = round(ffma_tf, 3) if ffma_tf else 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
         elif name == "adam":
             n_par = feats.numel() + params.numel()
             work, bound, unit, peak = n_par * 28.0 / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]  # features, network
@@ -518,6 +520,7 @@ def run_ours(args, rank, world, local_rank):
         tr = ncu_traffic(name, tag)
         return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
                 "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
+                                else "measured in this run: float32 FMA kernel (svlf_selftest_ffma)" if ffma_tf
                                 else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
                 "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": tr["bytes_per_launch"] if tr else None,
@@ -603,6 +606,20 @@ def cpu_sample_desc():
             f"training rays (teacher targets from the oracle) with Adam over all 54 M parameters, per step")
 
 
+def oracle_render_rate(W, tree_o, threads, n=1024):
+    """Render-only oracle rays/s on `n` random render rays with `threads` host threads."""
+    from oracle import oracle as O
+    full = O.max_threads()
+    O.set_threads(threads)
+    try:
+        rr = W["render_rays"][np.random.default_rng(777).choice(W["render_rays"].shape[0], n, replace=False)]
+        t0 = time.perf_counter()
+        O.render(tree_o, W["feats"], W["params"], O.layer_dims(FEAT, HIDDEN, N_HIDDEN), rr, K_HITS)
+        return round(n / (time.perf_counter() - t0), 2)
+    finally:
+        O.set_threads(full)
+
+
 def cpu_baseline(W, steps=2):
     from oracle import oracle as O
     tree_o, st = oracle_setup(W)
@@ -613,8 +630,12 @@ def cpu_baseline(W, steps=2):
     for _ in range(steps):
         rays += oracle_step(W, tree_o, rng, st)
     dt = time.perf_counter() - t0
-    return {"value": round(rays / dt, 2), "unit": "rays/s", "cores": O.max_threads(), "kind": "oracle",
-            "sample": cpu_sample_desc() + f"; {steps} steps timed after 1 untimed"}
+    cores = O.max_threads()
+    return {"value": round(rays / dt, 2), "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": cpu_sample_desc() + f"; {steps} steps timed after 1 untimed",
+            "render_only": {"rays_per_s_all_threads": oracle_render_rate(W, tree_o, cores),
+                            "rays_per_s_1_thread": oracle_render_rate(W, tree_o, 1),
+                            "sample": "1024 random render rays"}}
 
 
 def run_reference(args, rank, world):

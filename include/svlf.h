@@ -405,6 +405,15 @@ int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc *mlp, int6
 int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int K,
                       int a_mn_major, int b_mn_major, int bf16, int flags, void *stream);
 
+/* Measurement aid, not part of the rendering method: a float32 FMA
+ * throughput kernel, the denominator of the FP32 SIMT network's roofline.
+ * Launches one grid of `blocks` x 256 threads; each thread runs `iters`
+ * rounds of 16 independent fmaf chains (32 flop per round), so the launch
+ * does blocks x 256 x iters x 32 flop; the caller times it on `stream`.
+ * out: device, `blocks` floats (written only to keep the work live).
+ * Errors: SVLF_ERR_ARG for blocks < 1 or iters < 1. */
+int svlf_selftest_ffma(float *out, int blocks, int64_t iters, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -127,3 +127,26 @@ extern "C" int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D,
                                                                  b_mn_major, bf16, flags);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------- FP32 FMA rate
+namespace svlf {
+__global__ void __launch_bounds__(256) ffma_kernel(float *__restrict__ out, int64_t iters, float a, float b) {
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    if (s == -1.2345f) out[blockIdx.x] = s;  // never true for these inputs; keeps the chains live
+}
+}  // namespace svlf
+
+extern "C" int svlf_selftest_ffma(float *out, int blocks, int64_t iters, void *stream) {
+    if (!out || blocks < 1 || iters < 1) return SVLF_ERR_ARG;
+    svlf::ffma_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out, iters, 0.999f, 1e-4f);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}

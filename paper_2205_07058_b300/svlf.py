@@ -79,7 +79,7 @@ EXPORTS = [
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
-    "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_octree_parent_index",
+    "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_octree_parent_index", "svlf_selftest_ffma",
     "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
     "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth",
@@ -124,6 +124,7 @@ def lib():
     L.svlf_octree_build_vertices.argtypes = [vp, P(i64), vp]
     L.svlf_octree_leaf_vertices.argtypes = [vp, vp, vp]
     L.svlf_octree_parent_index.argtypes = [vp, vp, P(i64), vp]
+    L.svlf_selftest_ffma.argtypes = [vp, ctypes.c_int, i64, vp]
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
     L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
                                                vp, vp, vp, vp, vp, sz, vp]
@@ -520,6 +521,26 @@ def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_m
         _ptr(A), _ptr(B), _ptr(D), B.shape[0], A.shape[1], int(a_mn_major), int(b_mn_major),
         int(A.dtype == torch.bfloat16), int(flags), _stream(stream)))
     return D
+
+
+def svlf_measure_ffma_tflops(iters: int = 20000, repeats: int = 5) -> float:
+    """Measured float32 FMA throughput of this GPU (TFLOP/s), from the library's
+    FMA kernel timed with CUDA events: the FP32 SIMT roofline's denominator."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks, device="cuda")
+    _check("svlf_selftest_ffma", lib().svlf_selftest_ffma(_ptr(out), blocks, int(iters), _stream(None)))
+    best = None
+    for _ in range(repeats):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        _check("svlf_selftest_ffma", lib().svlf_selftest_ffma(_ptr(out), blocks, int(iters), _stream(None)))
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return blocks * 256 * iters * 32 / (best / 1e3) / 1e12
 
 
 def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0, trace_refill=0):
