@@ -276,6 +276,41 @@ def fixed_tuning(args):
     return {"tuning": svlf.svlf_get_tuning(), "searched": False}
 
 
+def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None):
+    """Roofline figures of kernel `name` in a render + training step: its
+    algorithmic work per launch (launches alternate render / training where
+    a kernel runs in both) over its live average launch time."""
+    launches, ms = kstats[name]
+    avg_s = ms / launches / 1e3
+    tensor_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    if name == "mlp_forward_tc":
+        work, bound, unit, peak = (S_r + S_t) * fps / 2.0, "tensor", "TFLOP/s", tensor_peak
+    elif name == "mlp_backward_tc":
+        work, bound, unit, peak = S_t * 3.0 * fps, "tensor", "TFLOP/s", tensor_peak
+    elif name in ("mlp_forward_f32", "mlp_backward_f32"):
+        mult = 1.0 if name == "mlp_forward_f32" else 3.0
+        work = ((S_r + S_t) / 2.0 if name == "mlp_forward_f32" else S_t) * mult * fps
+        bound, unit = "alu", "TFLOP/s"
+        peak = round(ffma_tf, 3) if ffma_tf else 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    elif name == "adam":
+        work, bound, unit, peak = n_par * 28.0 / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]  # features, network
+    elif name == "trace":  # ray in (24 B), span out (8 B), a 16-byte record per sample
+        work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+    elif name == "composite":  # span in, colour + depth out (16 B) per ray; record + output per sample
+        work, bound, unit, peak = ((N + NT) * 24.0 + (S_r + S_t) * 32.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+    else:
+        return None
+    achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
+    tr = ncu_traffic(name, tag) if tag else None
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+            "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
+                            else "measured in this run: float32 FMA kernel (svlf_selftest_ffma)" if ffma_tf
+                            else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
+            "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": tr["bytes_per_launch"] if tr else None,
+            "avg_launch_ms": round(ms / launches, 4)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2205_07058_b300 import svlf
@@ -493,38 +528,8 @@ def run_ours(args, rank, world, local_rank):
     tag = workload_tag(args.views, args.res, args.precision)
 
     def kernel_roofline(name):
-        """Algorithmic work per launch (launches alternate render / training
-        where a kernel runs in both) over the live average launch time."""
-        launches, ms = kstats[name]
-        avg_s = ms / launches / 1e3
-        tensor_peak = peaks.get("bf16_tflops_sustained", 1400.0)
-        if name == "mlp_forward_tc":
-            work, bound, unit, peak = (S_r + S_t) * fps / 2.0, "tensor", "TFLOP/s", tensor_peak
-        elif name == "mlp_backward_tc":
-            work, bound, unit, peak = S_t * 3.0 * fps, "tensor", "TFLOP/s", tensor_peak
-        elif name in ("mlp_forward_f32", "mlp_backward_f32"):
-            mult = 1.0 if name == "mlp_forward_f32" else 3.0
-            work = ((S_r + S_t) / 2.0 if name == "mlp_forward_f32" else S_t) * mult * fps
-            bound, unit = "alu", "TFLOP/s"
-            peak = round(ffma_tf, 3) if ffma_tf else 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-        elif name == "adam":
-            n_par = feats.numel() + params.numel()
-            work, bound, unit, peak = n_par * 28.0 / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]  # features, network
-        elif name == "trace":  # ray in (24 B), span out (8 B), a 16-byte record per sample
-            work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
-        elif name == "composite":  # span in, colour + depth out (16 B) per ray; record + output per sample
-            work, bound, unit, peak = ((N + NT) * 24.0 + (S_r + S_t) * 32.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
-        else:
-            return None
-        achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
-        tr = ncu_traffic(name, tag)
-        return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
-                "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
-                                else "measured in this run: float32 FMA kernel (svlf_selftest_ffma)" if ffma_tf
-                                else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
-                "unit": unit, "frac": round(achieved / peak, 4),
-                "traffic": tr["bytes_per_launch"] if tr else None,
-                "avg_launch_ms": round(ms / launches, 4)}
+        return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
+                                    peak_src, ffma_tf, tag)
 
     if dom:
         roof = kernel_roofline(dom)
@@ -775,6 +780,28 @@ def run_batched(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = a.elapsed_time(b) / args.steps
     status = svlf.svlf_get_device_status()
+    # per-kernel shares and rooflines from eager steps (the same kernels the graph replays)
+    svlf.svlf_profile_enable(True)
+    svlf.svlf_profile_report()
+    for _ in range(3):
+        step()
+    kstats = svlf.svlf_profile_report()
+    svlf.svlf_profile_enable(False)
+    S_r = svlf.svlf_workspace_samples_batched(ws_r, net, rend, K_HITS)
+    S_t = svlf.svlf_workspace_samples_batched(ws_t, net, train, K_HITS)
+    peaks, peak_src = measured_peaks()
+    tot = max(1e-9, sum(v[1] for v in kstats.values()))
+    per_kernel = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / tot, 4)}
+                  for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+    rl = {}
+    for k in kstats:
+        r = step_kernel_roofline(k, kstats, S_r, S_t, NR, NT, feat_all.numel() + par_all.numel(), flops_per_sample(),
+                                 peaks, peak_src)
+        if r is not None:
+            rl[k] = {key: r[key] for key in ("bound", "achieved", "peak", "unit", "frac", "avg_launch_ms")}
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+    roof = step_kernel_roofline(dom, kstats, S_r, S_t, NR, NT, feat_all.numel() + par_all.numel(),
+                                flops_per_sample(), peaks, peak_src) if dom else None
     return {
         "metric": "rays/s: 64 scenes batched (render 256^2 + train 2^14 rays each, fwd+bwd+Adam), one CUDA-graph step",
         "value": round((NR + NT) / (ms / 1e3), 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
@@ -783,6 +810,8 @@ def run_batched(args, rank, world, local_rank):
         "config": {"workload": f"{BATCH_SCENES} scenes, depth in 7..10, {min(n_leaves)}..{max(n_leaves)} leaves "
                                f"({sum(n_leaves)} total), F=32, MLP 41->3x128->4, K=8",
                    "render_rays": NR, "train_rays": NT, "autotune": tuned, "graph": True},
+        "samples_per_step": {"render": S_r, "train": S_t},
+        "kernels": per_kernel, "roofline": roof, "kernel_rooflines": rl,
         "clocks": clk, "device_status": status, "setup_s": round(time.time() - t0, 1),
     }
 

@@ -215,6 +215,12 @@ int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
                                       const svlf_mlp_desc *mlp, const svlf_render_opts *opts,
                                       void *workspace, size_t ws_bytes, void *stream);
 
+/* Samples (hits evaluated) that the last batched render or backward wrote
+ * into `workspace`, summed over the scenes (host result; synchronises
+ * `stream`). n_rays: host, n_scenes ray counts, as in the call. */
+int svlf_workspace_samples_batched(const void *workspace, const svlf_mlp_desc *mlp, const int64_t *n_rays,
+                                   int n_scenes, int K, int64_t *n_samples, void *stream);
+
 /* ------------------------------------------------ two-decoder form (Sec. 4.1-4.2) */
 /* The paper's full SVLF: features live on octree vertices (Sec. 4.1 "Scene
  * volume": one vector per leaf corner, shared by the voxels meeting there)

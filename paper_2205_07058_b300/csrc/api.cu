@@ -209,7 +209,8 @@ int launch_pack_weights(const svlf_mlp_desc &mlp, const SceneTable &T, const Wor
     if (mlp.precision == SVLF_FP32) {
         int rc = SVLF_OK;
         for (int i = 0; i < T.n && !rc; ++i)
-            rc = launch_pack_f32(md, T.s[i].params, (float *)((char *)ws.packed_w + i * ws.packed_stride), s);
+            if (T.s[i].params)  // a scene without rays may come without parameters
+                rc = launch_pack_f32(md, T.s[i].params, (float *)((char *)ws.packed_w + i * ws.packed_stride), s);
         return rc;
     }
     return launch_pack_tc(md, mlp.precision, T, ws.packed_w, ws.packed_stride, s);
@@ -367,6 +368,31 @@ extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc
         return SVLF_ERR_CUDA;
     const int64_t cap = n_rays * (int64_t)K;
     *n_samples = (int64_t)c < cap ? (int64_t)c : cap;
+    return SVLF_OK;
+}
+
+extern "C" int svlf_workspace_samples_batched(const void *workspace, const svlf_mlp_desc *mlp,
+                                              const int64_t *n_rays, int n_scenes, int K, int64_t *n_samples,
+                                              void *stream) {
+    if (!workspace || !mlp || !n_rays || !n_samples || n_scenes < 1 || n_scenes > kMaxScenes || K < 1)
+        return SVLF_ERR_ARG;
+    int64_t total = 0;
+    for (int i = 0; i < n_scenes; ++i) {
+        if (n_rays[i] < 0) return SVLF_ERR_ARG;
+        total += n_rays[i];
+    }
+    *n_samples = 0;
+    if (total == 0) return SVLF_OK;
+    Workspace ws = carve_workspace(const_cast<void *>(workspace), *mlp, total, K, n_scenes);
+    unsigned int c[kMaxScenes];
+    if (cudaMemcpyAsync(c, ws.counter + kCtrScene, sizeof(unsigned int) * n_scenes, cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return SVLF_ERR_CUDA;
+    for (int i = 0; i < n_scenes; ++i) {
+        const int64_t cap = n_rays[i] * (int64_t)K;
+        *n_samples += (int64_t)c[i] < cap ? (int64_t)c[i] : cap;
+    }
     return SVLF_OK;
 }
 

@@ -98,8 +98,12 @@ size_t packed_tc_bytes(const MlpDims &md) {
 }
 
 // ---------------------------------------------------------------- packing
-__global__ void pack_tc_kernel(MlpDims md, TcLayout lay, int fp16, const float *__restrict__ params,
-                               uint8_t *__restrict__ image) {
+// One launch packs every scene of the table: blockIdx.y = scene.
+__global__ void pack_tc_kernel(const __grid_constant__ SceneTable T, MlpDims md, TcLayout lay, int fp16,
+                               uint8_t *__restrict__ packed, size_t stride) {
+    const float *__restrict__ params = T.s[blockIdx.y].params;
+    if (!params) return;  // a scene without rays may come without parameters; nothing reads its image
+    uint8_t *__restrict__ image = packed + blockIdx.y * stride;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     for (int l = 0; l <= md.nh; ++l) {
         const int R = lay.w_rows[l], C = lay.w_cols[l];
@@ -156,9 +160,9 @@ int launch_pack_tc(const MlpDims &md, int precision, const SceneTable &T, void *
     if (!tc_supported(md)) return SVLF_ERR_UNSUPPORTED;
     const TcLayout lay = tc_layout(md);
     prof_begin("pack_weights_tc", s);
-    for (int i = 0; i < T.n; ++i)
-        pack_tc_kernel<<<32, 256, 0, s>>>(md, lay, precision == SVLF_FP16, T.s[i].params,
-                                          (uint8_t *)packed + i * stride);
+    if (T.n > 0)
+        pack_tc_kernel<<<dim3(32, (unsigned)T.n), 256, 0, s>>>(T, md, lay, precision == SVLF_FP16, (uint8_t *)packed,
+                                                               stride);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

@@ -139,3 +139,25 @@ def test_batched_trace_refill_shapes_agree():
     for refill in (16, 1, 0):
         for (c0, d0), (c1, d1) in zip(out[32], out[refill]):
             assert torch.equal(c0, c1) and torch.equal(d0, d1)
+
+
+def test_scene_without_rays_may_omit_its_parameters():
+    """A scene with no rays is skipped whole: its parameter pointer may be null."""
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes(n=3, seed=43)
+    net = svlf.Network(32, 128, 3, svlf.BF16)
+    batch = _batch(scenes)
+    ref = [None] * len(batch)
+    svlf.svlf_render_rays_batched(batch, net, 8)
+    torch.cuda.synchronize()
+    ref = [(b.rgb.clone(), b.depth.clone()) for b in batch]
+    empty = svlf.BatchScene(batch[0].tree, batch[0].features, None, torch.zeros((0, 6), device="cuda"))
+    batch2 = [batch[0], empty, batch[1], batch[2]]
+    for b in (batch[0], batch[1], batch[2]):
+        b.rgb = None
+        b.depth = None
+    svlf.svlf_render_rays_batched(batch2, net, 8)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    for (c0, d0), b in zip(ref, (batch2[0], batch2[2], batch2[3])):
+        assert torch.equal(c0, b.rgb) and torch.equal(d0, b.depth)
