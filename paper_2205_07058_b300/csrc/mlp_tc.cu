@@ -795,7 +795,8 @@ struct TcBwdParams {
     // together): only the image tail from w_off[nh] (output layer + biases) is
     // resident at offset 0; hidden W_l is loaded into slot l % 2 when needed.
     int stream;
-    uint32_t res_bytes;    // resident tail size
+    uint32_t res_bytes;    // bytes of the image resident from img0 (whole image, or its tail when streamed)
+    int bias_mma;          // the image's forward tail is resident: recompute biases enter through the MMA
     uint32_t slot_off[2];  // byte offsets of the two weight slots
 };
 
@@ -816,14 +817,18 @@ static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
     // activations, deltas and ones take this many bytes after the weights
     const uint32_t act = (uint32_t)(kTcTile * lay.K0 * 2 + md.nh * kTcTile * kHp * 2 +
                                     2 * kTcTile * kTcOutN * 2);
-    uint32_t off = lay.bytes;
-    P.stream = 0;
-    if ((size_t)lay.bytes + act + 128 > 227 * 1024 - 2048) {
-        // stream the hidden layers' weights through two slots
-        P.stream = 1;
-        P.res_bytes = lay.bytes - lay.w_off[md.nh];
-        off = (P.res_bytes + 127) & ~127u;
-        const uint32_t slot = (uint32_t)(kHp * (lay.K0 > kHp ? lay.K0 : kHp) * 2);
+    const size_t limit = 227 * 1024 - 2048;
+    // stream the hidden layers' weights through two slots when the image and the
+    // activations do not fit together; keep the forward tail (bias MMA operands)
+    // resident when it fits as well
+    P.stream = (size_t)lay.bytes + act + 128 > limit ? 1 : 0;
+    const uint32_t img0 = P.stream ? lay.w_off[md.nh] : 0u;
+    const uint32_t slot = (uint32_t)(kHp * (lay.K0 > kHp ? lay.K0 : kHp) * 2);
+    const uint32_t slots = P.stream ? 2 * slot : 0u;
+    P.bias_mma = (size_t)(((lay.fwd_bytes - img0) + 127) & ~127u) + slots + act + 128 <= limit ? 1 : 0;
+    P.res_bytes = (P.bias_mma ? lay.fwd_bytes : lay.bytes) - img0;
+    uint32_t off = (P.res_bytes + 127) & ~127u;
+    if (P.stream) {
         P.slot_off[0] = off;
         P.slot_off[1] = off + slot;
         off += 2 * slot;
@@ -1126,7 +1131,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         if (row == 0) {
             // the whole image, or (streamed weights) its tail: output layer + biases
             const uint32_t mb = tc::smem_u32(&s_mbar[1]);
-            const uint32_t nbytes = lay.bytes - img0;
+            const uint32_t nbytes = P.res_bytes;
             tc::mbar_expect_tx(mb, nbytes);
             for (uint32_t off = 0; off < nbytes; off += 32768u)
                 tc::bulk_g2s(tc::smem_u32(wimg + off), img_sc + img0 + off, min(32768u, nbytes - off), mb);
@@ -1209,7 +1214,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 // backward use below it)
                 prefetch(l + 1 < nh ? l + 1 : (uses_dx(nh - 1, form_dz) ? nh - 2 : nh - 1), l);
                 const uint32_t wb = waddr(l);
-                {  // the accumulator starts at the bias
+                if (!P.bias_mma) {  // the accumulator starts at the bias
                     const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + lay.bias_l[l]);
 #pragma unroll 1
                     for (int c = 0; c < kHp / 32; ++c) {
@@ -1224,8 +1229,12 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     tc::tmem_wait_st();
                 }
                 if (!run([&] {
+                        const uint32_t idesc = tc::idesc_f16(kTcTile, kHp, bf16, 0, 0);
+                        if (P.bias_mma)  // the accumulator starts at the bias: ones x bias pieces
+                            tc::mma_f16(tmem, tc::sdesc(s_base + (lay.ones_off - img0), kTcTile * 16, 128),
+                                        tc::sdesc(s_base + (lay.bias_b_off[l] - img0), kHp * 16, 128), idesc, 0u);
                         mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
-                                128, Kl, tc::idesc_f16(kTcTile, kHp, bf16, 0, 0), true);
+                                128, Kl, idesc, true);
                     })) {
                     aborted = true;
                     break;
