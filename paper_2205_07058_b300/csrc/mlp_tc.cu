@@ -939,7 +939,7 @@ __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev
                         if (MODE == 1) gv = fmaf(wb[v], __uint_as_float(b[e + q]), gv);
                         g[q] = gv * ginv;
                     }
-                    atomicAdd(dst + (e >> 2), make_float4(g[0], g[1], g[2], g[3]));
+                    red_add_f4(dst + (e >> 2), g[0], g[1], g[2], g[3]);
                 }
             }
         }
@@ -1339,30 +1339,46 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         two_decoder_dz<MODE>(md, SD, rec, valid && sl < S_sc, s, carry0, carry1, prev, d_feat,
                                              tmem + lane_off, ginv, P);
                 } else if (d_feat) {
-                    // dL/dz: stage rows in shared memory (X_1's buffer is free now)
+                    // dL/dz scatter, aggregated over the lanes of a warp that hit the same leaf: a
+                    // lane alone with its leaf adds its row straight from the accumulator; groups
+                    // stage their rows in shared memory (X_1's buffer is free now; feature-major,
+                    // [f][sample], so a warp's stores hit distinct banks) and the group's lowest
+                    // lane adds their sum. 16-byte vector atomics throughout.
                     float *stage = reinterpret_cast<float *>(smem + P.x_off[1]);
                     const int F = md.F;
+                    const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
+                    const bool solo = __popc(grp) == 1;
+                    float4 *dst = reinterpret_cast<float4 *>(d_feat + (int64_t)(leaf >= 0 ? leaf : 0) * F);
                     for (int c = 0; c < Fn; c += 16) {
                         uint32_t v[16];
                         tc::tmem_ld16_wait(tmem + lane_off + (uint32_t)c, v);
-                        for (int e = 0; e < 16 && c + e < F; ++e) stage[row * F + c + e] = __uint_as_float(v[e]) * ginv;
+                        if (leaf < 0) continue;
+                        if (solo) {
+#pragma unroll
+                            for (int e = 0; e < 16; e += 4)
+                                if (c + e < F)
+                                    red_add_f4(dst + ((c + e) >> 2), __uint_as_float(v[e]) * ginv,
+                                               __uint_as_float(v[e + 1]) * ginv, __uint_as_float(v[e + 2]) * ginv,
+                                               __uint_as_float(v[e + 3]) * ginv);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                if (c + e < F) stage[(c + e) * kTcTile + row] = __uint_as_float(v[e]) * ginv;
+                        }
                     }
                     tc::fence_before_sync();
                     __syncwarp();
-                    // warp-aggregated scatter: the lowest lane of each group of equal leaves sums it
-                    const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
-                    if (leaf >= 0 && lane == __ffs(grp) - 1) {
-                        float4 *dst = reinterpret_cast<float4 *>(d_feat + (int64_t)leaf * F);
+                    if (leaf >= 0 && !solo && lane == __ffs(grp) - 1) {
                         for (int f4 = 0; f4 < F / 4; ++f4) {
-                            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                            float a[4] = {0.f, 0.f, 0.f, 0.f};
                             unsigned m = grp;
                             while (m) {
                                 const int src = (warp << 5) + __ffs(m) - 1;
                                 m &= m - 1;
-                                const float4 v = *reinterpret_cast<const float4 *>(stage + src * F + 4 * f4);
-                                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) a[q] += stage[(4 * f4 + q) * kTcTile + src];
                             }
-                            atomicAdd(dst + f4, a);
+                            red_add_f4(dst + f4, a[0], a[1], a[2], a[3]);
                         }
                     }
                     __syncwarp();
@@ -1398,9 +1414,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         float *dst = dW + row * in + c;
                         for (int e = 0; e < 16; e += 4) {
                             if (c + e + 4 <= in && ((uintptr_t)(dst + e) & 15u) == 0) {  // 16-byte vector atomic
-                                atomicAdd(reinterpret_cast<float4 *>(dst + e),
-                                          make_float4(__uint_as_float(v[e]) * ginv, __uint_as_float(v[e + 1]) * ginv,
-                                                      __uint_as_float(v[e + 2]) * ginv, __uint_as_float(v[e + 3]) * ginv));
+                                red_add_f4(reinterpret_cast<float4 *>(dst + e), __uint_as_float(v[e]) * ginv,
+                                           __uint_as_float(v[e + 1]) * ginv, __uint_as_float(v[e + 2]) * ginv,
+                                           __uint_as_float(v[e + 3]) * ginv);
                             } else {
                                 for (int q = e; q < e + 4; ++q)
                                     if (c + q < in) atomicAdd(dst + q, __uint_as_float(v[q]) * ginv);

@@ -256,4 +256,11 @@ __device__ __forceinline__ void sphere_param(const float o[3], const float d[3],
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
+// Four float32 adds to 16 aligned bytes of global memory as one reduction
+// (no value returned, so the thread never waits for it).
+__device__ __forceinline__ void red_add_f4(float4 *addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 }  // namespace svlf
