@@ -62,7 +62,7 @@ __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, con
     const float o[3] = {a.x, a.y, b.x};
     const float d[3] = {b.y, c.x, c.y};
     float p1[3], p2[3];
-    sphere_param(o, d, sm.cell, depth, p1, p2);
+    sphere_param_at(o, d, sm.tmid, sm.cell, depth, p1, p2);
     h0[F + 0] = d[0]; h0[F + 1] = d[1]; h0[F + 2] = d[2];
     h0[F + 3] = p1[0]; h0[F + 4] = p1[1]; h0[F + 5] = p1[2];
     h0[F + 6] = p2[0]; h0[F + 7] = p2[1]; h0[F + 8] = p2[2];

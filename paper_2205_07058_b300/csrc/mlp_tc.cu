@@ -272,7 +272,7 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
         const float o[3] = {ra.x, ra.y, rb.x};
         const float d[3] = {rb.y, rc.x, rc.y};
         float p1[3], p2[3];
-        sphere_param(o, d, sm.cell, depth, p1, p2);
+        sphere_param_at(o, d, sm.tmid, sm.cell, depth, p1, p2);
         st_chunk(abuf, row, kb++, tc::pack2(d[0], d[1], fp16), tc::pack2(d[2], p1[0], fp16),
                  tc::pack2(p1[1], p1[2], fp16), tc::pack2(p2[0], p2[1], fp16));
         st_chunk(abuf, row, kb++, tc::pack2(p2[2], 0.f, fp16), 0u, 0u, 0u);
