@@ -7,8 +7,9 @@
 //    (TMA) copies and stay resident.
 //  * Each warpgroup owns a tile of 128 samples at a time: thread t builds the
 //    network input of sample t (feature gather with 16-byte loads, ray
-//    parameterisation in double-float), rounds it to 16 bits and stores it in
-//    the warpgroup's activation buffer (the A operand).
+//    parameterisation from an exactly formed point of the ray), rounds it to
+//    16 bits and stores it in the warpgroup's activation buffer (the A
+//    operand).
 //  * One thread issues the layer's tcgen05.mma instructions (M = 128 samples,
 //    N = layer width, K = 16 each) into the warpgroup's 128 TMEM columns and
 //    commits them to an mbarrier. A hidden layer's first MMA multiplies a

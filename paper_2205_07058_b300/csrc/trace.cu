@@ -17,20 +17,23 @@
 //    k 2^-L - o is split exactly into hi + lo (TwoSum) and multiplied by 1/d
 //    held as a double-float (r_hi + r_lo, formed once per ray with an FMA
 //    residual), so each crossing carries about half an ulp of error. The cell
-//    after a crossing is found by counting the planes whose crossing is <= the
-//    current t. A voxel is therefore entered at the t its slab test gives as
-//    t_in and left at its t_out, every visited voxel has t_out > t_in, and no
-//    voxel with a positive segment is skipped.
+//    after a crossing is the one whose planes' crossings bracket the current
+//    t: floor of the position where that is provably exact (an error bound
+//    per ray), else found by counting the planes whose crossing is <= t. A
+//    voxel is therefore entered at the t its slab test gives as t_in and left
+//    at its t_out, every visited voxel has t_out > t_in, and no voxel with a
+//    positive segment is skipped.
 //  * Hits go to the lane's K slots, in shared memory (interleaved by thread)
 //    for K <= 16, else in a global scratch area (the network output buffer,
 //    not yet in use), keeping registers free for occupancy; at the end each
 //    warp reserves space for its rays' samples with one atomic and copies them
 //    contiguously per ray from the slots.
 //  * Many scenes can be traced in one launch (see SceneTable).
-//  * Warps fetch their own chunks of rays and refill lanes as rays finish,
-//    claiming the next chunk as soon as the current one runs dry (persistent
-//    warps), so no lane waits for the longest ray of its warp and no warp
-//    waits for the rest of its block.
+//  * Warps fetch their own chunks of rays and refill lanes as rays finish
+//    (persistent warps); once a chunk is handed out, the warp claims the next
+//    one when enough lanes are idle (all of them for coherent image rays,
+//    half for small incoherent batches), and no warp waits for the rest of
+//    its block.
 #include "svlf_internal.cuh"
 
 namespace svlf {
