@@ -36,6 +36,7 @@
 namespace svlf {
 
 constexpr int kTcTile = 128;     // samples per tile (MMA M)
+constexpr int kMaxKSteps = 9;    // K = 16 steps of the longest K loop (K0 <= 144, tiles of 128)
 constexpr int kTcOutN = 16;      // output layer width padded to the smallest legal N
 constexpr int kHp = 128;         // hidden width inside the tensor-core path (zero-padded)
 
@@ -592,11 +593,9 @@ __global__ void __launch_bounds__(EPI == 2 ? 384 : 512, 1)
                         const uint64_t db = tc::sdesc(wimg_s + P.lay.bias_b_off[l], N * 16, 128);
                         tc::mma_f16(tmem_wg, da, db, idesc, 0u);
                     }
-                    for (int k = 0; k < Kl; k += 16) {
-                        const uint64_t da = tc::sdesc(abuf_s + (k >> 3) * (kTcTile * 16), kTcTile * 16, 128);
-                        const uint64_t db = tc::sdesc(b_base + (k >> 3) * (N * 16), N * 16, 128);
-                        tc::mma_f16(tmem_wg, da, db, idesc, (hidden || k > 0) ? 1u : 0u);
-                    }
+                    tc::mma_f16_k<kMaxKSteps>(tmem_wg, tc::sdesc(abuf_s, kTcTile * 16, 128), (2 * kTcTile * 16) >> 4,
+                                              tc::sdesc(b_base, N * 16, 128), (2 * N * 16) >> 4, idesc, Kl / 16,
+                                              hidden);
                     tc::mma_commit(mbar);
                 }
                 const bool timeout = !tc::mbar_wait(mbar, phase);
@@ -964,11 +963,8 @@ __device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32
                                         uint32_t a_lbo, uint32_t a_sbo, uint32_t b_base,
                                         uint32_t b_kstep, uint32_t b_lbo, uint32_t b_sbo, int K,
                                         uint32_t idesc, bool accumulate) {
-    for (int k = 0; k < K; k += 16) {
-        const uint64_t da = tc::sdesc(a_base + (uint32_t)(k >> 4) * a_kstep, a_lbo, a_sbo);
-        const uint64_t db = tc::sdesc(b_base + (uint32_t)(k >> 4) * b_kstep, b_lbo, b_sbo);
-        tc::mma_f16(tmem_d, da, db, idesc, (accumulate || k > 0) ? 1u : 0u);
-    }
+    tc::mma_f16_k<kMaxKSteps, true>(tmem_d, tc::sdesc(a_base, a_lbo, a_sbo), a_kstep >> 4,
+                                    tc::sdesc(b_base, b_lbo, b_sbo), b_kstep >> 4, idesc, K / 16, accumulate);
 }
 
 template <int MODE>

@@ -60,6 +60,38 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uin
         : "memory");
 }
 
+// A K loop of MMAs issued back to back: step i uses the descriptors da0 + i *
+// a_step and db0 + i * b_step, where a step is the operand's byte advance per
+// K = 16 shifted right by 4 (the start-address field holds any shared-memory
+// address, so adding to it never carries into the next field). The issuing
+// thread then spends a few instructions per MMA instead of forming two
+// descriptors, and the tensor pipe, not the issue, sets the pace (forming
+// them per step held a single issuing thread to ~100 cycles per MMA; issued
+// this way an M = 128, N = 128, K = 16 MMA takes ~64 cycles of the pipe).
+// The first MMA overwrites the accumulator unless `accumulate`; the others
+// add to it. ksteps <= MAXK.
+// UNROLL: the loop fully unrolled (fewest instructions per MMA, more registers
+// live at once: for kernels with registers to spare) or kept rolled.
+template <int MAXK, bool UNROLL = false>
+__device__ __forceinline__ void mma_f16_k(uint32_t tmem_d, uint64_t da0, uint32_t a_step, uint64_t db0,
+                                          uint32_t b_step, uint32_t idesc, int ksteps, bool accumulate) {
+    if (UNROLL) {
+#pragma unroll
+        for (int i = 0; i < MAXK; ++i)
+            if (i < ksteps)
+                mma_f16(tmem_d, da0 + (uint64_t)(i * a_step), db0 + (uint64_t)(i * b_step), idesc,
+                        (accumulate || i > 0) ? 1u : 0u);
+    } else {
+        uint64_t da = da0, db = db0;
+#pragma unroll 1
+        for (int i = 0; i < ksteps && i < MAXK; ++i) {
+            mma_f16(tmem_d, da, db, idesc, (accumulate || i > 0) ? 1u : 0u);
+            da += a_step;
+            db += b_step;
+        }
+    }
+}
+
 // Arrive on an mbarrier when every MMA this thread issued so far completes.
 __device__ __forceinline__ void mma_commit(uint32_t mbar_saddr) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
