@@ -154,11 +154,13 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
     const int n = R.n;
     const int max_steps = 3 * n + 64;
     const int ps = T.pgrid_shift;
+    // the step bound is checked once per call (it may overrun by one budget)
+    if (w.steps > max_steps) {
+        raise_status(SVLF_DEV_STEP_LIMIT);
+        return true;
+    }
+    w.steps += budget;
     for (int it = 0; it < budget; ++it) {
-        if (++w.steps > max_steps) {
-            raise_status(SVLF_DEV_STEP_LIMIT);
-            return true;
-        }
         int *c = w.c;
         TRACE_STAT(0, 1);
         const uint32_t key = (uint32_t)(c[0] >> 2) | ((uint32_t)(c[1] >> 2) << 10) |
