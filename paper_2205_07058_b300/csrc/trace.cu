@@ -256,7 +256,8 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
             const float fr = p - fl;
             const int lo = up ? c[a] : blo[a];
             const int hi = up ? bhi[a] - 1 : c[a];
-            const bool ok = k >= lo && k <= hi && fr > w.eps && fr < 1.0f - w.eps;
+            // fr in (eps, 1 - eps), as one comparison (its rounding is far inside eps's 16x margin)
+            const bool ok = k >= lo && k <= hi && fabsf(fr - 0.5f) < 0.5f - w.eps;
             const bool ex = ta[a] <= tx;
             const bool stay = !ex && bhi[a] - blo[a] > 1 && R.d[a] != 0.f;
             slow |= (stay && !ok) ? (1 << a) : 0;
