@@ -161,3 +161,21 @@ def test_scene_without_rays_may_omit_its_parameters():
     assert svlf.svlf_get_device_status() == 0
     for (c0, d0), b in zip(ref, (batch2[0], batch2[2], batch2[3])):
         assert torch.equal(c0, b.rgb) and torch.equal(d0, b.depth)
+
+
+def test_workspace_samples_batched_equals_per_scene_counts():
+    from paper_2205_07058_b300 import svlf
+    scenes = _scenes(seed=44)
+    net = svlf.Network(32, 128, 3, svlf.BF16)
+    batch = _batch(scenes)
+    ws = svlf.svlf_render_rays_batched(batch, net, 8)
+    torch.cuda.synchronize()
+    total = svlf.svlf_workspace_samples_batched(ws, net, batch, 8)
+    expect = 0
+    for b in batch:
+        n = b.rays.shape[0]
+        if n == 0:
+            continue
+        _, _, hits, _, _ = svlf.svlf_render_rays(b.tree, b.features, b.params, net, b.rays, 8, want_hits=True)
+        expect += int((hits >= 0).sum())
+    assert total == expect > 0

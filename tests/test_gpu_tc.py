@@ -114,3 +114,14 @@ def test_repeated_renders_are_bit_identical(prec):
         else:
             assert torch.equal(rgb, ref[0]) and torch.equal(depth, ref[1])
     assert svlf.svlf_get_device_status() == 0
+
+
+def test_ffma_rate_kernel_is_plausible():
+    """The FP32 roofline denominator: the FMA kernel's measured rate lies
+    between a tenth of and the nominal 148 SMs x 128 lanes x 2 flop x clock."""
+    from paper_2205_07058_b300 import svlf
+    tf = svlf.svlf_measure_ffma_tflops(iters=4000, repeats=2)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2 * 2.2e9 / 1e12  # generous clock bound
+    assert nominal / 10 < tf < nominal
+    assert svlf.svlf_get_device_status() == 0
