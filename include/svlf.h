@@ -118,7 +118,8 @@ int svlf_octree_leaf_ijk(svlf_octree tree, int32_t *out_ijk, void *stream);
  * empty box of level L-3 cells around the cell, lo = x | y << 8 | z << 16
  * inclusive, hi exclusive, with bits 24..31 zero. The box is the largest
  * empty octree block holding the cell, grown face by face (x, y, z; low face
- * then high) while the added layer holds no leaf, until no face can grow.
+ * then high) by slabs that hold no leaf, each face's slab doubling after a
+ * success and halving after a failure, until no face can grow by one layer.
  * out: device, 2 x *n_entries uint32, or NULL to query *n_entries (host; 0
  * for depths below 3 or an empty tree). */
 int svlf_octree_parent_index(svlf_octree tree, uint32_t *out, int64_t *n_entries, void *stream);

@@ -49,32 +49,44 @@ __host__ __device__ inline int64_t svt_count(const int32_t *S, int G, const int 
 }
 
 // Grows the empty box [lo, hi) of a G^3 grid face by face (axes x, y, z in
-// turn, low face then high face) while the layer it would add is empty, until
-// no face can grow. Deterministic, so the host and the GPU builds agree. A ray
-// inside the box can jump to where it leaves the box: it meets no occupied
-// cell on the way.
+// turn, low face then high face) while the slab it would add is empty, until
+// no face can grow by one layer. Each face tries a slab of `step` layers:
+// on success the face moves and its step doubles, on failure the step halves,
+// and a face that cannot take one layer is finished for good (growing the
+// other faces only enlarges its slab). So the faces grow at similar rates and
+// a long empty run costs a logarithmic number of tests, not one per layer.
+// Deterministic, so the host and the GPU builds agree. A ray inside the box
+// can jump to where it leaves the box: it meets no occupied cell on the way.
 __host__ __device__ inline void grow_empty_box(const int32_t *S, int G, int lo[3], int hi[3]) {
+    int step[6] = {1, 1, 1, 1, 1, 1};
     for (int round = 0; round <= 6 * G; ++round) {
-        bool grown = false;
-        for (int a = 0; a < 3; ++a) {
-            for (int side = 0; side < 2; ++side) {
-                int l[3] = {lo[0], lo[1], lo[2]}, h[3] = {hi[0], hi[1], hi[2]};
-                if (side == 0) {
-                    if (lo[a] == 0) continue;
-                    l[a] = lo[a] - 1;
-                    h[a] = lo[a];
-                } else {
-                    if (hi[a] == G) continue;
-                    l[a] = hi[a];
-                    h[a] = hi[a] + 1;
-                }
-                if (svt_count(S, G, l, h) == 0) {
-                    if (side == 0) --lo[a]; else ++hi[a];
-                    grown = true;
-                }
+        bool active = false;
+        for (int f = 0; f < 6; ++f) {
+            if (step[f] == 0) continue;  // finished
+            const int a = f >> 1, side = f & 1;
+            const int room = side == 0 ? lo[a] : G - hi[a];
+            if (room == 0) {
+                step[f] = 0;
+                continue;
             }
+            const int s = step[f] < room ? step[f] : room;
+            int l[3] = {lo[0], lo[1], lo[2]}, h[3] = {hi[0], hi[1], hi[2]};
+            if (side == 0) {
+                l[a] = lo[a] - s;
+                h[a] = lo[a];
+            } else {
+                l[a] = hi[a];
+                h[a] = hi[a] + s;
+            }
+            if (svt_count(S, G, l, h) == 0) {
+                if (side == 0) lo[a] -= s; else hi[a] += s;
+                step[f] = 2 * s;
+            } else {
+                step[f] = s > 1 ? s / 2 : 0;
+            }
+            active |= step[f] != 0;
         }
-        if (!grown) break;
+        if (!active) break;
     }
 }
 
