@@ -630,7 +630,6 @@ __global__ void __launch_bounds__(EPI == 2 ? 384 : 512, 1)
 #pragma unroll
                     for (int c0 = 0; EPI != 3 && c0 < H / 32; c0 += EPI) {
                         uint32_t v[EPI == 2 ? 2 : 1][32];
-#pragma unroll
                         if (EPI == 2)
                             tc::tmem_ld64_wait(tmem_row + (uint32_t)(c0 * 32), reinterpret_cast<uint32_t(&)[64]>(v));
                         else
