@@ -132,6 +132,29 @@ int svlf_octree_info(svlf_octree tree, int *depth, int64_t *n_leaves, int64_t *n
 int svlf_free_octree(svlf_octree tree);
 
 /* ------------------------------------------------------------ rendering */
+/* Pinhole cameras: rays generated on the device (row a1's optional in-kernel
+ * ray generation; the rays of svlf_render_rays are otherwise the caller's).
+ * eye: the centre of projection; fwd, right, up: an orthonormal basis (the
+ * viewing direction, the image's +x and +y); tan_half_fov: tan of half the
+ * (square) field of view. */
+typedef struct {
+    float eye[3];
+    float fwd[3];
+    float right[3];
+    float up[3];
+    float tan_half_fov;
+} svlf_camera;
+
+/* rays_out (device, n_views x height x width x 6 float32; view-major, then
+ * row-major over pixels) receives, for pixel (r, c) of view v, origin eye
+ * and the unit direction of fwd + x right + y up with x = (2 (c + 1/2) /
+ * width - 1) tan_half_fov, y = (1 - 2 (r + 1/2) / height) tan_half_fov,
+ * normalised in float32 (within a few ulp of the same formula in FP64).
+ * cams: host, n_views cameras (copied into the launch). Errors: SVLF_ERR_ARG
+ * for a null pointer, n_views < 1 or a non-positive size. */
+int svlf_pinhole_rays(const svlf_camera *cams, int n_views, int width, int height, float *rays_out,
+                      void *stream);
+
 /* Bytes of workspace a render (and the matching backward) needs. */
 int svlf_workspace_size(const svlf_mlp_desc *mlp, int64_t n_rays, int K, size_t *bytes);
 

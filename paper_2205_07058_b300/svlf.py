@@ -12,6 +12,7 @@ import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -68,6 +69,11 @@ class Tuning(ctypes.Structure):
                 ("trace_refill", ctypes.c_int)]
 
 
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("tan_half_fov", ctypes.c_float)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -80,7 +86,7 @@ EXPORTS = [
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
     "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_octree_parent_index", "svlf_selftest_ffma",
-    "svlf_workspace_samples_batched",
+    "svlf_workspace_samples_batched", "svlf_pinhole_rays",
     "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
     "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth",
@@ -127,6 +133,7 @@ def lib():
     L.svlf_octree_parent_index.argtypes = [vp, vp, P(i64), vp]
     L.svlf_selftest_ffma.argtypes = [vp, ctypes.c_int, i64, vp]
     L.svlf_workspace_samples_batched.argtypes = [vp, P(MlpDesc), P(i64), i32, i32, P(i64), vp]
+    L.svlf_pinhole_rays.argtypes = [P(Camera), i32, i32, i32, vp, vp]
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
     L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
                                                vp, vp, vp, vp, vp, sz, vp]
@@ -535,6 +542,27 @@ def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_m
         _ptr(A), _ptr(B), _ptr(D), B.shape[0], A.shape[1], int(a_mn_major), int(b_mn_major),
         int(A.dtype == torch.bfloat16), int(flags), _stream(stream)))
     return D
+
+
+def cameras(eye, fwd, right, up, tan_half_fov):
+    """Camera array for svlf_pinhole_rays from (n, 3) basis arrays and (n,) tan(fov/2)."""
+    eye, fwd, right, up = (np.asarray(x, dtype=np.float64).reshape(-1, 3) for x in (eye, fwd, right, up))
+    th = np.broadcast_to(np.asarray(tan_half_fov, dtype=np.float64), (eye.shape[0],))
+    arr = (Camera * eye.shape[0])()
+    for i in range(eye.shape[0]):
+        arr[i] = Camera((ctypes.c_float * 3)(*eye[i]), (ctypes.c_float * 3)(*fwd[i]),
+                        (ctypes.c_float * 3)(*right[i]), (ctypes.c_float * 3)(*up[i]), float(th[i]))
+    return arr
+
+
+def svlf_pinhole_rays(cams, width: int, height: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Rays of len(cams) pinhole views of width x height, generated on the device."""
+    n = len(cams) * width * height
+    if out is None:
+        out = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    _check("svlf_pinhole_rays", lib().svlf_pinhole_rays(cams, len(cams), int(width), int(height), _ptr(out),
+                                                         _stream(stream)))
+    return out
 
 
 def svlf_measure_ffma_tflops(iters: int = 20000, repeats: int = 5) -> float:
