@@ -882,12 +882,29 @@ def td_flops_per_sample():
 
 
 def td_bytes_per_sample():
-    """Algorithmic bytes of the two passes per sample (vertex rows counted once
-    per sample, not deduplicated): record 16 + ray 24 + 8 vertex ids 32 + the
-    rows, + 16 B output; the colour pass also reads the first pass's output."""
+    """Bytes of the two passes per sample with each sample's eight corner rows
+    counted (not deduplicated; what the gather moves through L2 and L1):
+    record 16 + ray 24 + 8 vertex ids 32 + the rows, + 16 B output; the colour
+    pass also reads the first pass's output."""
     ft = 16 + 24 + 32 + 8 * TD_FT * 4 + 16
     fc = 16 + 24 + 32 + 8 * TD_FC * 4 + 16 + 16
     return ft, fc
+
+
+def td_stream_bytes_per_sample():
+    """The per-sample part of the passes' HBM floor (everything but the vertex
+    rows, which count once per distinct vertex a launch touches)."""
+    return 16 + 24 + 32 + 16, 16 + 24 + 32 + 16 + 16
+
+
+def td_distinct_vertices(leaf_vertices, hits, n_vertices):
+    """Distinct vertices referenced by the corners of a render's hits."""
+    import torch
+    mark = torch.zeros(n_vertices, dtype=torch.bool, device=hits.device)
+    h = hits[hits >= 0].long()
+    for c in range(0, h.numel(), 1 << 24):
+        mark[leaf_vertices[h[c:c + (1 << 24)]].reshape(-1).long()] = True
+    return int(mark.sum().item())
 
 
 def run_twodec(args, rank, world, local_rank):
@@ -1015,14 +1032,25 @@ def run_twodec(args, rank, world, local_rank):
                 "frac": round(work / avg_s / 1e12 / peak, 4), "traffic": None,
                 "avg_launch_ms": round(kms / launches, 4)}
     elif dom in ("two_decoder_ft_tc", "two_decoder_fc_tc"):
-        # one launch renders, one trains: average over both
-        work = (S + ST) / 2.0 * (bft if dom == "two_decoder_ft_tc" else bfc)
+        # one launch renders, one trains: average over both. The HBM floor counts each distinct
+        # vertex row a launch touches once, plus the per-sample records, rays, ids and outputs;
+        # the gather rate (every sample's eight corner rows) is what L2 and L1 serve
+        lv = tree.leaf_vertices()
+        U, UT = td_distinct_vertices(lv, hits, n_vert), td_distinct_vertices(lv, thits, n_vert)
+        ft_k = dom == "two_decoder_ft_tc"
+        per_s = td_stream_bytes_per_sample()[0 if ft_k else 1]
+        row = (TD_FT if ft_k else TD_FC) * 4
+        work = ((S + ST) * per_s + (U + UT) * row) / 2.0
+        gather = (S + ST) / 2.0 * (bft if ft_k else bfc)
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],
                 "peak_source": f"{peak_src} (copy)", "unit": "GB/s",
                 "frac": round(work / avg_s / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
                 "avg_launch_ms": round(kms / launches, 4),
-                "work": f"({S} + {ST}) / 2 samples x {bft if dom == 'two_decoder_ft_tc' else bfc} B per launch "
-                        f"(vertex rows not deduplicated)"}
+                "work": f"(({S} + {ST}) samples x {per_s} B + ({U} + {UT}) distinct vertices x {row} B) / 2 "
+                        f"per launch",
+                "gather_gbs": round(gather / avg_s / 1e9, 1),
+                "gather_work": f"({S} + {ST}) / 2 samples x {bft if ft_k else bfc} B (eight corner rows per "
+                               f"sample, served mostly by L2 and L1)"}
     elif dom == "trace":
         work = ((N + NT) * 32.0 + (S + ST) * 16.0) / 2.0
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(work / avg_s / 1e9, 3), "peak": peaks["hbm_gbs"],

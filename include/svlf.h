@@ -380,6 +380,7 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
  * autotuner (paper_2205_07058_b300/autotune.py) times candidates on the
  * caller's workload and sets the best. They change speed, never results.
  *   mlp_warpgroups      tensor-core forward: tiles in flight per CTA, 1..4
+ *                       (the two-decoder F^T pass runs at most 3)
  *   mlp_epilogue_batch  tensor-core forward, hidden-layer epilogue: 1 = 32
  *                       TMEM columns per load and wait, 2 = 64 (limits the
  *                       CTA to 3 warpgroups), 3 = 16 with the next load in

@@ -219,6 +219,12 @@ __device__ __forceinline__ void st_chunk(uint8_t *abuf, int row, int kb, uint32_
         make_uint4(a, b, c, d);
 }
 
+// Half a chunk (8 bytes: four 16-bit values) of row `row`, chunk `kb`.
+__device__ __forceinline__ void st_half_chunk(uint8_t *abuf, int row, int kb, int half, uint32_t a, uint32_t b) {
+    *reinterpret_cast<uint2 *>(abuf + kb * (kTcTile * 16) + (row >> 3) * 128 + (row & 7) * 16 + half * 8) =
+        make_uint2(a, b);
+}
+
 // Network input h0 = [z | d | p~1 | p~2] of sample `s` written straight into
 // row `row` of a 16-bit A operand (K0 columns): F/8 chunks of features, two
 // chunks of ray direction and entry/exit parameters, zero chunks up to K0.
@@ -345,6 +351,91 @@ __device__ __forceinline__ void vertex_feat8(const void *feats, int feat_bf16, i
     }
 }
 
+// Position of o + t d inside voxel `cell`, clamped to [0, 1]^3 (the
+// trilinear coordinates behind corner_weights).
+__device__ __forceinline__ void voxel_coords(const float o[3], const float d[3], float t, const int cell[3], float n,
+                                             float u[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = fminf(fmaxf(fmaf(t, d[a], o[a]) * n - (float)cell[a], 0.f), 1.f);
+}
+
+// Weight of corner v (slot a + 2b + 4c) from the trilinear coordinates; the
+// same products in the same order as corner_weights.
+__device__ __forceinline__ float corner_weight(const float u[3], int v) {
+    return ((v & 1) ? u[0] : 1.f - u[0]) * ((v & 2) ? u[1] : 1.f - u[1]) * ((v & 4) ? u[2] : 1.f - u[2]);
+}
+
+// The corner rows are gathered by the warp as a whole: in pass b the 32 lanes
+// serve 32/G samples, G lanes per sample, and lane q of a group reads the
+// 16-byte segments q, q + G, ... of each of the sample's eight corner rows, so
+// a group reads G x 16 contiguous bytes of one vertex row per load instead of
+// 32 lanes reading 16 bytes of 32 different rows (one L1 wavefront per lane).
+// Eight loads (one per corner) are in flight per lane: more in flight per SM
+// evicts from L1 the corner rows that neighbouring samples share, and runs
+// slower. The sample's vertex ids and trilinear coordinates come from its
+// owner lane by shuffle; per feature the corner sum runs v = 0..7 in the same
+// order as a lane-per-sample loop would, so the result does not depend on the
+// mapping. Lanes write their segment's 16-bit values straight into the
+// sample's row of the A operand (the rows of one pass differ in row & 7, so
+// the stores spread over the banks).
+template <int MODE>
+__device__ __forceinline__ void gather_corner_seg(const void *feats, int feat_bf16, int F, int nq, const int vs[8],
+                                                  const float xa[8], const float xb[8], int seg, int fp16,
+                                                  uint8_t *abuf, int r) {
+    if (feat_bf16) {
+        const uint4 *base = reinterpret_cast<const uint4 *>(feats);
+        const int rq = F >> 3;  // 16-byte segments per row
+        uint4 t[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t[v] = __ldg(base + (int64_t)vs[v] * rq + seg);
+        float acc_a[8], acc_b[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc_a[e] = acc_b[e] = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const uint32_t w[4] = {t[v].x, t[v].y, t[v].z, t[v].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float z0 = __uint_as_float(w[e] << 16), z1 = __uint_as_float(w[e] & 0xFFFF0000u);
+                acc_a[2 * e] = fmaf(xa[v], z0, acc_a[2 * e]);
+                acc_a[2 * e + 1] = fmaf(xa[v], z1, acc_a[2 * e + 1]);
+                if (MODE == 1) {
+                    acc_b[2 * e] = fmaf(xb[v], z0, acc_b[2 * e]);
+                    acc_b[2 * e + 1] = fmaf(xb[v], z1, acc_b[2 * e + 1]);
+                }
+            }
+        }
+        st_chunk(abuf, r, seg, tc::pack2(acc_a[0], acc_a[1], fp16), tc::pack2(acc_a[2], acc_a[3], fp16),
+                 tc::pack2(acc_a[4], acc_a[5], fp16), tc::pack2(acc_a[6], acc_a[7], fp16));
+        if (MODE == 1)
+            st_chunk(abuf, r, nq + seg, tc::pack2(acc_b[0], acc_b[1], fp16), tc::pack2(acc_b[2], acc_b[3], fp16),
+                     tc::pack2(acc_b[4], acc_b[5], fp16), tc::pack2(acc_b[6], acc_b[7], fp16));
+    } else {
+        const float4 *base = reinterpret_cast<const float4 *>(feats);
+        const int rq = F >> 2;
+        float4 t[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t[v] = __ldg(base + (int64_t)vs[v] * rq + seg);
+        float acc_a[4], acc_b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc_a[e] = acc_b[e] = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const float z[4] = {t[v].x, t[v].y, t[v].z, t[v].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                acc_a[e] = fmaf(xa[v], z[e], acc_a[e]);
+                if (MODE == 1) acc_b[e] = fmaf(xb[v], z[e], acc_b[e]);
+            }
+        }
+        st_half_chunk(abuf, r, seg >> 1, seg & 1, tc::pack2(acc_a[0], acc_a[1], fp16),
+                      tc::pack2(acc_a[2], acc_a[3], fp16));
+        if (MODE == 1)
+            st_half_chunk(abuf, r, nq + (seg >> 1), seg & 1, tc::pack2(acc_b[0], acc_b[1], fp16),
+                          tc::pack2(acc_b[2], acc_b[3], fp16));
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void build_input_two_decoder(const MlpDims &md, int K0, int depth,
                                                         const int32_t *__restrict__ leaf_vertices,
@@ -353,10 +444,15 @@ __device__ __forceinline__ void build_input_two_decoder(const MlpDims &md, int K
                                                         const Sample &sm, bool valid, float4 prev, int fp16,
                                                         uint8_t *abuf, int row, float &carry0, float &carry1) {
     const int nq = md.F / 8;
-    int kb = 0;
+    float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f};
+    int vid[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) vid[v] = 0;
     if (valid) {
         const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
         const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
+        const int4 *vp = reinterpret_cast<const int4 *>(leaf_vertices + 8 * (int64_t)sm.leaf);
+        const int4 va = __ldg(vp), vb = __ldg(vp + 1);
         const float o[3] = {ra.x, ra.y, rb.x};
         const float d[3] = {rb.y, rc.x, rc.y};
         const int cell[3] = {(int)(sm.cell & 1023u), (int)((sm.cell >> 10) & 1023u), (int)((sm.cell >> 20) & 1023u)};
@@ -383,39 +479,50 @@ __device__ __forceinline__ void build_input_two_decoder(const MlpDims &md, int K
             carry0 = prev.x;
             carry1 = ts;
         }
-        float wa[8], wb[8];
-        corner_weights(o, d, ta, cell, n, wa);
-        if (MODE == 1) corner_weights(o, d, tb, cell, n, wb);
-        const int4 *vp = reinterpret_cast<const int4 *>(leaf_vertices + 8 * (int64_t)sm.leaf);
-        const int4 va = __ldg(vp), vb = __ldg(vp + 1);
-        const int vid[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        for (int q = 0; q < nq; ++q) {
-            float acc_a[8], acc_b[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) acc_a[e] = acc_b[e] = 0.f;
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                float z[8];
-                vertex_feat8(feats, feat_bf16, md.F, vid[v], q, z);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    acc_a[e] = fmaf(wa[v], z[e], acc_a[e]);
-                    if (MODE == 1) acc_b[e] = fmaf(wb[v], z[e], acc_b[e]);
-                }
-            }
-            st_chunk(abuf, row, q, tc::pack2(acc_a[0], acc_a[1], fp16), tc::pack2(acc_a[2], acc_a[3], fp16),
-                     tc::pack2(acc_a[4], acc_a[5], fp16), tc::pack2(acc_a[6], acc_a[7], fp16));
-            if (MODE == 1)
-                st_chunk(abuf, row, nq + q, tc::pack2(acc_b[0], acc_b[1], fp16), tc::pack2(acc_b[2], acc_b[3], fp16),
-                         tc::pack2(acc_b[4], acc_b[5], fp16), tc::pack2(acc_b[6], acc_b[7], fp16));
-        }
-        kb = (MODE == 1 ? 2 : 1) * nq;
+        voxel_coords(o, d, ta, cell, n, ua);
+        if (MODE == 1) voxel_coords(o, d, tb, cell, n, ub);
+        vid[0] = va.x; vid[1] = va.y; vid[2] = va.z; vid[3] = va.w;
+        vid[4] = vb.x; vid[5] = vb.y; vid[6] = vb.z; vid[7] = vb.w;
         float p1[3], p2[3];
         sphere_param(o, d, sm.cell, depth, p1, p2);
-        st_chunk(abuf, row, kb++, tc::pack2(p1[0], p1[1], fp16), tc::pack2(p1[2], p2[0], fp16),
+        st_chunk(abuf, row, (MODE == 1 ? 2 : 1) * nq, tc::pack2(p1[0], p1[1], fp16), tc::pack2(p1[2], p2[0], fp16),
                  tc::pack2(p2[1], p2[2], fp16), 0u);
     }
-    for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+    // ---- the owner's zero chunks (all of an empty row; after [p~1 | p~2] up to K0 otherwise): the
+    // gathered feature chunks below are written by other lanes and never overlap them
+    for (int kb = valid ? (MODE == 1 ? 2 : 1) * nq + 1 : 0; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+    // ---- cooperative corner gather: G lanes per sample
+    const int lane = threadIdx.x & 31;
+    const int row0 = row - lane;                         // the warp's first row of the tile
+    const int nseg = (md.F * (feat_bf16 ? 2 : 4)) >> 4;  // 16-byte segments of a vertex row
+    const int G = nseg >= 5 ? 8 : (nseg >= 3 ? 4 : nseg);
+    const int gsh = G == 8 ? 3 : (G == 4 ? 2 : (G == 2 ? 1 : 0));
+    const int q = lane & (G - 1);
+    const uint32_t full = 0xFFFFFFFFu;
+    const int ok_self = valid ? 1 : 0;
+#pragma unroll 1
+    for (int b = 0; b < G; ++b) {
+        const int src = (b << (5 - gsh)) + (lane >> gsh);  // sample (lane of the warp) served in this pass
+        const int ok = __shfl_sync(full, ok_self, src);
+        int vs[8];
+        float u0[3], u1[3];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) vs[v] = __shfl_sync(full, vid[v], src);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            u0[a] = __shfl_sync(full, ua[a], src);
+            u1[a] = MODE == 1 ? __shfl_sync(full, ub[a], src) : 0.f;
+        }
+        if (!ok) continue;
+        float xa[8], xb[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            xa[v] = corner_weight(u0, v);
+            xb[v] = MODE == 1 ? corner_weight(u1, v) : 0.f;
+        }
+        for (int seg = q; seg < nseg; seg += G)
+            gather_corner_seg<MODE>(feats, feat_bf16, md.F, nq, vs, xa, xb, seg, fp16, abuf, row0 + src);
+    }
 }
 
 // The gather of a tile is latency-bound, so each warpgroup keeps the sample
@@ -465,7 +572,7 @@ __device__ __forceinline__ void epi_chunk16(const uint32_t (&v)[16], uint8_t *ab
 // 3 loads 16 columns at a time with the next load in flight while a chunk is
 // packed.
 template <int H, int EPI, int MODE>
-__global__ void __launch_bounds__(EPI == 2 ? 384 : 512, 1)
+__global__ void __launch_bounds__(EPI == 2 || MODE == 1 ? 384 : 512, 1)
     mlp_forward_tc_kernel(const __grid_constant__ SceneTable T, const TcFwdParams P) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
@@ -712,7 +819,7 @@ static int fwd_tc(const SceneTable &T, const TcFwdParams &P0, const MlpDims &md,
     int rc = tc_forward_config(md, lay, P, smem);
     if (rc) return rc;
     if (n_wg_override > 0 && n_wg_override < P.n_wg) P.n_wg = n_wg_override;
-    if (EPI == 2 && P.n_wg > 3) P.n_wg = 3;
+    if ((EPI == 2 || MODE == 1) && P.n_wg > 3) P.n_wg = 3;
     if (cudaFuncSetAttribute(mlp_forward_tc_kernel<H, EPI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;

@@ -295,10 +295,81 @@ def _opts(K: int, bg: Sequence[float]) -> RenderOpts:
     return o
 
 
+# ---------------------------------------------------------------------------
+# argument checks: the C ABI takes raw device pointers, so a table of the wrong
+# dtype or shape would be read out of bounds on the GPU; the binding refuses it
+# ---------------------------------------------------------------------------
+def _param_count(dims) -> int:
+    """Flat parameter count of layers [(out, in), ...]: W (out x in) then b."""
+    return sum(o * i + o for o, i in dims)
+
+
+def _net_dims(net: "Network"):
+    return [(net.hidden, net.feat_dim + 9)] + [(net.hidden, net.hidden)] * (net.n_hidden - 1) + [(4, net.hidden)]
+
+
+def _td_dims(net: "TwoDecoder"):
+    dt = [(net.hidden_t, 2 * net.feat_t + 6)] + [(net.hidden_t, net.hidden_t)] * (net.n_hidden_t - 1) + \
+        [(2, net.hidden_t)]
+    dc = [(net.hidden_c, net.feat_c + 6)] + [(net.hidden_c, net.hidden_c)] * (net.n_hidden_c - 1) + \
+        [(3, net.hidden_c)]
+    return dt, dc
+
+
+def _check_table(name: str, t: Optional[torch.Tensor], rows: Optional[int], cols: int, feat_dtype: int,
+                 grad: bool = False):
+    """A feature table (or its float32 gradient) of at least `rows` x `cols`."""
+    if t is None:
+        return
+    want = torch.float32 if grad or feat_dtype != FEAT_BF16 else torch.bfloat16
+    if t.dtype != want:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {want} (feat_dtype {feat_dtype})")
+    if t.dim() != 2 or t.shape[1] != cols or (rows is not None and t.shape[0] < rows):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected ({rows}, {cols})")
+
+
+def _check_params(name: str, t: Optional[torch.Tensor], dims):
+    if t is None:
+        return
+    n = _param_count(dims)
+    if t.dtype != torch.float32 or t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} x {t.dtype}, expected at least {n} x torch.float32")
+
+
+def _check_rays(rays: torch.Tensor):
+    if rays.dtype != torch.float32 or rays.dim() != 2 or rays.shape[1] != 6:
+        raise ValueError(f"rays: {tuple(rays.shape)} x {rays.dtype}, expected (N, 6) x torch.float32")
+
+
+def _check_single(tree, features, params, net, rays, d_features=None, d_params=None):
+    _check_rays(rays)
+    _check_table("features", features, tree.n_leaves, net.feat_dim, net.feat_dtype)
+    _check_table("d_features", d_features, tree.n_leaves, net.feat_dim, net.feat_dtype, grad=True)
+    dims = _net_dims(net)
+    _check_params("params", params, dims)
+    _check_params("d_params", d_params, dims)
+
+
+def _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays, d_z_t=None, d_z_c=None, d_params_t=None,
+                       d_params_c=None):
+    _check_rays(rays)
+    nv = getattr(tree, "n_vertices", None)
+    _check_table("z_t", z_t, nv, net.feat_t, net.feat_dtype)
+    _check_table("z_c", z_c, nv, net.feat_c, net.feat_dtype)
+    _check_table("d_z_t", d_z_t, nv, net.feat_t, net.feat_dtype, grad=True)
+    _check_table("d_z_c", d_z_c, nv, net.feat_c, net.feat_dtype, grad=True)
+    dt, dc = _td_dims(net)
+    _check_params("params_t", params_t, dt)
+    _check_params("params_c", params_c, dc)
+    _check_params("d_params_t", d_params_t, dt)
+    _check_params("d_params_c", d_params_c, dc)
+
+
 def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                      rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
                      want_hits: bool = False, out: Optional[tuple] = None, stream=None):
     """Returns (rgb (N,3), depth (N,), hits (N,K) or None, t_io (N,K,2) or None, workspace)."""
+    _check_single(tree, features, params, net, rays)
     N = rays.shape[0]
     if workspace is None:
         workspace = alloc_workspace(net, N, K)
@@ -349,6 +420,7 @@ def svlf_render_rays_two_decoder(tree: Octree, z_t: torch.Tensor, z_c: torch.Ten
                                  want_hits: bool = False, out: Optional[tuple] = None, stream=None):
     """Two-decoder render (the octree's vertex table must be built).
     Returns (rgb, depth, hits or None, t_io or None, workspace)."""
+    _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays)
     N = rays.shape[0]
     if workspace is None:
         workspace = torch.empty(workspace_size_two_decoder(net, N, K) + 256, dtype=torch.uint8, device="cuda")
@@ -374,6 +446,7 @@ def svlf_render_rays_backward_two_decoder(tree: Octree, z_t, z_c, params_t, para
                                           workspace: torch.Tensor = None, stream=None):
     """Accumulates the gradients (those passed) of the two-decoder render whose
     workspace is given."""
+    _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays, d_z_t, d_z_c, d_params_t, d_params_c)
     d = net.desc()
     o = _opts(K, bg)
     wp, wb = _ws_ptr(workspace)
@@ -390,6 +463,7 @@ def svlf_surface_loss_two_decoder(tree: Octree, z_t, z_c, params_t, params_c, ne
     """Stage 1 of the staged training (Eq. 4 on the rays' surface voxels);
     adds to `loss` (1-element float64) and accumulates the given gradients.
     Returns the workspace."""
+    _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays, d_z_t, d_z_c, d_params_t, d_params_c)
     N = rays.shape[0]
     if workspace is None:
         workspace = torch.empty(workspace_size_two_decoder(net, N, 1) + 256, dtype=torch.uint8, device="cuda")
@@ -419,6 +493,7 @@ def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.
                             stream=None):
     """Render without a workspace (the library's fixed scratch array); for
     callers that may not allocate device memory. Returns (rgb, depth)."""
+    _check_single(tree, features, params, net, rays)
     N = rays.shape[0]
     if out is None:
         out = (torch.empty((N, 3), dtype=torch.float32, device="cuda"),
@@ -471,6 +546,8 @@ def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int,
     """Render every scene in one call; fills each scene's rgb/depth (allocated
     here when missing). Returns the workspace (needed by the backward)."""
     for s in scenes:
+        _check_single(s.tree, s.features, s.params, net, s.rays)
+    for s in scenes:
         if s.rgb is None:
             s.rgb = torch.empty((s.rays.shape[0], 3), dtype=torch.float32, device="cuda")
         if s.depth is None:
@@ -500,6 +577,8 @@ def svlf_workspace_samples_batched(workspace: torch.Tensor, net: Network, scenes
 
 def svlf_render_rays_backward_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg, workspace,
                                       stream=None):
+    for s in scenes:
+        _check_single(s.tree, s.features, s.params, net, s.rays, s.d_features, s.d_params)
     arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
     d = net.desc()
     o = _opts(K, bg)
@@ -512,6 +591,7 @@ def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torc
                               rays: torch.Tensor, K: int, bg, d_rgb: torch.Tensor, d_depth: torch.Tensor,
                               d_features: Optional[torch.Tensor], d_params: Optional[torch.Tensor],
                               workspace: torch.Tensor, stream=None):
+    _check_single(tree, features, params, net, rays, d_features, d_params)
     d = net.desc()
     o = _opts(K, bg)
     wp, wb = _ws_ptr(workspace)

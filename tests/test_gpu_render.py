@@ -139,8 +139,9 @@ def test_bad_arguments_are_reported(tiny):
     with pytest.raises(svlf.SvlfError) as e:
         svlf.svlf_render_rays(tree, f, p, net_for(tiny, svlf.FP32), r, 33, workspace=ws32)
     assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
-    bad = svlf.Network(16, 64, 2, svlf.FP32)
     ws = torch.empty(64, dtype=torch.uint8, device="cuda")
-    with pytest.raises(svlf.SvlfError) as e:
-        svlf.svlf_render_rays(tree, f, p, bad, r, 4, workspace=ws)
+    with pytest.raises(svlf.SvlfError) as e:  # workspace too small
+        svlf.svlf_render_rays(tree, f, p, net_for(tiny, svlf.FP32), r, 4, workspace=ws)
     assert e.value.code == svlf.SVLF_ERR_WORKSPACE
+    with pytest.raises(ValueError):  # feature table narrower than the descriptor's feat_dim
+        svlf.svlf_render_rays(tree, f[:, :8].contiguous(), p, net_for(tiny, svlf.FP32), r, 4)

@@ -136,19 +136,27 @@ def test_argument_errors():
     ijk = torch.from_numpy(np.unique(rng.integers(0, 8, size=(40, 3)), axis=0).astype(np.int32))
     tree = svlf.Octree(ijk, 3)
     net = svlf.TwoDecoder(16, 8, 32, 1, 32, 1)
-    z = torch.zeros((1000, 16), device="cuda")
+    zt = torch.zeros((1000, 16), device="cuda")
+    zc = torch.zeros((1000, 8), device="cuda")
     p = torch.zeros(10000, device="cuda")
     rays = torch.from_numpy(I.pinhole_rays(0.3, 0.2, 8, 8)).cuda()
     with pytest.raises(svlf.SvlfError) as e:  # vertex table not built
-        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, net, rays, 4)
+        svlf.svlf_render_rays_two_decoder(tree, zt, zc, p, p, net, rays, 4)
     assert e.value.code == svlf.SVLF_ERR_ARG
     tree.build_vertices()
     with pytest.raises(svlf.SvlfError) as e:
-        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, svlf.TwoDecoder(16, 8, 32, 1, 32, 1, svlf.FP32), rays, 4)
+        svlf.svlf_render_rays_two_decoder(tree, zt, zc, p, p, svlf.TwoDecoder(16, 8, 32, 1, 32, 1, svlf.FP32), rays,
+                                          4)
     assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
     with pytest.raises(svlf.SvlfError) as e:
-        svlf.svlf_render_rays_two_decoder(tree, z, z, p, p, svlf.TwoDecoder(12, 8, 32, 1, 32, 1), rays, 4)
+        svlf.svlf_render_rays_two_decoder(tree, torch.zeros((1000, 12), device="cuda"), zc, p, p,
+                                          svlf.TwoDecoder(12, 8, 32, 1, 32, 1), rays, 4)
     assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
+    # a table whose dtype or width disagrees with the descriptor is refused before any launch
+    with pytest.raises(ValueError):
+        svlf.svlf_render_rays_two_decoder(tree, zt.bfloat16(), zc.bfloat16(), p, p, net, rays, 4)
+    with pytest.raises(ValueError):
+        svlf.svlf_render_rays_two_decoder(tree, zt, zt, p, p, net, rays, 4)
 
 
 def _rel(g, r):
