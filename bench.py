@@ -9,8 +9,10 @@ the hits saved, L2 colour + 0.1 L1 depth loss, backward with recomputation,
 Adam over every feature and network parameter). Every rays/s figure counts
 render rays plus training rays.
 
-Prints one JSON line (see README of the driver contract in the design doc).
-`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+Prints one JSON line: the metric and its value (whole-job rays/s), ms per
+step, the end-to-end rate through host buffers, the dominant kernel's
+roofline (achieved vs the measured peak, with ncu DRAM traffic), per-kernel
+shares, live clocks and the oracle's CPU rate. `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload instead.
 """
 from __future__ import annotations

@@ -43,7 +43,7 @@ extern "C" {
 #define SVLF_ERR_ARG (-1)          /* invalid argument (null pointer, size, range) */
 #define SVLF_ERR_CUDA (-2)         /* a CUDA runtime call failed */
 #define SVLF_ERR_DEVICE (-3)       /* a kernel latched an error (see device status) */
-#define SVLF_ERR_UNSUPPORTED (-4)  /* shape or mode this build does not handle */
+#define SVLF_ERR_UNSUPPORTED (-4)  /* shape or mode the library does not handle */
 #define SVLF_ERR_WORKSPACE (-5)    /* workspace missing, misaligned or too small */
 
 /* device status bits (svlf_get_device_status) */
