@@ -332,25 +332,6 @@ __device__ __forceinline__ void corner_weight_grads(const float o[3], const floa
     }
 }
 
-// Eight consecutive features (block q) of vertex v, widened to float32.
-__device__ __forceinline__ void vertex_feat8(const void *feats, int feat_bf16, int F, int v, int q, float z[8]) {
-    if (feat_bf16) {
-        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(feats) +
-                                                              (int64_t)v * F) + q);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            z[2 * e] = __uint_as_float(w[e] << 16);
-            z[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
-        }
-    } else {
-        const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(feats) + (int64_t)v * F) + 2 * q;
-        const float4 a = __ldg(src), b = __ldg(src + 1);
-        z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
-        z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
-    }
-}
-
 // Position of o + t d inside voxel `cell`, clamped to [0, 1]^3 (the
 // trilinear coordinates behind corner_weights).
 __device__ __forceinline__ void voxel_coords(const float o[3], const float d[3], float t, const int cell[3], float n,
@@ -979,23 +960,34 @@ static bool tc_bwd_plan(const MlpDims &md, TcBwdParams &P, size_t &smem) {
 
 // Layer-0 epilogue of the two-decoder backward: dL/dpsi (fp32 in TMEM columns
 // [0, F) and, for F^T, [F, 2F) for the exit point) spread to the hit voxel's
-// corner features by their trilinear weights (one float atomic each). The
+// corner features by their trilinear weights (16-byte float reductions). The
 // colour pass (MODE 2) also carries dL/dpsi through the surface point:
 // dL/dx_s = sum_c (Z^C_c . dL/dpsi) grad w_c(x_s), dL/dt_s = w dL/dD + dL/dx_s . d,
 // dL/deta = dL/dt_s (t_in - t_out), and leaves (dL/dtau_pre, dL/deta_pre) in
-// aux for the optical-thickness pass. Every lane runs the TMEM loads; rows
-// without a sample skip the rest.
+// aux for the optical-thickness pass.
+//
+// The corner rows are updated by the warp as a whole, as the forward gathers
+// them: per block of 32 columns each lane stages its sample's dL/dpsi (and
+// dL/dpsi2) in `stage` (a free 32 KB activation buffer: 128 rows of 64
+// floats, 16-byte segment q of row r at position q ^ (r & 7) so that both the
+// owners' writes and the groups' reads spread over the banks), then in pass b
+// the 8 lanes of a group serve one sample, lane q reducing segment q into the
+// eight corner rows: 128 contiguous bytes of a row per group and instruction.
+// Vertex ids and trilinear coordinates come from the owner by shuffle; the
+// weights are recomputed with the owner's products. MODE 2's Z^C . dL/dpsi per
+// corner is summed over the group's lanes (a fixed tree order) into the spare
+// half of the sample's stage row, where its owner reads it. Every lane runs the
+// TMEM loads; rows without a sample skip the rest.
 template <int MODE>
 __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev &SD, const Sample &rec, bool valid,
                                                int64_t s, float carry0, float carry1, float4 prev,
                                                float *__restrict__ dZ, uint32_t trow, float ginv,
-                                               const TcBwdParams &P) {
+                                               const TcBwdParams &P, float *stage) {
     const int F = md.F;
     float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
     int cell[3] = {0, 0, 0};
     int vid[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float wa[8], wb[8];
-    float gw[8][3];
+    float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f};
     const float n = (float)(1 << SD.tree.depth);
     if (valid) {
         const float2 *rp = reinterpret_cast<const float2 *>(SD.rays + 6 * ((int64_t)rec.ray - SD.ray_begin));
@@ -1010,52 +1002,138 @@ __device__ __forceinline__ void two_decoder_dz(const MlpDims &md, const SceneDev
         vid[0] = va.x; vid[1] = va.y; vid[2] = va.z; vid[3] = va.w;
         vid[4] = vb.x; vid[5] = vb.y; vid[6] = vb.z; vid[7] = vb.w;
         if (MODE == 1) {  // carry = (t_in, t_out)
-            corner_weights(o, d, carry0, cell, n, wa);
-            corner_weights(o, d, carry1, cell, n, wb);
+            voxel_coords(o, d, carry0, cell, n, ua);
+            voxel_coords(o, d, carry1, cell, n, ub);
         } else {          // carry = (tau, t_s)
-            corner_weights(o, d, carry1, cell, n, wa);
-            corner_weight_grads(o, d, carry1, cell, n, gw);
+            voxel_coords(o, d, carry1, cell, n, ua);
         }
     }
-    float zdot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int c = 0; c < F; c += 16) {
-        uint32_t a[16], b[16];
-        if (MODE == 1)
-            tc::tmem_ld16x2_wait(trow + (uint32_t)c, trow + (uint32_t)(F + c), a, b);
-        else
-            tc::tmem_ld16_wait(trow + (uint32_t)c, a);
-        if (!valid) continue;
-        const int ne = min(16, F - c);
+    const int lane = threadIdx.x & 31;
+    const int row = threadIdx.x;        // this lane's sample row (the backward runs one warpgroup)
+    const int row0 = row - lane;
+    const int q = lane & 7;             // the group lane's 16-byte segment of a 32-column block
+    const uint32_t full = 0xFFFFFFFFu;
+    const int ok_self = valid ? 1 : 0;
+    float *my = stage + row * 64;
+    for (int c0 = 0; c0 < F; c0 += 32) {
+        // ---- the owner stages its columns c0..c0+31 (those below F)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            if (MODE == 2) {
-                float z[16];
-                vertex_feat8(SD.feats, P.feat_bf16, F, vid[v], c >> 3, z);
-                if (ne > 8) vertex_feat8(SD.feats, P.feat_bf16, F, vid[v], (c >> 3) + 1, z + 8);
-                for (int e = 0; e < ne; ++e) zdot[v] = fmaf(z[e], __uint_as_float(a[e]) * ginv, zdot[v]);
+        for (int h = 0; h < 2; ++h) {
+            const int c = c0 + 16 * h;
+            if (c >= F) break;
+            uint32_t a[16], b[16];
+            if (MODE == 1)
+                tc::tmem_ld16x2_wait(trow + (uint32_t)c, trow + (uint32_t)(F + c), a, b);
+            else
+                tc::tmem_ld16_wait(trow + (uint32_t)c, a);
+            if (!valid) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int pos = ((4 * h + j) ^ (row & 7)) * 4;
+                *reinterpret_cast<float4 *>(my + pos) =
+                    make_float4(__uint_as_float(a[4 * j]), __uint_as_float(a[4 * j + 1]),
+                                __uint_as_float(a[4 * j + 2]), __uint_as_float(a[4 * j + 3]));
+                if (MODE == 1)
+                    *reinterpret_cast<float4 *>(my + 32 + pos) =
+                        make_float4(__uint_as_float(b[4 * j]), __uint_as_float(b[4 * j + 1]),
+                                    __uint_as_float(b[4 * j + 2]), __uint_as_float(b[4 * j + 3]));
             }
-            if (dZ) {
-                // 16-byte vector atomics (rows are F floats, F a multiple of 8)
-                float4 *dst = reinterpret_cast<float4 *>(dZ + (int64_t)vid[v] * F + c);
-                for (int e = 0; e < ne; e += 4) {
-                    float g[4];
+        }
+        __syncwarp();
+        // ---- 8 passes: 4 samples per pass, 8 lanes per sample
+#pragma unroll 1
+        for (int pb = 0; pb < 8; ++pb) {
+            const int src = 4 * pb + (lane >> 3);
+            const int ok = __shfl_sync(full, ok_self, src);
+            int vs[8];
+            float u0[3], u1[3];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float gv = wa[v] * __uint_as_float(a[e + q]);
-                        if (MODE == 1) gv = fmaf(wb[v], __uint_as_float(b[e + q]), gv);
-                        g[q] = gv * ginv;
+            for (int v = 0; v < 8; ++v) vs[v] = __shfl_sync(full, vid[v], src);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                u0[k] = __shfl_sync(full, ua[k], src);
+                u1[k] = MODE == 1 ? __shfl_sync(full, ub[k], src) : 0.f;
+            }
+            const bool act = ok && c0 + 4 * q < F;
+            const float *srow = stage + (row0 + src) * 64;
+            const int pos = (q ^ ((row0 + src) & 7)) * 4;
+            float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+            if (act) {
+                ga = *reinterpret_cast<const float4 *>(srow + pos);
+                if (MODE == 1) gb = *reinterpret_cast<const float4 *>(srow + 32 + pos);
+            }
+            // MODE 2: the eight corner segments of Z^C are loaded before the first reduction
+            // (a reduction orders the memory accesses around it)
+            float4 zc[8];
+            if (MODE == 2 && act) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    if (P.feat_bf16) {
+                        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(
+                            reinterpret_cast<const __nv_bfloat16 *>(SD.feats) + (int64_t)vs[v] * F + c0 + 4 * q));
+                        zc[v] = make_float4(__uint_as_float(t.x << 16), __uint_as_float(t.x & 0xFFFF0000u),
+                                            __uint_as_float(t.y << 16), __uint_as_float(t.y & 0xFFFF0000u));
+                    } else {
+                        zc[v] = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(SD.feats) +
+                                                                        (int64_t)vs[v] * F + c0 + 4 * q));
                     }
-                    red_add_f4(dst + (e >> 2), g[0], g[1], g[2], g[3]);
+                }
+            }
+            float zp[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                zp[v] = 0.f;
+                if (!act) continue;
+                const float wa = corner_weight(u0, v);
+                if (MODE == 2) {
+                    const float z[4] = {zc[v].x, zc[v].y, zc[v].z, zc[v].w};
+                    zp[v] = fmaf(z[0], ga.x * ginv, zp[v]);
+                    zp[v] = fmaf(z[1], ga.y * ginv, zp[v]);
+                    zp[v] = fmaf(z[2], ga.z * ginv, zp[v]);
+                    zp[v] = fmaf(z[3], ga.w * ginv, zp[v]);
+                }
+                if (dZ) {
+                    float g[4];
+                    const float gav[4] = {ga.x, ga.y, ga.z, ga.w};
+                    const float gbv[4] = {gb.x, gb.y, gb.z, gb.w};
+                    const float wb = MODE == 1 ? corner_weight(u1, v) : 0.f;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float gv = wa * gav[e];
+                        if (MODE == 1) gv = fmaf(wb, gbv[e], gv);
+                        g[e] = gv * ginv;
+                    }
+                    red_add_f4(reinterpret_cast<float4 *>(dZ + (int64_t)vs[v] * F + c0 + 4 * q), g[0], g[1], g[2],
+                               g[3]);
+                }
+            }
+            if (MODE == 2) {
+                // the group's sum per corner (lanes of inactive segments add 0), kept in the
+                // spare half of the sample's stage row across 32-column blocks
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    zp[v] += __shfl_xor_sync(full, zp[v], 1);
+                    zp[v] += __shfl_xor_sync(full, zp[v], 2);
+                    zp[v] += __shfl_xor_sync(full, zp[v], 4);
+                }
+                if (ok && q == 0) {
+                    float *zs = stage + (row0 + src) * 64 + 32;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) zs[v] = c0 == 0 ? zp[v] : zs[v] + zp[v];
                 }
             }
         }
+        __syncwarp();
     }
     if (MODE == 2 && valid) {
+        float gw[8][3];
+        corner_weight_grads(o, d, carry1, cell, n, gw);
+        const float *zs = my + 32;
         float dx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int v = 0; v < 8; ++v)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) dx[a] = fmaf(zdot[v], gw[v][a], dx[a]);
+            for (int a = 0; a < 3; ++a) dx[a] = fmaf(zs[v], gw[v][a], dx[a]);
         const float dts = P.w_dD[s] + dx[0] * d[0] + dx[1] * d[1] + dx[2] * d[2];
         const float eta = prev.y;
         const float deta = fmaf(dts, prev.z - prev.w, P.deta ? P.deta[s] : 0.f);
@@ -1440,7 +1518,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 } else if (MODE != 0) {
                     if (form_dz)
                         two_decoder_dz<MODE>(md, SD, rec, valid && sl < S_sc, s, carry0, carry1, prev, d_feat,
-                                             tmem + lane_off, ginv, P);
+                                             tmem + lane_off, ginv, P,
+                                             reinterpret_cast<float *>(smem + P.x_off[1]));
                 } else if (d_feat) {
                     // dL/dz scatter, aggregated over the lanes of a warp that hit the same leaf: a
                     // lane alone with its leaf adds its row straight from the accumulator; groups

@@ -163,21 +163,27 @@ def _rel(g, r):
     return float(np.linalg.norm(g - r) / np.linalg.norm(r))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_backward_matches_oracle_adjoint(prec):
+@pytest.mark.parametrize("prec,ft,fc,feat_bf16", [("bf16", 32, 16, False), ("fp16", 32, 16, False),
+                                                  ("bf16", 64, 40, False), ("bf16", 32, 16, True)])
+def test_backward_matches_oracle_adjoint(prec, ft, fc, feat_bf16):
     """Gradients of Z^T, Z^C and both networks through the GPU render + loss +
     backward against the oracle's adjoint with the same operand rounding.
     Near-degenerate rays are dropped and the L1 depth term is masked where
-    |D - D*| is within float32 noise (its kink)."""
+    |D - D*| is within float32 noise (its kink). The shapes cover the corner
+    scatter's 32-column blocks: one block, two full blocks (Z^T 64) and a
+    partly filled second block (Z^C 40); bfloat16 tables are read as such and
+    their gradients stay float32."""
     from paper_2205_07058_b300 import svlf
     rng = np.random.default_rng(1009)
     sc = I.make_scene(rng, 7, 10, 4)
     tree_o = O.build_octree(sc.leaf_ijk, 7)
     vt = T2.vertex_table(tree_o)
-    ft, fc = 32, 16
     dt, dc = T2.dims_t(ft, 64, 1), T2.dims_c(fc, 64, 2)
     zt = (rng.standard_normal((vt.n_vertices, ft)) * 0.3).astype(np.float32)
     zc = (rng.standard_normal((vt.n_vertices, fc)) * 0.3).astype(np.float32)
+    if feat_bf16:  # the oracle sees the tables the GPU reads
+        zt = torch.from_numpy(zt).to(torch.bfloat16).float().numpy()
+        zc = torch.from_numpy(zc).to(torch.bfloat16).float().numpy()
     pt, pc = _net(rng, dt, 0.3), _net(rng, dc, 0.3)
     az, el = I.random_view_angles(rng, 40)
     rays = I.training_rays(np.random.default_rng(2), 40, 200, 10000, az, el)
@@ -191,16 +197,21 @@ def test_backward_matches_oracle_adjoint(prec):
     # GPU
     tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), 7)
     tree.build_vertices()
-    net = svlf.TwoDecoder(ft, fc, 64, 1, 64, 2, svlf.PRECISIONS[prec])
+    net = svlf.TwoDecoder(ft, fc, 64, 1, 64, 2, svlf.PRECISIONS[prec],
+                          svlf.FEAT_BF16 if feat_bf16 else svlf.FEAT_F32)
     g = {k: torch.from_numpy(v).cuda() for k, v in dict(zt=zt, zc=zc, pt=pt, pc=pc, rays=rays).items()}
-    rgb, depth, _, _, ws = svlf.svlf_render_rays_two_decoder(tree, g["zt"], g["zc"], g["pt"], g["pc"], net,
+    if feat_bf16:
+        g["zt_k"], g["zc_k"] = g["zt"].bfloat16(), g["zc"].bfloat16()
+    else:
+        g["zt_k"], g["zc_k"] = g["zt"], g["zc"]
+    rgb, depth, _, _, ws = svlf.svlf_render_rays_two_decoder(tree, g["zt_k"], g["zc_k"], g["pt"], g["pc"], net,
                                                              g["rays"], K)
     d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     svlf.svlf_loss(rgb, depth, torch.from_numpy(rgb_t).cuda(), torch.from_numpy(depth_t).cuda(),
                    torch.from_numpy(mask).cuda(), 0.1, d_rgb, d_depth, loss)
     grads = {k: torch.zeros_like(g[k]) for k in ("zt", "zc", "pt", "pc")}
-    svlf.svlf_render_rays_backward_two_decoder(tree, g["zt"], g["zc"], g["pt"], g["pc"], net, g["rays"], K,
+    svlf.svlf_render_rays_backward_two_decoder(tree, g["zt_k"], g["zc_k"], g["pt"], g["pc"], net, g["rays"], K,
                                                (0.0, 0.0, 0.0), d_rgb, d_depth, grads["zt"], grads["zc"],
                                                grads["pt"], grads["pc"], ws)
     torch.cuda.synchronize()
