@@ -445,6 +445,17 @@ int svlf_selftest_mma(const uint16_t *A, const uint16_t *B, float *D, int N, int
  * Errors: SVLF_ERR_ARG for blocks < 1 or iters < 1. */
 int svlf_selftest_ffma(float *out, int blocks, int64_t iters, void *stream);
 
+/* Test aid, not part of the rendering method: the bounded mbarrier wait that
+ * every kernel uses. One thread waits for a barrier phase that completes only
+ * if `arrive` != 0, giving up after `limit_cycles` SM clocks (1 .. 4e9). When
+ * it gives up it latches SVLF_DEV_WAIT_TIMEOUT in the device status, as a
+ * kernel does when a copy or MMA it waits for never completes, and returns, so
+ * the context stays usable.
+ * out: device, 2 int64: [0] = 1 if the phase completed, 0 if the wait gave
+ * up; [1] = SM clocks spent waiting.
+ * Errors: SVLF_ERR_ARG for a null `out` or a limit out of range. */
+int svlf_selftest_wait(int64_t limit_cycles, int arrive, int64_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

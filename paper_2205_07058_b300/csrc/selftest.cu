@@ -150,3 +150,35 @@ extern "C" int svlf_selftest_ffma(float *out, int blocks, int64_t iters, void *s
     svlf::ffma_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out, iters, 0.999f, 1e-4f);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------- bounded waits
+namespace svlf {
+// One thread waits on an mbarrier (arrival count 1) that nothing arrives at
+// unless `arrive` is set, giving up after `limit_cycles` SM clocks: the
+// bounded wait every kernel of the library uses, and the status a kernel
+// latches when a copy or an MMA it waits for does not complete. The kernel
+// returns either way, so the context stays usable. out[0] = 1 if the phase
+// completed, 0 if the wait gave up; out[1] = clocks spent waiting.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(long long limit_cycles, int arrive,
+                                                           long long *__restrict__ out) {
+    __shared__ __align__(8) uint64_t s_mbar;
+    if (threadIdx.x != 0) return;
+    const uint32_t mb = tc::smem_u32(&s_mbar);
+    tc::mbar_init(mb, 1);
+    tc::mbar_init_fence();
+    if (arrive) tc::mbar_arrive(mb);
+    const long long t0 = clock64();
+    const bool ok = tc::mbar_wait(mb, 0, limit_cycles);
+    const long long t1 = clock64();
+    if (!ok) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+    out[0] = ok ? 1 : 0;
+    out[1] = t1 - t0;
+}
+}  // namespace svlf
+
+extern "C" int svlf_selftest_wait(int64_t limit_cycles, int arrive, int64_t *out, void *stream) {
+    if (!out || limit_cycles < 1 || limit_cycles > (int64_t)4000000000ll) return SVLF_ERR_ARG;
+    svlf::wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles, arrive ? 1 : 0,
+                                                                    reinterpret_cast<long long *>(out));
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}

@@ -81,7 +81,7 @@ class KernelStat(ctypes.Structure):
 EXPORTS = [
     "svlf_build_octree", "svlf_octree_leaf_ijk", "svlf_octree_info", "svlf_free_octree",
     "svlf_workspace_size", "svlf_render_rays", "svlf_render_rays_backward", "svlf_loss",
-    "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma",
+    "svlf_adam_step", "svlf_get_device_status", "svlf_status_string", "svlf_selftest_mma", "svlf_selftest_wait",
     "svlf_profile_enable", "svlf_profile_report", "svlf_workspace_samples",
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
@@ -132,6 +132,7 @@ def lib():
     L.svlf_octree_leaf_vertices.argtypes = [vp, vp, vp]
     L.svlf_octree_parent_index.argtypes = [vp, vp, P(i64), vp]
     L.svlf_selftest_ffma.argtypes = [vp, ctypes.c_int, i64, vp]
+    L.svlf_selftest_wait.argtypes = [i64, ctypes.c_int, vp, vp]
     L.svlf_workspace_samples_batched.argtypes = [vp, P(MlpDesc), P(i64), i32, i32, P(i64), vp]
     L.svlf_pinhole_rays.argtypes = [P(Camera), i32, i32, i32, vp, vp]
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
@@ -663,6 +664,16 @@ def svlf_measure_ffma_tflops(iters: int = 20000, repeats: int = 5) -> float:
         ms = a.elapsed_time(b)
         best = ms if best is None else min(best, ms)
     return blocks * 256 * iters * 32 / (best / 1e3) / 1e12
+
+
+def svlf_selftest_wait(limit_cycles: int, arrive: bool = False, stream=None):
+    """Runs the bounded-wait self-test; returns (completed, clocks waited).
+    Without `arrive` the wait gives up and latches SVLF_DEV_WAIT_TIMEOUT."""
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _check("svlf_selftest_wait", lib().svlf_selftest_wait(int(limit_cycles), 1 if arrive else 0, _ptr(out),
+                                                          _stream(stream)))
+    r = out.cpu()
+    return bool(r[0].item()), int(r[1].item())
 
 
 def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0, trace_refill=0):
