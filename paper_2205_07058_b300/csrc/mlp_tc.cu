@@ -538,6 +538,26 @@ __device__ __forceinline__ void prefetch_gather(const Sample &r, const void *fea
     prefetch_l2(ray + 5);
 }
 
+// The two-decoder passes: the sample's ray, its leaf's eight vertex ids and
+// the eight corner rows into L2. The ids are loaded (the rows' addresses
+// depend on them), so callers issue this where the thread would wait anyway.
+__device__ __forceinline__ void prefetch_corners(const Sample &r, const int32_t *__restrict__ leaf_vertices,
+                                                 const void *feats, int feat_bf16, int F, const float *rays,
+                                                 int64_t ray_begin) {
+    const float *ray = rays + 6 * ((int64_t)r.ray - ray_begin);
+    prefetch_l2(ray);
+    prefetch_l2(ray + 5);
+    const int4 *vp = reinterpret_cast<const int4 *>(leaf_vertices + 8 * (int64_t)r.leaf);
+    const int4 va = __ldg(vp), vb = __ldg(vp + 1);
+    const int vid[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+    const size_t row_bytes = (size_t)F * (feat_bf16 ? 2 : 4);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const char *f = reinterpret_cast<const char *>(feats) + (size_t)vid[v] * row_bytes;
+        for (size_t b = 0; b < row_bytes; b += 128) prefetch_l2(f + b);
+    }
+}
+
 // ReLU, 16-bit packing and A-operand store of 16 accumulator columns (two
 // 8-column chunks starting at chunk kb).
 __device__ __forceinline__ void epi_chunk16(const uint32_t (&v)[16], uint8_t *abuf, int row, int kb, int fp16) {
@@ -686,6 +706,11 @@ __global__ void __launch_bounds__(EPI == 2 || MODE == 1 ? 384 : 512, 1)
                                               hidden);
                     tc::mma_commit(mbar);
                 }
+                // two-decoder passes: while the first layer runs, the next tile's corner rows go to L2
+                // (its gather then waits on L2, not HBM)
+                if (MODE != 0 && l == 0 && pf.v_cur)
+                    prefetch_corners(pf.cur, SD.tree.leaf_vertices, SD.feats, P.feat_bf16, P.md.F, SD.rays,
+                                     SD.ray_begin);
                 const bool timeout = !tc::mbar_wait(mbar, phase);
                 phase ^= 1u;
                 if (tc::wg_sync_or(wg, timeout)) {
