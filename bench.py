@@ -959,10 +959,10 @@ def run_twodec(args, rank, world, local_rank):
            for k, v in (("zt", zt), ("zc", zc), ("pt", pt), ("pc", pc))}  # param, grad, m, v
     step_no = [0]
 
-    def render_phase():
+    def render_phase(rays=rays, rgb=rgb, depth=depth):
         svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws, out=(rgb, depth))
 
-    def train_phase():
+    def train_phase(trays=trays, loss=loss):
         step_no[0] += 1
         for _, g, _, _ in opt.values():
             g.zero_()
@@ -1063,35 +1063,78 @@ def run_twodec(args, rank, world, local_rank):
               for k, f in (("two_decoder_ft_tc", fft), ("two_decoder_fc_tc", ffc)) if k in kstats}
     tensor.update({k: round(ST * 3.0 * f / (kstats[k][1] / kstats[k][0] / 1e3) / 1e12, 2)
                    for k, f in (("two_decoder_ft_bwd_tc", fft), ("two_decoder_fc_bwd_tc", ffc)) if k in kstats})
-    # end to end: rays from pinned host memory, image back
+    # end to end: every step copies its render rays, training rays and training targets in from
+    # pinned host memory and its image, depth and loss out; steps are pipelined over two buffer
+    # sets and three streams (step k+1's inputs in and step k-1's results out while step k runs)
     e2e = None
     if not args.no_e2e:
         h_rays = torch.from_numpy(rays_h).pin_memory()
-        h_rgb = torch.empty((N, 3)).pin_memory()
-        h_depth = torch.empty((N,)).pin_memory()
-
         h_trays = torch.from_numpy(trays_h).pin_memory()
-        h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        h_tgt = torch.cat([rgb_t.cpu(), depth_t.cpu()[:, None], mask.cpu()[:, None]], dim=1).contiguous().pin_memory()
+        sets = []
+        for _ in range(2):
+            sets.append(dict(rays=torch.empty_like(rays), trays=torch.empty_like(trays),
+                             tgt=torch.empty(h_tgt.shape, device=dev), rgb=torch.empty_like(rgb),
+                             depth=torch.empty_like(depth), loss=torch.zeros_like(loss),
+                             h_rgb=torch.empty((N, 3)).pin_memory(), h_depth=torch.empty((N,)).pin_memory(),
+                             h_loss=torch.empty(1, dtype=torch.float64).pin_memory(),
+                             in_ready=torch.cuda.Event(), used=torch.cuda.Event(), done=torch.cuda.Event(),
+                             copied=torch.cuda.Event()))
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        for b in sets:
+            b["used"].record(stream)
+            b["copied"].record(stream)
 
-        def e2e_step():
-            rays.copy_(h_rays, non_blocking=True)
-            trays.copy_(h_trays, non_blocking=True)
-            step()
-            h_rgb.copy_(rgb, non_blocking=True)
-            h_depth.copy_(depth, non_blocking=True)
-            h_loss.copy_(loss, non_blocking=True)
+        def copy_in(b):
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(b["used"])
+                b["rays"].copy_(h_rays, non_blocking=True)
+                b["trays"].copy_(h_trays, non_blocking=True)
+                b["tgt"].copy_(h_tgt, non_blocking=True)
+                b["in_ready"].record(s_in)
 
-        e2e_step()
+        def compute(b):
+            stream.wait_event(b["in_ready"])
+            stream.wait_event(b["copied"])
+            rgb_t.copy_(b["tgt"][:, :3])
+            depth_t.copy_(b["tgt"][:, 3])
+            mask.copy_(b["tgt"][:, 4])
+            render_phase(b["rays"], b["rgb"], b["depth"])
+            train_phase(b["trays"], b["loss"])
+            b["used"].record(stream)
+            b["done"].record(stream)
+
+        def copy_out(b):
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(b["done"])
+                b["h_rgb"].copy_(b["rgb"], non_blocking=True)
+                b["h_depth"].copy_(b["depth"], non_blocking=True)
+                b["h_loss"].copy_(b["loss"], non_blocking=True)
+                b["copied"].record(s_out)
+
+        def e2e_run(n):
+            copy_in(sets[0])
+            for k in range(n):
+                if k + 1 < n:
+                    copy_in(sets[(k + 1) % 2])
+                compute(sets[k % 2])
+                copy_out(sets[k % 2])
+
+        e2e_run(2)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        b.record(stream)
+        s_in.wait_stream(stream)  # no copy starts before the timed region
+        e2e_run(args.steps)
+        for st in (s_in, s_out):
+            stream.wait_stream(st)
+        b_.record(stream)
         torch.cuda.synchronize()
-        e2e = {"value": (N + NT) * world * args.steps / (a.elapsed_time(b) / 1e3), "unit": "rays/s",
-               "h2d_bytes_per_step": int((h_rays.numel() + h_trays.numel()) * 4),
-               "d2h_bytes_per_step": int((h_rgb.numel() + N) * 4 + 8)}
+        e2e = {"value": (N + NT) * world * args.steps / (a.elapsed_time(b_) / 1e3), "unit": "rays/s",
+               "h2d_bytes_per_step": int((h_rays.numel() + h_trays.numel() + h_tgt.numel()) * 4),
+               "d2h_bytes_per_step": int((N * 3 + N) * 4 + 8),
+               "pipelined": "2 buffer sets; H2D of step k+1 and D2H of step k-1 overlap step k"}
     # ---- the paper's staged schedule (Sec. 4.4) on the same 2^18-ray batch: per stage one
     # training step (loss, backward, Adam on the parameters the stage trains), device-timed
     lam_eta, lam_tau = 1.0, 1.0
