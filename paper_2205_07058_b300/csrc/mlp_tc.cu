@@ -1240,7 +1240,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     const float ginv = 1.f / gscale;
 
     // issue (by row 0) the MMAs queued by `fn`, commit, wait; returns false on timeout
-    auto run = [&](auto &&fn) -> bool {
+    // `during` runs in every thread between the MMAs' issue and the wait for them
+    auto run_and = [&](auto &&fn, auto &&during) -> bool {
         tc::fence_async_smem();
         tc::fence_before_sync();
         tc::wg_sync_or(0, false);
@@ -1249,6 +1250,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             fn();
             tc::mma_commit(mbar);
         }
+        during();
         const bool to = !tc::mbar_wait(mbar, phase);
         phase ^= 1u;
         const bool any = tc::wg_sync_or(0, to);
@@ -1256,6 +1258,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         if (any && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
         return !any;
     };
+    auto run = [&](auto &&fn) -> bool { return run_and(fn, [] {}); };
 
     // ---- streamed weights: slot l % 2 holds W_l (uniform state in every thread)
     int slot_w[2] = {-1, -1};          // layer held (or being loaded) per slot
@@ -1434,14 +1437,22 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     }
                     tc::tmem_wait_st();
                 }
-                if (!run([&] {
-                        const uint32_t idesc = tc::idesc_f16(kTcTile, kHp, bf16, 0, 0);
-                        if (P.bias_mma)  // the accumulator starts at the bias: ones x bias pieces
-                            tc::mma_f16(tmem, tc::sdesc(s_base + (lay.ones_off - img0), kTcTile * 16, 128),
-                                        tc::sdesc(s_base + (lay.bias_b_off[l] - img0), kHp * 16, 128), idesc, 0u);
-                        mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
-                                128, Kl, idesc, true);
-                    })) {
+                if (!run_and(
+                        [&] {
+                            const uint32_t idesc = tc::idesc_f16(kTcTile, kHp, bf16, 0, 0);
+                            if (P.bias_mma)  // the accumulator starts at the bias: ones x bias pieces
+                                tc::mma_f16(tmem, tc::sdesc(s_base + (lay.ones_off - img0), kTcTile * 16, 128),
+                                            tc::sdesc(s_base + (lay.bias_b_off[l] - img0), kHp * 16, 128), idesc,
+                                            0u);
+                            mma_seq(tmem, xa, 2 * kTcTile * 16, kTcTile * 16, 128, wb, 2 * kHp * 16, kHp * 16,
+                                    128, Kl, idesc, true);
+                        },
+                        [&] {
+                            // two-decoder passes: the next tile's corner rows to L2 while layer 0 runs
+                            if (MODE != 0 && l == 0 && pf.v_cur)
+                                prefetch_corners(pf.cur, SD.tree.leaf_vertices, SD.feats, P.feat_bf16, md.F,
+                                                 SD.rays, SD.ray_begin);
+                        })) {
                     aborted = true;
                     break;
                 }
