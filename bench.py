@@ -279,10 +279,14 @@ def fixed_tuning(args):
     return {"tuning": svlf.svlf_get_tuning(), "searched": False}
 
 
-def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None):
+def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None,
+                         gather=None):
     """Roofline figures of kernel `name` in a render + training step: its
     algorithmic work per launch (launches alternate render / training where
-    a kernel runs in both) over its live average launch time."""
+    a kernel runs in both) over its live average launch time. `gather` =
+    (F, bytes per feature, table rows) adds, for the network forward, the
+    feature gather it fuses: one row per sample (not deduplicated), with the
+    table size as the deduplicated lower bound."""
     launches, ms = kstats[name]
     avg_s = ms / launches / 1e3
     tensor_peak = peaks.get("bf16_tflops_sustained", 1400.0)
@@ -305,7 +309,16 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
         return None
     achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
     tr = ncu_traffic(name, tag) if tag else None
-    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+    extra = {}
+    if name == "mlp_forward_tc" and gather is not None:
+        F_, fb, rows = gather
+        gb = (S_r + S_t) / 2.0 * F_ * fb
+        extra["gather"] = {"bytes_per_launch": int(gb), "dedup_lower_bound_bytes": int(rows * F_ * fb),
+                           "rate_gbs": round(gb / avg_s / 1e9, 1),
+                           "frac_of_hbm": round(gb / avg_s / 1e9 / peaks["hbm_gbs"], 4),
+                           "note": "the feature rows the fused gather reads, one per sample (not deduplicated); "
+                                   "the table size bounds the HBM part from below"}
+    return {**extra, "kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
             "peak_source": (f"{peak_src} (sustained)" if bound == "tensor" else f"{peak_src} (copy)" if bound == "hbm"
                             else "measured in this run: float32 FMA kernel (svlf_selftest_ffma)" if ffma_tf
                             else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
@@ -582,7 +595,7 @@ def run_ours(args, rank, world, local_rank):
 
     def kernel_roofline(name):
         return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
-                                    peak_src, ffma_tf, tag)
+                                    peak_src, ffma_tf, tag, gather=(FEAT, 2 if FEAT_BF16 else 4, feats.shape[0]))
 
     if dom:
         roof = kernel_roofline(dom)
@@ -592,7 +605,7 @@ def run_ours(args, rank, world, local_rank):
         r = kernel_roofline(k)
         if r is not None:
             kernel_rooflines[k] = {key: r[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic",
-                                                         "avg_launch_ms")}
+                                                         "avg_launch_ms", "gather") if key in r}
 
     gpu_launches = int(sum(v[0] for v in kstats.values()))
     out = None
