@@ -92,6 +92,29 @@ def test_render_matches_emulating_oracle(small, prec, feat_bf16):
     assert np.quantile(err, 0.99) <= 2e-4
 
 
+@pytest.mark.parametrize("ft,fc,feat_bf16", [(8, 8, False), (8, 8, True), (24, 40, False), (24, 40, True)])
+def test_render_feature_widths(ft, fc, feat_bf16):
+    """The cooperative corner gather at the widths where its lane groups change
+    shape: rows of 1 and 2 16-byte segments (1 and 2 lanes per sample), 3, 5
+    and 6 segments (groups of 4 and 8 with idle lanes) and 10 (lanes taking a
+    second segment), in float32 and bfloat16 storage."""
+    w = _setup(1011, 6, 6, 3, 1, 80, ft=ft, fc=fc, ht=64, nt=1, hc=64, nc=2)
+    K = 5
+    rgb, depth, hits, tio = _gpu(w, "bf16", K, (0.0, 0.0, 0.0), feat_bf16)
+    zt, zc = w["zt"], w["zc"]
+    if feat_bf16:
+        zt = torch.from_numpy(zt).to(torch.bfloat16).float().numpy()
+        zc = torch.from_numpy(zc).to(torch.bfloat16).float().numpy()
+    ref = T2.render2(w["tree_o"], w["vt"], zt, zc, w["pt"], w["pc"], w["dt"], w["dc"], w["rays"], K, lowp="bf16")
+    compare_hits(ref.hits, hits, tio)
+    ok = ~ref.hits.degenerate
+    assert (ref.hits.n[ok] > 0).sum() > 300
+    err = np.abs(rgb[ok] - ref.rgb[ok]).max(axis=1)
+    derr = np.abs(depth[ok] - ref.depth[ok]) / (1 + ref.depth[ok])
+    print(ft, fc, "bf16 storage" if feat_bf16 else "fp32 storage", "colour max", err.max(), "depth max", derr.max())
+    assert err.max() <= 2e-3 and derr.max() <= 2e-3
+
+
 def test_constant_networks_closed_form(small):
     """Zero weights: every hit has tau = relu(b_tau), eta = sigmoid(b_eta),
     c = sigmoid(b_c), so the image depends only on the hit segments."""
