@@ -275,15 +275,16 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, bool fp16) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// ReLU of two float32 values as one packed 16-bit pair: rounding first and
-// taking max(., 0) on the pair gives the same bits as the other order.
+// ReLU of two float32 values as one packed 16-bit pair (a in the low half):
+// one conversion, rounding to nearest and clamping negative results to 0
+// (rounding and the clamp commute, so this is the ReLU of the rounded pair).
 __device__ __forceinline__ uint32_t relu_pack2(float a, float b, bool fp16) {
-    if (fp16) {
-        __half2 h = __hmax2(__floats2half2_rn(a, b), __float2half2_rn(0.f));
-        return *reinterpret_cast<uint32_t *>(&h);
-    }
-    __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(a, b), __float2bfloat162_rn(0.f));
-    return *reinterpret_cast<uint32_t *>(&h);
+    uint32_t r;
+    if (fp16)
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    else
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
 }
 
 // (g0, g1) rounded to a 16-bit pair, each kept where the matching half of the
