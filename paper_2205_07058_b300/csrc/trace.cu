@@ -250,10 +250,12 @@ __device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const bool up = R.d[a] > 0.f;
+            // floor(pos) by one saturating conversion: a position outside the block
+            // (even one far outside int range) gives k outside [lo, hi] and takes the
+            // exact search, which clamps its start itself
             const float p = fmaf(tx, R.d[a], R.o[a]) * fn;
-            const float fl = floorf(fminf(fmaxf(p, -1.0f), fn));
-            const int k = (int)fl;
-            const float fr = p - fl;
+            const int k = __float2int_rd(p);
+            const float fr = p - (float)k;
             const int lo = up ? c[a] : blo[a];
             const int hi = up ? bhi[a] - 1 : c[a];
             // fr in (eps, 1 - eps), as one comparison (its rounding is far inside eps's 16x margin)
