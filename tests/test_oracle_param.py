@@ -3,14 +3,16 @@ entry and exit points on the voxel's minimum bounding sphere, relative to
 the voxel centre, scaled to unit norm."""
 import math
 
+import pytest
+
 import numpy as np
 
 from oracle import oracle as O
 
 
-def _rand(rng, n):
+def _rand(rng, n, L=9):
     c = rng.uniform(0.2, 0.8, size=(n, 3))
-    R = 0.5 * math.sqrt(3.0) * 2.0 ** -9
+    R = 0.5 * math.sqrt(3.0) * 2.0 ** -L
     d = rng.standard_normal((n, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     # aim at a random point inside the sphere from about 2.5 away
@@ -59,10 +61,17 @@ def test_reversed_ray_swaps_entry_and_exit():
     np.testing.assert_allclose(q2, p1, atol=1e-10)
 
 
-def test_matches_textbook_quadratic_in_extended_precision():
-    """Solve a t^2 + 2 b t + cc = 0 directly in long double and compare."""
+@pytest.mark.parametrize("L", [2, 4, 6, 9, 10])
+def test_matches_textbook_quadratic_in_extended_precision(L):
+    """Solve a t^2 + 2 b t + cc = 0 directly in long double and compare.
+
+    In float64 the foot of the perpendicular carries a rounding error of a
+    few ulp of |o - c| (~2.5), which the normalisation divides by R, so the
+    attainable agreement is about eps64 |o - c| / R: 1e-13 holds for voxels
+    down to depth 4 and the bound 16 eps64 |o - c| / R (1.4e-12 at depth 10)
+    holds at every depth."""
     rng = np.random.default_rng(3)
-    o, d, c, R = _rand(rng, 500)
+    o, d, c, R = _rand(rng, 2000, L)
     p1, p2 = O.sphere_params(o, d, c, R)
     ld = np.longdouble
     oL, dL, cL = o.astype(ld), d.astype(ld), c.astype(ld)
@@ -71,7 +80,115 @@ def test_matches_textbook_quadratic_in_extended_precision():
     b = np.sum(dL * oc, axis=1)
     cc = np.sum(oc * oc, axis=1) - ld(R) * ld(R)
     disc = np.sqrt(b * b - a * cc)
+    bound = 16.0 * np.finfo(np.float64).eps * np.linalg.norm(o - c, axis=1) / R
+    if L <= 4:
+        bound = np.minimum(bound, 1e-13)
     for t, p in (((-b - disc) / a, p1), ((-b + disc) / a, p2)):
         x = oL + t[:, None] * dL - cL
         x /= np.sqrt(np.sum(x * x, axis=1))[:, None]
-        np.testing.assert_allclose(p, x.astype(np.float64), atol=1e-8)
+        err = np.abs(p - x.astype(np.float64)).max(axis=1)
+        assert np.all(err <= bound), float((err / bound).max())
+
+
+# ----------------------------------------------------------------------------
+# The voxel's minimum bounding sphere and the network input assembly
+# (Sec. 4.1 "Ray parameterization"): the sphere of a cube voxel
+# [ijk, ijk + 1] * 2^-L is the one through its eight corners, centred on the
+# voxel centre with radius half the cube diagonal. These pins fail for the
+# inscribed radius 2^-L / 2 and for a centre at the voxel's low corner.
+# ----------------------------------------------------------------------------
+def _corners(ijk, L):
+    h = 2.0 ** -L
+    offs = np.array([[a, b, c] for c in (0, 1) for b in (0, 1) for a in (0, 1)], dtype=np.float64)
+    return (ijk[:, None, :].astype(np.float64) + offs[None]) * h
+
+
+def test_bounding_sphere_passes_through_all_eight_corners():
+    rng = np.random.default_rng(11)
+    for L in range(2, 11):
+        ijk = rng.integers(0, 2 ** L, size=(64, 3))
+        c, R = O.voxel_centre_radius(ijk, L)
+        dist = np.linalg.norm(_corners(ijk, L) - c[:, None, :], axis=2)
+        # equidistant corners: c is the cube centre; the common distance is R
+        np.testing.assert_allclose(dist, R, rtol=1e-15, atol=0)
+        # half the cube diagonal, from the voxel's own corners
+        diag = np.linalg.norm(_corners(ijk, L)[:, 7] - _corners(ijk, L)[:, 0], axis=1)
+        np.testing.assert_allclose(R, 0.5 * diag, rtol=1e-15)
+
+
+def _corner_ray(L, ijk, d):
+    """A float32 ray whose line passes (to float32 rounding of the origin)
+    through the low corner of voxel ijk, entering the voxel there."""
+    h = 2.0 ** -L
+    d32 = (np.asarray(d, dtype=np.float64) / np.linalg.norm(d)).astype(np.float32)
+    corner = np.asarray(ijk, dtype=np.float64) * h
+    o32 = (corner - 0.25 * d32.astype(np.float64)).astype(np.float32)
+    return np.concatenate([o32, d32])[None, :].astype(np.float32)
+
+
+@pytest.mark.parametrize("direction", [(1.0, 2.0, 3.0), (3.0, 1.0, 2.0), (1.0, 1.0, 1.0)])
+def test_ray_entering_at_a_corner_enters_the_sphere_there(direction):
+    """A ray that enters the voxel exactly at its low corner enters the
+    bounding sphere at that corner too (the corner lies on the sphere and the
+    voxel lies inside it), so through trace + sample_inputs p~1 =
+    (corner - c) / R = -(1, 1, 1)/sqrt(3) for every such direction, not only
+    the cube diagonal."""
+    L = 3
+    ijk = np.array([3, 4, 2])
+    tree = O.build_octree(ijk[None, :].astype(np.int32), L)
+    ray = _corner_ray(L, ijk, direction)
+    hits = O.trace(tree, ray, 4)
+    assert hits.n[0] == 1 and hits.rank[0, 0] == 0
+    F = 4
+    feats = np.arange(F, dtype=np.float32)[None, :] + 1.0
+    ray_of, slot, rank, h0, tmid = O.sample_inputs(tree, ray, hits, feats)
+    p1 = h0[0, F + 3:F + 6]
+    np.testing.assert_allclose(p1, -np.ones(3) / math.sqrt(3.0), atol=2e-6)
+    if np.allclose(direction, 1.0):
+        # along the diagonal the exit is the opposite corner
+        np.testing.assert_allclose(h0[0, F + 6:F + 9], np.ones(3) / math.sqrt(3.0), atol=2e-6)
+
+
+def _scene_hits(seed, L, n_rays):
+    from paper_2205_07058_b300 import inputs as I
+    rng = np.random.default_rng(seed)
+    scene = I.make_scene(rng, L, 6, 3)
+    tree = O.build_octree(scene.leaf_ijk, L)
+    az, el = I.random_view_angles(rng, 1)
+    rays = I.pinhole_rays(az[0], el[0], 48, 48)[:n_rays]
+    hits = O.trace(tree, rays, 6)
+    return tree, rays, hits
+
+
+@pytest.mark.parametrize("L", [4, 6, 9])
+def test_sample_inputs_columns_and_sphere_points_on_the_ray(L):
+    """h0 = [z | d | p~1 | p~2]: z is the hit leaf's feature row, d the ray
+    direction; c + R p~i (c, R written out here from the voxel's corners) lie
+    on the ray, p~1 before p~2 along d, and the hit segment's midpoint lies
+    inside the voxel of the hit leaf's coordinates."""
+    tree, rays, hits = _scene_hits(100 + L, L, 48 * 48)
+    F = 5
+    feats = np.random.default_rng(1).standard_normal((tree.n_leaves, F)).astype(np.float32)
+    ray_of, slot, rank, h0, tmid = O.sample_inputs(tree, rays, hits, feats)
+    assert h0.shape == (ray_of.shape[0], F + 9) and ray_of.shape[0] > 100
+    np.testing.assert_array_equal(h0[:, :F], feats[hits.rank[ray_of, slot]].astype(np.float64))
+    o = rays[ray_of, :3].astype(np.float64)
+    d = rays[ray_of, 3:].astype(np.float64)
+    np.testing.assert_array_equal(h0[:, F:F + 3], d)
+    ijk = tree.leaf_ijk()[rank]
+    cr = _corners(ijk, L)
+    c = cr.mean(axis=1)
+    R = 0.5 * np.linalg.norm(cr[:, 7] - cr[:, 0], axis=1)
+    h = 2.0 ** -L
+    for col in (F + 3, F + 6):
+        pt = c + R[:, None] * h0[:, col:col + 3]
+        off = np.cross(pt - o, d)  # distance from the ray's line
+        assert np.abs(off).max() <= 1e-9 * max(1.0, 1.0 / (R.min() * 1e3)), np.abs(off).max()
+    t1 = np.sum((c + R[:, None] * h0[:, F + 3:F + 6] - o) * d, axis=1)
+    t2 = np.sum((c + R[:, None] * h0[:, F + 6:F + 9] - o) * d, axis=1)
+    assert np.all(t2 > t1)
+    # the sphere chord contains the voxel's slab segment
+    t_in, t_out = hits.t_in[ray_of, slot], hits.t_out[ray_of, slot]
+    assert np.all(t1 <= t_in + 1e-12) and np.all(t2 >= t_out - 1e-12)
+    mid = o + tmid[:, None] * d
+    assert np.all(mid >= ijk * h - 1e-12) and np.all(mid <= (ijk + 1) * h + 1e-12)
