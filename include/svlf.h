@@ -203,6 +203,19 @@ int svlf_loss(const float *rgb, const float *depth, const float *rgb_target,
               const float *depth_target, const float *mask, int64_t n, float depth_weight,
               float *d_rgb, float *d_depth, double *loss_accum, void *stream);
 
+/* The loss of one shard of a training batch of n_total rays split across
+ * ranks (data-parallel training over the ray batch): the same per-ray terms
+ * over this shard's n rays, divided by n_total instead of n,
+ *   L_shard = (1/n_total) sum_{r in shard} [ |C_r - C*_r|^2 + w m_r |D_r - D*_r| ],
+ * with d_rgb, d_depth scaled alike. The shards' losses, and therefore their
+ * gradients after the backward, sum exactly to the whole batch's mean loss
+ * and its gradient, so one all-reduce (sum) of the gradient buffers completes
+ * the batch's gradient on every rank. svlf_loss is the case n_total = n.
+ * Errors: SVLF_ERR_ARG also for n_total < n. */
+int svlf_loss_shard(const float *rgb, const float *depth, const float *rgb_target,
+                    const float *depth_target, const float *mask, int64_t n, int64_t n_total,
+                    float depth_weight, float *d_rgb, float *d_depth, double *loss_accum, void *stream);
+
 /* ------------------------------------------------------------ batched form */
 /* Many scenes of uneven octree size in one call (one launch per kernel for
  * all of them; the calls queue no host-device copy and can be captured in a
@@ -348,10 +361,43 @@ int svlf_adam_step(float *params, const float *grads, float *m, float *v, int64_
                    float beta1, float beta2, float eps, int64_t step, void *bf16_shadow,
                    void *stream);
 
+/* svlf_adam_step with the step count read from device memory when the
+ * kernels run (step: device, one int64_t, values < 1 act as 1), so that a
+ * captured CUDA graph that replays a whole training step, Adam included,
+ * needs no host argument that changes from step to step. The bias
+ * corrections 1 / (1 - beta^t) are formed in float64 by the same sequence of
+ * multiplications as in svlf_adam_step, so both give identical results for
+ * the same step. */
+int svlf_adam_step_device(float *params, const float *grads, float *m, float *v, int64_t n, float lr,
+                          float beta1, float beta2, float eps, const int64_t *step, void *bf16_shadow,
+                          void *stream);
+
+/* Adds one to the device step counter of svlf_adam_step_device (device, one
+ * int64_t), queued on `stream`: one launch at the start of each training
+ * step's optimiser phase. */
+int svlf_step_advance(int64_t *step, void *stream);
+
 /* ------------------------------------------------------------ status */
-/* Reads and clears the device status word (bitwise OR of SVLF_DEV_*).
- * Synchronises the device. */
-int svlf_get_device_status(int *status);
+/* Reads and clears the device status word (bitwise OR of SVLF_DEV_*) in one
+ * atomic exchange queued on `stream`, after the work already queued there,
+ * then synchronises `stream` only and writes the value to *status (host).
+ * Bits latched by work on other streams that has not finished yet are left
+ * for a later read. Two reads that overlap on different streams share one
+ * device-side result slot: issue reads from one host thread at a time.
+ * Errors: SVLF_ERR_ARG for a null `status`, SVLF_ERR_CUDA if the launch or
+ * copy fails. */
+int svlf_get_device_status(void *stream, int *status);
+
+/* Safety bound of the traversal (process-wide): a ray that has taken more
+ * than max_steps walk steps (cells or empty boxes visited; the bound is
+ * checked between rounds of trace_budget steps, so a ray may overrun it by
+ * one round) stops with the hits found so far and latches
+ * SVLF_DEV_STEP_LIMIT. A walk over the finest grid of depth L never needs
+ * more than 3 * 2^L steps, so the default (max_steps = 0) of 3 * 2^L + 64
+ * trips only on a corrupted octree. Lower values truncate real walks: they
+ * serve to exercise the error path. Errors: SVLF_ERR_ARG outside
+ * [0, 2^30]. */
+int svlf_set_step_limit(int64_t max_steps);
 
 const char *svlf_status_string(int status);
 
@@ -369,8 +415,11 @@ const char *svlf_status_string(int status);
  * SVLF_ERR_WORKSPACE before any work is queued. The call allocates nothing.
  * All calls share the array and it keeps the previous call's contents (the
  * sample counter is cleared by each call): calls that overlap on the GPU
- * race. The first call on a device looks up the array's device address;
- * make it before any stream capture. */
+ * race. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for that device's current context;
+ * make that first call before any stream capture. After cudaDeviceReset the
+ * library is loaded into a new context at a possibly different address: the
+ * next call sees the new context and looks the address up again. */
 int svlf_render_rays_static(svlf_octree tree, const void *features, const float *mlp_params,
                             const svlf_mlp_desc *mlp, const float *rays, int64_t n_rays,
                             const svlf_render_opts *opts, float *rgb, float *depth, void *stream);

@@ -331,21 +331,25 @@ def render(tree: Octree, features: np.ndarray, params: np.ndarray, dims, rays: n
 DEPTH_WEIGHT = 0.1
 
 
-def loss(rgb, depth, rgb_t, depth_t, mask) -> float:
-    """Mean over rays of sum_ch (C - C*)^2 + 0.1 * m * |D - D*|."""
-    N = rgb.shape[0]
+def loss(rgb, depth, rgb_t, depth_t, mask, norm=None) -> float:
+    """Mean over rays of sum_ch (C - C*)^2 + 0.1 * m * |D - D*|. With `norm`
+    the sum is divided by norm instead of the ray count: the share of one
+    shard of a batch of `norm` rays, whose shares sum to the batch's mean."""
+    N = rgb.shape[0] if norm is None else norm
     e = np.sum((rgb - rgb_t) ** 2) + DEPTH_WEIGHT * np.sum(mask * np.abs(depth - depth_t))
     return float(e / N)
 
 
 def backward(tree: Octree, r: Render, params: np.ndarray, dims, rgb_t, depth_t, mask, bg,
-             n_leaves: int, feat_dim: int, bf16=False):
-    """Hand-derived adjoint of loss(render(...)). Returns (dL/dfeatures (dense,
-    n_leaves x F), dL/dparams (flat, same layout as params), dC, dD)."""
+             n_leaves: int, feat_dim: int, bf16=False, norm=None):
+    """Hand-derived adjoint of loss(render(...), norm=norm). Returns
+    (dL/dfeatures (dense, n_leaves x F), dL/dparams (flat, same layout as
+    params), dC, dD)."""
     N, K = r.hits.rank.shape
+    M = N if norm is None else norm
     bg = np.asarray(bg, dtype=np.float64)
-    dC = 2.0 * (r.rgb - rgb_t) / N
-    dD = DEPTH_WEIGHT * mask * np.sign(r.depth - depth_t) / N
+    dC = 2.0 * (r.rgb - rgb_t) / M
+    dD = DEPTH_WEIGHT * mask * np.sign(r.depth - depth_t) / M
     # per-slot arrays
     col_k = np.zeros((N, K, 3))
     tm_k = np.zeros((N, K))

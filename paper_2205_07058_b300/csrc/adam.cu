@@ -7,6 +7,33 @@
 
 namespace svlf {
 
+// beta^step by repeated squaring in float64: the same sequence of IEEE
+// multiplications on the host and on the device, so a bias correction formed
+// from a device-side step count equals the one formed from a host argument.
+__host__ __device__ inline double pow_step(double beta, int64_t step) {
+    double r = 1.0, b = beta;
+    for (int64_t e = step; e > 0; e >>= 1) {
+        if (e & 1) r *= b;
+        b *= b;
+    }
+    return r;
+}
+
+// Bias corrections 1 / (1 - beta^t) for t = *step_dev, formed once per block
+// and shared through shared memory.
+__device__ __forceinline__ void device_corrections(const int64_t *step_dev, float b1, float b2, float &c1,
+                                                   float &c2) {
+    __shared__ float s_c[2];
+    if (threadIdx.x == 0) {
+        const int64_t t = *step_dev < 1 ? 1 : *step_dev;
+        s_c[0] = (float)(1.0 / (1.0 - pow_step((double)b1, t)));
+        s_c[1] = (float)(1.0 / (1.0 - pow_step((double)b2, t)));
+    }
+    __syncthreads();
+    c1 = s_c[0];
+    c2 = s_c[1];
+}
+
 __device__ __forceinline__ float adam_update(float &pi, float gi, float &mi, float &vi, float lr,
                                              float b1, float b2, float eps, float c1, float c2) {
     mi = fmaf(b1, mi, (1.f - b1) * gi);
@@ -20,7 +47,8 @@ __device__ __forceinline__ float adam_update(float &pi, float gi, float &mi, flo
 __global__ void adam4_kernel(float4 *__restrict__ p, const float4 *__restrict__ g,
                              float4 *__restrict__ m, float4 *__restrict__ v, int64_t n4, float lr,
                              float b1, float b2, float eps, float c1, float c2,
-                             uint2 *__restrict__ shadow) {
+                             uint2 *__restrict__ shadow, const int64_t *__restrict__ step_dev) {
+    if (step_dev) device_corrections(step_dev, b1, b2, c1, c2);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
         float4 pi = p[i], mi = m[i], vi = v[i];
@@ -42,7 +70,8 @@ __global__ void adam4_kernel(float4 *__restrict__ p, const float4 *__restrict__ 
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v, int64_t n, float lr,
                             float b1, float b2, float eps, float c1, float c2,
-                            __nv_bfloat16 *__restrict__ shadow) {
+                            __nv_bfloat16 *__restrict__ shadow, const int64_t *__restrict__ step_dev) {
+    if (step_dev) device_corrections(step_dev, b1, b2, c1, c2);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -60,14 +89,11 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
 
 using namespace svlf;
 
-extern "C" int svlf_adam_step(float *params, const float *grads, float *m, float *v, int64_t n,
-                              float lr, float beta1, float beta2, float eps, int64_t step,
-                              void *bf16_shadow, void *stream) {
-    if (n < 0 || step < 1 || (n > 0 && (!params || !grads || !m || !v))) return SVLF_ERR_ARG;
-    if (n == 0) return SVLF_OK;
-    const double c1 = 1.0 / (1.0 - std::pow((double)beta1, (double)step));
-    const double c2 = 1.0 / (1.0 - std::pow((double)beta2, (double)step));
-    cudaStream_t s = (cudaStream_t)stream;
+namespace {
+
+int launch_adam(float *params, const float *grads, float *m, float *v, int64_t n, float lr, float beta1,
+                float beta2, float eps, float c1, float c2, const int64_t *step_dev, void *bf16_shadow,
+                cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(grads) |
                       reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(bf16_shadow) % 8 == 0;
@@ -79,7 +105,7 @@ extern "C" int svlf_adam_step(float *params, const float *grads, float *m, float
         if (blocks > cap) blocks = cap;
         adam4_kernel<<<(unsigned)blocks, 256, 0, s>>>(
             (float4 *)params, (const float4 *)grads, (float4 *)m, (float4 *)v, n4, lr, beta1, beta2,
-            eps, (float)c1, (float)c2, (uint2 *)bf16_shadow);
+            eps, c1, c2, (uint2 *)bf16_shadow, step_dev);
     }
     const int64_t done = 4 * n4;
     if (done < n) {
@@ -88,9 +114,39 @@ extern "C" int svlf_adam_step(float *params, const float *grads, float *m, float
         const int64_t cap = (int64_t)num_sms() * 16;
         if (blocks > cap) blocks = cap;
         adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(
-            params + done, grads + done, m + done, v + done, rest, lr, beta1, beta2, eps, (float)c1,
-            (float)c2, bf16_shadow ? (__nv_bfloat16 *)bf16_shadow + done : nullptr);
+            params + done, grads + done, m + done, v + done, rest, lr, beta1, beta2, eps, c1, c2,
+            bf16_shadow ? (__nv_bfloat16 *)bf16_shadow + done : nullptr, step_dev);
     }
     prof_end(s);
+    return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+__global__ void step_advance_kernel(int64_t *step) { *step += 1; }
+
+}  // namespace
+
+extern "C" int svlf_adam_step(float *params, const float *grads, float *m, float *v, int64_t n,
+                              float lr, float beta1, float beta2, float eps, int64_t step,
+                              void *bf16_shadow, void *stream) {
+    if (n < 0 || step < 1 || (n > 0 && (!params || !grads || !m || !v))) return SVLF_ERR_ARG;
+    if (n == 0) return SVLF_OK;
+    const double c1 = 1.0 / (1.0 - pow_step((double)beta1, step));
+    const double c2 = 1.0 / (1.0 - pow_step((double)beta2, step));
+    return launch_adam(params, grads, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2, nullptr, bf16_shadow,
+                       (cudaStream_t)stream);
+}
+
+extern "C" int svlf_adam_step_device(float *params, const float *grads, float *m, float *v, int64_t n,
+                                     float lr, float beta1, float beta2, float eps, const int64_t *step,
+                                     void *bf16_shadow, void *stream) {
+    if (n < 0 || !step || (n > 0 && (!params || !grads || !m || !v))) return SVLF_ERR_ARG;
+    if (n == 0) return SVLF_OK;
+    return launch_adam(params, grads, m, v, n, lr, beta1, beta2, eps, 0.f, 0.f, step, bf16_shadow,
+                       (cudaStream_t)stream);
+}
+
+extern "C" int svlf_step_advance(int64_t *step, void *stream) {
+    if (!step) return SVLF_ERR_ARG;
+    step_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(step);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

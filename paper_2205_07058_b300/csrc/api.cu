@@ -26,6 +26,9 @@ static svlf_tuning g_tuning = {0, 1, 16, 256, 0};
 
 const svlf_tuning &tuning() { return g_tuning; }
 
+// traversal step bound per ray (svlf_set_step_limit); 0 = 3 * 2^L + 64
+int g_step_limit = 0;
+
 MlpDims make_dims(const svlf_mlp_desc &d) {
     return make_dims_io(d.feat_dim, d.feat_dim + 9, d.hidden, d.n_hidden, 4);
 }
@@ -417,15 +420,30 @@ extern "C" int svlf_get_tuning(svlf_tuning *t) {
     return SVLF_OK;
 }
 
-extern "C" int svlf_get_device_status(int *status) {
+namespace svlf {
+// the value the last status read took out of the status word
+__device__ unsigned int g_status_taken = 0;
+
+__global__ void take_status_kernel() { g_status_taken = atomicExch(&g_device_status, 0u); }
+}  // namespace svlf
+
+extern "C" int svlf_get_device_status(void *stream, int *status) {
     if (!status) return SVLF_ERR_ARG;
-    if (cudaDeviceSynchronize() != cudaSuccess) return SVLF_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // read-and-clear in one atomic, ordered after the work queued on `stream`
+    take_status_kernel<<<1, 1, 0, s>>>();
+    if (cudaGetLastError() != cudaSuccess) return SVLF_ERR_CUDA;
     unsigned int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_device_status, sizeof(v)) != cudaSuccess) return SVLF_ERR_CUDA;
-    const unsigned int zero = 0;
-    if (cudaMemcpyToSymbol(g_device_status, &zero, sizeof(zero)) != cudaSuccess)
+    if (cudaMemcpyFromSymbolAsync(&v, g_status_taken, sizeof(v), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SVLF_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SVLF_ERR_CUDA;
     *status = (int)v;
+    return SVLF_OK;
+}
+
+extern "C" int svlf_set_step_limit(int64_t max_steps) {
+    if (max_steps < 0 || max_steps > (int64_t)1 << 30) return SVLF_ERR_ARG;
+    g_step_limit = (int)max_steps;
     return SVLF_OK;
 }
 

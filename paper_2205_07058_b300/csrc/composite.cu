@@ -93,15 +93,15 @@ __global__ void composite_backward_kernel(const __grid_constant__ SceneTable Tb,
     if ((threadIdx.x & 31) == 0 && gmax > 0.f) atomicMax(max_abs_bits, __float_as_uint(gmax));
 }
 
-// L = (1/n) sum_r [ |C - C*|^2 + lambda m |D - D*| ]
+// L = (1/n_norm) sum_{r < n} [ |C - C*|^2 + lambda m |D - D*| ]  (n_norm = n: the mean)
 __global__ void loss_kernel(const float *__restrict__ rgb, const float *__restrict__ depth,
                             const float *__restrict__ rgb_t, const float *__restrict__ depth_t,
-                            const float *__restrict__ mask, int64_t n, float lambda,
+                            const float *__restrict__ mask, int64_t n, int64_t n_norm, float lambda,
                             float *__restrict__ d_rgb, float *__restrict__ d_depth,
                             double *__restrict__ loss_accum) {
     __shared__ double red[32];
     double acc = 0.0;
-    const float inv_n = 1.0f / (float)n;
+    const float inv_n = 1.0f / (float)n_norm;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         float e = 0.f;
@@ -123,7 +123,7 @@ __global__ void loss_kernel(const float *__restrict__ rgb, const float *__restri
     if (threadIdx.x < 32) {
         acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
-        if (threadIdx.x == 0) atomicAdd(loss_accum, acc / (double)n);
+        if (threadIdx.x == 0) atomicAdd(loss_accum, acc / (double)n_norm);
     }
 }
 
@@ -156,16 +156,24 @@ int launch_composite_backward(const SceneTable &T, const Workspace &ws, const fl
 
 using namespace svlf;
 
-extern "C" int svlf_loss(const float *rgb, const float *depth, const float *rgb_target,
-                         const float *depth_target, const float *mask, int64_t n,
-                         float depth_weight, float *d_rgb, float *d_depth, double *loss_accum,
-                         void *stream) {
-    if (n <= 0 || !rgb || !depth || !rgb_target || !depth_target || !d_rgb || !d_depth ||
+extern "C" int svlf_loss_shard(const float *rgb, const float *depth, const float *rgb_target,
+                               const float *depth_target, const float *mask, int64_t n, int64_t n_total,
+                               float depth_weight, float *d_rgb, float *d_depth, double *loss_accum,
+                               void *stream) {
+    if (n <= 0 || n_total < n || !rgb || !depth || !rgb_target || !depth_target || !d_rgb || !d_depth ||
         !loss_accum)
         return SVLF_ERR_ARG;
     prof_begin("loss", (cudaStream_t)stream);
     loss_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        rgb, depth, rgb_target, depth_target, mask, n, depth_weight, d_rgb, d_depth, loss_accum);
+        rgb, depth, rgb_target, depth_target, mask, n, n_total, depth_weight, d_rgb, d_depth, loss_accum);
     prof_end((cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+extern "C" int svlf_loss(const float *rgb, const float *depth, const float *rgb_target,
+                         const float *depth_target, const float *mask, int64_t n,
+                         float depth_weight, float *d_rgb, float *d_depth, double *loss_accum,
+                         void *stream) {
+    return svlf_loss_shard(rgb, depth, rgb_target, depth_target, mask, n, n, depth_weight, d_rgb, d_depth,
+                           loss_accum, stream);
 }

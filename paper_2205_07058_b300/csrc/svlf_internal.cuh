@@ -161,6 +161,9 @@ int num_sms();
 // process-wide launch-shape settings (svlf_set_tuning), with defaults filled in
 const svlf_tuning &tuning();
 
+// traversal step bound per ray set by svlf_set_step_limit (0: 3 * 2^L + 64)
+extern int g_step_limit;
+
 // per-kernel timing (profile.cu); no-ops unless svlf_profile_enable(1)
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(cudaStream_t s);

@@ -149,10 +149,11 @@ __device__ __forceinline__ bool walk_init(const OctreeView &T, Walk &w) {
 // Up to `budget` steps of the walk; hit j goes to slot[j * stride] (16 bytes:
 // rank, packed cell, t_in, t_out). Returns true when the ray is finished (K
 // hits, left the cube, or an error was latched).
-__device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict__ slot, int stride, int budget) {
+__device__ bool walk_steps(const OctreeView &T, Walk &w, int K, int4 *__restrict__ slot, int stride, int budget,
+                           int step_limit) {
     const RayState &R = w.R;
     const int n = R.n;
-    const int max_steps = 3 * n + 64;
+    const int max_steps = step_limit > 0 ? step_limit : 3 * n + 64;
     const int ps = T.pgrid_shift;
     // the step bound is checked once per call (it may overrun by one budget)
     if (w.steps > max_steps) {
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(256, SVLF_TRACE_MIN_BLOCKS) trace_kernel(const
                                                     unsigned int *__restrict__ counter,
                                                     int32_t *__restrict__ hits,
                                                     float *__restrict__ t_io, int budget, int smem_slots,
-                                                    int refill) {
+                                                    int refill, int step_limit) {
     // a lane's hit slots: in shared memory, interleaved [hit][thread] (conflict-free
     // warp stores), when they fit; else its ray's K slots in the global scratch
     extern __shared__ int4 s_slots[];
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(256, SVLF_TRACE_MIN_BLOCKS) trace_kernel(const
         bool done = false;
         if (have) {
             int4 *slot = smem_slots ? s_slots + threadIdx.x : slots + g * K;
-            if (walk_steps(T.s[MULTI ? sc : 0].tree, w, K, slot, ss, budget)) {
+            if (walk_steps(T.s[MULTI ? sc : 0].tree, w, K, slot, ss, budget, step_limit)) {
                 have = false;
                 done = true;
             }
@@ -463,7 +464,7 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     prof_begin("trace", s);
     kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples, reinterpret_cast<int4 *>(ws.outputs),
                                                    ws.ray_span, ws.counter, hits, t_io, tuning().trace_budget,
-                                                   smem_slots, refill);
+                                                   smem_slots, refill, g_step_limit);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }

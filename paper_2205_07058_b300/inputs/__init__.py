@@ -38,7 +38,8 @@ def build_voxelizer(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src,
+                               "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -54,6 +55,10 @@ def _voxlib():
         _lib.svlf_voxelize_union.argtypes = [
             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
             ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+        _lib.svlf_analytic_depth.restype = None
+        _lib.svlf_analytic_depth.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_void_p]
     return _lib
 
 
@@ -233,7 +238,20 @@ def training_rays(rng: np.random.Generator, n_views: int, res: int, batch: int,
 # --------------------------------------------------------------------------
 def analytic_depth(rays: np.ndarray, scene: Scene):
     """D* = first t >= 0 where the ray meets a sphere or box surface; mask = 1
-    where one exists. Computed in float64 from the float32 rays."""
+    where one exists. Computed in float64 from the float32 rays (C helper,
+    threaded; the same arithmetic as _analytic_depth_numpy)."""
+    r = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
+    sph = np.ascontiguousarray(scene.spheres, dtype=np.float64).reshape(-1, 4)
+    box = np.ascontiguousarray(scene.boxes, dtype=np.float64).reshape(-1, 6)
+    depth = np.empty(r.shape[0], dtype=np.float32)
+    mask = np.empty(r.shape[0], dtype=np.float32)
+    _voxlib().svlf_analytic_depth(r.ctypes.data, r.shape[0], sph.ctypes.data, sph.shape[0], box.ctypes.data,
+                                  box.shape[0], depth.ctypes.data, mask.ctypes.data)
+    return depth, mask
+
+
+def _analytic_depth_numpy(rays: np.ndarray, scene: Scene):
+    """Array formulation of analytic_depth (slow; kept to check the C helper)."""
     o = rays[:, :3].astype(np.float64)
     d = rays[:, 3:].astype(np.float64)
     best = np.full(o.shape[0], np.inf)

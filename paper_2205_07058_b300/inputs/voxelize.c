@@ -102,3 +102,64 @@ int64_t svlf_voxelize_union(const double *sph, int n_sph, const double *box, int
     free(all);
     return c.n;
 }
+
+/*
+ * Analytic depth targets (input generation only): for each float32 ray, the
+ * first t >= 0 at which it meets the surface of any primitive (sphere entry,
+ * or its exit when the origin is inside; box-shell slab entry, or exit from
+ * inside), in float64. mask = 1 where such a t exists, else depth = 0 and
+ * mask = 0. The operations and their order follow the array formulation in
+ * inputs/__init__.py (_analytic_depth_numpy), which a test compares this with
+ * bit for bit. One OpenMP thread per ray block.
+ */
+static double np_min(double a, double b) { return (isnan(a) || isnan(b)) ? NAN : (a < b ? a : b); }
+static double np_max(double a, double b) { return (isnan(a) || isnan(b)) ? NAN : (a > b ? a : b); }
+
+void svlf_analytic_depth(const float *rays, int64_t n, const double *sph, int n_sph, const double *box,
+                         int n_box, float *depth, float *mask) {
+#pragma omp parallel for schedule(static, 4096)
+    for (int64_t r = 0; r < n; ++r) {
+        double o[3], d[3];
+        for (int a = 0; a < 3; ++a) {
+            o[a] = (double)rays[6 * r + a];
+            d[a] = (double)rays[6 * r + 3 + a];
+        }
+        double best = INFINITY;
+        for (int p = 0; p < n_sph; ++p) {
+            const double *s = sph + 4 * p;
+            double oc[3] = {o[0] - s[0], o[1] - s[1], o[2] - s[2]};
+            double A = d[0] * d[0] + d[1] * d[1];
+            A = A + d[2] * d[2];
+            double B = oc[0] * d[0] + oc[1] * d[1];
+            B = B + oc[2] * d[2];
+            double C = oc[0] * oc[0] + oc[1] * oc[1];
+            C = C + oc[2] * oc[2];
+            C = C - s[3] * s[3];
+            const double disc = B * B - A * C;
+            const int ok = disc >= 0;
+            const double sq = sqrt(ok ? disc : 0.0);
+            const double t0 = (-B - sq) / A;
+            const double t1 = (-B + sq) / A;
+            double t = t0 >= 0 ? t0 : t1;
+            t = (ok && t >= 0) ? t : INFINITY;
+            best = np_min(best, t);
+        }
+        for (int p = 0; p < n_box; ++p) {
+            const double *b = box + 6 * p;
+            double tmin = NAN, tmax = NAN;
+            for (int a = 0; a < 3; ++a) {
+                const double lo = b[a] - b[3 + a], hi = b[a] + b[3 + a];
+                const double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+                const double mn = np_min(ta, tb), mx = np_max(ta, tb);
+                if (!isnan(mn)) tmin = isnan(tmin) ? mn : (mn > tmin ? mn : tmin);
+                if (!isnan(mx)) tmax = isnan(tmax) ? mx : (mx < tmax ? mx : tmax);
+            }
+            const int hit = tmax >= np_max(tmin, 0.0);
+            const double t = tmin >= 0 ? tmin : tmax;
+            best = np_min(best, hit ? t : INFINITY);
+        }
+        const int m = isfinite(best);
+        depth[r] = (float)(m ? best : 0.0);
+        mask[r] = (float)m;
+    }
+}

@@ -89,7 +89,8 @@ EXPORTS = [
     "svlf_workspace_samples_batched", "svlf_pinhole_rays",
     "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
-    "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth",
+    "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth", "svlf_set_step_limit",
+    "svlf_adam_step_device", "svlf_step_advance", "svlf_loss_shard",
 ]
 
 _lib = None
@@ -116,8 +117,12 @@ def lib():
     L.svlf_render_rays_backward.argtypes = [vp, vp, vp, P(MlpDesc), vp, i64, P(RenderOpts), vp,
                                             vp, vp, vp, vp, sz, vp]
     L.svlf_loss.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp, vp, vp]
+    L.svlf_loss_shard.argtypes = [vp, vp, vp, vp, vp, i64, i64, f32, vp, vp, vp, vp]
     L.svlf_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
-    L.svlf_get_device_status.argtypes = [P(i32)]
+    L.svlf_adam_step_device.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, vp, vp, vp]
+    L.svlf_step_advance.argtypes = [vp, vp]
+    L.svlf_get_device_status.argtypes = [vp, P(i32)]
+    L.svlf_set_step_limit.argtypes = [i64]
     L.svlf_selftest_mma.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]
     L.svlf_workspace_size_batched.argtypes = [P(MlpDesc), i64, i32, i32, P(sz)]
     L.svlf_render_rays_batched.argtypes = [P(SceneDesc), i32, P(MlpDesc), P(RenderOpts), vp, sz, vp]
@@ -602,10 +607,18 @@ def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torc
         _stream(stream)))
 
 
-def svlf_loss(rgb, depth, rgb_t, depth_t, mask, depth_weight: float, d_rgb, d_depth, loss_accum, stream=None):
-    _check("svlf_loss", lib().svlf_loss(_ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), _ptr(mask),
-                                        rgb.shape[0], float(depth_weight), _ptr(d_rgb), _ptr(d_depth),
-                                        _ptr(loss_accum), _stream(stream)))
+def svlf_loss(rgb, depth, rgb_t, depth_t, mask, depth_weight: float, d_rgb, d_depth, loss_accum, stream=None,
+              n_total: Optional[int] = None):
+    """Training loss and its output gradients. With n_total (a data-parallel
+    shard of a batch of n_total rays) the sum is divided by n_total."""
+    if n_total is None:
+        _check("svlf_loss", lib().svlf_loss(_ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), _ptr(mask),
+                                            rgb.shape[0], float(depth_weight), _ptr(d_rgb), _ptr(d_depth),
+                                            _ptr(loss_accum), _stream(stream)))
+    else:
+        _check("svlf_loss_shard", lib().svlf_loss_shard(
+            _ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), _ptr(mask), rgb.shape[0], int(n_total),
+            float(depth_weight), _ptr(d_rgb), _ptr(d_depth), _ptr(loss_accum), _stream(stream)))
 
 
 def svlf_adam_step(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
@@ -613,6 +626,24 @@ def svlf_adam_step(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.9
     _check("svlf_adam_step", lib().svlf_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(),
                                                   float(lr), float(beta1), float(beta2), float(eps), int(step),
                                                   _ptr(bf16_shadow), _stream(stream)))
+
+
+def svlf_adam_step_device(params, grads, m, v, step: torch.Tensor, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                          bf16_shadow: Optional[torch.Tensor] = None, stream=None):
+    """Adam with the step count read from `step` (a 1-element int64 CUDA
+    tensor) when the kernel runs: capturable in a CUDA graph."""
+    if step.dtype != torch.int64 or step.numel() != 1:
+        raise ValueError("step: expected a 1-element torch.int64 tensor")
+    _check("svlf_adam_step_device", lib().svlf_adam_step_device(
+        _ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(), float(lr), float(beta1), float(beta2),
+        float(eps), _ptr(step), _ptr(bf16_shadow), _stream(stream)))
+
+
+def svlf_step_advance(step: torch.Tensor, stream=None):
+    """step += 1 on the device (the counter svlf_adam_step_device reads)."""
+    if step.dtype != torch.int64 or step.numel() != 1:
+        raise ValueError("step: expected a 1-element torch.int64 tensor")
+    _check("svlf_step_advance", lib().svlf_step_advance(_ptr(step), _stream(stream)))
 
 
 def svlf_selftest_mma(A: torch.Tensor, B: torch.Tensor, a_mn_major=False, b_mn_major=False, flags=0,
@@ -709,10 +740,17 @@ def svlf_workspace_samples(workspace: torch.Tensor, net: Network, n_rays: int, K
     return int(n.value)
 
 
-def svlf_get_device_status() -> int:
+def svlf_get_device_status(stream=None) -> int:
+    """Reads and clears the device status word after the work queued on
+    `stream` (default: the current stream); synchronises that stream."""
     s = ctypes.c_int()
-    _check("svlf_get_device_status", lib().svlf_get_device_status(ctypes.byref(s)))
+    _check("svlf_get_device_status", lib().svlf_get_device_status(_stream(stream), ctypes.byref(s)))
     return int(s.value)
+
+
+def svlf_set_step_limit(max_steps: int = 0):
+    """Traversal safety bound per ray (0 = the default 3 * 2^L + 64)."""
+    _check("svlf_set_step_limit", lib().svlf_set_step_limit(int(max_steps)))
 
 
 # ---------------------------------------------------------------------------

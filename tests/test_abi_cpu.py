@@ -66,6 +66,10 @@ def test_host_side_argument_errors(L):
         == svlf.SVLF_ERR_ARG
     assert L.svlf_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None, None) \
         == svlf.SVLF_ERR_ARG
+    assert L.svlf_get_device_status(None, None) == svlf.SVLF_ERR_ARG
+    assert L.svlf_set_step_limit(-1) == svlf.SVLF_ERR_ARG
+    assert L.svlf_set_step_limit(1 << 31) == svlf.SVLF_ERR_ARG
+    assert L.svlf_set_step_limit(0) == svlf.SVLF_OK
 
 
 def test_tuning_arguments_are_checked(L):

@@ -95,6 +95,65 @@ def test_batched_backward_matches_single_calls(prec, nh):
         assert (torch.linalg.norm(b.d_features - df) / torch.linalg.norm(df)).item() <= 1e-4
 
 
+@pytest.mark.parametrize("prec,nh", [("bf16", 3), ("fp16", 3), ("bf16", 4)])
+def test_batched_backward_matches_oracle_adjoint(prec, nh):
+    """The batched backward against the oracle's adjoint scene by scene (the
+    oracle rounding activations and weights to the same 16-bit format), on the
+    training loss of each scene's own rays (L2 colour + 0.1 masked L1 depth,
+    mean over the scene's rays). Near-degenerate rays are dropped beforehand,
+    and the depth term is masked where |D - D*| is within rounding noise (the
+    L1 kink). Tolerance: the single-scene tensor-core gradient tests' 1e-2
+    normwise."""
+    from paper_2205_07058_b300 import svlf
+    shape = I.MLPShape(32, 128, nh)
+    dims = O.layer_dims(32, 128, nh)
+    scenes = _scenes(seed=43, shape=shape)
+    trees_o = []
+    for s in scenes:
+        t = O.build_octree(s["scene"].leaf_ijk, s["scene"].depth)
+        trees_o.append(t)
+        if s["rays"].shape[0]:
+            s["rays"] = s["rays"][~O.trace(t, s["rays"], 8).degenerate]
+    net = svlf.Network(32, 128, nh, svlf.PRECISIONS[prec])
+    batch = _batch(scenes)
+    ws = svlf.svlf_render_rays_batched(batch, net, 8)
+    rng = np.random.default_rng(11)
+    refs = []
+    for s, t, b in zip(scenes, trees_o, batch):
+        n = s["rays"].shape[0]
+        rgb_t = rng.uniform(0, 1, size=(n, 3)).astype(np.float32)
+        depth_t, mask = I.analytic_depth(s["rays"], s["scene"])
+        r = O.render(t, s["feats"], s["params"], dims, s["rays"], 8, bf16=prec)
+        mask = np.where(np.abs(r.depth - depth_t) < 1e-4, 0.0, mask).astype(np.float32)
+        b.d_rgb = torch.empty((n, 3), device="cuda")
+        b.d_depth = torch.empty((n,), device="cuda")
+        b.d_features = torch.zeros_like(b.features)
+        b.d_params = torch.zeros_like(b.params)
+        if n:
+            loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            svlf.svlf_loss(b.rgb, b.depth, torch.from_numpy(rgb_t).cuda(), torch.from_numpy(depth_t).cuda(),
+                           torch.from_numpy(mask).cuda(), 0.1, b.d_rgb, b.d_depth, loss)
+            refs.append(O.backward(t, r, s["params"], dims, rgb_t.astype(np.float64), depth_t.astype(np.float64),
+                                   mask.astype(np.float64), (0, 0, 0), t.n_leaves, 32, bf16=prec)[:2])
+        else:
+            refs.append(None)
+    svlf.svlf_render_rays_backward_batched(batch, net, 8, (0, 0, 0), ws)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    checked = 0
+    for b, ref in zip(batch, refs):
+        if ref is None:
+            assert torch.all(b.d_params == 0) and torch.all(b.d_features == 0)
+            continue
+        dfr, dpr = ref
+        df, dp = b.d_features.cpu().numpy().astype(np.float64), b.d_params.cpu().numpy().astype(np.float64)
+        e_f = np.linalg.norm(df - dfr) / np.linalg.norm(dfr)
+        e_p = np.linalg.norm(dp - dpr) / np.linalg.norm(dpr)
+        assert e_f <= 1e-2 and e_p <= 1e-2, (e_f, e_p)
+        checked += 1
+    assert checked >= 4
+
+
 def test_batched_render_under_cuda_graph():
     from paper_2205_07058_b300 import svlf
     scenes = _scenes(seed=42)

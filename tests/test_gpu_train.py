@@ -96,6 +96,50 @@ def test_adam_matches_oracle():
                                   tp.cpu().to(torch.bfloat16).float().numpy())
 
 
+def test_adam_with_device_step_matches_host_step_and_replays_in_a_graph():
+    """svlf_adam_step_device reads the step from device memory: eager calls
+    after svlf_step_advance equal the host-step calls bit for bit, and a CUDA
+    graph of [advance, Adam] replayed three times equals three eager steps."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(3)
+    n = 50001  # vector body + scalar tail
+    p0 = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    grads = [torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda() for _ in range(3)]
+    ref = [p0.clone(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")]
+    for t, g in enumerate(grads, 1):
+        svlf.svlf_adam_step(ref[0], g, ref[1], ref[2], t, lr=1e-3)
+    dev = [p0.clone(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")]
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for g in grads:
+        svlf.svlf_step_advance(step)
+        svlf.svlf_adam_step_device(dev[0], g, dev[1], dev[2], step, lr=1e-3)
+    torch.cuda.synchronize()
+    assert step.item() == 3
+    for a, b in zip(dev, ref):
+        assert torch.equal(a, b)
+    # the same three steps replayed from one captured graph
+    gp = [p0.clone(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")]
+    gstep = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gin = torch.empty(n, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            svlf.svlf_step_advance(gstep)
+            svlf.svlf_adam_step_device(gp[0], gin, gp[1], gp[2], gstep, lr=1e-3)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    assert gstep.item() == 0  # capture runs nothing
+    for g in grads:
+        gin.copy_(g)
+        graph.replay()
+    torch.cuda.synchronize()
+    assert gstep.item() == 3
+    for a, b in zip(gp, ref):
+        assert torch.equal(a, b)
+
+
 def test_autograd_function_matches_direct_calls(tiny):
     from paper_2205_07058_b300 import svlf
     tree, f, p, r = gpu_inputs(tiny)
@@ -117,3 +161,40 @@ def test_autograd_function_matches_direct_calls(tiny):
     # sums, scaled by the gradient's magnitude
     torch.testing.assert_close(f.grad, df, rtol=1e-5, atol=1e-6 * float(df.abs().max()))
     torch.testing.assert_close(p.grad, dp, rtol=1e-5, atol=1e-6 * float(dp.abs().max()))
+
+
+def test_shard_losses_and_gradients_sum_to_the_batch(tiny):
+    """Data-parallel training's arithmetic on one GPU: the tiny view's rays
+    split into three uneven shards, each shard's loss divided by the whole
+    batch's ray count (svlf_loss_shard) and its backward accumulated into the
+    same gradient buffers, give the batch's loss and gradients (up to the
+    order of float32 atomic additions)."""
+    from paper_2205_07058_b300 import svlf
+    from paper_2205_07058_b300 import dp
+    rng = np.random.default_rng(5)
+    params = I.make_mlp(rng, tiny.mlp, bias_std=0.3)
+    rgb_t, depth_t, mask = _targets(tiny)
+    tree, f, p, r = gpu_inputs(tiny, params=params)
+    net = net_for(tiny, svlf.FP32)
+    N, K = r.shape[0], tiny.K
+    tg = [torch.from_numpy(x).cuda() for x in (rgb_t, depth_t, mask)]
+
+    def run(sl, gbuf, loss):
+        rr = r[sl].contiguous()
+        rgb, depth, _, _, ws = svlf.svlf_render_rays(tree, f, p, net, rr, K)
+        d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+        svlf.svlf_loss(rgb, depth, *(t[sl].contiguous() for t in tg), 0.1, d_rgb, d_depth, loss, n_total=N)
+        svlf.svlf_render_rays_backward(tree, f, p, net, rr, K, (0, 0, 0), d_rgb, d_depth, gbuf.views[0],
+                                       gbuf.views[1], ws)
+
+    full, parts = (dp.GradientBuffer([tuple(f.shape), tuple(p.shape)], device="cuda") for _ in range(2))
+    L_full = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L_parts = torch.zeros(1, dtype=torch.float64, device="cuda")
+    run(slice(0, N), full, L_full)
+    for k in range(3):
+        run(dp.shard(N, k, 3), parts, L_parts)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    assert abs(L_parts.item() - L_full.item()) <= 1e-12 * abs(L_full.item())
+    e = (torch.linalg.norm(parts.flat - full.flat) / torch.linalg.norm(full.flat)).item()
+    assert e <= 1e-6, e
