@@ -80,9 +80,26 @@ typedef struct {
     int feat_dtype; /* SVLF_FEAT_F32 | SVLF_FEAT_BF16 */
 } svlf_mlp_desc;
 
+/* Ray parameterisation r of the network input (Sec. 4.1 "Ray
+ * parameterization"; the text takes the bounding-sphere points relative to
+ * the "voxel origin", which it does not define further):
+ *   SVLF_RPARAM_SPHERE (default): r = [p~1 | p~2], the ray's entry and exit
+ *     points on the voxel's minimum bounding sphere (centre c = the voxel
+ *     centre (ijk + 1/2) 2^-L, radius (sqrt(3)/2) 2^-L), taken from c and
+ *     scaled to unit norm;
+ *   SVLF_RPARAM_AABB: r = [x~1 | x~2], the ray's entry and exit points of the
+ *     voxel box itself (its slab segment, entry clipped at t = 0), in
+ *     voxel-local coordinates (x - c) / (2^-L / 2), each component in
+ *     [-1, 1] (the "local entry/exit points" reading, with the voxel's own
+ *     frame as the origin). */
+#define SVLF_RPARAM_SPHERE 0
+#define SVLF_RPARAM_AABB 1
+
 typedef struct {
     int K;        /* hits evaluated per ray (the first K leaves): 1..32 */
     float bg[3];  /* colour multiplied by the transmittance left after the K-th hit */
+    int rparam_mode; /* SVLF_RPARAM_SPHERE or SVLF_RPARAM_AABB (the single-network
+                      * calls; the two-decoder calls take SVLF_RPARAM_SPHERE only) */
 } svlf_render_opts;
 
 /* ------------------------------------------------------------ octree */

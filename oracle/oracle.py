@@ -11,7 +11,9 @@ float32 inputs to float64:
   order of intersection along the ray, Sec. 4.3);
 * ray parameterisation r = [p~1 | p~2] from the ray's intersections with the
   voxel's minimum bounding sphere, taken relative to the voxel centre and
-  scaled to unit norm (Sec. 4.1, "Ray parameterization");
+  scaled to unit norm (Sec. 4.1, "Ray parameterization"), or, under the
+  other reading of its "voxel origin", the ray's entry and exit points of
+  the voxel box in voxel-local coordinates (aabb_params);
 * the per-sample network: ReLU hidden layers, colour through a sigmoid and
   optical thickness through a ReLU (Sec. 4.5, "Architecture"); the single
   network over [feature | ray direction | r] is the workload's form of the
@@ -273,9 +275,20 @@ class Render:
     w: np.ndarray       # (N, K) compositing weights T_i * alpha_i
 
 
-def sample_inputs(tree: Octree, rays: np.ndarray, hits: Hits, features: np.ndarray):
+def aabb_params(o: np.ndarray, d: np.ndarray, t_in: np.ndarray, t_out: np.ndarray, c: np.ndarray, h: float):
+    """The other reading of "voxel origin": r = [x~1 | x~2], the ray's entry
+    and exit points of the voxel box itself, x_i = o + t_i d with (t_in,
+    t_out) the slab segment (entry clipped at t = 0), in voxel-local
+    coordinates (x_i - c) / (h / 2), each component in [-1, 1]."""
+    x1 = o + t_in[:, None] * d
+    x2 = o + t_out[:, None] * d
+    return (x1 - c) / (0.5 * h), (x2 - c) / (0.5 * h)
+
+
+def sample_inputs(tree: Octree, rays: np.ndarray, hits: Hits, features: np.ndarray, rparam: str = "sphere"):
     """Network inputs h0 = [z | d | p~1 | p~2] of every hit, samples grouped by
-    ray in hit order."""
+    ray in hit order. rparam = "sphere": the bounding-sphere parameterisation
+    (Sec. 4.1); "aabb": the voxel-box reading (aabb_params)."""
     N, K = hits.rank.shape
     ray_of, slot = np.nonzero(hits.rank >= 0)
     rank = hits.rank[ray_of, slot]
@@ -283,7 +296,12 @@ def sample_inputs(tree: Octree, rays: np.ndarray, hits: Hits, features: np.ndarr
     d = rays[ray_of, 3:].astype(np.float64)
     ijk = tree.leaf_ijk()[rank]
     c, R = voxel_centre_radius(ijk, tree.depth)
-    p1, p2 = sphere_params(o, d, c, R)
+    if rparam == "sphere":
+        p1, p2 = sphere_params(o, d, c, R)
+    elif rparam == "aabb":
+        p1, p2 = aabb_params(o, d, hits.t_in[ray_of, slot], hits.t_out[ray_of, slot], c, 2.0 ** -tree.depth)
+    else:
+        raise ValueError(rparam)
     z = np.asarray(features)[rank].astype(np.float64)
     h0 = np.concatenate([z, d, p1, p2], axis=1)
     tmid = 0.5 * (hits.t_in[ray_of, slot] + hits.t_out[ray_of, slot])
@@ -309,13 +327,13 @@ def composite(N: int, K: int, ray_of, slot, colour, tau, tmid, bg):
 
 def render(tree: Octree, features: np.ndarray, params: np.ndarray, dims, rays: np.ndarray,
            K: int, bg=(0.0, 0.0, 0.0), bf16=False, hits: Optional[Hits] = None,
-           feat_bf16_storage: bool = False) -> Render:
+           feat_bf16_storage: bool = False, rparam: str = "sphere") -> Render:
     rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 6)
     N = rays.shape[0]
     if hits is None:
         hits = trace(tree, rays, K)
     feats = np.asarray(features, dtype=np.float32)
-    ray_of, slot, rank, h0, tmid = sample_inputs(tree, rays, hits, feats)
+    ray_of, slot, rank, h0, tmid = sample_inputs(tree, rays, hits, feats, rparam)
     layers = split_params(params, dims)
     xs, pres = mlp_forward(h0, layers, bf16=bf16)
     out = pres[-1]

@@ -166,9 +166,11 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
     int rc = SVLF_OK;
     const int K = opts->K;
     if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
+    if (opts->rparam_mode != SVLF_RPARAM_SPHERE && opts->rparam_mode != SVLF_RPARAM_AABB) return SVLF_ERR_ARG;
     std::memset(&T, 0, sizeof(T));
     T.n = n_scenes;
     T.K = K;
+    T.rparam = opts->rparam_mode;
     int64_t rays = 0, chunks = 0;
     // Traversal work items: kTraceChunk rays each, or fewer for small launches
     // so that every resident warp of the traversal kernel gets work.
@@ -231,7 +233,7 @@ static int render_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svl
     const int fb = mlp.feat_dtype == SVLF_FEAT_BF16;
     if (mlp.precision == SVLF_FP32) {
         if (T.n != 1) return SVLF_ERR_UNSUPPORTED;
-        rc = launch_mlp_forward_f32(md, T.s[0].tree.depth, T.s[0].feats, fb, (const float *)ws.packed_w,
+        rc = launch_mlp_forward_f32(md, T.s[0].tree.depth, T.rparam, T.s[0].feats, fb, (const float *)ws.packed_w,
                                     T.s[0].rays, ws, T.total_rays * (int64_t)T.K, s);
     } else {
         rc = launch_mlp_forward_tc(md, mlp.precision, fb, T, ws, s);
@@ -253,7 +255,7 @@ static int backward_table(const SceneTable &T, const svlf_mlp_desc &mlp, const s
     if (mlp.precision == SVLF_FP32) {
         if (T.n != 1) return SVLF_ERR_UNSUPPORTED;
         const SceneDev &d = T.s[0];
-        return launch_mlp_backward_f32(md, d.tree.depth, d.feats, fb, d.params, (const float *)ws.packed_w,
+        return launch_mlp_backward_f32(md, d.tree.depth, T.rparam, d.feats, fb, d.params, (const float *)ws.packed_w,
                                        d.rays, ws, T.total_rays * (int64_t)T.K,
                                        want_feat ? d.d_feat : nullptr, want_params ? d.d_params : nullptr, s);
     }
@@ -531,6 +533,7 @@ extern "C" int svlf_render_rays_two_decoder(svlf_octree tree, const void *z_t, c
     if (!view.leaf_vertices && view.n_leaves > 0) return SVLF_ERR_ARG;  // svlf_octree_build_vertices first
     if (n_rays > 0 && view.n_leaves > 0 && (!z_t || !z_c || !params_t || !params_c)) return SVLF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(z_c) % 16) return SVLF_ERR_ARG;
+    if (opts && opts->rparam_mode != SVLF_RPARAM_SPHERE) return SVLF_ERR_UNSUPPORTED;
     svlf_scene sc = one_scene(tree, z_t, params_t, rays, n_rays);
     sc.rgb = rgb;
     sc.depth = depth;
@@ -580,6 +583,7 @@ extern "C" int svlf_render_rays_backward_two_decoder(
     sc.d_features = d_z_t;
     sc.d_mlp_params = d_params_t;
     SceneTable T;
+    if (opts && opts->rparam_mode != SVLF_RPARAM_SPHERE) return SVLF_ERR_UNSUPPORTED;
     if ((rc = make_table_core(&sc, 1, opts, true, T))) return rc;
     if (T.total_rays == 0 || (!d_z_t && !d_z_c && !d_params_t && !d_params_c)) return SVLF_OK;
     const size_t stride = two_decoder_stride(*desc, T.total_rays, T.K);

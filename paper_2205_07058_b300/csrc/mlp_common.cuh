@@ -23,17 +23,17 @@ MlpDims make_dims(const svlf_mlp_desc &d);
 MlpDims make_dims_io(int F, int in0, int H, int nh, int out);
 size_t packed_f32_floats(const MlpDims &md);
 int launch_pack_f32(const MlpDims &md, const float *params, float *packed, cudaStream_t s);
-int launch_mlp_forward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+int launch_mlp_forward_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb,
                            const float *packed, const float *rays, const Workspace &ws,
                            int64_t max_samples, cudaStream_t s);
-int launch_mlp_backward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+int launch_mlp_backward_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb,
                             const float *params, const float *packed, const float *rays,
                             const Workspace &ws, int64_t max_samples, float *d_feat,
                             float *d_params, cudaStream_t s);
 size_t backward_f32_smem(const MlpDims &md);
 
-// h0 = [z | d | p~1 | p~2] of one sample, in float32.
-__device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, const void *feats,
+// h0 = [z | d | p~1 | p~2] of one sample, in float32 (rparam: SVLF_RPARAM_*).
+__device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int rparam, const void *feats,
                                                int feat_bf16, const float *rays, const Sample &sm,
                                                float *h0) {
     const int F = md.F;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, con
     const float o[3] = {a.x, a.y, b.x};
     const float d[3] = {b.y, c.x, c.y};
     float p1[3], p2[3];
-    sphere_param_at(o, d, sm.tmid, sm.cell, depth, p1, p2);
+    voxel_param_at(rparam, o, d, sm.tmid, sm.cell, depth, p1, p2);
     h0[F + 0] = d[0]; h0[F + 1] = d[1]; h0[F + 2] = d[2];
     h0[F + 3] = p1[0]; h0[F + 4] = p1[1]; h0[F + 5] = p1[2];
     h0[F + 6] = p2[0]; h0[F + 7] = p2[1]; h0[F + 8] = p2[2];

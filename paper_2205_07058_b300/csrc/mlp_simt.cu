@@ -68,14 +68,14 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
 }
 
 // Write h0 of sample s (or zeros) into column `col` of X (row stride ts).
-__device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
+__device__ __forceinline__ void build_input_column(const MlpDims &md, int depth, int rparam,
                                                    const void *feats, int feat_bf16,
                                                    const float *rays, const Sample *samples,
                                                    int64_t s, int64_t S, float *X, int ts,
                                                    int col, int rows_padded) {
     float h0[kMaxIn];
     if (s < S) {
-        make_input_row(md, depth, feats, feat_bf16, rays, samples[s], h0);
+        make_input_row(md, depth, rparam, feats, feat_bf16, rays, samples[s], h0);
         for (int k = 0; k < md.in0; ++k) X[k * ts + col] = h0[k];
     } else {
         for (int k = 0; k < md.in0; ++k) X[k * ts + col] = 0.f;
@@ -85,7 +85,7 @@ __device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
 
 template <int H>
 __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
-    MlpDims md, int depth, const void *__restrict__ feats, int feat_bf16,
+    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ packed, const float *__restrict__ rays,
     const Sample *__restrict__ samples, const unsigned int *__restrict__ counter,
     int64_t max_samples, float4 *__restrict__ outputs) {
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t s0 = tile * kTsF;
         if (threadIdx.x < kTsF)
-            build_input_column(md, depth, feats, feat_bf16, rays, samples, s0 + threadIdx.x, S, X,
+            build_input_column(md, depth, rparam, feats, feat_bf16, rays, samples, s0 + threadIdx.x, S, X,
                                kTsF, threadIdx.x, md.in0);
         __syncthreads();
         int in = md.in0;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void backprop_delta(const float *__restrict__ W, int 
 
 template <int H>
 __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
-    MlpDims md, int depth, const void *__restrict__ feats, int feat_bf16,
+    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ params, const float *__restrict__ packed,
     const float *__restrict__ rays, const Sample *__restrict__ samples,
     const unsigned int *__restrict__ counter, int64_t max_samples,
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
         const int64_t s0 = tile * kTsB;
         if (threadIdx.x < kTsB) {
             const int64_t s = s0 + threadIdx.x;
-            build_input_column(md, depth, feats, feat_bf16, rays, samples, s, S, A[0], kPadB,
+            build_input_column(md, depth, rparam, feats, feat_bf16, rays, samples, s, S, A[0], kPadB,
                                threadIdx.x, in0p);
             s_leaf[threadIdx.x] = s < S ? samples[s].leaf : -1;
             const float4 g = s < S ? dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -297,7 +297,7 @@ int launch_pack_f32(const MlpDims &md, const float *params, float *packed, cudaS
 }
 
 template <int H>
-static int fwd_f32(const MlpDims &md, int depth, const void *feats, int fb, const float *packed,
+static int fwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *packed,
                    const float *rays, const Workspace &ws, int64_t max_samples, cudaStream_t s) {
     const int dmax = md.in0 > H ? md.in0 : H;
     const size_t smem = sizeof(float) * (size_t)(dmax + H) * kTsF;
@@ -306,21 +306,21 @@ static int fwd_f32(const MlpDims &md, int depth, const void *feats, int fb, cons
         return SVLF_ERR_CUDA;
     int blocks = num_sms() * (smem <= 100 * 1024 ? 2 : 1);
     prof_begin("mlp_forward_f32", s);
-    mlp_forward_f32_kernel<H><<<blocks, 256, smem, s>>>(md, depth, feats, fb, packed, rays,
+    mlp_forward_f32_kernel<H><<<blocks, 256, smem, s>>>(md, depth, rparam, feats, fb, packed, rays,
                                                         ws.samples, ws.counter, max_samples,
                                                         ws.outputs);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
-int launch_mlp_forward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+int launch_mlp_forward_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb,
                            const float *packed, const float *rays, const Workspace &ws,
                            int64_t max_samples, cudaStream_t s) {
     switch (md.H) {
-        case 32: return fwd_f32<32>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
-        case 64: return fwd_f32<64>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
-        case 128: return fwd_f32<128>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
-        case 256: return fwd_f32<256>(md, depth, feats, fb, packed, rays, ws, max_samples, s);
+        case 32: return fwd_f32<32>(md, depth, rparam, feats, fb, packed, rays, ws, max_samples, s);
+        case 64: return fwd_f32<64>(md, depth, rparam, feats, fb, packed, rays, ws, max_samples, s);
+        case 128: return fwd_f32<128>(md, depth, rparam, feats, fb, packed, rays, ws, max_samples, s);
+        case 256: return fwd_f32<256>(md, depth, rparam, feats, fb, packed, rays, ws, max_samples, s);
         default: return SVLF_ERR_UNSUPPORTED;
     }
 }
@@ -332,7 +332,7 @@ size_t backward_f32_smem(const MlpDims &md) {
 }
 
 template <int H>
-static int bwd_f32(const MlpDims &md, int depth, const void *feats, int fb, const float *params,
+static int bwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *params,
                    const float *packed, const float *rays, const Workspace &ws,
                    int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
     const size_t smem = backward_f32_smem(md);
@@ -341,21 +341,21 @@ static int bwd_f32(const MlpDims &md, int depth, const void *feats, int fb, cons
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     prof_begin("mlp_backward_f32", s);
-    mlp_backward_f32_kernel<H><<<num_sms(), 256, smem, s>>>(md, depth, feats, fb, params, packed,
+    mlp_backward_f32_kernel<H><<<num_sms(), 256, smem, s>>>(md, depth, rparam, feats, fb, params, packed,
                                                             rays, ws.samples, ws.counter,
                                                             max_samples, ws.dout, d_feat, d_params);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
 
-int launch_mlp_backward_f32(const MlpDims &md, int depth, const void *feats, int fb,
+int launch_mlp_backward_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb,
                             const float *params, const float *packed, const float *rays,
                             const Workspace &ws, int64_t max_samples, float *d_feat,
                             float *d_params, cudaStream_t s) {
     switch (md.H) {
-        case 32: return bwd_f32<32>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
-        case 64: return bwd_f32<64>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
-        case 128: return bwd_f32<128>(md, depth, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        case 32: return bwd_f32<32>(md, depth, rparam, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        case 64: return bwd_f32<64>(md, depth, rparam, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
+        case 128: return bwd_f32<128>(md, depth, rparam, feats, fb, params, packed, rays, ws, max_samples, d_feat, d_params, s);
         default: return SVLF_ERR_UNSUPPORTED;
     }
 }

@@ -228,7 +228,7 @@ __device__ __forceinline__ void st_half_chunk(uint8_t *abuf, int row, int kb, in
 // Network input h0 = [z | d | p~1 | p~2] of sample `s` written straight into
 // row `row` of a 16-bit A operand (K0 columns): F/8 chunks of features, two
 // chunks of ray direction and entry/exit parameters, zero chunks up to K0.
-__device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, int depth,
+__device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, int depth, int rparam,
                                                    const void *feats, int feat_bf16,
                                                    const float *rays, int64_t ray_begin,
                                                    const Sample &sm, bool valid, int fp16,
@@ -280,7 +280,7 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
         const float o[3] = {ra.x, ra.y, rb.x};
         const float d[3] = {rb.y, rc.x, rc.y};
         float p1[3], p2[3];
-        sphere_param_at(o, d, sm.tmid, sm.cell, depth, p1, p2);
+        voxel_param_at(rparam, o, d, sm.tmid, sm.cell, depth, p1, p2);
         st_chunk(abuf, row, kb++, tc::pack2(d[0], d[1], fp16), tc::pack2(d[2], p1[0], fp16),
                  tc::pack2(p1[1], p1[2], fp16), tc::pack2(p2[0], p2[1], fp16));
         st_chunk(abuf, row, kb++, tc::pack2(p2[2], 0.f, fp16), 0u, 0u, 0u);
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(EPI == 2 || MODE == 1 ? 384 : 512, 1)
             // ---- network input row -> A operand (K0 columns)
             float carry0 = 0.f, carry1 = 0.f;
             if (MODE == 0) {
-                build_input_chunks(P.md, P.lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                build_input_chunks(P.md, P.lay.K0, depth, T.rparam, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
                                    rec, valid, P.fp16, abuf, row, nullptr);
             } else {
                 const float4 prev = (MODE == 2 && valid) ? P.aux[s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1381,7 +1381,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             {
                 float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (MODE == 0) {
-                    build_input_chunks(md, lay.K0, depth, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
+                    build_input_chunks(md, lay.K0, depth, T.rparam, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
                                        rec, valid, P.fp16, smem + P.x_off[0], row, &leaf);
                     if (valid) g = P.dout[s];
                 } else {

@@ -93,7 +93,7 @@ struct SceneTable {
     int64_t total_rays;
     int64_t total_chunks;
     int chunk_rays;  // rays per traversal work item: 32, 64 or kTraceChunk
-    int pad_;
+    int rparam;      // ray parameterisation of the network input (SVLF_RPARAM_*)
     SceneDev s[kMaxScenes];
 };
 
@@ -301,6 +301,53 @@ __device__ __forceinline__ void sphere_param_at(const float o[3], const float d[
         p1[a] = __fmul_rn(p1[a], i1);
         p2[a] = __fmul_rn(p2[a], i2);
     }
+}
+
+// The alternative reading of "voxel origin" (svlf_render_opts.rparam_mode =
+// SVLF_RPARAM_AABB): r = [x~1 | x~2], the ray's entry and exit points of the
+// voxel itself (its slab segment, entry clipped at t = 0) in voxel-local
+// coordinates x~ = (x - c) / (h / 2), each component in [-1, 1]. Formed
+// around the exactly formed point x_t = o + t d of the segment (t = its
+// midpoint), like sphere_param_at: delta = x_t - c, then the segment's ends
+// delta + u d with u found by the slab test in the voxel's own frame, so the
+// result carries no rounding of the distance from the ray origin.
+__device__ __forceinline__ void aabb_param_at(const float o[3], const float d[3], float t, uint32_t cell,
+                                              int depth, float p1[3], float p2[3]) {
+    const float h = ldexpf(1.0f, -depth);
+    const float half = __fmul_rn(0.5f, h);
+    float del[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float pr, pe, sx, se;
+        two_prod(t, d[a], pr, pe);
+        two_sum(o[a], pr, sx, se);
+        const float c = __fmul_rn(__fadd_rn((float)((cell >> (10 * a)) & 1023u), 0.5f), h);  // exact
+        del[a] = __fadd_rn(__fsub_rn(sx, c), __fadd_rn(se, pe));
+    }
+    float u_in = -t, u_out = INFINITY;  // the entry never precedes the ray origin
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.f) continue;  // parallel to this slab: it never bounds the segment
+        const float lo = __fdiv_rn(__fsub_rn(-half, del[a]), d[a]);
+        const float hi = __fdiv_rn(__fsub_rn(half, del[a]), d[a]);
+        u_in = fmaxf(u_in, fminf(lo, hi));
+        u_out = fminf(u_out, fmaxf(lo, hi));
+    }
+    const float inv = __fdiv_rn(1.0f, half);  // a power of two: exact
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p1[a] = __fmul_rn(fmaf(u_in, d[a], del[a]), inv);
+        p2[a] = __fmul_rn(fmaf(u_out, d[a], del[a]), inv);
+    }
+}
+
+// r = [p~1 | p~2] of a sample under the chosen reading (SVLF_RPARAM_*).
+__device__ __forceinline__ void voxel_param_at(int rparam, const float o[3], const float d[3], float t,
+                                               uint32_t cell, int depth, float p1[3], float p2[3]) {
+    if (rparam == SVLF_RPARAM_AABB)
+        aabb_param_at(o, d, t, cell, depth, p1, p2);
+    else
+        sphere_param_at(o, d, t, cell, depth, p1, p2);
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }

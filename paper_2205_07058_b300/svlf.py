@@ -31,6 +31,7 @@ SVLF_DEV_SAMPLE_OVERFLOW = 4
 SVLF_DEV_WAIT_TIMEOUT = 8
 
 FP32, BF16, FP16 = 0, 1, 2
+RPARAM_SPHERE, RPARAM_AABB = 0, 1  # ray parameterisation of the network input (svlf_render_opts.rparam_mode)
 FEAT_F32, FEAT_BF16 = 0, 1
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
 
@@ -53,7 +54,7 @@ class TwoDecoderDescC(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3)]
+    _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3), ("rparam_mode", ctypes.c_int)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -293,11 +294,12 @@ def _ws_ptr(ws: torch.Tensor):
     return ctypes.c_void_p(aligned), ws.numel() - (aligned - p)
 
 
-def _opts(K: int, bg: Sequence[float]) -> RenderOpts:
+def _opts(K: int, bg: Sequence[float], rparam: int = RPARAM_SPHERE) -> RenderOpts:
     o = RenderOpts()
     o.K = int(K)
     for i in range(3):
         o.bg[i] = float(bg[i])
+    o.rparam_mode = int(rparam)
     return o
 
 
@@ -373,7 +375,7 @@ def _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays, d_z_t=None
 
 def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                      rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
-                     want_hits: bool = False, out: Optional[tuple] = None, stream=None):
+                     want_hits: bool = False, out: Optional[tuple] = None, stream=None, rparam: int = RPARAM_SPHERE):
     """Returns (rgb (N,3), depth (N,), hits (N,K) or None, t_io (N,K,2) or None, workspace)."""
     _check_single(tree, features, params, net, rays)
     N = rays.shape[0]
@@ -387,7 +389,7 @@ def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor,
     hits = torch.empty((N, K), dtype=torch.int32, device="cuda") if want_hits else None
     t_io = torch.empty((N, K, 2), dtype=torch.float32, device="cuda") if want_hits else None
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, rparam)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays", lib().svlf_render_rays(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
@@ -496,7 +498,7 @@ def svlf_eta_loss_two_decoder(tree: Octree, net: TwoDecoder, rays, K: int, depth
 
 def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                             rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), out: Optional[tuple] = None,
-                            stream=None):
+                            stream=None, rparam: int = RPARAM_SPHERE):
     """Render without a workspace (the library's fixed scratch array); for
     callers that may not allocate device memory. Returns (rgb, depth)."""
     _check_single(tree, features, params, net, rays)
@@ -506,7 +508,7 @@ def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.
                torch.empty((N,), dtype=torch.float32, device="cuda"))
     rgb, depth = out
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, rparam)
     _check("svlf_render_rays_static", lib().svlf_render_rays_static(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
         _ptr(rgb), _ptr(depth), _stream(stream)))
@@ -548,7 +550,7 @@ def alloc_workspace_batched(net: Network, scenes: Sequence[BatchScene], K: int) 
 
 
 def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg=(0.0, 0.0, 0.0),
-                             workspace: Optional[torch.Tensor] = None, stream=None):
+                             workspace: Optional[torch.Tensor] = None, stream=None, rparam: int = RPARAM_SPHERE):
     """Render every scene in one call; fills each scene's rgb/depth (allocated
     here when missing). Returns the workspace (needed by the backward)."""
     for s in scenes:
@@ -562,7 +564,7 @@ def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int,
         workspace = alloc_workspace_batched(net, scenes, K)
     arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, rparam)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays_batched", lib().svlf_render_rays_batched(
         arr, len(scenes), ctypes.byref(d), ctypes.byref(o), wp, wb, _stream(stream)))
@@ -582,12 +584,12 @@ def svlf_workspace_samples_batched(workspace: torch.Tensor, net: Network, scenes
 
 
 def svlf_render_rays_backward_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg, workspace,
-                                      stream=None):
+                                      stream=None, rparam: int = RPARAM_SPHERE):
     for s in scenes:
         _check_single(s.tree, s.features, s.params, net, s.rays, s.d_features, s.d_params)
     arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, rparam)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays_backward_batched", lib().svlf_render_rays_backward_batched(
         arr, len(scenes), ctypes.byref(d), ctypes.byref(o), wp, wb, _stream(stream)))
@@ -596,10 +598,10 @@ def svlf_render_rays_backward_batched(scenes: Sequence[BatchScene], net: Network
 def svlf_render_rays_backward(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                               rays: torch.Tensor, K: int, bg, d_rgb: torch.Tensor, d_depth: torch.Tensor,
                               d_features: Optional[torch.Tensor], d_params: Optional[torch.Tensor],
-                              workspace: torch.Tensor, stream=None):
+                              workspace: torch.Tensor, stream=None, rparam: int = RPARAM_SPHERE):
     _check_single(tree, features, params, net, rays, d_features, d_params)
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, rparam)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays_backward", lib().svlf_render_rays_backward(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), rays.shape[0],
@@ -761,10 +763,10 @@ class SvlfRender(torch.autograd.Function):
     hand-written kernels (activations recomputed, not stored)."""
 
     @staticmethod
-    def forward(ctx, features, params, tree, net, rays, K, bg):
-        rgb, depth, _, _, ws = svlf_render_rays(tree, features, params, net, rays, K, bg)
+    def forward(ctx, features, params, tree, net, rays, K, bg, rparam=RPARAM_SPHERE):
+        rgb, depth, _, _, ws = svlf_render_rays(tree, features, params, net, rays, K, bg, rparam=rparam)
         ctx.save_for_backward(features, params, rays)
-        ctx.tree, ctx.net, ctx.K, ctx.bg, ctx.ws = tree, net, K, bg, ws
+        ctx.tree, ctx.net, ctx.K, ctx.bg, ctx.ws, ctx.rparam = tree, net, K, bg, ws, rparam
         return rgb, depth
 
     @staticmethod
@@ -773,10 +775,11 @@ class SvlfRender(torch.autograd.Function):
         df = torch.zeros(features.shape, dtype=torch.float32, device="cuda") if ctx.needs_input_grad[0] else None
         dp = torch.zeros_like(params) if ctx.needs_input_grad[1] else None
         svlf_render_rays_backward(ctx.tree, features, params, ctx.net, rays, ctx.K, ctx.bg,
-                                  g_rgb.contiguous(), g_depth.contiguous(), df, dp, ctx.ws)
+                                  g_rgb.contiguous(), g_depth.contiguous(), df, dp, ctx.ws, rparam=ctx.rparam)
         ctx.ws = None
-        return df, dp, None, None, None, None, None
+        return df, dp, None, None, None, None, None, None
 
 
-def render(features, params, tree: Octree, net: Network, rays, K: int, bg=(0.0, 0.0, 0.0)):
-    return SvlfRender.apply(features, params, tree, net, rays, K, tuple(bg))
+def render(features, params, tree: Octree, net: Network, rays, K: int, bg=(0.0, 0.0, 0.0),
+           rparam: int = RPARAM_SPHERE):
+    return SvlfRender.apply(features, params, tree, net, rays, K, tuple(bg), rparam)

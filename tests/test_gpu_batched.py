@@ -107,7 +107,7 @@ def test_batched_backward_matches_oracle_adjoint(prec, nh):
     from paper_2205_07058_b300 import svlf
     shape = I.MLPShape(32, 128, nh)
     dims = O.layer_dims(32, 128, nh)
-    scenes = _scenes(seed=43, shape=shape)
+    scenes = _scenes(seed=49, shape=shape)
     trees_o = []
     for s in scenes:
         t = O.build_octree(s["scene"].leaf_ijk, s["scene"].depth)
@@ -147,11 +147,13 @@ def test_batched_backward_matches_oracle_adjoint(prec, nh):
             continue
         dfr, dpr = ref
         df, dp = b.d_features.cpu().numpy().astype(np.float64), b.d_params.cpu().numpy().astype(np.float64)
+        assert np.isfinite(df).all() and np.isfinite(dp).all()
+        assert np.any(dpr)  # the seed gives every scene samples with tau > 0
         e_f = np.linalg.norm(df - dfr) / np.linalg.norm(dfr)
         e_p = np.linalg.norm(dp - dpr) / np.linalg.norm(dpr)
         assert e_f <= 1e-2 and e_p <= 1e-2, (e_f, e_p)
         checked += 1
-    assert checked >= 4
+    assert checked == 4
 
 
 def test_batched_render_under_cuda_graph():

@@ -192,3 +192,53 @@ def test_sample_inputs_columns_and_sphere_points_on_the_ray(L):
     assert np.all(t1 <= t_in + 1e-12) and np.all(t2 >= t_out - 1e-12)
     mid = o + tmid[:, None] * d
     assert np.all(mid >= ijk * h - 1e-12) and np.all(mid <= (ijk + 1) * h + 1e-12)
+
+
+# ----------------------------------------------------------------------------
+# The voxel-box reading (rparam "aabb"): r = [x~1 | x~2] = the slab segment's
+# ends in voxel-local coordinates (x - c) / (h / 2).
+# ----------------------------------------------------------------------------
+def test_aabb_reading_axis_column_closed_form():
+    """A ray along +z through the centre of a column enters every leaf at its
+    low z face and leaves at its high face: x~1 = (0, 0, -1), x~2 = (0, 0, 1)
+    exactly; for a ray off the column centre by (a, b) h / 2 the first two
+    components are (a, b)."""
+    L, i, j = 3, 5, 2
+    h = 2.0 ** -L
+    tree = O.build_octree(np.array([[i, j, k] for k in (0, 2, 3)], dtype=np.int32), L)
+    for a, b in ((0.0, 0.0), (0.5, -0.25)):
+        ray = np.array([[(i + 0.5 + 0.5 * a) * h, (j + 0.5 + 0.5 * b) * h, -0.5, 0, 0, 1]], dtype=np.float32)
+        hits = O.trace(tree, ray, 4)
+        F = 2
+        _, _, _, h0, _ = O.sample_inputs(tree, ray, hits, np.zeros((3, F), np.float32), rparam="aabb")
+        assert h0.shape[0] == 3
+        np.testing.assert_array_equal(h0[:, F + 3:F + 6], np.tile([a, b, -1.0], (3, 1)))
+        np.testing.assert_array_equal(h0[:, F + 6:F + 9], np.tile([a, b, 1.0], (3, 1)))
+
+
+@pytest.mark.parametrize("L", [4, 9])
+def test_aabb_reading_points_are_the_segment_ends_inside_the_box(L):
+    """Every x~ lies in [-1, 1]^3; x~2 lies on a face (a component of
+    magnitude 1); x~1 lies on a face unless the origin is inside the voxel
+    (then x~1 is the origin); c + (h/2) x~i are the points o + t_in d and
+    o + t_out d of the slab segment (checked by collinearity with the ray and
+    their distance along it), and their midpoint is the sample's midpoint."""
+    tree, rays, hits = _scene_hits(300 + L, L, 48 * 48)
+    F = 3
+    feats = np.zeros((tree.n_leaves, F), np.float32)
+    ray_of, slot, rank, h0, tmid = O.sample_inputs(tree, rays, hits, feats, rparam="aabb")
+    x1, x2 = h0[:, F + 3:F + 6], h0[:, F + 6:F + 9]
+    assert np.all(np.abs(x1) <= 1 + 1e-9) and np.all(np.abs(x2) <= 1 + 1e-9)
+    assert np.all(np.abs(np.abs(x2).max(axis=1) - 1.0) <= 1e-9)
+    inside = hits.t_in[ray_of, slot] == 0.0
+    assert np.all(np.abs(np.abs(x1[~inside]).max(axis=1) - 1.0) <= 1e-9)
+    o = rays[ray_of, :3].astype(np.float64)
+    d = rays[ray_of, 3:].astype(np.float64)
+    h = 2.0 ** -L
+    c = (tree.leaf_ijk()[rank] + 0.5) * h
+    p1, p2 = c + 0.5 * h * x1, c + 0.5 * h * x2
+    for p in (p1, p2):
+        assert np.abs(np.cross(p - o, d)).max() <= 1e-12
+    np.testing.assert_allclose(np.sum((p2 - p1) * d, axis=1),
+                               hits.t_out[ray_of, slot] - hits.t_in[ray_of, slot], atol=1e-12)
+    np.testing.assert_allclose(0.5 * (p1 + p2), o + tmid[:, None] * d, atol=1e-12)
