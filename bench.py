@@ -638,10 +638,15 @@ def run_ours(args, rank, world, local_rank):
                                                          "frac_of_burst") if key in r}
 
     gpu_launches = int(sum(v[0] for v in kstats.values()))
-    if rank == 0:  # the last timed render's outputs on a seeded ray sample (compared in the cpu_baseline leg)
+    if rank == 0:
+        # one more (untimed) render with the parameters as training left them, on a seeded
+        # ray sample, for the parity check of the cpu_baseline leg (which takes those parameters)
+        render_phase()
+        torch.cuda.synchronize()
         idx = np.sort(np.random.default_rng(4242).choice(N, PARITY_SAMPLE, replace=False))
         it = torch.from_numpy(idx).to(dev)
-        W["gpu_sample"] = (idx, rgb[it].cpu().numpy(), depth[it].cpu().numpy(), args.precision)
+        W["gpu_sample"] = (idx, rgb[it].cpu().numpy(), depth[it].cpu().numpy(), args.precision,
+                           feats_k.float().cpu().numpy(), params.cpu().numpy())
     out = None
     if rank == 0:
         out = {
@@ -758,10 +763,10 @@ def parity_sample(W, tree_o):
     near-degenerate (a voxel face within 1e-6 decides a hit) are excluded and
     counted."""
     from oracle import oracle as O
-    idx, g_rgb, g_depth, prec = W["gpu_sample"]
+    idx, g_rgb, g_depth, prec, feats, params = W["gpu_sample"]
     rays = W["render_rays"][idx]
     dims = O.layer_dims(FEAT, HIDDEN, N_HIDDEN)
-    ref = O.render(tree_o, W["feats"], W["params"], dims, rays, K_HITS, feat_bf16_storage=FEAT_BF16)
+    ref = O.render(tree_o, feats, params, dims, rays, K_HITS, feat_bf16_storage=FEAT_BF16)
     ok = ~ref.hits.degenerate
     hit = ok & (ref.hits.n > 0)
 
@@ -774,10 +779,11 @@ def parity_sample(W, tree_o):
 
     outp = {"rays": int(len(idx)), "rays_with_hits": int(hit.sum()), "degenerate_excluded": int((~ok).sum()),
             "precision": prec, "vs_fp64": errs(ref),
-            "note": "the last timed render's outputs on seeded render rays vs the FP64 oracle (depth error "
-                    "relative to 1 + D); computed in the cpu_baseline leg, outside every timed region"}
+            "note": "an untimed render after the timed steps, with the parameters training left, on seeded "
+                    "render rays vs the FP64 oracle on the same parameters (depth error relative to 1 + D); "
+                    "computed in the cpu_baseline leg, outside every timed region"}
     if prec in ("bf16", "fp16"):
-        emu = O.render(tree_o, W["feats"], W["params"], dims, rays, K_HITS, bf16=prec, hits=ref.hits,
+        emu = O.render(tree_o, feats, params, dims, rays, K_HITS, bf16=prec, hits=ref.hits,
                        feat_bf16_storage=FEAT_BF16)
         outp["vs_operand_rounding_oracle"] = errs(emu)
     return outp
