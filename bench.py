@@ -254,8 +254,12 @@ def workload_tag(views: int, res: int, precision: str) -> str:
 
 
 def ncu_traffic(kernel: str, tag: str):
-    """DRAM bytes per launch for `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source and on this workload; else None."""
+    """DRAM traffic of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel source; else None. An entry holds either the bytes
+    per launch of this very workload ("bytes_per_launch", matched by tag) or,
+    for a kernel whose traffic grows with its samples, the bytes per sample
+    measured on a smaller case of the same step ("bytes_per_sample"), which the
+    caller scales by the samples of a launch here."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -267,6 +271,8 @@ def ncu_traffic(kernel: str, tag: str):
         return None
     if ent.get("source_hash") != kernel_source_hash(KERNEL_SOURCES[kernel]):
         return None
+    if "bytes_per_sample" in ent:
+        return ent
     if ent.get("workload") != tag:
         return None
     return ent
@@ -344,7 +350,10 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
                             else "measured in this run: float32 FMA kernel (svlf_selftest_ffma)" if ffma_tf
                             else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
             "unit": unit, "frac": round(achieved / peak, 4),
-            "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic": (None if not tr else int(tr["bytes_per_launch"]) if "bytes_per_launch" in tr
+                        else int(tr["bytes_per_sample"] * ((S_r + S_t) / 2.0 if name == "mlp_forward_tc" else S_t))),
+            **({"traffic_source": f"ncu DRAM bytes per sample on {tr.get('workload')} x this launch's samples"}
+               if tr and "bytes_per_sample" in tr else {}),
             "avg_launch_ms": round(ms / launches, 4)}
 
 
