@@ -46,6 +46,7 @@ SCENE_SEED = 1002
 TEACHER_SEED = 2000
 LR = 1e-3
 DEPTH_WEIGHT = 0.1
+TRAIN_ORDER = "coherent"  # the training batch's rays ordered by view, then pixel Z order (same draws)
 WORKLOAD = ("render 4x1600^2 + train 2^18 rays (100 views of 800^2); depth-9 octree over 64 "
             "spheres + 32 box shells (1.69 M leaves), F=32 fp32, MLP 41->3x128->4, K=8")
 METRIC = "rays/s: render 4x1600^2 + train 2^18 rays (fwd+bwd+Adam), one step each"
@@ -122,11 +123,15 @@ def parse():
                         "mlp_warpgroups=4,mlp_epilogue_batch=1,trace_budget=16,trace_block=128")
     p.add_argument("--render-only", action="store_true",
                    help="time only the render pass (profiling aid; not the benchmark step)")
+    p.add_argument("--train-order", default="coherent", choices=["coherent", "random"],
+                   help="order of the training batch's rays: by view, then pixel Z order (the same uniform draws), "
+                        "or as drawn")
     p.add_argument("--views", type=int, default=None, help="render views (default: the workload's)")
     p.add_argument("--res", type=int, default=None, help="render resolution (default: the workload's)")
     a = p.parse_args()
     if a.workload == "large":
         use_profile(LARGE)
+    globals()["TRAIN_ORDER"] = a.train_order
     if a.views is None:
         a.views = RENDER_VIEWS
     if a.res is None:
@@ -150,7 +155,8 @@ def make_workload(rank: int, views: int, res: int):
     render_rays = np.concatenate([I.pinhole_rays(az[v], el[v], res, res) for v in range(views)])
     trng = np.random.default_rng(SCENE_SEED + 1 + 7919 * rank)
     taz, tel = I.random_view_angles(trng, TRAIN_VIEWS)
-    train_rays = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel)
+    train_rays = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel,
+                                 coherent=TRAIN_ORDER == "coherent")
     depth_t, mask = I.analytic_depth(train_rays, scene)
     teacher = I.make_mlp(np.random.default_rng(TEACHER_SEED), shape)
     return dict(scene=scene, shape=shape, feats=feats, params=params, render_rays=render_rays,
@@ -254,12 +260,14 @@ def workload_tag(views: int, res: int, precision: str) -> str:
 
 
 def ncu_traffic(kernel: str, tag: str):
-    """DRAM traffic of `kernel` from the committed ncu summary, if it was taken
-    on the current kernel source; else None. An entry holds either the bytes
-    per launch of this very workload ("bytes_per_launch", matched by tag) or,
-    for a kernel whose traffic grows with its samples, the bytes per sample
-    measured on a smaller case of the same step ("bytes_per_sample"), which the
-    caller scales by the samples of a launch here."""
+    """ncu figures of `kernel` for the workload `tag` from the committed
+    summary, if they were taken on the current kernel source; else None. An
+    entry holds the DRAM bytes per launch of this workload
+    ("bytes_per_launch"), or, for a kernel whose traffic grows with its
+    samples, the bytes per sample ("bytes_per_sample", possibly measured on a
+    smaller case of the same step, named in "measured_on"), which the caller
+    scales by the samples of a launch; and for the traversal its warp
+    instructions per render and per training ray ("warp_inst_per_ray")."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -271,8 +279,6 @@ def ncu_traffic(kernel: str, tag: str):
         return None
     if ent.get("source_hash") != kernel_source_hash(KERNEL_SOURCES[kernel]):
         return None
-    if "bytes_per_sample" in ent:
-        return ent
     if ent.get("workload") != tag:
         return None
     return ent
@@ -303,7 +309,7 @@ def tensor_peak(peaks, clk, window_s):
 
 
 def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None,
-                         gather=None, tpeak=None):
+                         gather=None, tpeak=None, clk_mhz=None):
     """Roofline figures of kernel `name` in a render + training step: its
     algorithmic work per launch (launches alternate render / training where
     a kernel runs in both) over its live average launch time. `gather` =
@@ -334,6 +340,17 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
     achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
     tr = ncu_traffic(name, tag) if tag else None
     extra = {}
+    if name == "trace" and tr and "warp_inst_per_ray" in tr and clk_mhz:
+        # issue-slot roofline: the launch's warp instructions (ncu counts per render and per training
+        # ray x the rays of each launch, averaged like the time) over its time, against 4 schedulers x 1
+        # instruction per clock on every SM
+        ipr = tr["warp_inst_per_ray"]
+        inst = (ipr["render"] * N + ipr["train"] * NT) / 2.0
+        ipeak = 148 * 4 * clk_mhz * 1e6
+        extra["issue"] = {"warp_inst_per_launch": int(inst), "achieved_warp_inst_per_s": round(inst / avg_s, 1),
+                          "peak_warp_inst_per_s": ipeak, "frac": round(inst / avg_s / ipeak, 4),
+                          "source": f"smsp__inst_executed.sum per ray on {tr.get('measured_on', tr.get('workload'))}, "
+                                    "148 SMs x 4 issue slots per clock at the median SM clock of the timed region"}
     if name == "mlp_forward_tc" and gather is not None:
         F_, fb, rows = gather
         gb = (S_r + S_t) / 2.0 * F_ * fb
@@ -351,8 +368,10 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
                             else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
             "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": (None if not tr else int(tr["bytes_per_launch"]) if "bytes_per_launch" in tr
-                        else int(tr["bytes_per_sample"] * ((S_r + S_t) / 2.0 if name == "mlp_forward_tc" else S_t))),
-            **({"traffic_source": f"ncu DRAM bytes per sample on {tr.get('workload')} x this launch's samples"}
+                        else int(tr["bytes_per_sample"] * ((S_r + S_t) / 2.0 if name == "mlp_forward_tc" else S_t))
+                        if "bytes_per_sample" in tr else None),
+            **({"traffic_source": f"ncu DRAM bytes per sample on {tr.get('measured_on', tr.get('workload'))} "
+                                  "x this launch's samples"}
                if tr and "bytes_per_sample" in tr else {}),
             "avg_launch_ms": round(ms / launches, 4)}
 
@@ -633,7 +652,7 @@ def run_ours(args, rank, world, local_rank):
     def kernel_roofline(name):
         return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
                                     peak_src, ffma_tf, tag, gather=(FEAT, 2 if FEAT_BF16 else 4, feats.shape[0]),
-                                    tpeak=tensor_peak(peaks, clk, total_ms / 1e3))
+                                    tpeak=tensor_peak(peaks, clk, total_ms / 1e3), clk_mhz=clk.get("sm_mhz"))
 
     if dom:
         roof = kernel_roofline(dom)
@@ -644,7 +663,7 @@ def run_ours(args, rank, world, local_rank):
         if r is not None:
             kernel_rooflines[k] = {key: r[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic",
                                                          "avg_launch_ms", "gather", "frac_of_sustained",
-                                                         "frac_of_burst") if key in r}
+                                                         "frac_of_burst", "issue", "traffic_source") if key in r}
 
     gpu_launches = int(sum(v[0] for v in kstats.values()))
     if rank == 0:
@@ -899,7 +918,7 @@ def run_batched(args, rank, world, local_rank):
         trees.append(svlf.Octree(torch.from_numpy(sc.leaf_ijk), sc.depth))
         az, el = I.random_view_angles(rng, 100)
         r_rays.append(I.pinhole_rays(az[0], el[0], BATCH_RES, BATCH_RES))
-        t_rays.append(I.training_rays(rng, 100, BATCH_RES, BATCH_TRAIN, az, el))
+        t_rays.append(I.training_rays(rng, 100, BATCH_RES, BATCH_TRAIN, az, el, coherent=TRAIN_ORDER == "coherent"))
     r_all = torch.from_numpy(np.concatenate(r_rays)).to(dev)
     t_all = torch.from_numpy(np.concatenate(t_rays)).to(dev)
     NR, NT = r_all.shape[0], t_all.shape[0]
@@ -1083,7 +1102,7 @@ def run_twodec(args, rank, world, local_rank):
     # weights (colour) and the analytic surface depth
     trng = np.random.default_rng(SCENE_SEED + 1 + 7919 * rank)
     taz, tel = I.random_view_angles(trng, TRAIN_VIEWS)
-    trays_h = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel)
+    trays_h = I.training_rays(trng, TRAIN_VIEWS, TRAIN_RES, TRAIN_BATCH, taz, tel, coherent=TRAIN_ORDER == "coherent")
     dt_h, mask_h = I.analytic_depth(trays_h, scene)
     trays = torch.from_numpy(trays_h).to(dev)
     NT = trays.shape[0]

@@ -221,11 +221,29 @@ def random_view_angles(rng: np.random.Generator, n: int):
     return az, el
 
 
+def _morton2(r: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Interleave the bits of two non-negative integers below 2^16 (Z order)."""
+    def spread(x):
+        x = x.astype(np.uint64) & np.uint64(0xFFFF)
+        x = (x | (x << np.uint64(8))) & np.uint64(0x00FF00FF)
+        x = (x | (x << np.uint64(4))) & np.uint64(0x0F0F0F0F)
+        x = (x | (x << np.uint64(2))) & np.uint64(0x33333333)
+        return (x | (x << np.uint64(1))) & np.uint64(0x55555555)
+    return spread(c) | (spread(r) << np.uint64(1))
+
+
 def training_rays(rng: np.random.Generator, n_views: int, res: int, batch: int,
-                  az: np.ndarray, el: np.ndarray) -> np.ndarray:
-    """`batch` rays drawn uniformly over (view, pixel) of n_views res x res views."""
+                  az: np.ndarray, el: np.ndarray, coherent: bool = False) -> np.ndarray:
+    """`batch` rays drawn uniformly over (view, pixel) of n_views res x res views.
+    With `coherent` the same draws are returned ordered by view, then by the Z
+    order of the pixel (neighbouring rows of the batch are neighbouring rays);
+    the batch as a set, and every draw, are unchanged."""
     views = rng.integers(0, n_views, size=batch)
     pix = rng.integers(0, res, size=(batch, 2))
+    if coherent:
+        key = (views.astype(np.uint64) << np.uint64(32)) | _morton2(pix[:, 0], pix[:, 1])
+        order = np.argsort(key, kind="stable")
+        views, pix = views[order], pix[order]
     rays = np.empty((batch, 6), dtype=np.float32)
     for v in np.unique(views):
         sel = np.nonzero(views == v)[0]
