@@ -20,15 +20,24 @@ constexpr int kTsF = 128;  // forward tile (samples)
 constexpr int kTsB = 64;   // backward tile (samples)
 constexpr int kPadB = 68;  // row stride (floats) of backward tiles
 
-// Y[j][s] = relu(b_j + sum_k WT[k][j] X[k][s]) for j < H, s < TS (row stride ts)
-template <int H, int TS, int SPT>
+// Y[j][s] = relu(b_j + sum_k WT[k][j] X[k][s]) for j < H, s < TS (row stride ts).
+// W^T is read from shared memory (W_SMEM, staged by the caller) or through
+// the read-only cache. Thread (ty, tx) of 256 computes rows j0 .. j0 + H/16 - 1 for SPT samples in
+// SPT/4 groups of four, group g at g TS / (SPT/4) + 4 tx: the eight lanes of a
+// quarter warp then read 128 contiguous bytes of X per load (no bank
+// conflict). The loads of step k + 1 (X from shared memory, W^T through the
+// read-only cache) are issued before the FMAs of step k. Each output is the
+// same fmaf chain in ascending k whatever the thread mapping.
+template <int H, int TS, int SPT, bool W_SMEM = false>
 __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int in, int ts,
                                               const float *__restrict__ WT,
                                               const float *__restrict__ bias, float *__restrict__ Y,
                                               bool relu) {
     constexpr int JT = H / 16;
+    constexpr int NG = SPT / 4;
+    static_assert(SPT % 4 == 0 && TS == 16 * SPT, "16 threads x SPT samples cover the tile");
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-    const int j0 = ty * JT, s0 = tx * SPT;
+    const int j0 = ty * JT;
     float acc[JT][SPT];
 #pragma unroll
     for (int j = 0; j < JT; ++j) {
@@ -36,34 +45,45 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
 #pragma unroll
         for (int s = 0; s < SPT; ++s) acc[j][s] = b;
     }
-    for (int k = 0; k < in; ++k) {
-        float x[SPT];
+    auto load = [&](int k, float (&x)[SPT], float (&w)[JT]) {
 #pragma unroll
-        for (int s4 = 0; s4 < SPT / 4; ++s4) {
-            const float4 v = *reinterpret_cast<const float4 *>(X + k * ts + s0 + 4 * s4);
-            x[4 * s4] = v.x; x[4 * s4 + 1] = v.y; x[4 * s4 + 2] = v.z; x[4 * s4 + 3] = v.w;
+        for (int g = 0; g < NG; ++g) {
+            const float4 a = *reinterpret_cast<const float4 *>(X + k * ts + g * (TS / NG) + 4 * tx);
+            x[4 * g] = a.x; x[4 * g + 1] = a.y; x[4 * g + 2] = a.z; x[4 * g + 3] = a.w;
         }
-        float w[JT];
 #pragma unroll
         for (int j4 = 0; j4 < JT / 4; ++j4) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(WT + k * H + j0 + 4 * j4));
+            const float4 *p = reinterpret_cast<const float4 *>(WT + k * H + j0 + 4 * j4);
+            const float4 v = W_SMEM ? *p : __ldg(p);
             w[4 * j4] = v.x; w[4 * j4 + 1] = v.y; w[4 * j4 + 2] = v.z; w[4 * j4 + 3] = v.w;
         }
+    };
+    auto fma_step = [&](const float (&x)[SPT], const float (&w)[JT]) {
 #pragma unroll
         for (int j = 0; j < JT; ++j)
 #pragma unroll
             for (int s = 0; s < SPT; ++s) acc[j][s] = fmaf(w[j], x[s], acc[j][s]);
+    };
+    float xa[SPT], wa[JT], xb[SPT], wb[JT];
+    if (in > 0) load(0, xa, wa);
+    for (int k = 0; k < in; k += 2) {
+        if (k + 1 < in) load(k + 1, xb, wb);
+        fma_step(xa, wa);
+        if (k + 1 < in) {
+            if (k + 2 < in) load(k + 2, xa, wa);
+            fma_step(xb, wb);
+        }
     }
 #pragma unroll
     for (int j = 0; j < JT; ++j)
 #pragma unroll
-        for (int s4 = 0; s4 < SPT / 4; ++s4) {
+        for (int g = 0; g < NG; ++g) {
             float4 v;
-            v.x = relu ? fmaxf(acc[j][4 * s4], 0.f) : acc[j][4 * s4];
-            v.y = relu ? fmaxf(acc[j][4 * s4 + 1], 0.f) : acc[j][4 * s4 + 1];
-            v.z = relu ? fmaxf(acc[j][4 * s4 + 2], 0.f) : acc[j][4 * s4 + 2];
-            v.w = relu ? fmaxf(acc[j][4 * s4 + 3], 0.f) : acc[j][4 * s4 + 3];
-            *reinterpret_cast<float4 *>(Y + (j0 + j) * ts + s0 + 4 * s4) = v;
+            v.x = relu ? fmaxf(acc[j][4 * g], 0.f) : acc[j][4 * g];
+            v.y = relu ? fmaxf(acc[j][4 * g + 1], 0.f) : acc[j][4 * g + 1];
+            v.z = relu ? fmaxf(acc[j][4 * g + 2], 0.f) : acc[j][4 * g + 2];
+            v.w = relu ? fmaxf(acc[j][4 * g + 3], 0.f) : acc[j][4 * g + 3];
+            *reinterpret_cast<float4 *>(Y + (j0 + j) * ts + g * (TS / NG) + 4 * tx) = v;
         }
 }
 
@@ -83,7 +103,11 @@ __device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
     for (int k = md.in0; k < rows_padded; ++k) X[k * ts + col] = 0.f;
 }
 
-template <int H>
+// WSTAGE: each layer's W^T is copied into shared memory before the layer
+// (when it fits next to the two activation tiles): read from L1 / L2 instead,
+// the rows of W^T of the network's layers together exceed L1, and every K
+// step of the GEMM waited on a miss.
+template <int H, bool WSTAGE>
 __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
     MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ packed, const float *__restrict__ rays,
@@ -93,6 +117,7 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
     float *X = reinterpret_cast<float *>(smem_f4);
     const int dmax = md.in0 > H ? md.in0 : H;
     float *Y = X + dmax * kTsF;
+    float *Wsm = Y + H * kTsF;
     const int64_t S = min((int64_t)counter[kCtrScene], max_samples);
     const int64_t n_tiles = (S + kTsF - 1) / kTsF;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -104,8 +129,15 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
         int in = md.in0;
         float *A = X, *B = Y;
         for (int l = 0; l < md.nh; ++l) {
-            gemm_relu_f32<H, kTsF, 8>(A, in, kTsF, packed + md.wt_off[l], packed + md.b_off[l], B,
-                                      true);
+            if (WSTAGE) {
+                const float4 *src = reinterpret_cast<const float4 *>(packed + md.wt_off[l]);
+                float4 *dst = reinterpret_cast<float4 *>(Wsm);
+                for (int i = threadIdx.x; i < in * H / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+                __syncthreads();
+                gemm_relu_f32<H, kTsF, 8, true>(A, in, kTsF, Wsm, packed + md.b_off[l], B, true);
+            } else {
+                gemm_relu_f32<H, kTsF, 8>(A, in, kTsF, packed + md.wt_off[l], packed + md.b_off[l], B, true);
+            }
             __syncthreads();
             float *t = A; A = B; B = t;
             in = H;
@@ -300,15 +332,17 @@ template <int H>
 static int fwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *packed,
                    const float *rays, const Workspace &ws, int64_t max_samples, cudaStream_t s) {
     const int dmax = md.in0 > H ? md.in0 : H;
-    const size_t smem = sizeof(float) * (size_t)(dmax + H) * kTsF;
-    if (cudaFuncSetAttribute(mlp_forward_f32_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    const size_t act = sizeof(float) * (size_t)(dmax + H) * kTsF;
+    const size_t wst = sizeof(float) * (size_t)dmax * H;  // the widest layer's W^T
+    const bool stage = act + wst <= 227 * 1024 && (md.in0 * H) % 4 == 0;
+    const size_t smem = stage ? act + wst : act;
+    const auto kernel = stage ? mlp_forward_f32_kernel<H, true> : mlp_forward_f32_kernel<H, false>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     int blocks = num_sms() * (smem <= 100 * 1024 ? 2 : 1);
     prof_begin("mlp_forward_f32", s);
-    mlp_forward_f32_kernel<H><<<blocks, 256, smem, s>>>(md, depth, rparam, feats, fb, packed, rays,
-                                                        ws.samples, ws.counter, max_samples,
-                                                        ws.outputs);
+    kernel<<<blocks, 256, smem, s>>>(md, depth, rparam, feats, fb, packed, rays, ws.samples, ws.counter,
+                                     max_samples, ws.outputs);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
