@@ -104,14 +104,25 @@ typedef struct {
 
 /* ------------------------------------------------------------ octree */
 /* Build the sparse octree over the given leaves (Sec. 4.1 "Scene volume":
- * only voxels that contain a surface are stored).
+ * only voxels that contain a surface are stored), on the GPU: each leaf sets
+ * one bit of a Morton-indexed occupancy bitmap (duplicates merge), prefix
+ * scans give the brick and leaf ranks and the node levels, and the parent
+ * index with its grown empty boxes is built from them.
  *   leaf_ijk: device, n x 3 int32 (i, j, k); duplicates are merged.
- *   depth: L, 2..10. Coordinates must lie in [0, 2^L), else SVLF_ERR_ARG.
+ *   depth: L, 2..10. Coordinates must lie in [0, 2^L), else SVLF_ERR_ARG
+ *     (counted on the device and checked before the build goes on).
  *   out: receives the handle. n_leaves_out (host, may be NULL): unique leaves.
- * Synchronises `stream` (the leaf list is read back to the host, sorted there
- * and the node arrays uploaded). Not on the per-frame path. */
+ * Synchronises `stream`; allocates 2^(3 depth) bits of temporary device
+ * memory (128 MB at depth 10). Not on the per-frame path. */
 int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
                       svlf_octree *out, int64_t *n_leaves_out);
+
+/* The same octree built on the host (the leaf list is copied to the host,
+ * sorted and de-duplicated there, and the arrays uploaded): an independent
+ * construction of the arrays svlf_build_octree builds, kept for checking one
+ * against the other. Same arguments and errors; synchronises `stream`. */
+int svlf_build_octree_host(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
+                           svlf_octree *out, int64_t *n_leaves_out);
 
 /* Builds the octree on the GPU from depth maps (Sec. 4.1: the voxel grid
  * comes from the dataset's depth maps; Sec. 4.5: 128^3, i.e. depth 7). Pixel

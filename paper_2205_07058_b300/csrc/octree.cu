@@ -102,8 +102,8 @@ struct svlf_octree_s {
     OctreeHost h;
 };
 
-extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
-                                 svlf_octree *out, int64_t *n_leaves_out) {
+extern "C" int svlf_build_octree_host(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
+                                      svlf_octree *out, int64_t *n_leaves_out) {
     if (!out || n < 0 || (n > 0 && !leaf_ijk)) return SVLF_ERR_ARG;
     if (depth < 2 || depth > kMaxDepth) return SVLF_ERR_UNSUPPORTED;
     *out = nullptr;
@@ -692,12 +692,74 @@ int exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, 
 }  // namespace
 }  // namespace svlf
 
+namespace svlf {
+namespace {
+
+// One bit per given leaf in the Morton-indexed occupancy bitmap (duplicates
+// merge); coordinates outside [0, 2^L) are counted in *bad and skipped.
+__global__ void leaves_to_bitmap_kernel(const int32_t *__restrict__ ijk, int64_t n, int L,
+                                        unsigned long long *__restrict__ bitmap, unsigned int *__restrict__ bad) {
+    const int side = 1 << L;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = ijk[3 * p], j = ijk[3 * p + 1], k = ijk[3 * p + 2];
+        if (i < 0 || j < 0 || k < 0 || i >= side || j >= side || k >= side) {
+            atomicAdd(bad, 1u);
+            continue;
+        }
+        const uint64_t code = spread3_dev((uint32_t)i) | (spread3_dev((uint32_t)j) << 1) | (spread3_dev((uint32_t)k) << 2);
+        atomicOr(bitmap + (code >> 6), 1ull << (code & 63));
+    }
+}
+
+// The octree of the leaves a fill step marks in a zeroed occupancy bitmap of
+// 2^(3L) bits (one 64-bit word per level L-2 cell): brick and leaf ranks by
+// prefix scans, node levels bottom-up, the parent index with its grown empty
+// boxes. `fill(bitmap)` queues the marking on `s` and may return an error.
+template <typename Fill>
+int build_octree_gpu(int L, cudaStream_t s, Fill fill, svlf_octree *out, int64_t *n_leaves_out);
+
+}  // namespace
+}  // namespace svlf
+
+extern "C" int svlf_build_octree(const int32_t *leaf_ijk, int64_t n, int depth, void *stream,
+                                 svlf_octree *out, int64_t *n_leaves_out) {
+    if (!out || n < 0 || (n > 0 && !leaf_ijk)) return SVLF_ERR_ARG;
+    if (depth < 2 || depth > kMaxDepth) return SVLF_ERR_UNSUPPORTED;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    return build_octree_gpu(depth, s, [&](unsigned long long *bitmap) -> int {
+        if (n == 0) return SVLF_OK;
+        unsigned int *bad = nullptr;
+        if (cudaMalloc(&bad, sizeof(unsigned int)) != cudaSuccess) return SVLF_ERR_CUDA;
+        unsigned int h_bad = 0;
+        int rc = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s) == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+        if (!rc) leaves_to_bitmap_kernel<<<grid_for_n(n), 256, 0, s>>>(leaf_ijk, n, depth, bitmap, bad);
+        if (!rc && (cudaGetLastError() != cudaSuccess ||
+                    cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess))
+            rc = SVLF_ERR_CUDA;
+        cudaFree(bad);
+        if (!rc && h_bad) rc = SVLF_ERR_ARG;
+        return rc;
+    }, out, n_leaves_out);
+}
+
 extern "C" int svlf_build_octree_from_depth(const float *rays, const float *depth, int64_t n, int L, void *stream,
                                             svlf_octree *out, int64_t *n_leaves_out) {
     if (!out || n < 0 || (n > 0 && (!rays || !depth))) return SVLF_ERR_ARG;
     if (L < 2 || L > kMaxDepth) return SVLF_ERR_UNSUPPORTED;
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
+    return build_octree_gpu(L, s, [&](unsigned long long *bitmap) -> int {
+        if (n > 0) backproject_kernel<<<grid_for_n(n), 256, 0, s>>>(rays, depth, n, L, bitmap);
+        return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+    }, out, n_leaves_out);
+}
+
+namespace svlf {
+namespace {
+template <typename Fill>
+int build_octree_gpu(int L, cudaStream_t s, Fill fill, svlf_octree *out, int64_t *n_leaves_out) {
     const int n_levels = L - 2;
     const int64_t W = (int64_t)1 << (3 * L - 6);  // bitmap words = level L-2 cells
     std::vector<void *> scratch;
@@ -728,7 +790,7 @@ extern "C" int svlf_build_octree_from_depth(const float *rays, const float *dept
     int rc = SVLF_OK;
     uint32_t n_leaves = 0;
     if (cudaMemsetAsync(bitmap, 0, sizeof(unsigned long long) * (size_t)W, s) != cudaSuccess) rc = SVLF_ERR_CUDA;
-    if (!rc && n > 0) backproject_kernel<<<grid_for_n(n), 256, 0, s>>>(rays, depth, n, L, bitmap);
+    if (!rc) rc = fill(bitmap);
     if (!rc) word_stats_kernel<<<grid_for_n(W), 256, 0, s>>>(bitmap, W, flag[n_levels], cnt);
     if (!rc) rc = exclusive_scan(flag[n_levels], idx[n_levels], W, tmp, s, &count[n_levels]);
     if (!rc) rc = exclusive_scan(cnt, leaf_base, W, tmp, s, &n_leaves);
@@ -821,3 +883,5 @@ extern "C" int svlf_build_octree_from_depth(const float *rays, const float *dept
     if (n_leaves_out) *n_leaves_out = n_leaves;
     return SVLF_OK;
 }
+}  // namespace
+}  // namespace svlf

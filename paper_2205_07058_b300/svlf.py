@@ -91,7 +91,7 @@ EXPORTS = [
     "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
     "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth", "svlf_set_step_limit",
-    "svlf_adam_step_device", "svlf_step_advance", "svlf_loss_shard",
+    "svlf_adam_step_device", "svlf_step_advance", "svlf_loss_shard", "svlf_build_octree_host",
 ]
 
 _lib = None
@@ -108,6 +108,7 @@ def lib():
     vp, i64, i32, f32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
     P = ctypes.POINTER
     L.svlf_build_octree.argtypes = [vp, i64, i32, vp, P(vp), P(i64)]
+    L.svlf_build_octree_host.argtypes = [vp, i64, i32, vp, P(vp), P(i64)]
     L.svlf_octree_leaf_ijk.argtypes = [vp, vp, vp]
     L.svlf_build_octree_from_depth.argtypes = [vp, vp, i64, i32, vp, P(vp), P(i64)]
     L.svlf_octree_info.argtypes = [vp, P(i32), P(i64), P(i64), P(i64)]
@@ -189,11 +190,14 @@ def _stream(stream=None):
 class Octree:
     """Library-owned sparse octree (svlf_build_octree)."""
 
-    def __init__(self, leaf_ijk: torch.Tensor, depth: int, stream=None):
+    def __init__(self, leaf_ijk: torch.Tensor, depth: int, stream=None, host: bool = False):
+        """Octree over the leaves (n x 3 ijk), built on the GPU (or, with
+        host=True, by the library's independent host construction)."""
         ijk = leaf_ijk.to(device="cuda", dtype=torch.int32).contiguous()
         h = ctypes.c_void_p()
         n = ctypes.c_int64()
-        _check("svlf_build_octree", lib().svlf_build_octree(
+        fn = "svlf_build_octree_host" if host else "svlf_build_octree"
+        _check(fn, getattr(lib(), fn)(
             _ptr(ijk), ijk.shape[0], int(depth), _stream(stream), ctypes.byref(h), ctypes.byref(n)))
         self.handle = h
         self.depth = int(depth)

@@ -40,8 +40,8 @@ def test_leaves_nodes_and_traversal(L, views, res):
     # rank order = Morton order of the oracle's voxels
     ref = vox[np.argsort(_morton(vox, L))]
     assert np.array_equal(tree.leaf_ijk().cpu().numpy(), ref)
-    # the same structure as the host build of those leaves
-    host = svlf.Octree(torch.from_numpy(ref.astype(np.int32)), L)
+    # the same structure as the library's host construction of those leaves
+    host = svlf.Octree(torch.from_numpy(ref.astype(np.int32)), L, host=True)
     assert tree.info() == host.info()
     assert torch.equal(tree.parent_index(), host.parent_index())
     # hit lists on the GPU-built tree, bit-exact against the oracle's walk
@@ -74,3 +74,34 @@ def test_empty_and_invalid_depths():
     assert torch.all(rgb.cpu() == torch.tensor([0.25, 0.5, 1.0])) and torch.all(dep == 0)
     with pytest.raises(svlf.SvlfError):
         svlf.Octree.from_depth(rays, depth, 11)
+
+
+@pytest.mark.parametrize("L,n_sph,n_box", [(2, 1, 0), (3, 2, 1), (6, 8, 3), (9, 24, 8), (10, 8, 4)])
+def test_leaf_list_build_on_gpu_equals_host_construction(L, n_sph, n_box):
+    """svlf_build_octree (on the GPU) and svlf_build_octree_host give the same
+    arrays: sizes, leaf coordinates in rank order, the parent index entry for
+    entry; the leaf list is shuffled and holds duplicates."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(300 + L)
+    sc = I.make_scene(rng, L, n_sph, n_box)
+    ijk = sc.leaf_ijk[rng.permutation(sc.n_leaves)]
+    ijk = np.concatenate([ijk, ijk[: max(1, sc.n_leaves // 7)]]).astype(np.int32)
+    gpu = svlf.Octree(torch.from_numpy(ijk), L)
+    host = svlf.Octree(torch.from_numpy(ijk), L, host=True)
+    torch.cuda.synchronize()
+    assert gpu.n_leaves == host.n_leaves == sc.n_leaves
+    assert gpu.info() == host.info()
+    assert torch.equal(gpu.leaf_ijk(), host.leaf_ijk())
+    assert np.array_equal(gpu.leaf_ijk().cpu().numpy(), sc.leaf_ijk)
+    assert torch.equal(gpu.parent_index(), host.parent_index())
+
+
+def test_leaf_list_build_rejects_out_of_range_and_handles_empty():
+    from paper_2205_07058_b300 import svlf
+    for bad in ([[0, 0, 4]], [[-1, 0, 0]], [[1, 1, 1], [0, 9, 0]]):
+        with pytest.raises(svlf.SvlfError) as e:
+            svlf.Octree(torch.tensor(bad, dtype=torch.int32), 2)
+        assert e.value.code == svlf.SVLF_ERR_ARG
+    empty = svlf.Octree(torch.zeros((0, 3), dtype=torch.int32), 5)
+    assert empty.n_leaves == 0 and empty.info()["n_bricks"] == 0
+    assert svlf.svlf_get_device_status() == 0

@@ -73,7 +73,7 @@ def _check_index(pidx, leaf_ijk, L):
 def test_parent_index_boxes_host_build(L, n_sph, n_box):
     from paper_2205_07058_b300 import svlf
     sc = I.make_scene(np.random.default_rng(70 + L), L, n_sph, n_box)
-    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), L)
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), L, host=True)
     pidx = tree.parent_index().cpu().numpy().view(np.uint32)
     assert pidx.shape == ((1 << (L - 3)) ** 3, 2)
     _check_index(pidx, sc.leaf_ijk, L)
@@ -101,7 +101,7 @@ def test_parent_index_gpu_build_equals_host_build(L):
     depth = np.where(mask > 0, depth, np.nan).astype(np.float32)
     gt = svlf.Octree.from_depth(torch.from_numpy(rays), torch.from_numpy(depth), L)
     leaves = gt.leaf_ijk()
-    ht = svlf.Octree(leaves, L)
+    ht = svlf.Octree(leaves, L, host=True)
     pg = gt.parent_index().cpu().numpy()
     ph = ht.parent_index().cpu().numpy()
     assert np.array_equal(pg, ph)
