@@ -74,5 +74,14 @@ def test_tc_gradients_full_scene_subset():
         print(name, "features", _rel(res[prec][5], f_ref), "network", _rel(res[prec][6], p_ref),
               "| vs FP64:", _rel(res[prec][5], dfr), _rel(res[prec][6], dpr))
     assert _rel(res[svlf.FP32][5], dfr) <= 1e-4 and _rel(res[svlf.FP32][6], dpr) <= 1e-4
+    # FP32 per parameter: 64 random network parameters and 64 random feature entries with gradient,
+    # relative error floored at 1e-3 of the largest of each set (the tiny workload's bar)
+    pick = np.random.default_rng(0)
+    for g, gr in ((res[svlf.FP32][6], dpr), (res[svlf.FP32][5].reshape(-1), dfr.reshape(-1))):
+        nz = np.nonzero(gr != 0)[0]
+        sel = pick.choice(nz, 64, replace=False)
+        scale = np.maximum(np.abs(gr[sel]), 1e-3 * np.abs(gr[sel]).max())
+        rel = np.abs(g[sel] - gr[sel]) / scale
+        assert rel.max() <= 1e-4, rel.max()
     assert _rel(res[svlf.FP16][5], dfh) <= 1e-2 and _rel(res[svlf.FP16][6], dph) <= 1e-2
     assert _rel(res[svlf.BF16][5], dfe) <= 1e-2 and _rel(res[svlf.BF16][6], dpe) <= 1e-2
