@@ -400,6 +400,7 @@ def run_ours(args, rank, world, local_rank):
     # what the kernels read: the master itself, or its bf16 shadow that Adam rewrites
     feats_k = feats.to(torch.bfloat16) if FEAT_BF16 else feats
     params = torch.from_numpy(W["params"]).to(dev)
+    feats0_k, params0 = feats_k.clone(), params.clone()  # the initial parameters, for the parity sample
     rays = torch.from_numpy(W["render_rays"]).to(dev)
     trays = torch.from_numpy(W["train_rays"]).to(dev)
     N, NT = rays.shape[0], trays.shape[0]
@@ -667,14 +668,16 @@ def run_ours(args, rank, world, local_rank):
 
     gpu_launches = int(sum(v[0] for v in kstats.values()))
     if rank == 0:
-        # one more (untimed) render with the parameters as training left them, on a seeded
-        # ray sample, for the parity check of the cpu_baseline leg (which takes those parameters)
-        render_phase()
-        torch.cuda.synchronize()
+        # one more (untimed) render of the headline views with the initial parameters (training
+        # may drive a synthetic student's optical thickness to zero, which would make every
+        # colour the background), on a seeded ray sample, for the parity check of the
+        # cpu_baseline leg
         idx = np.sort(np.random.default_rng(4242).choice(N, PARITY_SAMPLE, replace=False))
         it = torch.from_numpy(idx).to(dev)
-        W["gpu_sample"] = (idx, rgb[it].cpu().numpy(), depth[it].cpu().numpy(), args.precision,
-                           feats_k.float().cpu().numpy(), params.cpu().numpy())
+        prgb, pdep, _, _, _ = svlf.svlf_render_rays(tree, feats0_k, params0, net, rays[it].contiguous(), K_HITS)
+        torch.cuda.synchronize()
+        W["gpu_sample"] = (idx, prgb.cpu().numpy(), pdep.cpu().numpy(), args.precision,
+                           feats0_k.float().cpu().numpy(), params0.cpu().numpy())
     out = None
     if rank == 0:
         out = {
@@ -807,8 +810,8 @@ def parity_sample(W, tree_o):
 
     outp = {"rays": int(len(idx)), "rays_with_hits": int(hit.sum()), "degenerate_excluded": int((~ok).sum()),
             "precision": prec, "vs_fp64": errs(ref),
-            "note": "an untimed render after the timed steps, with the parameters training left, on seeded "
-                    "render rays vs the FP64 oracle on the same parameters (depth error relative to 1 + D); "
+            "note": "an untimed render of seeded headline rays after the timed steps, with the initial "
+                    "parameters, vs the FP64 oracle on the same parameters (depth error relative to 1 + D); "
                     "computed in the cpu_baseline leg, outside every timed region"}
     if prec in ("bf16", "fp16"):
         emu = O.render(tree_o, feats, params, dims, rays, K_HITS, bf16=prec, hits=ref.hits,
