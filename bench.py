@@ -1,5 +1,7 @@
 #!/usr/bin/env python
-"""Benchmark of the SVLF hot path on one B300 (or N replicas under torchrun).
+"""Benchmark of the SVLF hot path on one B300 (or N GPUs under torchrun:
+rendering sharded by views, training data-parallel over the ray batch with
+one all-reduce of the gradients per step).
 
 One step = one render pass over 4 views of 1600 x 1600 rays (10.24 M rays) of
 the depth-9 union-of-primitives scene (1.69 M leaves, features 32 x fp32,
@@ -12,7 +14,11 @@ render rays plus training rays.
 Prints one JSON line: the metric and its value (whole-job rays/s), ms per
 step, the end-to-end rate through host buffers, the dominant kernel's
 roofline (achieved vs the measured peak, with ncu DRAM traffic), per-kernel
-shares, live clocks and the oracle's CPU rate. `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+rooflines and shares, live clocks, the oracle's CPU rate and the BF16 error
+against it on a ray sample, and (default run, one GPU) the arms the metric
+names beside the headline: the FP32 plain form of the step, the large
+scene and the 64-scene batch, each timed in a child process.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload instead.
 """
 from __future__ import annotations

@@ -1,7 +1,9 @@
-"""The N > 1 path of bench.py on CPU: two gloo ranks (127.0.0.1), one
-independent replica each (no data-path collective): the job time is the
-slowest rank's, the job value counts every rank's units, replicas render
-different views of the same scene, and the reference arm runs on rank 0 only."""
+"""The N > 1 path on CPU with gloo ranks (127.0.0.1): the bench's job time is
+the slowest rank's and its value counts every rank's units, ranks render
+different views of the same scene, the reference arm runs on rank 0 only;
+and data-parallel training (paper_2205_07058_b300/dp.py): shard losses over
+the batch's ray count plus one all-reduce of the contiguous gradient buffer
+give every rank the oracle gradient of the union batch."""
 import os
 import socket
 import sys
