@@ -19,32 +19,38 @@ namespace svlf {
 constexpr int kTsF = 128;  // forward tile (samples)
 constexpr int kTsB = 64;   // backward tile (samples)
 constexpr int kPadB = 68;  // row stride (floats) of backward tiles
+constexpr int kBwdWRows = 32;  // rows of W^T staged at a time in the backward's recompute
 
-// Y[j][s] = relu(b_j + sum_k WT[k][j] X[k][s]) for j < H, s < TS (row stride ts).
+// Y[j][s] = relu(b_j + sum_k WT[k][j] X[k][s]) for j < H, s < TS (row stride ts),
+// also in three parts so that a caller can stage W^T in shared memory in row
+// ranges: gemm_init (the bias), gemm_rows (the K steps [k0, k1), with WT
+// pointing at row k0 of W^T), gemm_store (ReLU and the store of Y).
 // W^T is read from shared memory (W_SMEM, staged by the caller) or through
-// the read-only cache. Thread (ty, tx) of 256 computes rows j0 .. j0 + H/16 - 1 for SPT samples in
-// SPT/4 groups of four, group g at g TS / (SPT/4) + 4 tx: the eight lanes of a
-// quarter warp then read 128 contiguous bytes of X per load (no bank
-// conflict). The loads of step k + 1 (X from shared memory, W^T through the
-// read-only cache) are issued before the FMAs of step k. Each output is the
-// same fmaf chain in ascending k whatever the thread mapping.
-template <int H, int TS, int SPT, bool W_SMEM = false>
-__device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int in, int ts,
-                                              const float *__restrict__ WT,
-                                              const float *__restrict__ bias, float *__restrict__ Y,
-                                              bool relu) {
+// the read-only cache. Thread (ty, tx) of 256 computes rows j0 .. j0 + H/16 - 1
+// for SPT samples in SPT/4 groups of four, group g at g TS / (SPT/4) + 4 tx:
+// the eight lanes of a quarter warp then read 128 contiguous bytes of X per
+// load (no bank conflict). The loads of step k + 1 are issued before the FMAs
+// of step k. Each output is the same fmaf chain in ascending k whatever the
+// thread mapping and the row ranges.
+template <int H, int SPT>
+__device__ __forceinline__ void gemm_init(float (&acc)[H / 16][SPT], const float *__restrict__ bias) {
+    const int j0 = (threadIdx.x >> 4) * (H / 16);
+#pragma unroll
+    for (int j = 0; j < H / 16; ++j) {
+        const float b = __ldg(bias + j0 + j);
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) acc[j][s] = b;
+    }
+}
+
+template <int H, int TS, int SPT, bool W_SMEM>
+__device__ __forceinline__ void gemm_rows(float (&acc)[H / 16][SPT], const float *__restrict__ X, int k0, int k1,
+                                          int ts, const float *__restrict__ WT) {
     constexpr int JT = H / 16;
     constexpr int NG = SPT / 4;
     static_assert(SPT % 4 == 0 && TS == 16 * SPT, "16 threads x SPT samples cover the tile");
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
     const int j0 = ty * JT;
-    float acc[JT][SPT];
-#pragma unroll
-    for (int j = 0; j < JT; ++j) {
-        const float b = __ldg(bias + j0 + j);
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) acc[j][s] = b;
-    }
     auto load = [&](int k, float (&x)[SPT], float (&w)[JT]) {
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -53,7 +59,7 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
         }
 #pragma unroll
         for (int j4 = 0; j4 < JT / 4; ++j4) {
-            const float4 *p = reinterpret_cast<const float4 *>(WT + k * H + j0 + 4 * j4);
+            const float4 *p = reinterpret_cast<const float4 *>(WT + (k - k0) * H + j0 + 4 * j4);
             const float4 v = W_SMEM ? *p : __ldg(p);
             w[4 * j4] = v.x; w[4 * j4 + 1] = v.y; w[4 * j4 + 2] = v.z; w[4 * j4 + 3] = v.w;
         }
@@ -65,17 +71,24 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
             for (int s = 0; s < SPT; ++s) acc[j][s] = fmaf(w[j], x[s], acc[j][s]);
     };
     float xa[SPT], wa[JT], xb[SPT], wb[JT];
-    if (in > 0) load(0, xa, wa);
-    for (int k = 0; k < in; k += 2) {
-        if (k + 1 < in) load(k + 1, xb, wb);
+    if (k0 < k1) load(k0, xa, wa);
+    for (int k = k0; k < k1; k += 2) {
+        if (k + 1 < k1) load(k + 1, xb, wb);
         fma_step(xa, wa);
-        if (k + 1 < in) {
-            if (k + 2 < in) load(k + 2, xa, wa);
+        if (k + 1 < k1) {
+            if (k + 2 < k1) load(k + 2, xa, wa);
             fma_step(xb, wb);
         }
     }
+}
+
+template <int H, int TS, int SPT>
+__device__ __forceinline__ void gemm_store(const float (&acc)[H / 16][SPT], float *__restrict__ Y, int ts, bool relu) {
+    constexpr int NG = SPT / 4;
+    const int tx = threadIdx.x & 15;
+    const int j0 = (threadIdx.x >> 4) * (H / 16);
 #pragma unroll
-    for (int j = 0; j < JT; ++j)
+    for (int j = 0; j < H / 16; ++j)
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             float4 v;
@@ -85,6 +98,26 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
             v.w = relu ? fmaxf(acc[j][4 * g + 3], 0.f) : acc[j][4 * g + 3];
             *reinterpret_cast<float4 *>(Y + (j0 + j) * ts + g * (TS / NG) + 4 * tx) = v;
         }
+}
+
+template <int H, int TS, int SPT, bool W_SMEM = false>
+__device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int in, int ts,
+                                              const float *__restrict__ WT,
+                                              const float *__restrict__ bias, float *__restrict__ Y,
+                                              bool relu) {
+    float acc[H / 16][SPT];
+    gemm_init<H, SPT>(acc, bias);
+    gemm_rows<H, TS, SPT, W_SMEM>(acc, X, 0, in, ts, WT);
+    gemm_store<H, TS, SPT>(acc, Y, ts, relu);
+}
+
+// Rows [r0, r1) of W^T (H columns) copied into shared memory by all threads
+// of the block; the caller synchronises before reading them.
+template <int H>
+__device__ __forceinline__ void copy_wt_rows(const float *__restrict__ WT, int r0, int r1, float *dst) {
+    const float4 *src = reinterpret_cast<const float4 *>(WT + (size_t)r0 * H);
+    float4 *d = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < (r1 - r0) * H / 4; i += blockDim.x) d[i] = __ldg(src + i);
 }
 
 // Write h0 of sample s (or zeros) into column `col` of X (row stride ts).
@@ -226,7 +259,7 @@ __device__ __forceinline__ void backprop_delta(const float *__restrict__ W, int 
     }
 }
 
-template <int H>
+template <int H, bool WST>
 __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ params, const float *__restrict__ packed,
@@ -243,6 +276,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     const int dmax = in0p > H ? in0p : H;
     float *Dc = A[md.nh] + H * kPadB;  // delta of the current layer's output
     float *Dn = Dc + dmax * kPadB;     // delta one layer down (or dL/dz)
+    float *Wst = Dn + dmax * kPadB;    // kBwdWRows rows of W^T (recompute)
     __shared__ int s_leaf[kTsB];
     const int64_t S = min((int64_t)counter[kCtrScene], max_samples);
     const int64_t n_tiles = (S + kTsB - 1) / kTsB;
@@ -260,10 +294,26 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             Dc[3 * kPadB + threadIdx.x] = g.w;
         }
         __syncthreads();
-        // recompute the forward (inputs of every layer)
+        // recompute the forward (inputs of every layer), W^T staged in shared memory
+        // kBwdWRows rows at a time (read from L1 / L2 instead, every K step waited on a miss)
         for (int l = 0; l < md.nh; ++l) {
-            gemm_relu_f32<H, kTsB, 4>(A[l], l == 0 ? md.in0 : H, kPadB, packed + md.wt_off[l],
-                                      packed + md.b_off[l], A[l + 1], true);
+            const int in = l == 0 ? md.in0 : H;
+            if (!WST) {
+                gemm_relu_f32<H, kTsB, 4>(A[l], in, kPadB, packed + md.wt_off[l], packed + md.b_off[l], A[l + 1],
+                                          true);
+                __syncthreads();
+                continue;
+            }
+            float acc[H / 16][4];
+            gemm_init<H, 4>(acc, packed + md.b_off[l]);
+            for (int r0 = 0; r0 < in; r0 += kBwdWRows) {
+                const int r1 = min(in, r0 + kBwdWRows);
+                copy_wt_rows<H>(packed + md.wt_off[l], r0, r1, Wst);
+                __syncthreads();
+                gemm_rows<H, kTsB, 4, true>(acc, A[l], r0, r1, kPadB, Wst);
+                __syncthreads();
+            }
+            gemm_store<H, kTsB, 4>(acc, A[l + 1], kPadB, true);
             __syncthreads();
         }
         // layers from the output down
@@ -359,25 +409,28 @@ int launch_mlp_forward_f32(const MlpDims &md, int depth, int rparam, const void 
     }
 }
 
-size_t backward_f32_smem(const MlpDims &md) {
+// Shared memory of the backward: the activation and delta tiles, plus (when
+// `staged`) the rows of W^T the recompute stages.
+size_t backward_f32_smem(const MlpDims &md, bool staged) {
     const int in0p = (md.in0 + 3) & ~3;
     const int dmax = in0p > md.H ? in0p : md.H;
-    return sizeof(float) * (size_t)kPadB * (size_t)(in0p + md.nh * md.H + 2 * dmax);
+    return sizeof(float) * ((size_t)kPadB * (size_t)(in0p + md.nh * md.H + 2 * dmax) +
+                            (staged ? (size_t)kBwdWRows * md.H : 0));
 }
 
 template <int H>
 static int bwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *params,
                    const float *packed, const float *rays, const Workspace &ws,
                    int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
-    const size_t smem = backward_f32_smem(md);
+    const bool staged = backward_f32_smem(md, true) <= 220 * 1024 && (md.in0 * H) % 4 == 0;
+    const size_t smem = backward_f32_smem(md, staged);
     if (smem > 220 * 1024) return SVLF_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(mlp_backward_f32_kernel<H>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const auto kernel = staged ? mlp_backward_f32_kernel<H, true> : mlp_backward_f32_kernel<H, false>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SVLF_ERR_CUDA;
     prof_begin("mlp_backward_f32", s);
-    mlp_backward_f32_kernel<H><<<num_sms(), 256, smem, s>>>(md, depth, rparam, feats, fb, params, packed,
-                                                            rays, ws.samples, ws.counter,
-                                                            max_samples, ws.dout, d_feat, d_params);
+    kernel<<<num_sms(), 256, smem, s>>>(md, depth, rparam, feats, fb, params, packed, rays, ws.samples, ws.counter,
+                                        max_samples, ws.dout, d_feat, d_params);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
 }
