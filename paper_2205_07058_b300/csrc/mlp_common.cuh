@@ -30,7 +30,7 @@ int launch_mlp_backward_f32(const MlpDims &md, int depth, int rparam, const void
                             const float *params, const float *packed, const float *rays,
                             const Workspace &ws, int64_t max_samples, float *d_feat,
                             float *d_params, cudaStream_t s);
-size_t backward_f32_smem(const MlpDims &md, bool staged);
+size_t backward_f32_smem(const MlpDims &md);
 
 // h0 = [z | d | p~1 | p~2] of one sample, in float32 (rparam: SVLF_RPARAM_*).
 __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int rparam, const void *feats,

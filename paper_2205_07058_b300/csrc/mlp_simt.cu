@@ -411,19 +411,23 @@ int launch_mlp_forward_f32(const MlpDims &md, int depth, int rparam, const void 
 
 // Shared memory of the backward: the activation and delta tiles, plus (when
 // `staged`) the rows of W^T the recompute stages.
-size_t backward_f32_smem(const MlpDims &md, bool staged) {
+static size_t backward_f32_smem_with(const MlpDims &md, bool staged) {
     const int in0p = (md.in0 + 3) & ~3;
     const int dmax = in0p > md.H ? in0p : md.H;
     return sizeof(float) * ((size_t)kPadB * (size_t)(in0p + md.nh * md.H + 2 * dmax) +
                             (staged ? (size_t)kBwdWRows * md.H : 0));
 }
 
+size_t backward_f32_smem(const MlpDims &md) {
+    return backward_f32_smem_with(md, backward_f32_smem_with(md, true) <= 220 * 1024);
+}
+
 template <int H>
 static int bwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *params,
                    const float *packed, const float *rays, const Workspace &ws,
                    int64_t max_samples, float *d_feat, float *d_params, cudaStream_t s) {
-    const bool staged = backward_f32_smem(md, true) <= 220 * 1024 && (md.in0 * H) % 4 == 0;
-    const size_t smem = backward_f32_smem(md, staged);
+    const bool staged = backward_f32_smem_with(md, true) <= 220 * 1024 && (md.in0 * H) % 4 == 0;
+    const size_t smem = backward_f32_smem_with(md, staged);
     if (smem > 220 * 1024) return SVLF_ERR_UNSUPPORTED;
     const auto kernel = staged ? mlp_backward_f32_kernel<H, true> : mlp_backward_f32_kernel<H, false>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
