@@ -397,16 +397,25 @@ def run_ours(args, rank, world, local_rank):
     W = make_workload(rank, args.views, args.res)
     prec = svlf.PRECISIONS[args.precision]
     tprec = svlf.PRECISIONS[args.train_precision or args.precision]
-    fdt = svlf.FEAT_BF16 if FEAT_BF16 else svlf.FEAT_F32
+    # The kernels read the features as stored (bf16 storage: a bf16 copy of the float32
+    # master that Adam updates), or, with float32 storage and BF16 networks on both
+    # passes, a bf16 copy too: the tensor-core network rounds every feature to bf16
+    # (nearest even) as it forms its input row, so reading the copy that the Adam pass
+    # writes beside the table gives the same network inputs bit for bit, with one
+    # conversion per feature per step instead of one per sample and half the gather bytes
+    read_bf16 = FEAT_BF16 or (args.precision == "bf16" and (args.train_precision or "bf16") == "bf16")
+    fdt = svlf.FEAT_BF16 if read_bf16 else svlf.FEAT_F32
     net = svlf.Network(FEAT, HIDDEN, N_HIDDEN, prec, fdt)
     tnet = svlf.Network(FEAT, HIDDEN, N_HIDDEN, tprec, fdt)
     scene = W["scene"]
     tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), scene.depth)
     feats = torch.from_numpy(W["feats"]).to(dev)  # float32 master copy (what Adam updates)
-    # what the kernels read: the master itself, or its bf16 shadow that Adam rewrites
-    feats_k = feats.to(torch.bfloat16) if FEAT_BF16 else feats
+    # what the kernels read: the master itself, or its bf16 copy that Adam rewrites
+    feats_k = feats.to(torch.bfloat16) if read_bf16 else feats
     params = torch.from_numpy(W["params"]).to(dev)
-    feats0_k, params0 = feats_k.clone(), params.clone()  # the initial parameters, for the parity sample
+    # the initial parameters, for the parity sample (the oracle takes the stored table)
+    feats0, params0 = (feats.to(torch.bfloat16) if FEAT_BF16 else feats).clone(), params.clone()
+    feats0_k = feats_k.clone()
     rays = torch.from_numpy(W["render_rays"]).to(dev)
     trays = torch.from_numpy(W["train_rays"]).to(dev)
     N, NT = rays.shape[0], trays.shape[0]
@@ -415,8 +424,9 @@ def run_ours(args, rank, world, local_rank):
     if args.render_only:
         rgb_t = torch.zeros((NT, 3), device=dev)
     else:
-        rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats_k, teacher,
-                                                  svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32, fdt), trays, K_HITS)
+        sdt = svlf.FEAT_BF16 if FEAT_BF16 else svlf.FEAT_F32  # the table as stored
+        rgb_t, _, _, _, _ = svlf.svlf_render_rays(tree, feats_k if FEAT_BF16 else feats, teacher,
+                                                  svlf.Network(FEAT, HIDDEN, N_HIDDEN, svlf.FP32, sdt), trays, K_HITS)
     depth_t = torch.from_numpy(W["depth_t"]).to(dev)
     mask = torch.from_numpy(W["mask"]).to(dev)
     del teacher
@@ -458,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dp.allreduce_gradients(gbuf)  # the data-parallel exchange (NCCL)
         svlf.svlf_adam_step(feats, g_feat, m_feat, v_feat, step_no[0], lr=LR,
-                            bf16_shadow=feats_k if FEAT_BF16 else None)
+                            bf16_shadow=feats_k if read_bf16 else None)
         svlf.svlf_adam_step(params, g_par, m_par, v_par, step_no[0], lr=LR)
 
     def step(record=None):
@@ -658,7 +668,7 @@ def run_ours(args, rank, world, local_rank):
 
     def kernel_roofline(name):
         return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
-                                    peak_src, ffma_tf, tag, gather=(FEAT, 2 if FEAT_BF16 else 4, feats.shape[0]),
+                                    peak_src, ffma_tf, tag, gather=(FEAT, 2 if read_bf16 else 4, feats.shape[0]),
                                     tpeak=tensor_peak(peaks, clk, total_ms / 1e3), clk_mhz=clk.get("sm_mhz"))
 
     if dom:
@@ -683,7 +693,7 @@ def run_ours(args, rank, world, local_rank):
         prgb, pdep, _, _, _ = svlf.svlf_render_rays(tree, feats0_k, params0, net, rays[it].contiguous(), K_HITS)
         torch.cuda.synchronize()
         W["gpu_sample"] = (idx, prgb.cpu().numpy(), pdep.cpu().numpy(), args.precision,
-                           feats0_k.float().cpu().numpy(), params0.cpu().numpy())
+                           feats0.float().cpu().numpy(), params0.cpu().numpy())
     out = None
     if rank == 0:
         out = {
@@ -698,8 +708,16 @@ def run_ours(args, rank, world, local_rank):
                                        f"{world} x {NT} rays (one NCCL all-reduce of the contiguous "
                                        f"{gbuf.flat.numel() * 4 / 1e6:.0f} MB gradient buffer per step); "
                                        f"render rays sharded (each rank its own views)") if world > 1 else "single",
-                       "l2": f"inputs larger than L2 (features {feats_k.numel() * feats_k.element_size() / 1e6:.0f} MB"
-                             f" + rays {(N + NT) * 24 / 1e6:.0f} MB per step)",
+                       "feature_reads": ("bf16 storage (a bf16 copy of the float32 master that Adam updates)"
+                                         if FEAT_BF16 else
+                                         "float32 storage; the BF16 networks read the bf16 copy the Adam pass "
+                                         "writes beside it (the rounding they apply to every feature: "
+                                         "bit-identical outputs)" if read_bf16 else "float32 storage, read as stored"),
+                       "l2": f"inputs larger than L2 (each step streams the rays, {(N + NT) * 24 / 1e6:.0f} MB, and "
+                             f"writes and reads back {(n_samples_render + n_samples_train) * 16 / 1e6:.0f} MB of "
+                             f"sample records; feature table {feats.numel() * 4 / 1e6:.0f} MB"
+                             + (f", read as a {feats_k.numel() * 2 / 1e6:.0f} MB bf16 copy" if read_bf16 else "")
+                             + ")",
                        "autotune": tuned},
             "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
             "train_rays_per_s": None if args.render_only else round(NT * args.steps / (train_ms / 1e3), 1),
