@@ -57,11 +57,18 @@ __device__ __forceinline__ void gemm_rows(float (&acc)[H / 16][SPT], const float
             const float4 a = *reinterpret_cast<const float4 *>(X + k * ts + g * (TS / NG) + 4 * tx);
             x[4 * g] = a.x; x[4 * g + 1] = a.y; x[4 * g + 2] = a.z; x[4 * g + 3] = a.w;
         }
+        if (JT % 4 == 0) {
 #pragma unroll
-        for (int j4 = 0; j4 < JT / 4; ++j4) {
-            const float4 *p = reinterpret_cast<const float4 *>(WT + (k - k0) * H + j0 + 4 * j4);
-            const float4 v = W_SMEM ? *p : __ldg(p);
-            w[4 * j4] = v.x; w[4 * j4 + 1] = v.y; w[4 * j4 + 2] = v.z; w[4 * j4 + 3] = v.w;
+            for (int j4 = 0; j4 < JT / 4; ++j4) {
+                const float4 *p = reinterpret_cast<const float4 *>(WT + (k - k0) * H + j0 + 4 * j4);
+                const float4 v = W_SMEM ? *p : __ldg(p);
+                w[4 * j4] = v.x; w[4 * j4 + 1] = v.y; w[4 * j4 + 2] = v.z; w[4 * j4 + 3] = v.w;
+            }
+        } else {  // H = 32: two rows per thread
+            static_assert(JT % 4 == 0 || JT == 2, "rows per thread");
+            const float2 *p = reinterpret_cast<const float2 *>(WT + (k - k0) * H + j0);
+            const float2 v = W_SMEM ? *p : __ldg(p);
+            w[0] = v.x; w[JT - 1] = v.y;
         }
     };
     auto fma_step = [&](const float (&x)[SPT], const float (&w)[JT]) {
@@ -186,6 +193,108 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
                 o2 = fmaf(w.z, a, o2); o3 = fmaf(w.w, a, o3);
             }
             outputs[s0 + threadIdx.x] = output_activation(o0, o1, o2, o3);
+        }
+        __syncthreads();
+    }
+}
+
+// Weights-resident form: the whole packed float32 network (every layer's W^T)
+// copied into shared memory once per CTA, next to one activation tile of
+// kTsR samples that each layer overwrites in place (its outputs are held in
+// registers until every thread has read the layer's input); all 256 threads
+// build a tile's input columns (two per sample: feature chunks c with
+// c % 2 = q, and q = 1 also the direction and entry/exit parameters) and form
+// its outputs (two per thread). Every value is the one the staged form
+// computes: the same input row, the same ascending-k fmaf chain per output
+// (biases read from the packed buffer in global memory).
+constexpr int kTsR = 128;
+
+template <int H>
+__global__ void __launch_bounds__(256) mlp_forward_f32_res_kernel(
+    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
+    const float *__restrict__ packed, int packed_floats, const float *__restrict__ rays,
+    const Sample *__restrict__ samples, const unsigned int *__restrict__ counter,
+    int64_t max_samples, float4 *__restrict__ outputs) {
+    extern __shared__ float4 smem_f4[];
+    float *Wsm = reinterpret_cast<float *>(smem_f4);
+    float *X = Wsm + packed_floats;  // max(in0, H) x kTsR
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(packed);
+        for (int i = threadIdx.x; i < packed_floats / 4; i += blockDim.x) smem_f4[i] = __ldg(src + i);
+    }
+    const int F = md.F;
+    const int col = threadIdx.x & (kTsR - 1);  // sample within the tile
+    const int q = threadIdx.x >> 7;            // which half of its input row / of its outputs
+    const int64_t S = min((int64_t)counter[kCtrScene], max_samples);
+    const int64_t n_tiles = (S + kTsR - 1) / kTsR;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t s0 = tile * kTsR;
+        const int64_t s = s0 + col;
+        if (s < S) {
+            const Sample sm = samples[s];
+            if (feat_bf16) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(
+                    reinterpret_cast<const __nv_bfloat16 *>(feats) + (int64_t)sm.leaf * F);
+                for (int c = q; c < F / 8; c += 2) {
+                    const uint4 v = __ldg(src + c);
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        X[(8 * c + 2 * e) * kTsR + col] = __uint_as_float(w[e] << 16);
+                        X[(8 * c + 2 * e + 1) * kTsR + col] = __uint_as_float(w[e] & 0xFFFF0000u);
+                    }
+                }
+            } else {
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    reinterpret_cast<const float *>(feats) + (int64_t)sm.leaf * F);
+                for (int c = q; c < F / 4; c += 2) {
+                    const float4 v = __ldg(src + c);
+                    X[(4 * c) * kTsR + col] = v.x;
+                    X[(4 * c + 1) * kTsR + col] = v.y;
+                    X[(4 * c + 2) * kTsR + col] = v.z;
+                    X[(4 * c + 3) * kTsR + col] = v.w;
+                }
+            }
+            if (q == 1) {
+                const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * (int64_t)sm.ray);
+                const float2 a = __ldg(rp), b = __ldg(rp + 1), c = __ldg(rp + 2);
+                const float o[3] = {a.x, a.y, b.x};
+                const float d[3] = {b.y, c.x, c.y};
+                float p1[3], p2[3];
+                voxel_param_at(rparam, o, d, sm.tmid, sm.cell, depth, p1, p2);
+                const float v[9] = {d[0], d[1], d[2], p1[0], p1[1], p1[2], p2[0], p2[1], p2[2]};
+#pragma unroll
+                for (int k = 0; k < 9; ++k) X[(F + k) * kTsR + col] = v[k];
+            }
+        } else {
+            for (int k = q; k < md.in0; k += 2) X[k * kTsR + col] = 0.f;
+        }
+        __syncthreads();
+        int in = md.in0;
+        for (int l = 0; l < md.nh; ++l) {
+            float acc[H / 16][8];
+            gemm_init<H, 8>(acc, packed + md.b_off[l]);
+            gemm_rows<H, kTsR, 8, true>(acc, X, 0, in, kTsR, Wsm + md.wt_off[l]);
+            __syncthreads();  // every thread has read the layer's input
+            gemm_store<H, kTsR, 8>(acc, X, kTsR, true);
+            __syncthreads();
+            in = H;
+        }
+        if (s < S) {
+            const float *WT = Wsm + md.wt_off[md.nh];  // H x 4
+            const int o0 = 2 * q;
+            float a0 = __ldg(packed + md.b_off[md.nh] + o0), a1 = __ldg(packed + md.b_off[md.nh] + o0 + 1);
+            for (int k = 0; k < H; ++k) {
+                const float x = X[k * kTsR + col];
+                const float2 w = *reinterpret_cast<const float2 *>(WT + 4 * k + o0);
+                a0 = fmaf(w.x, x, a0);
+                a1 = fmaf(w.y, x, a1);
+            }
+            float2 r;
+            r.x = sigmoidf_(a0);
+            r.y = q == 0 ? sigmoidf_(a1) : fmaxf(a1, 0.f);
+            reinterpret_cast<float2 *>(outputs)[2 * s + q] = r;
         }
         __syncthreads();
     }
@@ -382,6 +491,19 @@ template <int H>
 static int fwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb, const float *packed,
                    const float *rays, const Workspace &ws, int64_t max_samples, cudaStream_t s) {
     const int dmax = md.in0 > H ? md.in0 : H;
+    // the weights-resident form where the whole packed network fits beside its activation tile
+    const int pf = (int)packed_f32_floats(md);
+    const size_t res = sizeof(float) * ((size_t)pf + (size_t)dmax * kTsR);
+    if (res <= 227 * 1024 && pf % 4 == 0 && md.out == 4 && md.F % 4 == 0 && H % 32 == 0) {
+        const auto kernel = mlp_forward_f32_res_kernel<H>;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res) != cudaSuccess)
+            return SVLF_ERR_CUDA;
+        prof_begin("mlp_forward_f32", s);
+        kernel<<<num_sms() * (res <= 100 * 1024 ? 2 : 1), 256, res, s>>>(
+            md, depth, rparam, feats, fb, packed, pf, rays, ws.samples, ws.counter, max_samples, ws.outputs);
+        prof_end(s);
+        return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+    }
     const size_t act = sizeof(float) * (size_t)(dmax + H) * kTsF;
     const size_t wst = sizeof(float) * (size_t)dmax * H;  // the widest layer's W^T
     const bool stage = act + wst <= 227 * 1024 && (md.in0 * H) % 4 == 0;
