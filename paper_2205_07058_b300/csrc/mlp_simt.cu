@@ -368,6 +368,67 @@ __device__ __forceinline__ void backprop_delta(const float *__restrict__ W, int 
     }
 }
 
+// The same product with W read from shared memory: rows [j0, j0 + kBwdWRows)
+// of W are staged into Wst (row stride nk rounded up to 4) by all threads,
+// then every thread adds their terms to its (up to two) 4 x 4 blocks, in
+// ascending j as above, so every output is the same fmaf chain. Called by
+// all threads of the block (it synchronises); nk <= 128, and the staged rows
+// (kBwdWRows x nk rounded up to 4) fit the caller's buffer.
+template <bool MASK>
+__device__ __forceinline__ void backprop_delta_staged(const float *__restrict__ W, int nj, int nk, int ldw,
+                                                      const float *D, const float *A, float *Dst, float *Wst) {
+    const int bk = (nk + 3) / 4;
+    const int nblk = bk * (kTsB / 4);
+    const int nk4 = bk * 4;
+    float acc[2][4][4] = {};
+    for (int j0 = 0; j0 < nj; j0 += kBwdWRows) {
+        const int nr = min(nj - j0, kBwdWRows);
+        for (int e = threadIdx.x; e < nr * nk4; e += blockDim.x) {
+            const int r = e / nk4, c = e % nk4;
+            Wst[e] = c < nk ? __ldg(W + (size_t)(j0 + r) * ldw + c) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int blk = threadIdx.x + b * blockDim.x;
+            if (blk >= nblk) break;
+            const int k0 = (blk % bk) * 4, s0 = (blk / bk) * 4;
+            for (int r = 0; r < nr; ++r) {
+                const float4 d = *reinterpret_cast<const float4 *>(D + (j0 + r) * kPadB + s0);
+                const float4 w4 = *reinterpret_cast<const float4 *>(Wst + r * nk4 + k0);
+                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[b][q][0] = fmaf(w[q], d.x, acc[b][q][0]);
+                    acc[b][q][1] = fmaf(w[q], d.y, acc[b][q][1]);
+                    acc[b][q][2] = fmaf(w[q], d.z, acc[b][q][2]);
+                    acc[b][q][3] = fmaf(w[q], d.w, acc[b][q][3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int blk = threadIdx.x + b * blockDim.x;
+        if (blk >= nblk) break;
+        const int k0 = (blk % bk) * 4, s0 = (blk / bk) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (k0 + q >= nk) continue;
+            float4 v = make_float4(acc[b][q][0], acc[b][q][1], acc[b][q][2], acc[b][q][3]);
+            if (MASK) {
+                const float4 a = *reinterpret_cast<const float4 *>(A + (k0 + q) * kPadB + s0);
+                v.x = a.x > 0.f ? v.x : 0.f;
+                v.y = a.y > 0.f ? v.y : 0.f;
+                v.z = a.z > 0.f ? v.z : 0.f;
+                v.w = a.w > 0.f ? v.w : 0.f;
+            }
+            *reinterpret_cast<float4 *>(Dst + (k0 + q) * kPadB + s0) = v;
+        }
+    }
+}
+
 template <int H, bool WST>
 __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
@@ -441,9 +502,15 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             }
             const float *W = params + md.w_off[l];
             if (l > 0) {
-                backprop_delta<true>(W, nj, nk, nk, Dc, A[l], Dn);
+                if (WST && H <= 128)
+                    backprop_delta_staged<true>(W, nj, nk, nk, Dc, A[l], Dn, Wst);
+                else
+                    backprop_delta<true>(W, nj, nk, nk, Dc, A[l], Dn);
             } else if (d_feat) {
-                backprop_delta<false>(W, nj, md.F, nk, Dc, nullptr, Dn);
+                if (WST && (md.F + 3) / 4 * 4 <= H)  // the staged rows fit the H-wide buffer
+                    backprop_delta_staged<false>(W, nj, md.F, nk, Dc, nullptr, Dn, Wst);
+                else
+                    backprop_delta<false>(W, nj, md.F, nk, Dc, nullptr, Dn);
             }
             __syncthreads();
             float *t = Dc; Dc = Dn; Dn = t;
