@@ -301,19 +301,27 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_res_kernel(
 }
 
 // ---------------------------------------------------------------- backward
-// dW[j][k] += sum_s D[j][s] A[k][s] over a tile (rows j < nj, k < nk).
+// dW[j][k] += sum_s D[j][s] A[k][s] over a tile (rows j < nj, k < nk). A
+// thread's block is rows j0 .. j0 + 3 of D and four rows of A: k0 .. k0 + 3,
+// or, where nk is a multiple of 32 (STRIDED), rows k0, k0 + 8, k0 + 16,
+// k0 + 24 of a 32-row group, so that the lanes of a warp read rows one apart
+// (at the 68-float row stride, consecutive rows fall on different banks;
+// rows four apart share two bank groups).
+template <bool STRIDED>
 __device__ __forceinline__ void accumulate_dw(const float *D, const float *A, int nj, int nk,
                                               float *__restrict__ dW, int ld) {
     const int bj = (nj + 3) / 4, bk = (nk + 3) / 4;
     for (int blk = threadIdx.x; blk < bj * bk; blk += blockDim.x) {
-        const int j0 = (blk / bk) * 4, k0 = (blk % bk) * 4;
+        const int j0 = (blk / bk) * 4, kb = blk % bk;
+        const int k0 = STRIDED ? (kb >> 3) * 32 + (kb & 7) : kb * 4;
+        constexpr int ks = STRIDED ? 8 : 1;  // row step within the block
         float acc[4][4] = {};
         for (int s = 0; s < kTsB; s += 4) {
             float4 d[4], a[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 d[q] = *reinterpret_cast<const float4 *>(D + (j0 + q) * kPadB + s);
-                a[q] = *reinterpret_cast<const float4 *>(A + (k0 + q) * kPadB + s);
+                a[q] = *reinterpret_cast<const float4 *>(A + (k0 + ks * q) * kPadB + s);
             }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
@@ -326,7 +334,7 @@ __device__ __forceinline__ void accumulate_dw(const float *D, const float *A, in
         for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (j0 + p < nj && k0 + q < nk) atomicAdd(dW + (j0 + p) * ld + k0 + q, acc[p][q]);
+                if (j0 + p < nj && k0 + ks * q < nk) atomicAdd(dW + (j0 + p) * ld + k0 + ks * q, acc[p][q]);
     }
 }
 
@@ -493,7 +501,10 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             float *dW = d_params + md.w_off[l];
             float *db = dW + nj * nk;
             if (d_params) {
-                accumulate_dw(Dc, A[l], nj, nk, dW, nk);
+                if (nk % 32 == 0)
+                    accumulate_dw<true>(Dc, A[l], nj, nk, dW, nk);
+                else
+                    accumulate_dw<false>(Dc, A[l], nj, nk, dW, nk);
                 for (int j = threadIdx.x; j < nj; j += blockDim.x) {
                     float acc = 0.f;
                     for (int s = 0; s < kTsB; ++s) acc += Dc[j * kPadB + s];
