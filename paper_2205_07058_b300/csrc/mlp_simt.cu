@@ -118,15 +118,6 @@ __device__ __forceinline__ void gemm_relu_f32(const float *__restrict__ X, int i
     gemm_store<H, TS, SPT>(acc, Y, ts, relu);
 }
 
-// Rows [r0, r1) of W^T (H columns) copied into shared memory by all threads
-// of the block; the caller synchronises before reading them.
-template <int H>
-__device__ __forceinline__ void copy_wt_rows(const float *__restrict__ WT, int r0, int r1, float *dst) {
-    const float4 *src = reinterpret_cast<const float4 *>(WT + (size_t)r0 * H);
-    float4 *d = reinterpret_cast<float4 *>(dst);
-    for (int i = threadIdx.x; i < (r1 - r0) * H / 4; i += blockDim.x) d[i] = __ldg(src + i);
-}
-
 // Write h0 of sample s (or zeros) into column `col` of X (row stride ts).
 __device__ __forceinline__ void build_input_column(const MlpDims &md, int depth, int rparam,
                                                    const void *feats, int feat_bf16,
@@ -437,6 +428,96 @@ __device__ __forceinline__ void backprop_delta_staged(const float *__restrict__ 
     }
 }
 
+// Up to kBwdWRows rows of a row-major matrix with H floats per row (16-byte
+// aligned), held in registers between their global load and their store to
+// shared memory: the next chunk's loads are issued before the current
+// chunk's products, so their latency hides behind them.
+template <int H>
+struct RowStage {
+    static constexpr int NV = (kBwdWRows * H / 4 + 255) / 256;  // float4 per thread (256 threads)
+    float4 v[NV];
+    __device__ __forceinline__ void load(const float *__restrict__ src, int nrows) {
+        const float4 *p = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = threadIdx.x + i * 256;
+            if (e < nrows * H / 4) v[i] = __ldg(p + e);
+        }
+    }
+    __device__ __forceinline__ void store(float *dst, int nrows) const {
+        float4 *d = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = threadIdx.x + i * 256;
+            if (e < nrows * H / 4) d[e] = v[i];
+        }
+    }
+};
+
+// backprop_delta_staged for nk = H with W's rows 16-byte aligned: the next
+// chunk of W rows is loaded into registers while the current one is used.
+// The same products in the same order (every output the same fmaf chain).
+template <int H, bool MASK>
+__device__ __forceinline__ void backprop_delta_pipe(const float *__restrict__ W, int nj, const float *D,
+                                                    const float *A, float *Dst, float *Wst) {
+    constexpr int bk = H / 4;
+    constexpr int nblk = bk * (kTsB / 4);
+    static_assert(nblk <= 512, "two blocks per thread");
+    float acc[2][4][4] = {};
+    RowStage<H> st;
+    int j0 = 0, nr = min(nj, kBwdWRows);
+    st.load(W, nr);
+    st.store(Wst, nr);
+    __syncthreads();
+    for (;;) {
+        const int n0 = j0 + nr, nn = min(nj - n0, kBwdWRows);
+        const bool more = n0 < nj;
+        if (more) st.load(W + (size_t)n0 * H, nn);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int blk = threadIdx.x + b * 256;
+            if (blk >= nblk) break;
+            const int k0 = (blk % bk) * 4, s0 = (blk / bk) * 4;
+            for (int r = 0; r < nr; ++r) {
+                const float4 d = *reinterpret_cast<const float4 *>(D + (j0 + r) * kPadB + s0);
+                const float4 w4 = *reinterpret_cast<const float4 *>(Wst + r * H + k0);
+                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[b][q][0] = fmaf(w[q], d.x, acc[b][q][0]);
+                    acc[b][q][1] = fmaf(w[q], d.y, acc[b][q][1]);
+                    acc[b][q][2] = fmaf(w[q], d.z, acc[b][q][2]);
+                    acc[b][q][3] = fmaf(w[q], d.w, acc[b][q][3]);
+                }
+            }
+        }
+        __syncthreads();
+        if (!more) break;
+        st.store(Wst, nn);
+        __syncthreads();
+        j0 = n0;
+        nr = nn;
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int blk = threadIdx.x + b * 256;
+        if (blk >= nblk) break;
+        const int k0 = (blk % bk) * 4, s0 = (blk / bk) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 v = make_float4(acc[b][q][0], acc[b][q][1], acc[b][q][2], acc[b][q][3]);
+            if (MASK) {
+                const float4 a = *reinterpret_cast<const float4 *>(A + (k0 + q) * kPadB + s0);
+                v.x = a.x > 0.f ? v.x : 0.f;
+                v.y = a.y > 0.f ? v.y : 0.f;
+                v.z = a.z > 0.f ? v.z : 0.f;
+                v.w = a.w > 0.f ? v.w : 0.f;
+            }
+            *reinterpret_cast<float4 *>(Dst + (k0 + q) * kPadB + s0) = v;
+        }
+    }
+}
+
 template <int H, bool WST>
 __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
@@ -484,12 +565,24 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             }
             float acc[H / 16][4];
             gemm_init<H, 4>(acc, packed + md.b_off[l]);
-            for (int r0 = 0; r0 < in; r0 += kBwdWRows) {
-                const int r1 = min(in, r0 + kBwdWRows);
-                copy_wt_rows<H>(packed + md.wt_off[l], r0, r1, Wst);
-                __syncthreads();
+            // the next chunk of W^T rows is loaded into registers while the current one is used
+            const float *WT = packed + md.wt_off[l];
+            RowStage<H> st;
+            int r0 = 0, r1 = min(in, kBwdWRows);
+            st.load(WT, r1);
+            st.store(Wst, r1);
+            __syncthreads();
+            for (;;) {
+                const int n1 = min(in, r1 + kBwdWRows);
+                const bool more = r1 < in;
+                if (more) st.load(WT + (size_t)r1 * H, n1 - r1);
                 gemm_rows<H, kTsB, 4, true>(acc, A[l], r0, r1, kPadB, Wst);
                 __syncthreads();
+                if (!more) break;
+                st.store(Wst, n1 - r1);
+                __syncthreads();
+                r0 = r1;
+                r1 = n1;
             }
             gemm_store<H, kTsB, 4>(acc, A[l + 1], kPadB, true);
             __syncthreads();
@@ -513,7 +606,9 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             }
             const float *W = params + md.w_off[l];
             if (l > 0) {
-                if (WST && H <= 128)
+                if (WST && H <= 128 && reinterpret_cast<uintptr_t>(W) % 16 == 0)
+                    backprop_delta_pipe<H, true>(W, nj, Dc, A[l], Dn, Wst);
+                else if (WST && H <= 128)
                     backprop_delta_staged<true>(W, nj, nk, nk, Dc, A[l], Dn, Wst);
                 else
                     backprop_delta<true>(W, nj, nk, nk, Dc, A[l], Dn);
