@@ -43,9 +43,10 @@ __device__ __forceinline__ void gemm_init(float (&acc)[H / 16][SPT], const float
     }
 }
 
-template <int H, int TS, int SPT, bool W_SMEM>
+template <int H, int TS, int SPT, bool W_SMEM, int KF = 0>
 __device__ __forceinline__ void gemm_rows(float (&acc)[H / 16][SPT], const float *__restrict__ X, int k0, int k1,
                                           int ts, const float *__restrict__ WT) {
+    if (KF > 0) k1 = k0 + KF;  // a K known at compile time (even): no bounds checks in the loop
     constexpr int JT = H / 16;
     constexpr int NG = SPT / 4;
     static_assert(SPT % 4 == 0 && TS == 16 * SPT, "16 threads x SPT samples cover the tile");
@@ -78,6 +79,18 @@ __device__ __forceinline__ void gemm_rows(float (&acc)[H / 16][SPT], const float
             for (int s = 0; s < SPT; ++s) acc[j][s] = fmaf(w[j], x[s], acc[j][s]);
     };
     float xa[SPT], wa[JT], xb[SPT], wb[JT];
+    if (KF > 0) {
+        static_assert(KF % 2 == 0, "even K");
+        load(k0, xa, wa);
+#pragma unroll 2
+        for (int k = k0; k < k0 + KF; k += 2) {
+            load(k + 1, xb, wb);
+            fma_step(xa, wa);
+            if (k + 2 < k0 + KF) load(k + 2, xa, wa);
+            fma_step(xb, wb);
+        }
+        return;
+    }
     if (k0 < k1) load(k0, xa, wa);
     for (int k = k0; k < k1; k += 2) {
         if (k + 1 < k1) load(k + 1, xb, wb);
@@ -266,7 +279,10 @@ __global__ void __launch_bounds__(256) mlp_forward_f32_res_kernel(
         for (int l = 0; l < md.nh; ++l) {
             float acc[H / 16][8];
             gemm_init<H, 8>(acc, packed + md.b_off[l]);
-            gemm_rows<H, kTsR, 8, true>(acc, X, 0, in, kTsR, Wsm + md.wt_off[l]);
+            if (l > 0)
+                gemm_rows<H, kTsR, 8, true, H>(acc, X, 0, H, kTsR, Wsm + md.wt_off[l]);
+            else
+                gemm_rows<H, kTsR, 8, true>(acc, X, 0, in, kTsR, Wsm + md.wt_off[l]);
             __syncthreads();  // every thread has read the layer's input
             gemm_store<H, kTsR, 8>(acc, X, kTsR, true);
             __syncthreads();
@@ -576,7 +592,10 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
                 const int n1 = min(in, r1 + kBwdWRows);
                 const bool more = r1 < in;
                 if (more) st.load(WT + (size_t)r1 * H, n1 - r1);
-                gemm_rows<H, kTsB, 4, true>(acc, A[l], r0, r1, kPadB, Wst);
+                if (r1 - r0 == kBwdWRows)
+                    gemm_rows<H, kTsB, 4, true, kBwdWRows>(acc, A[l], r0, r1, kPadB, Wst);
+                else
+                    gemm_rows<H, kTsB, 4, true>(acc, A[l], r0, r1, kPadB, Wst);
                 __syncthreads();
                 if (!more) break;
                 st.store(Wst, n1 - r1);
