@@ -43,6 +43,7 @@ def test_fp32_shapes_render_and_gradients(scene, F, H, nh, fb):
     if fb:  # bf16 storage: the oracle takes the stored values
         feats = torch.from_numpy(feats).to(torch.bfloat16).float().numpy()
     params = I.make_mlp(rng, I.MLPShape(F, H, nh), bias_std=0.3)
+    params[-1] += 1.0  # the optical-thickness output's bias: tau > 0, so every shape has a gradient
     bg = (0.2, 0.1, 0.3)
     K = 4
     tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), sc.depth)
