@@ -315,7 +315,7 @@ def tensor_peak(peaks, clk, window_s):
 
 
 def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None,
-                         gather=None, tpeak=None, clk_mhz=None):
+                         gather=None, tpeak=None, clk_mhz=None, n_shadow=0):
     """Roofline figures of kernel `name` in a render + training step: its
     algorithmic work per launch (launches alternate render / training where
     a kernel runs in both) over its live average launch time. `gather` =
@@ -336,7 +336,9 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
         bound, unit = "alu", "TFLOP/s"
         peak = round(ffma_tf, 3) if ffma_tf else 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     elif name == "adam":
-        work, bound, unit, peak = n_par * 28.0 / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]  # features, network
+        # features, network: read p, g, m, v and write p, m, v (28 B), plus the bf16 copy (2 B)
+        # of the n_shadow parameters that have one
+        work, bound, unit, peak = (n_par * 28.0 + n_shadow * 2.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
     elif name == "trace":  # ray in (24 B), span out (8 B), a 16-byte record per sample
         work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
     elif name == "composite":  # span in, colour + depth out (16 B) per ray; record + output per sample
@@ -669,7 +671,8 @@ def run_ours(args, rank, world, local_rank):
     def kernel_roofline(name):
         return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
                                     peak_src, ffma_tf, tag, gather=(FEAT, 2 if read_bf16 else 4, feats.shape[0]),
-                                    tpeak=tensor_peak(peaks, clk, total_ms / 1e3), clk_mhz=clk.get("sm_mhz"))
+                                    tpeak=tensor_peak(peaks, clk, total_ms / 1e3), clk_mhz=clk.get("sm_mhz"),
+                                    n_shadow=feats.numel() if read_bf16 else 0)
 
     if dom:
         roof = kernel_roofline(dom)
