@@ -73,7 +73,12 @@ typedef struct svlf_octree_s *svlf_octree; /* opaque, library-owned */
  * row-major) followed by b (out). */
 typedef struct {
     int feat_dim;   /* F: 8..64, multiple of 8 */
-    int hidden;     /* H: 32..256, multiple of 16 (tensor-core paths: 64 or 128) */
+    int hidden;     /* H: 32..256, multiple of 16. Tensor-core precisions: H <= 128
+                       (padded to 128 inside). SVLF_FP32: H in {32, 64, 128, 256}; its
+                       forward needs two 128-sample activation tiles in shared memory
+                       and its backward every layer's activations for 64 samples
+                       (H <= 128, up to 4 x 128 or 6 x 64); calls outside these
+                       return SVLF_ERR_UNSUPPORTED */
     int n_hidden;   /* 1..6 */
     int out_dim;    /* must be 4 */
     int precision;  /* SVLF_FP32 | SVLF_BF16 | SVLF_FP16 */

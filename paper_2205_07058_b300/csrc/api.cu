@@ -4,6 +4,7 @@
 
 #include "svlf_internal.cuh"
 #include "mlp_common.cuh"
+#include "mlp_simt.h"
 
 namespace svlf {
 
@@ -119,9 +120,7 @@ static int check_mlp(const svlf_mlp_desc *m) {
     if (m->precision != SVLF_FP32 && m->precision != SVLF_BF16 && m->precision != SVLF_FP16)
         return SVLF_ERR_ARG;
     if (m->feat_dtype != SVLF_FEAT_F32 && m->feat_dtype != SVLF_FEAT_BF16) return SVLF_ERR_ARG;
-    if (m->precision == SVLF_FP32 && m->hidden != 32 && m->hidden != 64 && m->hidden != 128 &&
-        m->hidden != 256)
-        return SVLF_ERR_UNSUPPORTED;
+    if (m->precision == SVLF_FP32 && !f32_forward_fits(make_dims(*m))) return SVLF_ERR_UNSUPPORTED;
     if (m->precision != SVLF_FP32 && !tc_supported(make_dims(*m))) return SVLF_ERR_UNSUPPORTED;
     return SVLF_OK;
 }
@@ -245,6 +244,7 @@ static int render_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svl
 static int backward_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svlf_render_opts &opts,
                           void *workspace, bool want_feat, bool want_params, cudaStream_t s) {
     if (T.total_rays == 0 || (!want_feat && !want_params)) return SVLF_OK;
+    if (mlp.precision == SVLF_FP32 && (T.n != 1 || !f32_backward_fits(make_dims(mlp)))) return SVLF_ERR_UNSUPPORTED;
     Workspace ws = carve_workspace(workspace, mlp, T.total_rays, T.K, T.n);
     int rc;
     if (cudaMemsetAsync(ws.counter + kCtrMaxAbsDout, 0, sizeof(unsigned int), s) != cudaSuccess)

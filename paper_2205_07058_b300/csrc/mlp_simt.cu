@@ -13,6 +13,7 @@
 // element per tile; dz (the feature gradient) is scattered with atomics.
 #include "svlf_internal.cuh"
 #include "mlp_common.cuh"
+#include "mlp_simt.h"
 
 namespace svlf {
 
@@ -698,6 +699,7 @@ static int fwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, 
     }
     const size_t act = sizeof(float) * (size_t)(dmax + H) * kTsF;
     const size_t wst = sizeof(float) * (size_t)dmax * H;  // the widest layer's W^T
+    if (act > 227 * 1024) return SVLF_ERR_UNSUPPORTED;    // two activation tiles do not fit
     const bool stage = act + wst <= 227 * 1024 && (md.in0 * H) % 4 == 0;
     const size_t smem = stage ? act + wst : act;
     const auto kernel = stage ? mlp_forward_f32_kernel<H, true> : mlp_forward_f32_kernel<H, false>;
@@ -709,6 +711,15 @@ static int fwd_f32(const MlpDims &md, int depth, int rparam, const void *feats, 
                                      max_samples, ws.outputs);
     prof_end(s);
     return cudaGetLastError() == cudaSuccess ? SVLF_OK : SVLF_ERR_CUDA;
+}
+
+bool f32_forward_fits(const MlpDims &md) {
+    const int H = md.H;
+    if (H != 32 && H != 64 && H != 128 && H != 256) return false;
+    const size_t dmax = (size_t)(md.in0 > H ? md.in0 : H);
+    const size_t res = sizeof(float) * (packed_f32_floats(md) + dmax * kTsR);
+    const size_t act = sizeof(float) * (dmax + (size_t)H) * kTsF;
+    return res <= 227 * 1024 || act <= 227 * 1024;
 }
 
 int launch_mlp_forward_f32(const MlpDims &md, int depth, int rparam, const void *feats, int fb,
@@ -734,6 +745,10 @@ static size_t backward_f32_smem_with(const MlpDims &md, bool staged) {
 
 size_t backward_f32_smem(const MlpDims &md) {
     return backward_f32_smem_with(md, backward_f32_smem_with(md, true) <= 220 * 1024);
+}
+
+bool f32_backward_fits(const MlpDims &md) {
+    return (md.H == 32 || md.H == 64 || md.H == 128) && backward_f32_smem(md) <= 220 * 1024;
 }
 
 template <int H>

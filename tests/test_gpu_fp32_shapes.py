@@ -34,7 +34,7 @@ def scene():
 # the FP32 backward keeps every layer's activations (68-float rows) in shared
 # memory, without staged weights for 4 x 128, and refuses 5 x 128
 @pytest.mark.parametrize("F,H,nh", [(8, 32, 1), (16, 32, 2), (16, 64, 2), (32, 128, 3), (24, 64, 3), (16, 64, 6),
-                                    (32, 128, 4), (32, 128, 5)])
+                                    (32, 128, 4), (32, 128, 5), (16, 256, 1)])
 def test_fp32_shapes_render_and_gradients(scene, F, H, nh, fb):
     from paper_2205_07058_b300 import svlf
     sc, rays = scene
@@ -62,7 +62,7 @@ def test_fp32_shapes_render_and_gradients(scene, F, H, nh, fb):
     df = torch.zeros((sc.n_leaves, F), device="cuda")
     dp = torch.zeros_like(p)
     in0p = (F + 9 + 3) // 4 * 4
-    backward = 4 * 68 * (in0p + nh * H + 2 * max(in0p, H)) <= 220 * 1024
+    backward = H <= 128 and 4 * 68 * (in0p + nh * H + 2 * max(in0p, H)) <= 220 * 1024
     if backward:
         svlf.svlf_render_rays_backward(tree, f, p, net, r, K, bg, d_rgb, d_depth, df, dp, ws)
     else:
@@ -87,3 +87,20 @@ def test_fp32_shapes_render_and_gradients(scene, F, H, nh, fb):
     gr = np.concatenate([dfr.reshape(-1), dpr])
     e = np.linalg.norm(g - gr) / np.linalg.norm(gr)
     assert e <= 1e-4, e
+
+
+def test_fp32_forward_refuses_what_does_not_fit(scene):
+    """Two hidden layers of 256: neither the whole network nor two activation
+    tiles fit in shared memory; the call is refused before any launch."""
+    from paper_2205_07058_b300 import svlf
+    sc, rays = scene
+    rng = np.random.default_rng(3)
+    params = I.make_mlp(rng, I.MLPShape(16, 256, 2), bias_std=0.3)
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), sc.depth)
+    f = torch.from_numpy(I.make_features(rng, sc.n_leaves, 16)).cuda()
+    net = svlf.Network(16, 256, 2, svlf.FP32)
+    with pytest.raises(svlf.SvlfError) as e:
+        svlf.svlf_render_rays(tree, f, torch.from_numpy(params).cuda(), net, torch.from_numpy(rays).cuda(), 4)
+    assert e.value.code == svlf.SVLF_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
