@@ -472,13 +472,18 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
  *   trace_refill        traversal: idle lanes a warp needs before it claims
  *                       a new chunk of rays while rays of its current chunks
  *                       still walk, 1..32 (32: only once all lanes are idle;
- *                       default 32 for large launches, 16 for small ones) */
+ *                       default 32 for large launches, 16 for small ones)
+ *   mlp_bwd_warpgroups  tensor-core backward: warpgroups per tile, 1 or 2
+ *                       (2 adds a second warpgroup that takes half of every
+ *                       epilogue; used for the plain form with resident
+ *                       weights in one pass; default 2 there) */
 typedef struct {
     int mlp_warpgroups;
     int mlp_epilogue_batch;
     int trace_budget;
     int trace_block;
     int trace_refill;
+    int mlp_bwd_warpgroups;
 } svlf_tuning;
 
 int svlf_set_tuning(const svlf_tuning *t);

@@ -412,6 +412,7 @@ extern "C" int svlf_set_tuning(const svlf_tuning *t) {
     if (v.trace_block == 0) v.trace_block = 256;
     if (v.trace_block != 128 && v.trace_block != 256) return SVLF_ERR_ARG;
     if (v.trace_refill < 0 || v.trace_refill > 32) return SVLF_ERR_ARG;
+    if (v.mlp_bwd_warpgroups < 0 || v.mlp_bwd_warpgroups > 2) return SVLF_ERR_ARG;
     g_tuning = v;
     return SVLF_OK;
 }

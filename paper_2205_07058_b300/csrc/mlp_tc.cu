@@ -288,6 +288,72 @@ __device__ __forceinline__ void build_input_chunks(const MlpDims &md, int K0, in
     for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
 }
 
+// The part of build_input_chunks' row that warpgroup `half` of a tile shared by
+// two warpgroups writes: the feature chunks (half 0), or the direction and
+// entry/exit parameter chunks and the zero padding (half 1). F % 8 == 0.
+__device__ __forceinline__ void build_input_chunks_half(int half, const MlpDims &md, int K0, int depth, int rparam,
+                                                        const void *feats, int feat_bf16, const float *rays,
+                                                        int64_t ray_begin, const Sample &sm, bool valid, int fp16,
+                                                        uint8_t *abuf, int row) {
+    const int F = md.F;
+    if (half == 0) {
+        if (!valid) {
+            for (int kb = 0; kb < F / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+            return;
+        }
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(feats) +
+                                                           (int64_t)sm.leaf * F * (feat_bf16 ? 2 : 4));
+        const int nq = feat_bf16 ? F / 8 : F / 4;  // 16-byte loads in the row
+        int kb = 0;
+        for (int q0 = 0; q0 < nq; q0 += 8) {
+            uint4 buf[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q0 + q < nq) buf[q] = __ldg(src + q0 + q);
+            if (feat_bf16) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q0 + q >= nq) break;
+                    uint4 v = buf[q];
+                    if (fp16) {
+                        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                        uint32_t o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            o[e] = tc::pack2(__uint_as_float(w[e] << 16), __uint_as_float(w[e] & 0xFFFF0000u), true);
+                        v = make_uint4(o[0], o[1], o[2], o[3]);
+                    }
+                    st_chunk(abuf, row, kb++, v.x, v.y, v.z, v.w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q += 2) {
+                    if (q0 + q >= nq) break;
+                    const uint4 a = buf[q], b = buf[q + 1];
+                    st_chunk(abuf, row, kb++, tc::pack2(__uint_as_float(a.x), __uint_as_float(a.y), fp16),
+                             tc::pack2(__uint_as_float(a.z), __uint_as_float(a.w), fp16),
+                             tc::pack2(__uint_as_float(b.x), __uint_as_float(b.y), fp16),
+                             tc::pack2(__uint_as_float(b.z), __uint_as_float(b.w), fp16));
+                }
+            }
+        }
+        return;
+    }
+    int kb = F / 8;
+    if (valid) {
+        const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * ((int64_t)sm.ray - ray_begin));
+        const float2 ra = __ldg(rp), rb = __ldg(rp + 1), rc = __ldg(rp + 2);
+        const float o[3] = {ra.x, ra.y, rb.x};
+        const float d[3] = {rb.y, rc.x, rc.y};
+        float p1[3], p2[3];
+        voxel_param_at(rparam, o, d, sm.tmid, sm.cell, depth, p1, p2);
+        st_chunk(abuf, row, kb++, tc::pack2(d[0], d[1], fp16), tc::pack2(d[2], p1[0], fp16),
+                 tc::pack2(p1[1], p1[2], fp16), tc::pack2(p2[0], p2[1], fp16));
+        st_chunk(abuf, row, kb++, tc::pack2(p2[2], 0.f, fp16), 0u, 0u, 0u);
+    }
+    for (; kb < K0 / 8; ++kb) st_chunk(abuf, row, kb, 0u, 0u, 0u, 0u);
+}
+
 // ---------------------------------------------------------------- two-decoder
 // Input rows of the two-decoder form (Sec. 4.1-4.2). Each leaf corner holds a
 // feature vector (vertex table of the octree); psi(p; Z) is the trilinear
@@ -1176,9 +1242,18 @@ __device__ __forceinline__ void mma_seq(uint32_t tmem_d, uint32_t a_base, uint32
                                     tc::sdesc(b_base, b_lbo, b_sbo), b_kstep >> 4, idesc, K / 16, accumulate);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_constant__ SceneTable T,
-                                                                 const TcBwdParams P) {
+// NWG = 2 (MODE 0 with resident weights): two warpgroups share each tile.
+// Warpgroup `half` builds its part of the input row (build_input_chunks_half)
+// and takes columns [64 half, 64 half + 64) of every epilogue and of the
+// gradient flush, and its half of the feature-gradient columns; half 0 writes
+// G_out, sums the output bias gradient and issues the MMAs. TMEM, shared
+// memory and the MMAs are those of NWG = 1: the second warpgroup only adds
+// warps to cover the epilogues' latencies (one warpgroup leaves one warp per
+// scheduler).
+template <int MODE, int NWG = 1>
+__global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __grid_constant__ SceneTable T,
+                                                                       const TcBwdParams P) {
+    static_assert(NWG == 1 || (NWG == 2 && MODE == 0), "two warpgroups: MODE 0 only");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t s_mbar[2];  // [0] MMA commits, [1] weight load
@@ -1186,8 +1261,16 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     __shared__ float s_dbout[4];
     __shared__ TileMap s_map;
 
-    const int row = threadIdx.x;  // sample within the tile = TMEM lane
-    const int warp = row >> 5, lane = row & 31;
+    const int row = threadIdx.x & 127;  // sample within the tile = TMEM lane
+    const int warp = row >> 5, lane = row & 31;  // warp = the TMEM lane quarter it may access
+    const int half = NWG == 2 ? (int)(threadIdx.x >> 7) : 0;
+    const bool lead = threadIdx.x == 0;  // initialises, issues the MMAs and the bulk copies
+    // barrier over the CTA returning the OR of `pred`
+    auto sync_or = [&](bool pred) -> bool {
+        return NWG == 1 ? tc::wg_sync_or(0, pred) : __syncthreads_or(pred) != 0;
+    };
+    // 32-column chunks of the 128-wide accumulator this warpgroup handles
+    const int c32_lo = half * (kHp / 32) / NWG, c32_hi = (half + 1) * (kHp / 32) / NWG;
     const MlpDims &md = P.md;
     const TcLayout &lay = P.lay;
     uint8_t *wimg = smem;
@@ -1197,14 +1280,14 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     const uint32_t s_base = tc::smem_u32(smem);
     __shared__ __align__(8) uint64_t s_wslot[2];  // streamed weight slots
 
-    if (row == 0) {
+    if (lead) {
         tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
         tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
         tc::mbar_init(tc::smem_u32(&s_wslot[0]), 1);
         tc::mbar_init(tc::smem_u32(&s_wslot[1]), 1);
         tc::mbar_init_fence();
     }
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc::tmem_alloc(tc::smem_u32(&s_tmem), P.tmem_cols);
         tc::tmem_relinquish();
     }
@@ -1212,7 +1295,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     {
         const uint32_t one2 = tc::pack2(1.f, 1.f, P.fp16);
         uint4 *o = reinterpret_cast<uint4 *>(smem + P.ones_off);
-        for (int i = row; i < kTcOutN * kTcTile * 2 / 16; i += 128) o[i] = make_uint4(one2, one2, one2, one2);
+        for (int i = threadIdx.x; i < kTcOutN * kTcTile * 2 / 16; i += 128 * NWG)
+            o[i] = make_uint4(one2, one2, one2, one2);
     }
     __syncthreads();
     tile_map_build(T, P.counter, s_map);
@@ -1244,8 +1328,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     auto run_and = [&](auto &&fn, auto &&during) -> bool {
         tc::fence_async_smem();
         tc::fence_before_sync();
-        tc::wg_sync_or(0, false);
-        if (row == 0) {
+        sync_or(false);
+        if (lead) {
             tc::fence_after_sync();
             fn();
             tc::mma_commit(mbar);
@@ -1253,9 +1337,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         during();
         const bool to = !tc::mbar_wait(mbar, phase);
         phase ^= 1u;
-        const bool any = tc::wg_sync_or(0, to);
+        const bool any = sync_or(to);
         tc::fence_after_sync();
-        if (any && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+        if (any && lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
         return !any;
     };
     auto run = [&](auto &&fn) -> bool { return run_and(fn, [] {}); };
@@ -1268,7 +1352,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
     auto issue_load = [&](int l) {
         const int k = l & 1;
         const uint32_t bytes = (uint32_t)(lay.w_rows[l] * lay.w_cols[l] * 2);
-        if (row == 0) {
+        if (lead) {
             const uint32_t mb = tc::smem_u32(&s_wslot[k]);
             tc::mbar_expect_tx(mb, bytes);
             tc::bulk_g2s(s_base + P.slot_off[k], img_sc + lay.w_off[l], bytes, mb);
@@ -1285,8 +1369,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             const bool to = !tc::mbar_wait(tc::smem_u32(&s_wslot[k]), slot_phase[k]);
             slot_phase[k] ^= 1u;
             slot_busy[k] = false;
-            if (tc::wg_sync_or(0, to)) {
-                if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            if (sync_or(to)) {
+                if (lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
                 return false;
             }
         }
@@ -1310,7 +1394,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 slot_phase[k] ^= 1u;
                 slot_busy[k] = false;
             }
-        return !tc::wg_sync_or(0, to);
+        return !sync_or(to);
     };
     auto waddr = [&](int l) -> uint32_t {
         if (!P.stream) return s_base + lay.w_off[l];
@@ -1330,14 +1414,14 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
         const SceneDev &SD = T.s[sc];
         // this scene's resident weights
         __syncthreads();
-        if (row < 4) s_dbout[row] = 0.f;
+        if (threadIdx.x < 4) s_dbout[threadIdx.x] = 0.f;
         if (!drain()) {
-            if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            if (lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
             aborted = true;
             break;
         }
         img_sc = P.images + sc * P.image_stride;
-        if (row == 0) {
+        if (lead) {
             // the whole image, or (streamed weights) its tail: output layer + biases
             const uint32_t mb = tc::smem_u32(&s_mbar[1]);
             const uint32_t nbytes = P.res_bytes;
@@ -1346,11 +1430,11 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 tc::bulk_g2s(tc::smem_u32(wimg + off), img_sc + img0 + off, min(32768u, nbytes - off), mb);
         }
         slot_w[0] = slot_w[1] = -1;  // drained above
-        aborted = tc::wg_sync_or(0, !tc::mbar_wait(tc::smem_u32(&s_mbar[1]), wphase));
+        aborted = sync_or(!tc::mbar_wait(tc::smem_u32(&s_mbar[1]), wphase));
         wphase ^= 1u;
         tc::fence_after_sync();
         if (aborted) {
-            if (row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            if (lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
             break;
         }
         const int64_t S_sc = s_map.S[sc];
@@ -1370,7 +1454,8 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             const int64_t s = sbase + sl;
             const Sample rec = pf.cur;
             const bool valid = pf.v_cur;
-            if (MODE == 0 && pf.v_nxt) prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, md.F, SD.rays, SD.ray_begin);
+            if (MODE == 0 && half == 0 && pf.v_nxt)
+                prefetch_gather(pf.nxt, SD.feats, P.feat_bf16, md.F, SD.rays, SD.ray_begin);
             pf.cur = pf.nxt;
             pf.v_cur = pf.v_nxt;
             pf.v_nxt = load_record(P.samples, sbase, tile0, tile + 2, seg_end, S_sc, row, pf.nxt);
@@ -1380,7 +1465,12 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             // ---- 1. X_0 and G_out
             {
                 float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (MODE == 0) {
+                if (MODE == 0 && NWG == 2) {
+                    build_input_chunks_half(half, md, lay.K0, depth, T.rparam, SD.feats, P.feat_bf16, SD.rays,
+                                            SD.ray_begin, rec, valid, P.fp16, smem + P.x_off[0], row);
+                    if (valid) leaf = rec.leaf;
+                    if (valid && half == 0) g = P.dout[s];
+                } else if (MODE == 0) {
                     build_input_chunks(md, lay.K0, depth, T.rparam, SD.feats, P.feat_bf16, SD.rays, SD.ray_begin,
                                        rec, valid, P.fp16, smem + P.x_off[0], row, &leaf);
                     if (valid) g = P.dout[s];
@@ -1398,17 +1488,19 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         }
                     }
                 }
-                uint8_t *go = smem + P.gout_off;
-                st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
-                         tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
-                st_chunk(go, row, 1, 0u, 0u, 0u, 0u);
-                // bias gradient of the output layer: warp sums, then shared atomics
-                float gs[4] = {g.x, g.y, g.z, g.w};
+                if (half == 0) {
+                    uint8_t *go = smem + P.gout_off;
+                    st_chunk(go, row, 0, tc::pack2(g.x * gscale, g.y * gscale, P.fp16),
+                             tc::pack2(g.z * gscale, g.w * gscale, P.fp16), 0u, 0u);
+                    st_chunk(go, row, 1, 0u, 0u, 0u, 0u);
+                    // bias gradient of the output layer: warp sums, then shared atomics
+                    float gs[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float v = gs[c];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                    if (lane == 0) atomicAdd(&s_dbout[c], v);
+                    for (int c = 0; c < 4; ++c) {
+                        float v = gs[c];
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                        if (lane == 0) atomicAdd(&s_dbout[c], v);
+                    }
                 }
             }
             // ---- 2. forward recompute: X_{l+1} = relu(W_l X_l + b_l)
@@ -1426,7 +1518,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 if (!P.bias_mma) {  // the accumulator starts at the bias
                     const uint4 *b4 = reinterpret_cast<const uint4 *>(bias + lay.bias_l[l]);
 #pragma unroll 1
-                    for (int c = 0; c < kHp / 32; ++c) {
+                    for (int c = c32_lo; c < c32_hi; ++c) {
                         uint32_t v[32];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
@@ -1458,7 +1550,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 }
                 uint8_t *xn = smem + P.x_off[l + 1];
 #pragma unroll 1
-                for (int c = 0; c < kHp / 32; ++c) {
+                for (int c = c32_lo; c < c32_hi; ++c) {
                     uint32_t v[32];
                     tc::tmem_ld32_wait(tmem + lane_off + (uint32_t)(c * 32), v);
                     uint32_t p[16];
@@ -1493,7 +1585,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             auto mask_epilogue = [&](int l) {
                 uint8_t *x = smem + P.x_off[l];
 #pragma unroll 1
-                for (int c = 0; c < kHp / 32; ++c) {
+                for (int c = c32_lo; c < c32_hi; ++c) {
                     uint32_t v[32];
                     tc::tmem_ld32_wait(tmem + lane_off + (uint32_t)(c * 32), v);
 #pragma unroll
@@ -1567,7 +1659,9 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     const unsigned grp = __match_any_sync(0xFFFFFFFFu, leaf);
                     const bool solo = __popc(grp) == 1;
                     float4 *dst = reinterpret_cast<float4 *>(d_feat + (int64_t)(leaf >= 0 ? leaf : 0) * F);
-                    for (int c = 0; c < Fn; c += 16) {
+                    // this warpgroup's 16-column chunks of dL/dz
+                    const int c16_lo = half * (Fn / 16) / NWG * 16, c16_hi = (half + 1) * (Fn / 16) / NWG * 16;
+                    for (int c = c16_lo; c < c16_hi; c += 16) {
                         uint32_t v[16];
                         tc::tmem_ld16_wait(tmem + lane_off + (uint32_t)c, v);
                         if (leaf < 0) continue;
@@ -1587,7 +1681,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                     tc::fence_before_sync();
                     __syncwarp();
                     if (leaf >= 0 && !solo && lane == __ffs(grp) - 1) {
-                        for (int f4 = 0; f4 < F / 4; ++f4) {
+                        for (int f4 = c16_lo / 4; f4 < min(F, c16_hi) / 4; ++f4) {
                             float a[4] = {0.f, 0.f, 0.f, 0.f};
                             unsigned m = grp;
                             while (m) {
@@ -1612,7 +1706,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
             const int H = md.H;
             float *dpar = SD.d_params;
             // dW_out^T: lane = input feature k, columns = output j (< 4)
-            if (P.with_out) {
+            if (P.with_out && half == 0) {
                 uint32_t v[16];
                 tc::tmem_ld16_wait(tmem + lane_off + P.col_dwout, v);
                 if (row < H) {
@@ -1625,7 +1719,7 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                 const int in = md.in_l[l];
                 const int ncol = l == 0 ? lay.K0 : kHp;
                 float *dW = dpar + md.w_off[l];
-                for (int c = 0; c < ncol; c += 16) {
+                for (int c = half * (ncol / 16) / NWG * 16; c < (half + 1) * (ncol / 16) / NWG * 16; c += 16) {
                     uint32_t v[16];
                     tc::tmem_ld16_wait(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
                     if (row < H) {
@@ -1642,17 +1736,19 @@ __global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const __grid_co
                         }
                     }
                 }
-                uint32_t v[4];
-                tc::tmem_ld4_wait(tmem + lane_off + P.col_db[l], v);
-                if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
+                if (half == 0) {
+                    uint32_t v[4];
+                    tc::tmem_ld4_wait(tmem + lane_off + P.col_db[l], v);
+                    if (row < H) atomicAdd(dW + H * in + row, __uint_as_float(v[0]) * ginv);
+                }
             }
         }
         tc::fence_before_sync();
         seg = seg_end;
     }
-    if (!drain() && row == 0) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+    if (!drain() && lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, P.tmem_cols);
     }
@@ -1732,6 +1828,18 @@ int launch_mlp_backward_tc(const MlpDims &md, int precision, int fb, const Scene
         size_t smem;
         if (!tc_bwd_plan(md, P, smem)) return SVLF_ERR_UNSUPPORTED;
         if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM (it owns the TMEM it asks for)
+        // two warpgroups per tile: the plain form, one pass, resident weights
+        const int bwg = tuning().mlp_bwd_warpgroups;
+        if (mode == 0 && n_pass == 1 && !P.stream && bwg != 1) {
+            if (cudaFuncSetAttribute(mlp_backward_tc_kernel<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SVLF_ERR_CUDA;
+            prof_begin("mlp_backward_tc", s);
+            mlp_backward_tc_kernel<0, 2><<<num_sms(), 256, smem, s>>>(T, P);
+            prof_end(s);
+            if (cudaGetLastError() != cudaSuccess) return SVLF_ERR_CUDA;
+            continue;
+        }
         if (mode == 0) {
             if (cudaFuncSetAttribute(mlp_backward_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem) != cudaSuccess)

@@ -67,7 +67,7 @@ class SceneDesc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("mlp_warpgroups", ctypes.c_int), ("mlp_epilogue_batch", ctypes.c_int),
                 ("trace_budget", ctypes.c_int), ("trace_block", ctypes.c_int),
-                ("trace_refill", ctypes.c_int)]
+                ("trace_refill", ctypes.c_int), ("mlp_bwd_warpgroups", ctypes.c_int)]
 
 
 class Camera(ctypes.Structure):
@@ -713,9 +713,10 @@ def svlf_selftest_wait(limit_cycles: int, arrive: bool = False, stream=None):
     return bool(r[0].item()), int(r[1].item())
 
 
-def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0, trace_refill=0):
+def svlf_set_tuning(mlp_warpgroups=0, mlp_epilogue_batch=0, trace_budget=0, trace_block=0, trace_refill=0,
+                    mlp_bwd_warpgroups=0):
     t = Tuning(int(mlp_warpgroups), int(mlp_epilogue_batch), int(trace_budget), int(trace_block),
-               int(trace_refill))
+               int(trace_refill), int(mlp_bwd_warpgroups))
     _check("svlf_set_tuning", lib().svlf_set_tuning(ctypes.byref(t)))
 
 

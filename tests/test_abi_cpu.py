@@ -76,13 +76,15 @@ def test_tuning_arguments_are_checked(L):
     from paper_2205_07058_b300 import svlf
     svlf.svlf_set_tuning(3, 2, 32, 128, 8)
     assert svlf.svlf_get_tuning() == {"mlp_warpgroups": 3, "mlp_epilogue_batch": 2, "trace_budget": 32,
-                                      "trace_block": 128, "trace_refill": 8}
+                                      "trace_block": 128, "trace_refill": 8, "mlp_bwd_warpgroups": 0}
     with pytest.raises(svlf.SvlfError):
         svlf.svlf_set_tuning(mlp_warpgroups=9)
     with pytest.raises(svlf.SvlfError):
         svlf.svlf_set_tuning(trace_block=100)
     with pytest.raises(svlf.SvlfError):
         svlf.svlf_set_tuning(trace_refill=33)
+    with pytest.raises(svlf.SvlfError):
+        svlf.svlf_set_tuning(mlp_bwd_warpgroups=3)
     svlf.svlf_set_tuning()  # defaults
     assert svlf.svlf_get_tuning()["trace_budget"] == 16
     assert svlf.svlf_get_tuning()["trace_refill"] == 0

@@ -85,3 +85,58 @@ def test_tc_gradients_full_scene_subset():
         assert rel.max() <= 1e-4, rel.max()
     assert _rel(res[svlf.FP16][5], dfh) <= 1e-2 and _rel(res[svlf.FP16][6], dph) <= 1e-2
     assert _rel(res[svlf.BF16][5], dfe) <= 1e-2 and _rel(res[svlf.BF16][6], dpe) <= 1e-2
+
+
+@pytest.mark.parametrize("prec,fb", [("bf16", False), ("bf16", True), ("fp16", False)])
+def test_backward_two_warpgroups_equal_one(prec, fb):
+    """The tensor-core backward with a second warpgroup per tile (tuning
+    mlp_bwd_warpgroups 2: each warpgroup half of every epilogue, of the input
+    row and of the feature-gradient columns) against the one-warpgroup form:
+    the same MMAs and roundings, so the gradients agree up to the order of
+    the float32 atomic additions. Depth-9 scene, 41 -> 3x128 -> 4, 16384
+    training rays (hundreds of tiles, a ragged tail)."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(1002)
+    scene = I.make_scene(rng, 9, 64, 32)
+    shape = I.MLPShape(32, 128, 3)
+    feats = I.make_features(rng, scene.n_leaves, 32)
+    params = I.make_mlp(rng, shape, bias_std=0.1)
+    az, el = I.random_view_angles(np.random.default_rng(7), 100)
+    rays = I.training_rays(np.random.default_rng(8), 100, 800, 16384, az, el)
+    tree = svlf.Octree(torch.from_numpy(scene.leaf_ijk), 9)
+    f = torch.from_numpy(feats).cuda()
+    if fb:
+        f = f.to(torch.bfloat16)
+    p, r = torch.from_numpy(params).cuda(), torch.from_numpy(rays).cuda()
+    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec], svlf.FEAT_BF16 if fb else svlf.FEAT_F32)
+    rgb_t = torch.from_numpy(np.random.default_rng(9).uniform(0, 1, size=(rays.shape[0], 3)).astype(np.float32))
+    depth_t, mask = I.analytic_depth(rays, scene)
+    out = {}
+    try:
+        for wgs in (1, 2):
+            svlf.svlf_set_tuning(mlp_bwd_warpgroups=wgs)
+            rgb, depth, _, _, ws = svlf.svlf_render_rays(tree, f, p, net, r, 8)
+            d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+            loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            svlf.svlf_loss(rgb, depth, rgb_t.cuda(), torch.from_numpy(depth_t).cuda(), torch.from_numpy(mask).cuda(),
+                           0.1, d_rgb, d_depth, loss)
+            df = torch.zeros((scene.n_leaves, 32), device="cuda")
+            dp = torch.zeros_like(p)
+            svlf.svlf_render_rays_backward(tree, f, p, net, r, 8, (0.0, 0.0, 0.0), d_rgb, d_depth, df, dp, ws)
+            torch.cuda.synchronize()
+            assert svlf.svlf_get_device_status() == 0
+            out[wgs] = (df, dp)
+    finally:
+        svlf.svlf_set_tuning()
+    for a, b in zip(out[1], out[2]):
+        assert torch.linalg.norm(a) > 0
+        e = (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item()
+        assert e <= 1e-6, e
+    # every parameter block individually (weights and biases of each layer)
+    dims = O.layer_dims(32, 128, 3)
+    off = 0
+    for o, i in dims:
+        for n in (o * i, o):
+            a, b = out[1][1][off:off + n], out[2][1][off:off + n]
+            assert (torch.linalg.norm(a - b) / max(torch.linalg.norm(a).item(), 1e-30)).item() <= 1e-5
+            off += n
