@@ -315,45 +315,51 @@ def tensor_peak(peaks, clk, window_s):
 
 
 def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_src, ffma_tf=None, tag=None,
-                         gather=None, tpeak=None, clk_mhz=None, n_shadow=0):
+                         gather=None, tpeak=None, clk_mhz=None, n_shadow=0, steps=None):
     """Roofline figures of kernel `name` in a render + training step: its
-    algorithmic work per launch (launches alternate render / training where
-    a kernel runs in both) over its live average launch time. `gather` =
+    algorithmic work per launch over its live average launch time. The work
+    of a step is divided over the kernel's launches in a step (`steps` timed
+    steps: launches / steps of them; without it two, render and training,
+    where a kernel runs in both; Adam runs twice, features and network). `gather` =
     (F, bytes per feature, table rows) adds, for the network forward, the
     feature gather it fuses: one row per sample (not deduplicated), with the
     table size as the deduplicated lower bound."""
     launches, ms = kstats[name]
     avg_s = ms / launches / 1e3
+    lps = launches / steps if steps else 2.0  # launches per step
     tpk, tlabel, tsust = tpeak if tpeak else (peaks.get("bf16_tflops_sustained", 1400.0), "sustained",
                                              peaks.get("bf16_tflops_sustained", 1400.0))
     if name == "mlp_forward_tc":
-        work, bound, unit, peak = (S_r + S_t) * fps / 2.0, "tensor", "TFLOP/s", tpk
+        work, bound, unit, peak = (S_r + S_t) * fps / lps, "tensor", "TFLOP/s", tpk
     elif name == "mlp_backward_tc":
         work, bound, unit, peak = S_t * 3.0 * fps, "tensor", "TFLOP/s", tpk
     elif name in ("mlp_forward_f32", "mlp_backward_f32"):
         mult = 1.0 if name == "mlp_forward_f32" else 3.0
-        work = ((S_r + S_t) / 2.0 if name == "mlp_forward_f32" else S_t) * mult * fps
+        work = ((S_r + S_t) / lps if name == "mlp_forward_f32" else S_t) * mult * fps
         bound, unit = "alu", "TFLOP/s"
         peak = round(ffma_tf, 3) if ffma_tf else 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     elif name == "adam":
         # features, network: read p, g, m, v and write p, m, v (28 B), plus the bf16 copy (2 B)
         # of the n_shadow parameters that have one
-        work, bound, unit, peak = (n_par * 28.0 + n_shadow * 2.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+        work, bound, unit, peak = (n_par * 28.0 + n_shadow * 2.0) / lps, "hbm", "GB/s", peaks["hbm_gbs"]
     elif name == "trace":  # ray in (24 B), span out (8 B), a 16-byte record per sample
-        work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+        work, bound, unit, peak = ((N + NT) * 32.0 + (S_r + S_t) * 16.0) / lps, "hbm", "GB/s", peaks["hbm_gbs"]
     elif name == "composite":  # span in, colour + depth out (16 B) per ray; record + output per sample
-        work, bound, unit, peak = ((N + NT) * 24.0 + (S_r + S_t) * 32.0) / 2.0, "hbm", "GB/s", peaks["hbm_gbs"]
+        work, bound, unit, peak = ((N + NT) * 24.0 + (S_r + S_t) * 32.0) / lps, "hbm", "GB/s", peaks["hbm_gbs"]
     else:
         return None
     achieved = work / avg_s / (1e12 if unit == "TFLOP/s" else 1e9)
     tr = ncu_traffic(name, tag) if tag else None
     extra = {}
-    if name == "trace" and tr and "warp_inst_per_ray" in tr and clk_mhz:
-        # issue-slot roofline: the launch's warp instructions (ncu counts per render and per training
-        # ray x the rays of each launch, averaged like the time) over its time, against 4 schedulers x 1
-        # instruction per clock on every SM
-        ipr = tr["warp_inst_per_ray"]
-        inst = (ipr["render"] * N + ipr["train"] * NT) / 2.0
+    if name == "trace" and tr and ("warp_inst_per_ray" in tr or "warp_inst_per_step" in tr) and clk_mhz:
+        # issue-slot roofline: the launch's warp instructions (ncu's count for a step's launches,
+        # divided over them like the time) over its time, against 4 schedulers x 1 instruction per
+        # clock on every SM
+        if "warp_inst_per_step" in tr:
+            inst = tr["warp_inst_per_step"] / lps
+        else:
+            ipr = tr["warp_inst_per_ray"]
+            inst = (ipr["render"] * N + ipr["train"] * NT) / lps
         ipeak = 148 * 4 * clk_mhz * 1e6
         extra["issue"] = {"warp_inst_per_launch": int(inst), "achieved_warp_inst_per_s": round(inst / avg_s, 1),
                           "peak_warp_inst_per_s": ipeak, "frac": round(inst / avg_s / ipeak, 4),
@@ -361,7 +367,7 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
                                     "148 SMs x 4 issue slots per clock at the median SM clock of the timed region"}
     if name == "mlp_forward_tc" and gather is not None:
         F_, fb, rows = gather
-        gb = (S_r + S_t) / 2.0 * F_ * fb
+        gb = (S_r + S_t) / lps * F_ * fb
         extra["gather"] = {"bytes_per_launch": int(gb), "dedup_lower_bound_bytes": int(rows * F_ * fb),
                            "rate_gbs": round(gb / avg_s / 1e9, 1),
                            "frac_of_hbm": round(gb / avg_s / 1e9 / peaks["hbm_gbs"], 4),
@@ -376,7 +382,7 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
                             else "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
             "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": (None if not tr else int(tr["bytes_per_launch"]) if "bytes_per_launch" in tr
-                        else int(tr["bytes_per_sample"] * ((S_r + S_t) / 2.0 if name == "mlp_forward_tc" else S_t))
+                        else int(tr["bytes_per_sample"] * ((S_r + S_t) / lps if name == "mlp_forward_tc" else S_t))
                         if "bytes_per_sample" in tr else None),
             **({"traffic_source": f"ncu DRAM bytes per sample on {tr.get('measured_on', tr.get('workload'))} "
                                   "x this launch's samples"}
@@ -433,8 +439,19 @@ def run_ours(args, rank, world, local_rank):
     mask = torch.from_numpy(W["mask"]).to(dev)
     del teacher
 
-    ws_r = svlf.alloc_workspace(net, N, K_HITS)
-    ws_t = svlf.alloc_workspace(tnet, NT, K_HITS)
+    # With the same tensor-core network on both passes, the view rays and the
+    # training rays share one batched render call (one traversal, one network
+    # forward and one compositing launch for both), and the batched backward
+    # differentiates the training scene only (the view scene has no output
+    # gradients, so it takes no part). The FP32 plain form (single-scene calls)
+    # keeps two render calls.
+    merged = not args.render_only and prec == tprec and prec != svlf.FP32
+    if merged:
+        ws_b = svlf.alloc_workspace_batched(
+            net, [svlf.BatchScene(tree, feats_k, params, rays), svlf.BatchScene(tree, feats_k, params, trays)], K_HITS)
+    else:
+        ws_r = svlf.alloc_workspace(net, N, K_HITS)
+        ws_t = svlf.alloc_workspace(tnet, NT, K_HITS)
     rgb = torch.empty((N, 3), device=dev)
     depth = torch.empty((N,), device=dev)
     trgb = torch.empty((NT, 3), device=dev)
@@ -456,17 +473,32 @@ def run_ours(args, rank, world, local_rank):
     step_no = [0]
     ev = {}
 
-    def render_phase(rays=rays, rgb=rgb, depth=depth):
-        svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
+    def scenes_of(rays, rgb, depth, trays, grads):
+        v = svlf.BatchScene(tree, feats_k, params, rays, rgb, depth)
+        t = svlf.BatchScene(tree, feats_k, params, trays, trgb, tdepth)
+        if grads:
+            t.d_rgb, t.d_depth, t.d_features, t.d_params = d_rgb, d_depth, g_feat, g_par
+        return [v, t]
 
-    def train_phase(trays=trays, loss=loss):
+    def render_phase(rays=rays, rgb=rgb, depth=depth, trays=trays):
+        if merged:  # the view rays and the training rays' forward
+            svlf.svlf_render_rays_batched(scenes_of(rays, rgb, depth, trays, False), net, K_HITS, workspace=ws_b)
+        else:
+            svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
+
+    def train_phase(trays=trays, loss=loss, rays=rays, rgb=rgb, depth=depth):
         step_no[0] += 1
         gbuf.zero_()
         loss.zero_()
-        svlf.svlf_render_rays(tree, feats_k, params, tnet, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
+        if not merged:
+            svlf.svlf_render_rays(tree, feats_k, params, tnet, trays, K_HITS, workspace=ws_t, out=(trgb, tdepth))
         svlf.svlf_loss(trgb, tdepth, rgb_t, depth_t, mask, DEPTH_WEIGHT, d_rgb, d_depth, loss, n_total=n_batch)
-        svlf.svlf_render_rays_backward(tree, feats_k, params, tnet, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb,
-                                       d_depth, g_feat, g_par, ws_t)
+        if merged:
+            svlf.svlf_render_rays_backward_batched(scenes_of(rays, rgb, depth, trays, True), net, K_HITS,
+                                                   (0.0, 0.0, 0.0), ws_b)
+        else:
+            svlf.svlf_render_rays_backward(tree, feats_k, params, tnet, trays, K_HITS, (0.0, 0.0, 0.0), d_rgb,
+                                           d_depth, g_feat, g_par, ws_t)
         if dist is not None:
             dp.allreduce_gradients(gbuf)  # the data-parallel exchange (NCCL)
         svlf.svlf_adam_step(feats, g_feat, m_feat, v_feat, step_no[0], lr=LR,
@@ -494,8 +526,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     # FP32 SIMT roofline denominator: this GPU's measured FMA rate
     ffma_tf = svlf.svlf_measure_ffma_tflops() if "fp32" in (args.precision, args.train_precision) else None
-    n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
-    n_samples_train = 0 if args.render_only else svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
+    if merged:
+        n_samples_render, n_samples_train = svlf.svlf_workspace_scene_samples(
+            ws_b, net, [svlf.BatchScene(tree, feats_k, params, rays), svlf.BatchScene(tree, feats_k, params, trays)],
+            K_HITS)
+    else:
+        n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
+        n_samples_train = 0 if args.render_only else svlf.svlf_workspace_samples(ws_t, tnet, NT, K_HITS)
     loss_first = None
 
     def barrier():
@@ -570,8 +607,8 @@ def run_ours(args, rank, world, local_rank):
             rgb_t.copy_(b["tgt"][:, :3])
             depth_t.copy_(b["tgt"][:, 3])
             mask.copy_(b["tgt"][:, 4])
-            render_phase(b["rays"], b["rgb"], b["depth"])
-            train_phase(b["trays"], b["loss"])
+            render_phase(b["rays"], b["rgb"], b["depth"], b["trays"])
+            train_phase(b["trays"], b["loss"], b["rays"], b["rgb"], b["depth"])
             b["used"].record(stream)
             b["done"].record(stream)
 
@@ -672,7 +709,7 @@ def run_ours(args, rank, world, local_rank):
         return step_kernel_roofline(name, kstats, S_r, S_t, N, NT, feats.numel() + params.numel(), fps, peaks,
                                     peak_src, ffma_tf, tag, gather=(FEAT, 2 if read_bf16 else 4, feats.shape[0]),
                                     tpeak=tensor_peak(peaks, clk, total_ms / 1e3), clk_mhz=clk.get("sm_mhz"),
-                                    n_shadow=feats.numel() if read_bf16 else 0)
+                                    n_shadow=feats.numel() if read_bf16 else 0, steps=args.steps)
 
     if dom:
         roof = kernel_roofline(dom)
@@ -722,9 +759,13 @@ def run_ours(args, rank, world, local_rank):
                              + (f", read as a {feats_k.numel() * 2 / 1e6:.0f} MB bf16 copy" if read_bf16 else "")
                              + ")",
                        "autotune": tuned},
-            "render_rays_per_s": round(N * args.steps / (render_ms / 1e3), 1),
+            "render_rays_per_s": round((N + (NT if merged else 0)) * args.steps / (render_ms / 1e3), 1),
             "train_rays_per_s": None if args.render_only else round(NT * args.steps / (train_ms / 1e3), 1),
             "render_ms": round(render_ms / args.steps, 4), "train_ms": round(train_ms / args.steps, 4),
+            "phases": ("render_ms: one render call for the view rays and the training rays' forward "
+                       "(render_rays_per_s counts both); train_ms: the training loss, backward and Adam"
+                       if merged else "render_ms: the view rays' render call; train_ms: the training rays' "
+                       "render, loss, backward and Adam"),
             "samples_per_step": {"render": n_samples_render, "train": n_samples_train},
             "e2e": e2e, "e2e_camera": e2e_camera, "gpu_launches": gpu_launches, "kernels": per_kernel,
             "roofline": roof, "kernel_rooflines": kernel_rooflines, "clocks": clk, "device_status": status,
@@ -868,8 +909,8 @@ def extra_arms(args):
     its own child process after the headline's timed region: the FP32 plain
     form of the same step, the large scene (depth 10, bf16 features, 4x128,
     K = 16) and the 64-scene batched form under a CUDA graph."""
-    keep = ("value", "unit", "steps", "warmup", "ms_per_step", "render_rays_per_s", "train_rays_per_s", "dtype",
-            "roofline", "clocks", "device_status", "samples_per_step", "e2e")
+    keep = ("value", "unit", "steps", "warmup", "ms_per_step", "render_rays_per_s", "train_rays_per_s", "phases",
+            "dtype", "roofline", "clocks", "device_status", "samples_per_step", "e2e")
     arms = {}
     specs = [("fp32_plain", ["--precision", "fp32", "--steps", "5", "--warmup", "3"]),
              ("large", ["--workload", "large", "--steps", "5", "--warmup", "3"]),

@@ -280,7 +280,12 @@ int svlf_render_rays_batched(const svlf_scene *scenes, int n_scenes, const svlf_
 
 /* Backward of svlf_render_rays_batched for every scene (see
  * svlf_render_rays_backward). Either gradient may be skipped by passing NULL
- * for it in every scene. */
+ * for it in every scene. A scene whose d_rgb and d_depth are both NULL takes
+ * no part: its samples are not differentiated and its d_features and
+ * d_mlp_params are not touched (so rays that are only rendered, e.g. the views
+ * of a training step, can share the render call with the rays that are
+ * trained on). Errors: SVLF_ERR_ARG when exactly one of a scene's d_rgb,
+ * d_depth is NULL. */
 int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
                                       const svlf_mlp_desc *mlp, const svlf_render_opts *opts,
                                       void *workspace, size_t ws_bytes, void *stream);
@@ -290,6 +295,11 @@ int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n_scenes,
  * `stream`). n_rays: host, n_scenes ray counts, as in the call. */
 int svlf_workspace_samples_batched(const void *workspace, const svlf_mlp_desc *mlp, const int64_t *n_rays,
                                    int n_scenes, int K, int64_t *n_samples, void *stream);
+
+/* The same per scene: per_scene (host, n_scenes entries) receives each
+ * scene's samples. */
+int svlf_workspace_scene_samples(const void *workspace, const svlf_mlp_desc *mlp, const int64_t *n_rays,
+                                 int n_scenes, int K, int64_t *per_scene, void *stream);
 
 /* ------------------------------------------------ two-decoder form (Sec. 4.1-4.2) */
 /* The paper's full SVLF: features live on octree vertices (Sec. 4.1 "Scene

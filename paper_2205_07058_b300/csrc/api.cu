@@ -183,8 +183,12 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
     for (int i = 0; i < n_scenes; ++i) {
         const svlf_scene &sc = scenes[i];
         if ((rc = check_scene(sc, per_ray_io && !backward))) return rc;
-        if (per_ray_io && backward && sc.n_rays > 0 && (!sc.d_rgb || !sc.d_depth)) return SVLF_ERR_ARG;
+        // backward: a scene without output gradients (both NULL) takes no part
+        if (per_ray_io && backward && sc.n_rays > 0 && (!sc.d_rgb != !sc.d_depth)) return SVLF_ERR_ARG;
         SceneDev &d = T.s[i];
+        d.grad = !(per_ray_io && backward && !sc.d_rgb);
+        d.grad_begin = T.grad_rays;
+        if (d.grad) T.grad_rays += sc.n_rays;
         d.tree = octree_view(sc.tree);
         d.feats = sc.features;
         d.params = sc.mlp_params;
@@ -243,7 +247,7 @@ static int render_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svl
 
 static int backward_table(const SceneTable &T, const svlf_mlp_desc &mlp, const svlf_render_opts &opts,
                           void *workspace, bool want_feat, bool want_params, cudaStream_t s) {
-    if (T.total_rays == 0 || (!want_feat && !want_params)) return SVLF_OK;
+    if (T.grad_rays == 0 || (!want_feat && !want_params)) return SVLF_OK;
     if (mlp.precision == SVLF_FP32 && (T.n != 1 || !f32_backward_fits(make_dims(mlp)))) return SVLF_ERR_UNSUPPORTED;
     Workspace ws = carve_workspace(workspace, mlp, T.total_rays, T.K, T.n);
     int rc;
@@ -317,6 +321,7 @@ extern "C" int svlf_render_rays_backward(svlf_octree tree, const void *features,
                                          float *d_mlp_params, void *workspace, size_t ws_bytes,
                                          void *stream) {
     if (!tree) return SVLF_ERR_ARG;
+    if (n_rays > 0 && (!d_rgb || !d_depth)) return SVLF_ERR_ARG;
     svlf_scene sc = one_scene(tree, features, mlp_params, rays, n_rays);
     sc.d_rgb = d_rgb;
     sc.d_depth = d_depth;
@@ -349,12 +354,15 @@ extern "C" int svlf_render_rays_backward_batched(const svlf_scene *scenes, int n
     if (mlp->precision == SVLF_FP32 && n_scenes > 1) return SVLF_ERR_UNSUPPORTED;
     bool want_feat = false, want_params = false;
     for (int i = 0; i < n_scenes; ++i) {
+        if (!T.s[i].grad) continue;
         want_feat |= scenes[i].d_features != nullptr;
         want_params |= scenes[i].d_mlp_params != nullptr;
     }
-    for (int i = 0; i < n_scenes; ++i)  // a batched backward forms each gradient for all scenes or none
+    for (int i = 0; i < n_scenes; ++i) {  // each gradient for all scenes that take part, or none
+        if (!T.s[i].grad) continue;
         if ((want_feat && !scenes[i].d_features) || (want_params && !scenes[i].d_mlp_params))
             if (scenes[i].n_rays > 0) return SVLF_ERR_ARG;
+    }
     return backward_table(T, *mlp, *opts, workspace, want_feat, want_params, (cudaStream_t)stream);
 }
 
@@ -376,17 +384,17 @@ extern "C" int svlf_workspace_samples(const void *workspace, const svlf_mlp_desc
     return SVLF_OK;
 }
 
-extern "C" int svlf_workspace_samples_batched(const void *workspace, const svlf_mlp_desc *mlp,
-                                              const int64_t *n_rays, int n_scenes, int K, int64_t *n_samples,
-                                              void *stream) {
-    if (!workspace || !mlp || !n_rays || !n_samples || n_scenes < 1 || n_scenes > kMaxScenes || K < 1)
+extern "C" int svlf_workspace_scene_samples(const void *workspace, const svlf_mlp_desc *mlp,
+                                            const int64_t *n_rays, int n_scenes, int K, int64_t *per_scene,
+                                            void *stream) {
+    if (!workspace || !mlp || !n_rays || !per_scene || n_scenes < 1 || n_scenes > kMaxScenes || K < 1)
         return SVLF_ERR_ARG;
     int64_t total = 0;
     for (int i = 0; i < n_scenes; ++i) {
         if (n_rays[i] < 0) return SVLF_ERR_ARG;
         total += n_rays[i];
+        per_scene[i] = 0;
     }
-    *n_samples = 0;
     if (total == 0) return SVLF_OK;
     Workspace ws = carve_workspace(const_cast<void *>(workspace), *mlp, total, K, n_scenes);
     unsigned int c[kMaxScenes];
@@ -396,8 +404,21 @@ extern "C" int svlf_workspace_samples_batched(const void *workspace, const svlf_
         return SVLF_ERR_CUDA;
     for (int i = 0; i < n_scenes; ++i) {
         const int64_t cap = n_rays[i] * (int64_t)K;
-        *n_samples += (int64_t)c[i] < cap ? (int64_t)c[i] : cap;
+        per_scene[i] = (int64_t)c[i] < cap ? (int64_t)c[i] : cap;
     }
+    return SVLF_OK;
+}
+
+extern "C" int svlf_workspace_samples_batched(const void *workspace, const svlf_mlp_desc *mlp,
+                                              const int64_t *n_rays, int n_scenes, int K, int64_t *n_samples,
+                                              void *stream) {
+    if (!n_samples) return SVLF_ERR_ARG;
+    int64_t per[kMaxScenes];
+    if (n_scenes < 1 || n_scenes > kMaxScenes) return SVLF_ERR_ARG;
+    const int rc = svlf_workspace_scene_samples(workspace, mlp, n_rays, n_scenes, K, per, stream);
+    if (rc) return rc;
+    *n_samples = 0;
+    for (int i = 0; i < n_scenes; ++i) *n_samples += per[i];
     return SVLF_OK;
 }
 
@@ -578,6 +599,7 @@ extern "C" int svlf_render_rays_backward_two_decoder(
     if (!view.leaf_vertices && view.n_leaves > 0) return SVLF_ERR_ARG;
     if (n_rays > 0 && view.n_leaves > 0 && (!z_t || !z_c || !params_t || !params_c)) return SVLF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(z_c) % 16) return SVLF_ERR_ARG;
+    if (n_rays > 0 && (!d_rgb || !d_depth)) return SVLF_ERR_ARG;
     svlf_scene sc = one_scene(tree, z_t, params_t, rays, n_rays);
     sc.d_rgb = d_rgb;
     sc.d_depth = d_depth;
@@ -704,7 +726,8 @@ extern "C" int svlf_eta_loss_two_decoder(svlf_octree tree, const svlf_two_decode
     T.s[0].tree = octree_view(tree);
     T.s[0].rays = rays;
     T.s[0].n_rays = n_rays;
-    T.total_rays = n_rays;
+    T.s[0].grad = 1;
+    T.total_rays = T.grad_rays = n_rays;
     const size_t stride = two_decoder_stride(*desc, n_rays, T.K);
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return SVLF_ERR_WORKSPACE;
     if (ws_bytes < workspace_bytes_raw(n_rays, T.K, stride, 1)) return SVLF_ERR_WORKSPACE;

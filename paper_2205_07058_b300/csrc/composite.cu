@@ -51,12 +51,15 @@ __global__ void composite_backward_kernel(const __grid_constant__ SceneTable Tb,
                                           unsigned int *__restrict__ max_abs_bits,
                                           float *__restrict__ w_dD) {
     float gmax = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Tb.total_rays;
-         r += (int64_t)gridDim.x * blockDim.x) {
+    // the rays of the scenes that take part in the backward (scenes without
+    // output gradients are skipped)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Tb.grad_rays;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const SceneDev &S = Tb.s[scene_of_grad_ray(Tb, i)];
+        const int64_t rl = i - S.grad_begin;  // ray index within its scene
+        const int64_t r = S.ray_begin + rl;
         const int2 sp = ray_span[r];
         if (sp.y == 0) continue;
-        const SceneDev &S = Tb.s[scene_of_ray(Tb, r)];
-        const int64_t rl = r - S.ray_begin;
         const float g0 = S.d_rgb[3 * rl + 0], g1 = S.d_rgb[3 * rl + 1], g2 = S.d_rgb[3 * rl + 2];
         const float gD = S.d_depth[rl];
         float tau_sum = 0.f;
@@ -145,7 +148,7 @@ int launch_composite(const SceneTable &T, const Workspace &ws, const float bg[3]
 int launch_composite_backward(const SceneTable &T, const Workspace &ws, const float bg[3],
                               cudaStream_t s, float *w_dD) {
     prof_begin("composite_backward", s);
-    composite_backward_kernel<<<grid_for(T.total_rays, 256), 256, 0, s>>>(
+    composite_backward_kernel<<<grid_for(T.grad_rays, 256), 256, 0, s>>>(
         T, ws.ray_span, ws.samples, ws.outputs, bg[0], bg[1], bg[2], ws.dout,
         ws.counter + kCtrMaxAbsDout, w_dD);
     prof_end(s);

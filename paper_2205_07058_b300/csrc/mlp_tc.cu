@@ -202,7 +202,8 @@ __device__ __forceinline__ void tile_map_build(const SceneTable &T, const unsign
         int64_t acc = 0;
         for (int i = 0; i < T.n; ++i) {
             const int64_t cap = T.s[i].n_rays * (int64_t)T.K;
-            const int64_t Si = min((int64_t)counter[kCtrScene + i], cap);
+            // a scene without output gradients has no tiles in a backward
+            const int64_t Si = T.s[i].grad ? min((int64_t)counter[kCtrScene + i], cap) : 0;
             m.S[i] = Si;
             m.tile0[i] = acc;
             acc += (Si + kTcTile - 1) / kTcTile;

@@ -85,6 +85,10 @@ struct SceneDev {
     int64_t ray_begin;    // first global ray index of the scene
     int64_t n_rays;
     int64_t chunk_begin;  // first traversal chunk of the scene
+    // backward: the scene takes part (it has output gradients), and the index of
+    // its first ray among the rays of the scenes that take part
+    int grad;
+    int64_t grad_begin;
 };
 
 struct SceneTable {
@@ -94,8 +98,22 @@ struct SceneTable {
     int64_t total_chunks;
     int chunk_rays;  // rays per traversal work item: 32, 64 or kTraceChunk
     int rparam;      // ray parameterisation of the network input (SVLF_RPARAM_*)
+    int64_t grad_rays;  // backward: rays of the scenes that take part
     SceneDev s[kMaxScenes];
 };
+
+// Backward: index of the scene holding the `i`-th ray among the rays of the
+// scenes that take part (grad_begin is non-decreasing; scenes that take no
+// part, or have no rays, hold none and tie with the next, so the last scene
+// whose grad_begin <= i is the one).
+__host__ __device__ __forceinline__ int scene_of_grad_ray(const SceneTable &T, int64_t i) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.s[mid].grad_begin <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Index of the scene holding global ray g (the table is sorted by ray_begin).
 __host__ __device__ __forceinline__ int scene_of_ray(const SceneTable &T, int64_t g) {

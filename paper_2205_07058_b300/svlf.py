@@ -87,7 +87,7 @@ EXPORTS = [
     "svlf_render_rays_static", "svlf_workspace_size_batched", "svlf_render_rays_batched",
     "svlf_render_rays_backward_batched", "svlf_set_tuning", "svlf_get_tuning",
     "svlf_octree_build_vertices", "svlf_octree_leaf_vertices", "svlf_octree_parent_index", "svlf_selftest_ffma",
-    "svlf_workspace_samples_batched", "svlf_pinhole_rays",
+    "svlf_workspace_samples_batched", "svlf_workspace_scene_samples", "svlf_pinhole_rays",
     "svlf_workspace_size_two_decoder",
     "svlf_render_rays_two_decoder", "svlf_render_rays_backward_two_decoder", "svlf_surface_loss_two_decoder",
     "svlf_eta_loss_two_decoder", "svlf_build_octree_from_depth", "svlf_set_step_limit",
@@ -141,6 +141,7 @@ def lib():
     L.svlf_selftest_ffma.argtypes = [vp, ctypes.c_int, i64, vp]
     L.svlf_selftest_wait.argtypes = [i64, ctypes.c_int, vp, vp]
     L.svlf_workspace_samples_batched.argtypes = [vp, P(MlpDesc), P(i64), i32, i32, P(i64), vp]
+    L.svlf_workspace_scene_samples.argtypes = [vp, P(MlpDesc), P(i64), i32, i32, P(i64), vp]
     L.svlf_pinhole_rays.argtypes = [P(Camera), i32, i32, i32, vp, vp]
     L.svlf_workspace_size_two_decoder.argtypes = [P(TwoDecoderDescC), i64, i32, P(sz)]
     L.svlf_render_rays_two_decoder.argtypes = [vp, vp, vp, vp, vp, P(TwoDecoderDescC), vp, i64, P(RenderOpts),
@@ -585,6 +586,18 @@ def svlf_workspace_samples_batched(workspace: torch.Tensor, net: Network, scenes
     _check("svlf_workspace_samples_batched", lib().svlf_workspace_samples_batched(
         wp, ctypes.byref(d), rays, len(scenes), int(K), ctypes.byref(n), _stream(stream)))
     return n.value
+
+
+def svlf_workspace_scene_samples(workspace: torch.Tensor, net: Network, scenes: Sequence[BatchScene], K: int,
+                                 stream=None) -> list:
+    """Samples the last batched call over `scenes` wrote into `workspace`, per scene."""
+    rays = (ctypes.c_int64 * len(scenes))(*[int(s.rays.shape[0]) for s in scenes])
+    per = (ctypes.c_int64 * len(scenes))()
+    d = net.desc()
+    wp, _ = _ws_ptr(workspace)
+    _check("svlf_workspace_scene_samples", lib().svlf_workspace_scene_samples(
+        wp, ctypes.byref(d), rays, len(scenes), int(K), per, _stream(stream)))
+    return [int(x) for x in per]
 
 
 def svlf_render_rays_backward_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg, workspace,

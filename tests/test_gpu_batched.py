@@ -240,3 +240,67 @@ def test_workspace_samples_batched_equals_per_scene_counts():
         _, _, hits, _, _ = svlf.svlf_render_rays(b.tree, b.features, b.params, net, b.rays, 8, want_hits=True)
         expect += int((hits >= 0).sum())
     assert total == expect > 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_scene_without_output_gradients_takes_no_part(prec):
+    """A training step's two kinds of rays in one batched call: rays that are
+    only rendered (a scene whose d_rgb and d_depth are NULL) and rays that are
+    trained on, over the same octree, features and network. The rendered
+    outputs equal single calls, the gradients equal the single-scene backward
+    of the trained rays alone (up to the order of float32 atomic additions),
+    and a scene with exactly one of d_rgb, d_depth is refused."""
+    from paper_2205_07058_b300 import svlf
+    rng = np.random.default_rng(52)
+    sc = I.make_scene(rng, 8, 12, 4)
+    feats = torch.from_numpy(I.make_features(rng, sc.n_leaves, 32)).cuda()
+    params = torch.from_numpy(I.make_mlp(rng, SHAPE, bias_std=0.2)).cuda()
+    tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), 8)
+    az, el = I.random_view_angles(rng, 3)
+    view = torch.from_numpy(np.concatenate([I.pinhole_rays(az[v], el[v], 96, 96) for v in range(2)])).cuda()
+    train = torch.from_numpy(I.training_rays(np.random.default_rng(3), 3, 128, 6000, az, el)).cuda()
+    net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
+    K = 8
+    nt = train.shape[0]
+    rgb_t = torch.from_numpy(np.random.default_rng(4).uniform(0, 1, size=(nt, 3)).astype(np.float32)).cuda()
+    depth_t, mask = I.analytic_depth(train.cpu().numpy(), sc)
+    depth_t, mask = torch.from_numpy(depth_t).cuda(), torch.from_numpy(mask).cuda()
+
+    def loss_grads(rgb, depth):
+        d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        svlf.svlf_loss(rgb, depth, rgb_t, depth_t, mask, 0.1, d_rgb, d_depth, loss)
+        return d_rgb, d_depth
+
+    # one call for both: the view scene takes no part in the backward
+    batch = [svlf.BatchScene(tree, feats, params, view), svlf.BatchScene(tree, feats, params, train)]
+    ws = svlf.svlf_render_rays_batched(batch, net, K)
+    batch[1].d_rgb, batch[1].d_depth = loss_grads(batch[1].rgb, batch[1].depth)
+    batch[1].d_features = torch.zeros_like(feats)
+    batch[1].d_params = torch.zeros_like(params)
+    svlf.svlf_render_rays_backward_batched(batch, net, K, (0.0, 0.0, 0.0), ws)
+    torch.cuda.synchronize()
+    assert svlf.svlf_get_device_status() == 0
+    # single calls
+    per = svlf.svlf_workspace_scene_samples(ws, net, batch, K)
+    assert sum(per) == svlf.svlf_workspace_samples_batched(ws, net, batch, K)
+    vrgb, vdepth, _, _, vws = svlf.svlf_render_rays(tree, feats, params, net, view, K)
+    trgb, tdepth, _, _, tws = svlf.svlf_render_rays(tree, feats, params, net, train, K)
+    assert per == [svlf.svlf_workspace_samples(vws, net, view.shape[0], K),
+                   svlf.svlf_workspace_samples(tws, net, train.shape[0], K)]
+    d_rgb, d_depth = loss_grads(trgb, tdepth)
+    df, dp = torch.zeros_like(feats), torch.zeros_like(params)
+    svlf.svlf_render_rays_backward(tree, feats, params, net, train, K, (0.0, 0.0, 0.0), d_rgb, d_depth, df, dp, tws)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(batch[0].rgb, vrgb, rtol=0, atol=1e-6)
+    torch.testing.assert_close(batch[0].depth, vdepth, rtol=0, atol=1e-6)
+    torch.testing.assert_close(batch[1].rgb, trgb, rtol=0, atol=1e-6)
+    for a, b in ((batch[1].d_features, df), (batch[1].d_params, dp)):
+        assert torch.linalg.norm(b) > 0
+        e = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+        assert e <= 1e-5, e
+    # exactly one of the two output gradients: refused
+    batch[0].d_rgb = torch.zeros_like(batch[0].rgb)
+    with pytest.raises(svlf.SvlfError) as err:
+        svlf.svlf_render_rays_backward_batched(batch, net, K, (0.0, 0.0, 0.0), ws)
+    assert err.value.code == svlf.SVLF_ERR_ARG
