@@ -273,7 +273,8 @@ def ncu_traffic(kernel: str, tag: str):
     samples, the bytes per sample ("bytes_per_sample", possibly measured on a
     smaller case of the same step, named in "measured_on"), which the caller
     scales by the samples of a launch; and for the traversal its warp
-    instructions per render and per training ray ("warp_inst_per_ray")."""
+    instructions, per step ("warp_inst_per_step") or per render and per
+    training ray ("warp_inst_per_ray")."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -363,8 +364,10 @@ def step_kernel_roofline(name, kstats, S_r, S_t, N, NT, n_par, fps, peaks, peak_
         ipeak = 148 * 4 * clk_mhz * 1e6
         extra["issue"] = {"warp_inst_per_launch": int(inst), "achieved_warp_inst_per_s": round(inst / avg_s, 1),
                           "peak_warp_inst_per_s": ipeak, "frac": round(inst / avg_s / ipeak, 4),
-                          "source": f"smsp__inst_executed.sum per ray on {tr.get('measured_on', tr.get('workload'))}, "
-                                    "148 SMs x 4 issue slots per clock at the median SM clock of the timed region"}
+                          "source": ("smsp__inst_executed.sum of a step's traversal launches" if "warp_inst_per_step" in tr
+                                     else "smsp__inst_executed.sum per ray")
+                                    + f" on {tr.get('measured_on', tr.get('workload'))}, 148 SMs x 4 issue slots per "
+                                    "clock at the median SM clock of the timed region"}
     if name == "mlp_forward_tc" and gather is not None:
         F_, fb, rows = gather
         gb = (S_r + S_t) / lps * F_ * fb
