@@ -451,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
     merged = not args.render_only and prec == tprec and prec != svlf.FP32
     if merged:
         ws_b = svlf.alloc_workspace_batched(
-            net, [svlf.BatchScene(tree, feats_k, params, rays), svlf.BatchScene(tree, feats_k, params, trays)], K_HITS)
+            net, [svlf.BatchScene(tree, feats_k, params, trays), svlf.BatchScene(tree, feats_k, params, rays)], K_HITS)
     else:
         ws_r = svlf.alloc_workspace(net, N, K_HITS)
         ws_t = svlf.alloc_workspace(tnet, NT, K_HITS)
@@ -481,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
         t = svlf.BatchScene(tree, feats_k, params, trays, trgb, tdepth)
         if grads:
             t.d_rgb, t.d_depth, t.d_features, t.d_params = d_rgb, d_depth, g_feat, g_par
-        return [v, t]
+        return [t, v]  # the incoherent training rays first: the traversal's tail is coherent view rays
 
     def render_phase(rays=rays, rgb=rgb, depth=depth, trays=trays):
         if merged:  # the view rays and the training rays' forward
@@ -530,8 +530,8 @@ def run_ours(args, rank, world, local_rank):
     # FP32 SIMT roofline denominator: this GPU's measured FMA rate
     ffma_tf = svlf.svlf_measure_ffma_tflops() if "fp32" in (args.precision, args.train_precision) else None
     if merged:
-        n_samples_render, n_samples_train = svlf.svlf_workspace_scene_samples(
-            ws_b, net, [svlf.BatchScene(tree, feats_k, params, rays), svlf.BatchScene(tree, feats_k, params, trays)],
+        n_samples_train, n_samples_render = svlf.svlf_workspace_scene_samples(
+            ws_b, net, [svlf.BatchScene(tree, feats_k, params, trays), svlf.BatchScene(tree, feats_k, params, rays)],
             K_HITS)
     else:
         n_samples_render = svlf.svlf_workspace_samples(ws_r, net, N, K_HITS)
