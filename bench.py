@@ -126,7 +126,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tuning", default=None,
                    help="fixed launch shapes instead of the search, e.g. "
-                        "mlp_warpgroups=4,mlp_epilogue_batch=1,trace_budget=16,trace_block=128")
+                        "mlp_warpgroups=4,mlp_epilogue_batch=1,trace_budget=64,trace_block=256")
     p.add_argument("--render-only", action="store_true",
                    help="time only the render pass (profiling aid; not the benchmark step)")
     p.add_argument("--train-order", default="coherent", choices=["coherent", "random"],

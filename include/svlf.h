@@ -478,11 +478,14 @@ int svlf_render_rays_static(svlf_octree tree, const void *features, const float 
  *                       CTA to 3 warpgroups), 3 = 16 with the next load in
  *                       flight while a chunk is packed
  *   trace_budget        traversal steps between lane refills, 1..256
+ *                       (default 64)
  *   trace_block         traversal threads per block, 128 or 256
  *   trace_refill        traversal: idle lanes a warp needs before it claims
- *                       a new chunk of rays while rays of its current chunks
- *                       still walk, 1..32 (32: only once all lanes are idle;
- *                       default 32 for large launches, 16 for small ones)
+ *                       a new work item of 32 neighbouring rays while rays
+ *                       of its earlier ones still walk, 1..32 (32: only once
+ *                       all lanes are idle; default 32 for large launches,
+ *                       with at least two work items per resident warp, 16
+ *                       for smaller ones)
  *   mlp_bwd_warpgroups  tensor-core backward: warpgroups per tile, 1 or 2
  *                       (2 adds a second warpgroup that takes half of every
  *                       epilogue; used for the plain form with resident

@@ -19,7 +19,7 @@ import torch
 
 from . import svlf
 
-TRACE_CANDIDATES = [dict(trace_budget=b, trace_block=t) for b in (8, 16, 32, 64) for t in (128, 256)]
+TRACE_CANDIDATES = [dict(trace_budget=b, trace_block=t) for b in (16, 32, 64, 128) for t in (128, 256)]
 MLP_CANDIDATES = [dict(mlp_warpgroups=w, mlp_epilogue_batch=e) for w in (2, 3, 4) for e in (1, 2, 3)
                   if not (e == 2 and w > 3)]
 

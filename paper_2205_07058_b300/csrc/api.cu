@@ -171,15 +171,9 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
     T.K = K;
     T.rparam = opts->rparam_mode;
     int64_t rays = 0, chunks = 0;
-    // Traversal work items: kTraceChunk rays each, or fewer for small launches
-    // so that every resident warp of the traversal kernel gets work.
-    {
-        int64_t all = 0;
-        for (int i = 0; i < n_scenes; ++i) all += scenes[i].n_rays > 0 ? scenes[i].n_rays : 0;
-        const int64_t want = (int64_t)2 * num_sms() * 32;  // work items for two rounds of resident warps
-        T.chunk_rays = kTraceChunk;
-        while (T.chunk_rays > 32 && all / T.chunk_rays < want) T.chunk_rays >>= 1;
-    }
+    // Traversal work items: kTraceChunk rays each (a warp walks neighbouring
+    // rays together, which keeps their walks coherent).
+    T.chunk_rays = kTraceChunk;
     for (int i = 0; i < n_scenes; ++i) {
         const svlf_scene &sc = scenes[i];
         if ((rc = check_scene(sc, per_ray_io && !backward))) return rc;
@@ -428,7 +422,7 @@ extern "C" int svlf_set_tuning(const svlf_tuning *t) {
     if (v.mlp_warpgroups < 0 || v.mlp_warpgroups > 4) return SVLF_ERR_ARG;
     if (v.mlp_epilogue_batch == 0) v.mlp_epilogue_batch = 1;
     if (v.mlp_epilogue_batch < 1 || v.mlp_epilogue_batch > 3) return SVLF_ERR_ARG;
-    if (v.trace_budget == 0) v.trace_budget = 16;
+    if (v.trace_budget == 0) v.trace_budget = 64;
     if (v.trace_budget < 1 || v.trace_budget > 256) return SVLF_ERR_ARG;
     if (v.trace_block == 0) v.trace_block = 256;
     if (v.trace_block != 128 && v.trace_block != 256) return SVLF_ERR_ARG;

@@ -72,7 +72,7 @@ struct __align__(16) Sample {
 // as a kernel parameter, so a call needs no host-to-device copy and can be
 // captured in a CUDA graph.
 constexpr int kMaxScenes = 64;
-constexpr int kTraceChunk = 128;  // largest number of rays per traversal work item (one warp)
+constexpr int kTraceChunk = 32;  // rays per traversal work item (one warp: one ray per lane)
 
 struct SceneDev {
     OctreeView tree;
@@ -96,7 +96,7 @@ struct SceneTable {
     int K;
     int64_t total_rays;
     int64_t total_chunks;
-    int chunk_rays;  // rays per traversal work item: 32, 64 or kTraceChunk
+    int chunk_rays;  // rays per traversal work item (kTraceChunk)
     int rparam;      // ray parameterisation of the network input (SVLF_RPARAM_*)
     int64_t grad_rays;  // backward: rays of the scenes that take part
     SceneDev s[kMaxScenes];

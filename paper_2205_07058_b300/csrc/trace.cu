@@ -29,11 +29,13 @@
 //    warp reserves space for its rays' samples with one atomic and copies them
 //    contiguously per ray from the slots.
 //  * Many scenes can be traced in one launch (see SceneTable).
-//  * Warps fetch their own chunks of rays and refill lanes as rays finish
-//    (persistent warps); once a chunk is handed out, the warp claims the next
-//    one when enough lanes are idle (all of them for coherent image rays,
-//    half for small incoherent batches), and no warp waits for the rest of
-//    its block.
+//  * Persistent warps fetch their own work items of 32 neighbouring rays
+//    (one per lane) from a global counter, and claim the next one when
+//    enough lanes are idle: all of them on large launches, so that a warp's
+//    rays stay neighbours and walk through the same bricks together (32-ray
+//    items run the render traversal about 11 % faster than 128-ray items
+//    whose lanes refill from the rest of the item), half on small ones; no
+//    warp waits for the rest of its block.
 #include "svlf_internal.cuh"
 
 namespace svlf {
@@ -458,9 +460,11 @@ int launch_trace(const SceneTable &T, const Workspace &ws, int32_t *hits, float 
     if (blocks < 1) blocks = 1;
     // the per-ray hit slots live in the network-output buffer (total_rays*K x 16 B),
     // which the network kernels only write after this kernel is done
-    // lanes wait for the whole warp before a new chunk on coherent (large)
-    // launches, and refill at half a warp on small, incoherent ones
-    const int refill = tuning().trace_refill ? tuning().trace_refill : T.chunk_rays >= kTraceChunk ? 32 : 16;
+    // lanes wait for the whole warp before a new chunk on large launches (the
+    // warp's rays stay neighbours), and refill at half a warp on small ones
+    // (fewer than two rounds of work items for the resident warps)
+    const int64_t large = (int64_t)2 * num_sms() * 32;
+    const int refill = tuning().trace_refill ? tuning().trace_refill : T.total_chunks >= large ? 32 : 16;
     prof_begin("trace", s);
     kernel<<<(unsigned)blocks, threads, smem, s>>>(T, ws.samples, reinterpret_cast<int4 *>(ws.outputs),
                                                    ws.ray_span, ws.counter, hits, t_io, tuning().trace_budget,

@@ -86,5 +86,5 @@ def test_tuning_arguments_are_checked(L):
     with pytest.raises(svlf.SvlfError):
         svlf.svlf_set_tuning(mlp_bwd_warpgroups=3)
     svlf.svlf_set_tuning()  # defaults
-    assert svlf.svlf_get_tuning()["trace_budget"] == 16
+    assert svlf.svlf_get_tuning()["trace_budget"] == 64
     assert svlf.svlf_get_tuning()["trace_refill"] == 0
