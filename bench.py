@@ -485,9 +485,11 @@ def run_ours(args, rank, world, local_rank):
 
     def render_phase(rays=rays, rgb=rgb, depth=depth, trays=trays):
         if merged:  # the view rays and the training rays' forward
-            svlf.svlf_render_rays_batched(scenes_of(rays, rgb, depth, trays, False), net, K_HITS, workspace=ws_b)
+            svlf.svlf_render_rays_batched(scenes_of(rays, rgb, depth, trays, False), net, K_HITS, workspace=ws_b,
+                                          image_width=args.res)
         else:
-            svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth))
+            svlf.svlf_render_rays(tree, feats_k, params, net, rays, K_HITS, workspace=ws_r, out=(rgb, depth),
+                                  image_width=args.res)
 
     def train_phase(trays=trays, loss=loss, rays=rays, rgb=rgb, depth=depth):
         step_no[0] += 1
@@ -1024,7 +1026,7 @@ def run_batched(args, rank, world, local_rank):
     adam_t = torch.zeros(1, dtype=torch.int64, device=dev)  # Adam's step count, on the device
 
     def step():  # render + training forward/backward/Adam of all 64 scenes
-        svlf.svlf_render_rays_batched(rend, net, K_HITS, workspace=ws_r)
+        svlf.svlf_render_rays_batched(rend, net, K_HITS, workspace=ws_r, image_width=BATCH_RES)
         g_feat.zero_()
         g_par.zero_()
         loss.zero_()
@@ -1196,7 +1198,8 @@ def run_twodec(args, rank, world, local_rank):
     step_no = [0]
 
     def render_phase(rays=rays, rgb=rgb, depth=depth):
-        svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws, out=(rgb, depth))
+        svlf.svlf_render_rays_two_decoder(tree, zt, zc, pt, pc, net, rays, K_HITS, workspace=ws, out=(rgb, depth),
+                                          image_width=args.res)
 
     def train_phase(trays=trays, loss=loss):
         step_no[0] += 1

@@ -105,6 +105,14 @@ typedef struct {
     float bg[3];  /* colour multiplied by the transmittance left after the K-th hit */
     int rparam_mode; /* SVLF_RPARAM_SPHERE or SVLF_RPARAM_AABB (the single-network
                       * calls; the two-decoder calls take SVLF_RPARAM_SPHERE only) */
+    int image_width; /* traversal order only (results do not depend on it): 0 =
+                      * the rays' own order; W > 0 = the rays are the pixels of
+                      * images W wide, row-major, one image after another, and
+                      * are walked in tiles of 8 x 4 pixels, so that the 32 rays
+                      * a warp walks together are neighbours in both directions.
+                      * Applies to each scene whose ray count is a multiple of
+                      * 4 W with W a multiple of 8; other scenes keep their
+                      * order. Negative: SVLF_ERR_ARG. */
 } svlf_render_opts;
 
 /* ------------------------------------------------------------ octree */

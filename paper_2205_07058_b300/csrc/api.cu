@@ -166,14 +166,14 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
     const int K = opts->K;
     if (K < 1 || K > kMaxK) return SVLF_ERR_UNSUPPORTED;
     if (opts->rparam_mode != SVLF_RPARAM_SPHERE && opts->rparam_mode != SVLF_RPARAM_AABB) return SVLF_ERR_ARG;
+    if (opts->image_width < 0) return SVLF_ERR_ARG;
     std::memset(&T, 0, sizeof(T));
     T.n = n_scenes;
     T.K = K;
     T.rparam = opts->rparam_mode;
+    // traversal work items: kTraceChunk rays each (a warp walks neighbouring
+    // rays together, which keeps their walks coherent)
     int64_t rays = 0, chunks = 0;
-    // Traversal work items: kTraceChunk rays each (a warp walks neighbouring
-    // rays together, which keeps their walks coherent).
-    T.chunk_rays = kTraceChunk;
     for (int i = 0; i < n_scenes; ++i) {
         const svlf_scene &sc = scenes[i];
         if ((rc = check_scene(sc, per_ray_io && !backward))) return rc;
@@ -181,6 +181,10 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
         if (per_ray_io && backward && sc.n_rays > 0 && (!sc.d_rgb != !sc.d_depth)) return SVLF_ERR_ARG;
         SceneDev &d = T.s[i];
         d.grad = !(per_ray_io && backward && !sc.d_rgb);
+        // image rows walked in 8 x 4 tiles of 32 rays (kTraceChunk), where the scene's
+        // rays are whole bands of four rows of a width that is a multiple of 8
+        const int64_t iw = opts->image_width;
+        d.tile_w = (iw > 0 && iw % 8 == 0 && sc.n_rays % (4 * iw) == 0) ? (int)iw : 0;
         d.grad_begin = T.grad_rays;
         if (d.grad) T.grad_rays += sc.n_rays;
         d.tree = octree_view(sc.tree);
@@ -197,7 +201,7 @@ static int make_table_core(const svlf_scene *scenes, int n_scenes, const svlf_re
         d.n_rays = sc.n_rays;
         d.chunk_begin = chunks;
         rays += sc.n_rays;
-        chunks += (sc.n_rays + T.chunk_rays - 1) / T.chunk_rays;
+        chunks += (sc.n_rays + kTraceChunk - 1) / kTraceChunk;
     }
     T.total_rays = rays;
     T.total_chunks = chunks;

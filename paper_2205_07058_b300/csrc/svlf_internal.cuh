@@ -88,6 +88,9 @@ struct SceneDev {
     // backward: the scene takes part (it has output gradients), and the index of
     // its first ray among the rays of the scenes that take part
     int grad;
+    // traversal order: 0 = the given order; W = the rays are rows of images W
+    // pixels wide, walked in tiles of 8 x 4 pixels (one work item each)
+    int tile_w;
     int64_t grad_begin;
 };
 
@@ -96,7 +99,6 @@ struct SceneTable {
     int K;
     int64_t total_rays;
     int64_t total_chunks;
-    int chunk_rays;  // rays per traversal work item (kTraceChunk)
     int rparam;      // ray parameterisation of the network input (SVLF_RPARAM_*)
     int64_t grad_rays;  // backward: rays of the scenes that take part
     SceneDev s[kMaxScenes];

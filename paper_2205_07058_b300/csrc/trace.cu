@@ -289,8 +289,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Each warp claims chunks of T.chunk_rays rays from a global counter (in
-// order, so neighbouring warps walk neighbouring pixels). A lane whose ray is
+// Each warp claims work items of kTraceChunk rays from a global counter (in
+// order, so neighbouring warps walk neighbouring pixels; a scene's item is a
+// run of 32 rays, or a tile of 8 x 4 pixels when its rays are image rows). A lane whose ray is
 // finished takes the next ray of the warp's current chunk; once that chunk is
 // handed out, the warp claims another one when at least `refill` lanes are
 // idle (32: only when all are), so lanes may hold rays of different chunks
@@ -318,6 +319,8 @@ __global__ void __launch_bounds__(256, SVLF_TRACE_MIN_BLOCKS) trace_kernel(const
     const int K = T.K;
     const int ss = smem_slots ? (int)blockDim.x : 1;
     // warp-uniform: the chunk being handed out
+    // ray k of the work item (k < chunk_n) is r_begin + (k / 8) * row + k % 8,
+    // row = 8 for rays in their own order, the image width for 8 x 4 pixel tiles
     int64_t r_begin = 0;
     int chunk_n = 0, next = 0, csc = 0;
     bool exhausted = false;  // the launch has no chunk left
@@ -341,15 +344,25 @@ __global__ void __launch_bounds__(256, SVLF_TRACE_MIN_BLOCKS) trace_kernel(const
                     break;
                 }
                 csc = MULTI ? scene_of_chunk(T, chunk) : 0;
-                r_begin = (chunk - T.s[csc].chunk_begin) * T.chunk_rays;
-                chunk_n = (int)min((int64_t)T.chunk_rays, T.s[csc].n_rays - r_begin);
+                const int64_t q = chunk - T.s[csc].chunk_begin;  // work item within the scene
+                const int tw = T.s[csc].tile_w;
+                if (tw) {  // tile (q mod W/8, q div W/8) of 8 x 4 pixels; the scene holds whole tiles
+                    const int64_t tpb = tw >> 3;
+                    const int64_t band = q / tpb;
+                    r_begin = band * 4 * tw + (q - band * tpb) * 8;
+                    chunk_n = kTraceChunk;
+                } else {
+                    r_begin = q * kTraceChunk;
+                    chunk_n = (int)min((int64_t)kTraceChunk, T.s[csc].n_rays - r_begin);
+                }
                 next = 0;
             }
             if (!have) {
                 const int my = next + __popc(idle & lanemask_lt());
                 if (my < chunk_n) {
                     const SceneDev &S = T.s[csc];
-                    const int64_t rl = r_begin + my;
+                    const int row = S.tile_w ? S.tile_w : 8;
+                    const int64_t rl = r_begin + (int64_t)(my >> 3) * row + (my & 7);
                     g = S.ray_begin + rl;
                     sc = csc;
                     const float2 *rp = reinterpret_cast<const float2 *>(S.rays + 6 * rl);

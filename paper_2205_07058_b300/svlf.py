@@ -54,7 +54,8 @@ class TwoDecoderDescC(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3), ("rparam_mode", ctypes.c_int)]
+    _fields_ = [("K", ctypes.c_int), ("bg", ctypes.c_float * 3), ("rparam_mode", ctypes.c_int),
+                ("image_width", ctypes.c_int)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -299,12 +300,13 @@ def _ws_ptr(ws: torch.Tensor):
     return ctypes.c_void_p(aligned), ws.numel() - (aligned - p)
 
 
-def _opts(K: int, bg: Sequence[float], rparam: int = RPARAM_SPHERE) -> RenderOpts:
+def _opts(K: int, bg: Sequence[float], rparam: int = RPARAM_SPHERE, image_width: int = 0) -> RenderOpts:
     o = RenderOpts()
     o.K = int(K)
     for i in range(3):
         o.bg[i] = float(bg[i])
     o.rparam_mode = int(rparam)
+    o.image_width = int(image_width)
     return o
 
 
@@ -380,8 +382,11 @@ def _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays, d_z_t=None
 
 def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                      rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
-                     want_hits: bool = False, out: Optional[tuple] = None, stream=None, rparam: int = RPARAM_SPHERE):
-    """Returns (rgb (N,3), depth (N,), hits (N,K) or None, t_io (N,K,2) or None, workspace)."""
+                     want_hits: bool = False, out: Optional[tuple] = None, stream=None, rparam: int = RPARAM_SPHERE,
+                     image_width: int = 0):
+    """Returns (rgb (N,3), depth (N,), hits (N,K) or None, t_io (N,K,2) or None, workspace).
+    image_width > 0: the rays are rows of images that wide (traversal order
+    only; svlf_render_opts.image_width)."""
     _check_single(tree, features, params, net, rays)
     N = rays.shape[0]
     if workspace is None:
@@ -394,7 +399,7 @@ def svlf_render_rays(tree: Octree, features: torch.Tensor, params: torch.Tensor,
     hits = torch.empty((N, K), dtype=torch.int32, device="cuda") if want_hits else None
     t_io = torch.empty((N, K, 2), dtype=torch.float32, device="cuda") if want_hits else None
     d = net.desc()
-    o = _opts(K, bg, rparam)
+    o = _opts(K, bg, rparam, image_width)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays", lib().svlf_render_rays(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
@@ -430,7 +435,8 @@ def workspace_size_two_decoder(net: TwoDecoder, n_rays: int, K: int) -> int:
 def svlf_render_rays_two_decoder(tree: Octree, z_t: torch.Tensor, z_c: torch.Tensor, params_t: torch.Tensor,
                                  params_c: torch.Tensor, net: TwoDecoder, rays: torch.Tensor, K: int,
                                  bg=(0.0, 0.0, 0.0), workspace: Optional[torch.Tensor] = None,
-                                 want_hits: bool = False, out: Optional[tuple] = None, stream=None):
+                                 want_hits: bool = False, out: Optional[tuple] = None, stream=None,
+                                 image_width: int = 0):
     """Two-decoder render (the octree's vertex table must be built).
     Returns (rgb, depth, hits or None, t_io or None, workspace)."""
     _check_two_decoder(tree, z_t, z_c, params_t, params_c, net, rays)
@@ -445,7 +451,7 @@ def svlf_render_rays_two_decoder(tree: Octree, z_t: torch.Tensor, z_c: torch.Ten
     hits = torch.empty((N, K), dtype=torch.int32, device="cuda") if want_hits else None
     t_io = torch.empty((N, K, 2), dtype=torch.float32, device="cuda") if want_hits else None
     d = net.desc()
-    o = _opts(K, bg)
+    o = _opts(K, bg, image_width=image_width)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays_two_decoder", lib().svlf_render_rays_two_decoder(
         tree.handle, _ptr(z_t), _ptr(z_c), _ptr(params_t), _ptr(params_c), ctypes.byref(d), _ptr(rays), N,
@@ -503,7 +509,7 @@ def svlf_eta_loss_two_decoder(tree: Octree, net: TwoDecoder, rays, K: int, depth
 
 def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.Tensor, net: Network,
                             rays: torch.Tensor, K: int, bg=(0.0, 0.0, 0.0), out: Optional[tuple] = None,
-                            stream=None, rparam: int = RPARAM_SPHERE):
+                            stream=None, rparam: int = RPARAM_SPHERE, image_width: int = 0):
     """Render without a workspace (the library's fixed scratch array); for
     callers that may not allocate device memory. Returns (rgb, depth)."""
     _check_single(tree, features, params, net, rays)
@@ -513,7 +519,7 @@ def svlf_render_rays_static(tree: Octree, features: torch.Tensor, params: torch.
                torch.empty((N,), dtype=torch.float32, device="cuda"))
     rgb, depth = out
     d = net.desc()
-    o = _opts(K, bg, rparam)
+    o = _opts(K, bg, rparam, image_width)
     _check("svlf_render_rays_static", lib().svlf_render_rays_static(
         tree.handle, _ptr(features), _ptr(params), ctypes.byref(d), _ptr(rays), N, ctypes.byref(o),
         _ptr(rgb), _ptr(depth), _stream(stream)))
@@ -555,7 +561,8 @@ def alloc_workspace_batched(net: Network, scenes: Sequence[BatchScene], K: int) 
 
 
 def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int, bg=(0.0, 0.0, 0.0),
-                             workspace: Optional[torch.Tensor] = None, stream=None, rparam: int = RPARAM_SPHERE):
+                             workspace: Optional[torch.Tensor] = None, stream=None, rparam: int = RPARAM_SPHERE,
+                             image_width: int = 0):
     """Render every scene in one call; fills each scene's rgb/depth (allocated
     here when missing). Returns the workspace (needed by the backward)."""
     for s in scenes:
@@ -569,7 +576,7 @@ def svlf_render_rays_batched(scenes: Sequence[BatchScene], net: Network, K: int,
         workspace = alloc_workspace_batched(net, scenes, K)
     arr = (SceneDesc * len(scenes))(*[s.desc() for s in scenes])
     d = net.desc()
-    o = _opts(K, bg, rparam)
+    o = _opts(K, bg, rparam, image_width)
     wp, wb = _ws_ptr(workspace)
     _check("svlf_render_rays_batched", lib().svlf_render_rays_batched(
         arr, len(scenes), ctypes.byref(d), ctypes.byref(o), wp, wb, _stream(stream)))
@@ -781,8 +788,9 @@ class SvlfRender(torch.autograd.Function):
     hand-written kernels (activations recomputed, not stored)."""
 
     @staticmethod
-    def forward(ctx, features, params, tree, net, rays, K, bg, rparam=RPARAM_SPHERE):
-        rgb, depth, _, _, ws = svlf_render_rays(tree, features, params, net, rays, K, bg, rparam=rparam)
+    def forward(ctx, features, params, tree, net, rays, K, bg, rparam=RPARAM_SPHERE, image_width=0):
+        rgb, depth, _, _, ws = svlf_render_rays(tree, features, params, net, rays, K, bg, rparam=rparam,
+                                                image_width=image_width)
         ctx.save_for_backward(features, params, rays)
         ctx.tree, ctx.net, ctx.K, ctx.bg, ctx.ws, ctx.rparam = tree, net, K, bg, ws, rparam
         return rgb, depth
@@ -795,9 +803,9 @@ class SvlfRender(torch.autograd.Function):
         svlf_render_rays_backward(ctx.tree, features, params, ctx.net, rays, ctx.K, ctx.bg,
                                   g_rgb.contiguous(), g_depth.contiguous(), df, dp, ctx.ws, rparam=ctx.rparam)
         ctx.ws = None
-        return df, dp, None, None, None, None, None, None
+        return df, dp, None, None, None, None, None, None, None
 
 
 def render(features, params, tree: Octree, net: Network, rays, K: int, bg=(0.0, 0.0, 0.0),
-           rparam: int = RPARAM_SPHERE):
-    return SvlfRender.apply(features, params, tree, net, rays, K, tuple(bg), rparam)
+           rparam: int = RPARAM_SPHERE, image_width: int = 0):
+    return SvlfRender.apply(features, params, tree, net, rays, K, tuple(bg), rparam, image_width)
