@@ -30,7 +30,7 @@ def _check_sample(w, rgb, depth, hits, sample, lowp, tol):
 
 
 # launch shapes the benchmark's autotuner picks for the headline step (its trace
-# budget varies between 16 and 64 from run to run; hit lists do not depend on it)
+# budget varies between 64 and 128 from run to run; hit lists do not depend on it)
 BENCH_TUNING = dict(mlp_warpgroups=4, mlp_epilogue_batch=3, trace_budget=64, trace_block=256)
 
 
@@ -39,7 +39,8 @@ def test_full_render_4x1600_sampled(prec):
     """bf16 runs as the benchmark does: the network reads the bf16 copy of the
     float32 feature table, with the benchmark's launch shapes; the oracle
     takes the float32 table (the network's own rounding of it is what the
-    copy holds)."""
+    copy holds). Every precision walks the views in 8 x 4 pixel tiles, as
+    the benchmark's render call does."""
     from paper_2205_07058_b300 import svlf
     w = I.full_render_workload()
     tree = svlf.Octree(torch.from_numpy(w.scene.leaf_ijk), 9)
@@ -53,7 +54,7 @@ def test_full_render_4x1600_sampled(prec):
     else:
         net = svlf.Network(32, 128, 3, svlf.PRECISIONS[prec])
     try:
-        rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, w.K, want_hits=True)
+        rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, w.K, want_hits=True, image_width=1600)
         torch.cuda.synchronize()
     finally:
         svlf.svlf_set_tuning()
@@ -67,7 +68,7 @@ def test_full_render_4x1600_sampled(prec):
 
 def test_large_scene_bf16_features_sampled():
     """Depth 10 (7.9 M leaves), features stored as bf16, 41 -> 4x128 -> 4, K = 16,
-    8 views of 1600^2 (20.48 M rays) in one call."""
+    8 views of 1600^2 (20.48 M rays) in one call, walked in 8 x 4 pixel tiles."""
     from paper_2205_07058_b300 import svlf
     rng = np.random.default_rng(1005)
     scene = I.make_scene(rng, 10, 128, 128)
@@ -83,7 +84,7 @@ def test_large_scene_bf16_features_sampled():
     f = feats_bf.contiguous().cuda()
     p = torch.from_numpy(params).cuda()
     r = torch.from_numpy(rays).cuda()
-    rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, 16, want_hits=True)
+    rgb, depth, hits, _, _ = svlf.svlf_render_rays(tree, f, p, net, r, 16, want_hits=True, image_width=1600)
     torch.cuda.synchronize()
     assert svlf.svlf_get_device_status() == 0
     sample = np.random.default_rng(18).choice(rays.shape[0], 4096, replace=False)
