@@ -1346,9 +1346,12 @@ __global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __g
     auto run = [&](auto &&fn) -> bool { return run_and(fn, [] {}); };
 
     // ---- streamed weights: slot l % 2 holds W_l (uniform state in every thread)
-    int slot_w[2] = {-1, -1};          // layer held (or being loaded) per slot
-    bool slot_busy[2] = {false, false};  // load issued, not yet waited for
-    uint32_t slot_phase[2] = {0u, 0u};
+    struct Pair { int a0, a1; __device__ int &operator[](int k) { return k ? a1 : a0; } };
+    struct PairB { bool a0, a1; __device__ bool &operator[](int k) { return k ? a1 : a0; } };
+    struct PairU { uint32_t a0, a1; __device__ uint32_t &operator[](int k) { return k ? a1 : a0; } };
+    Pair slot_w{-1, -1};
+    PairB slot_busy{false, false};
+    PairU slot_phase{0u, 0u};
     const uint8_t *img_sc = nullptr;     // the current scene's packed image
     auto issue_load = [&](int l) {
         const int k = l & 1;
@@ -1712,7 +1715,9 @@ __global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __g
                 tc::tmem_ld16_wait(tmem + lane_off + P.col_dwout, v);
                 if (row < H) {
                     float *dW = dpar + md.w_off[nh];
-                    for (int j = 0; j < md.out; ++j) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < md.out) atomicAdd(dW + j * H + row, __uint_as_float(v[j]) * ginv);
                 }
                 if (row < md.out) atomicAdd(dpar + md.w_off[nh] + md.out * H + row, s_dbout[row]);
             }
@@ -1725,12 +1730,14 @@ __global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __g
                     tc::tmem_ld16_wait(tmem + lane_off + P.col_dw[l] + (uint32_t)c, v);
                     if (row < H) {
                         float *dst = dW + row * in + c;
+#pragma unroll
                         for (int e = 0; e < 16; e += 4) {
                             if (c + e + 4 <= in && ((uintptr_t)(dst + e) & 15u) == 0) {  // 16-byte vector atomic
                                 red_add_f4(reinterpret_cast<float4 *>(dst + e), __uint_as_float(v[e]) * ginv,
                                            __uint_as_float(v[e + 1]) * ginv, __uint_as_float(v[e + 2]) * ginv,
                                            __uint_as_float(v[e + 3]) * ginv);
                             } else {
+#pragma unroll
                                 for (int q = e; q < e + 4; ++q)
                                     if (c + q < in) atomicAdd(dst + q, __uint_as_float(v[q]) * ginv);
                             }
