@@ -32,10 +32,11 @@ int launch_mlp_backward_f32(const MlpDims &md, int depth, int rparam, const void
                             float *d_params, cudaStream_t s);
 size_t backward_f32_smem(const MlpDims &md);
 
-// h0 = [z | d | p~1 | p~2] of one sample, in float32 (rparam: SVLF_RPARAM_*).
+// h0 = [z | d | p~1 | p~2] of one sample, in float32 (rparam: SVLF_RPARAM_*),
+// value k written to h0[k * stride] (a column of a feature-major tile).
 __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int rparam, const void *feats,
                                                int feat_bf16, const float *rays, const Sample &sm,
-                                               float *h0) {
+                                               float *h0, int stride) {
     const int F = md.F;
     if (feat_bf16) {
         const uint4 *src = reinterpret_cast<const uint4 *>(
@@ -45,8 +46,8 @@ __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                h0[8 * q + 2 * e] = __uint_as_float(w[e] << 16);
-                h0[8 * q + 2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+                h0[(8 * q + 2 * e) * stride] = __uint_as_float(w[e] << 16);
+                h0[(8 * q + 2 * e + 1) * stride] = __uint_as_float(w[e] & 0xFFFF0000u);
             }
         }
     } else {
@@ -54,7 +55,10 @@ __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int
             reinterpret_cast<const float *>(feats) + (int64_t)sm.leaf * F);
         for (int q = 0; q < F / 4; ++q) {
             const float4 v = __ldg(src + q);
-            h0[4 * q] = v.x; h0[4 * q + 1] = v.y; h0[4 * q + 2] = v.z; h0[4 * q + 3] = v.w;
+            h0[(4 * q) * stride] = v.x;
+            h0[(4 * q + 1) * stride] = v.y;
+            h0[(4 * q + 2) * stride] = v.z;
+            h0[(4 * q + 3) * stride] = v.w;
         }
     }
     const float2 *rp = reinterpret_cast<const float2 *>(rays + 6 * (int64_t)sm.ray);
@@ -63,9 +67,9 @@ __device__ __forceinline__ void make_input_row(const MlpDims &md, int depth, int
     const float d[3] = {b.y, c.x, c.y};
     float p1[3], p2[3];
     voxel_param_at(rparam, o, d, sm.tmid, sm.cell, depth, p1, p2);
-    h0[F + 0] = d[0]; h0[F + 1] = d[1]; h0[F + 2] = d[2];
-    h0[F + 3] = p1[0]; h0[F + 4] = p1[1]; h0[F + 5] = p1[2];
-    h0[F + 6] = p2[0]; h0[F + 7] = p2[1]; h0[F + 8] = p2[2];
+    h0[(F + 0) * stride] = d[0]; h0[(F + 1) * stride] = d[1]; h0[(F + 2) * stride] = d[2];
+    h0[(F + 3) * stride] = p1[0]; h0[(F + 4) * stride] = p1[1]; h0[(F + 5) * stride] = p1[2];
+    h0[(F + 6) * stride] = p2[0]; h0[(F + 7) * stride] = p2[1]; h0[(F + 8) * stride] = p2[2];
 }
 
 // colour = sigmoid(o[0:3]), optical thickness tau = max(o[3], 0) (Sec. 4.5)

@@ -138,10 +138,8 @@ __device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
                                                    const float *rays, const Sample *samples,
                                                    int64_t s, int64_t S, float *X, int ts,
                                                    int col, int rows_padded) {
-    float h0[kMaxIn];
     if (s < S) {
-        make_input_row(md, depth, rparam, feats, feat_bf16, rays, samples[s], h0);
-        for (int k = 0; k < md.in0; ++k) X[k * ts + col] = h0[k];
+        make_input_row(md, depth, rparam, feats, feat_bf16, rays, samples[s], X + col, ts);
     } else {
         for (int k = 0; k < md.in0; ++k) X[k * ts + col] = 0.f;
     }
@@ -154,7 +152,7 @@ __device__ __forceinline__ void build_input_column(const MlpDims &md, int depth,
 // step of the GEMM waited on a miss.
 template <int H, bool WSTAGE>
 __global__ void __launch_bounds__(256) mlp_forward_f32_kernel(
-    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
+    const __grid_constant__ MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ packed, const float *__restrict__ rays,
     const Sample *__restrict__ samples, const unsigned int *__restrict__ counter,
     int64_t max_samples, float4 *__restrict__ outputs) {
@@ -216,7 +214,7 @@ constexpr int kTsR = 128;
 
 template <int H>
 __global__ void __launch_bounds__(256) mlp_forward_f32_res_kernel(
-    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
+    const __grid_constant__ MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ packed, int packed_floats, const float *__restrict__ rays,
     const Sample *__restrict__ samples, const unsigned int *__restrict__ counter,
     int64_t max_samples, float4 *__restrict__ outputs) {
@@ -537,7 +535,7 @@ __device__ __forceinline__ void backprop_delta_pipe(const float *__restrict__ W,
 
 template <int H, bool WST>
 __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
-    MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
+    const __grid_constant__ MlpDims md, int depth, int rparam, const void *__restrict__ feats, int feat_bf16,
     const float *__restrict__ params, const float *__restrict__ packed,
     const float *__restrict__ rays, const Sample *__restrict__ samples,
     const unsigned int *__restrict__ counter, int64_t max_samples,
@@ -545,12 +543,10 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
     extern __shared__ float4 smem_f4[];
     float *base = reinterpret_cast<float *>(smem_f4);
     const int in0p = (md.in0 + 3) & ~3;
-    // activations: A[0] = h0 (in0p rows), A[l] = input of layer l (H rows)
-    float *A[kMaxLayers];
-    A[0] = base;
-    for (int l = 1; l <= md.nh; ++l) A[l] = A[0] + in0p * kPadB + (l - 1) * H * kPadB;
+    // activations: A(0) = h0 (in0p rows), A(l) = input of layer l (H rows)
+    auto A = [&](int l) { return l == 0 ? base : base + in0p * kPadB + (l - 1) * H * kPadB; };
     const int dmax = in0p > H ? in0p : H;
-    float *Dc = A[md.nh] + H * kPadB;  // delta of the current layer's output
+    float *Dc = A(md.nh) + H * kPadB;  // delta of the current layer's output
     float *Dn = Dc + dmax * kPadB;     // delta one layer down (or dL/dz)
     float *Wst = Dn + dmax * kPadB;    // kBwdWRows rows of W^T (recompute)
     __shared__ int s_leaf[kTsB];
@@ -560,7 +556,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
         const int64_t s0 = tile * kTsB;
         if (threadIdx.x < kTsB) {
             const int64_t s = s0 + threadIdx.x;
-            build_input_column(md, depth, rparam, feats, feat_bf16, rays, samples, s, S, A[0], kPadB,
+            build_input_column(md, depth, rparam, feats, feat_bf16, rays, samples, s, S, A(0), kPadB,
                                threadIdx.x, in0p);
             s_leaf[threadIdx.x] = s < S ? samples[s].leaf : -1;
             const float4 g = s < S ? dout[s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -575,7 +571,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
         for (int l = 0; l < md.nh; ++l) {
             const int in = l == 0 ? md.in0 : H;
             if (!WST) {
-                gemm_relu_f32<H, kTsB, 4>(A[l], in, kPadB, packed + md.wt_off[l], packed + md.b_off[l], A[l + 1],
+                gemm_relu_f32<H, kTsB, 4>(A(l), in, kPadB, packed + md.wt_off[l], packed + md.b_off[l], A(l + 1),
                                           true);
                 __syncthreads();
                 continue;
@@ -594,9 +590,9 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
                 const bool more = r1 < in;
                 if (more) st.load(WT + (size_t)r1 * H, n1 - r1);
                 if (r1 - r0 == kBwdWRows)
-                    gemm_rows<H, kTsB, 4, true, kBwdWRows>(acc, A[l], r0, r1, kPadB, Wst);
+                    gemm_rows<H, kTsB, 4, true, kBwdWRows>(acc, A(l), r0, r1, kPadB, Wst);
                 else
-                    gemm_rows<H, kTsB, 4, true>(acc, A[l], r0, r1, kPadB, Wst);
+                    gemm_rows<H, kTsB, 4, true>(acc, A(l), r0, r1, kPadB, Wst);
                 __syncthreads();
                 if (!more) break;
                 st.store(Wst, n1 - r1);
@@ -604,7 +600,7 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
                 r0 = r1;
                 r1 = n1;
             }
-            gemm_store<H, kTsB, 4>(acc, A[l + 1], kPadB, true);
+            gemm_store<H, kTsB, 4>(acc, A(l + 1), kPadB, true);
             __syncthreads();
         }
         // layers from the output down
@@ -615,9 +611,9 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             float *db = dW + nj * nk;
             if (d_params) {
                 if (nk % 32 == 0)
-                    accumulate_dw<true>(Dc, A[l], nj, nk, dW, nk);
+                    accumulate_dw<true>(Dc, A(l), nj, nk, dW, nk);
                 else
-                    accumulate_dw<false>(Dc, A[l], nj, nk, dW, nk);
+                    accumulate_dw<false>(Dc, A(l), nj, nk, dW, nk);
                 for (int j = threadIdx.x; j < nj; j += blockDim.x) {
                     float acc = 0.f;
                     for (int s = 0; s < kTsB; ++s) acc += Dc[j * kPadB + s];
@@ -627,11 +623,11 @@ __global__ void __launch_bounds__(256) mlp_backward_f32_kernel(
             const float *W = params + md.w_off[l];
             if (l > 0) {
                 if (WST && H <= 128 && reinterpret_cast<uintptr_t>(W) % 16 == 0)
-                    backprop_delta_pipe<H, true>(W, nj, Dc, A[l], Dn, Wst);
+                    backprop_delta_pipe<H, true>(W, nj, Dc, A(l), Dn, Wst);
                 else if (WST && H <= 128)
-                    backprop_delta_staged<true>(W, nj, nk, nk, Dc, A[l], Dn, Wst);
+                    backprop_delta_staged<true>(W, nj, nk, nk, Dc, A(l), Dn, Wst);
                 else
-                    backprop_delta<true>(W, nj, nk, nk, Dc, A[l], Dn);
+                    backprop_delta<true>(W, nj, nk, nk, Dc, A(l), Dn);
             } else if (d_feat) {
                 if (WST && (md.F + 3) / 4 * 4 <= H)  // the staged rows fit the H-wide buffer
                     backprop_delta_staged<false>(W, nj, md.F, nk, Dc, nullptr, Dn, Wst);
