@@ -1326,22 +1326,28 @@ __global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __g
 
     // issue (by row 0) the MMAs queued by `fn`, commit, wait; returns false on timeout
     // `during` runs in every thread between the MMAs' issue and the wait for them
+    // A wait that gives up sets `pend`, which the next barrier (the next call's, or the
+    // flush's) turns into a uniform abort: no barrier is spent after each wait, since
+    // every thread reads only its own TMEM lanes and rewrites only its own rows once its
+    // wait has seen the MMAs complete.
+    bool pend = false;
     auto run_and = [&](auto &&fn, auto &&during) -> bool {
         tc::fence_async_smem();
         tc::fence_before_sync();
-        sync_or(false);
+        if (sync_or(pend)) {
+            if (lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            return false;
+        }
         if (lead) {
             tc::fence_after_sync();
             fn();
             tc::mma_commit(mbar);
         }
         during();
-        const bool to = !tc::mbar_wait(mbar, phase);
+        pend |= !tc::mbar_wait(mbar, phase);
         phase ^= 1u;
-        const bool any = sync_or(to);
         tc::fence_after_sync();
-        if (any && lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
-        return !any;
+        return true;
     };
     auto run = [&](auto &&fn) -> bool { return run_and(fn, [] {}); };
 
@@ -1704,7 +1710,10 @@ __global__ void __launch_bounds__(128 * NWG, 1) mlp_backward_tc_kernel(const __g
         }
         // ---- flush this scene's TMEM gradient accumulators (one atomic per element, or per 4
         // where a row is 16-byte aligned)
-        __syncthreads();
+        if (__syncthreads_or(pend) && !aborted) {  // a give-up in the segment's last MMAs
+            if (lead) raise_status(SVLF_DEV_WAIT_TIMEOUT);
+            aborted = true;
+        }
         tc::fence_after_sync();
         if (!aborted && tiles_done > 0 && P.want_params) {
             const int H = md.H;
