@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(EPI == 2 || MODE == 1 ? 384 : 512, 1)
                 // A operand written by all threads -> visible to the tensor core
                 tc::fence_async_smem();
                 tc::fence_before_sync();
-                tc::wg_sync_or(wg, false);
+                tc::wg_sync(wg);
                 if (row == 0) {
                     tc::fence_after_sync();
                     const uint32_t idesc = tc::idesc_f16(kTcTile, N, bf16, 0, 0);

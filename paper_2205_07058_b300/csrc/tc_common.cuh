@@ -266,6 +266,11 @@ __device__ __forceinline__ bool wg_sync_or(int group, bool pred) {
     return out != 0;
 }
 
+// The same barrier without the reduction.
+__device__ __forceinline__ void wg_sync(int group) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack2(float a, float b, bool fp16) {
     if (fp16) {
         __half2 h = __floats2half2_rn(a, b);
