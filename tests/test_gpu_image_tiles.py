@@ -3,7 +3,8 @@ whole images walked in tiles of 8 x 4 pixels instead of in their own order.
 The order is a schedule only, so colours, depth, hit lists and segments are
 bit-identical to the given-order walk, and agree with the FP64 oracle; the
 backward after a tiled render differs only in the summation order of the
-parameter gradients. Covers the single-scene call (FP32 and BF16), a batched
+parameter gradients. Covers the single-scene call (FP32 and BF16; hit slots
+in shared memory, K = 4, and in global scratch, K = 32), a batched
 call mixing an image scene with a scene of scattered rays and one whose ray
 count is not whole bands of four rows (both kept in their order), widths that
 fall back to the given order, and the argument check."""
@@ -42,11 +43,11 @@ def _render(svlf, tree, f, p, net, r, K, width):
     return rgb, depth, hits, t_io, ws
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_tiled_walk_is_bit_identical_and_matches_the_oracle(scene, precision):
+# K = 4: hit slots in shared memory; K = 32: in the global scratch area
+@pytest.mark.parametrize("precision,K", [("fp32", 4), ("bf16", 4), ("bf16", 32)])
+def test_tiled_walk_is_bit_identical_and_matches_the_oracle(scene, precision, K):
     from paper_2205_07058_b300 import svlf
     sc, rays, feats, params = scene
-    K = 4
     prec = svlf.FP32 if precision == "fp32" else svlf.BF16
     net = svlf.Network(16, 64, 2, prec)
     tree = svlf.Octree(torch.from_numpy(sc.leaf_ijk), sc.depth)
